@@ -1,0 +1,233 @@
+"""Plain FP64 CPU oracle for the Compton ring-localisation hot path.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The product path (the CUDA
+library and its Python binding) never imports this package, and this package
+never imports the product.  It shares no code with the CUDA library.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64; the site-ordering
+decision alone is taken in IEEE binary32, the precision the GPU decides in).
+This module compiles it with gcc and wraps each function for numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+# -ffp-contract=off: every binary32 operation of the ordering decision is
+# rounded on its own (no fused multiply-add), as the decision rule defines.
+CFLAGS = ["-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+          "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to the source (gcc, a few seconds)."""
+    if force or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                         os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        i64, i32, f64, f32 = C.c_int64, C.c_int, C.c_double, C.c_float
+        lib.or_order_event.argtypes = [i32, P, P, P, P, P, P, P]
+        lib.or_order_event.restype = i32
+        lib.or_order_chi2.argtypes = [i32, P, P, P, P, P]
+        lib.or_order_chi2.restype = f32
+        lib.or_kn_weight_f32.argtypes = [f32, f32]
+        lib.or_kn_weight_f32.restype = f32
+        lib.or_rings_from_events.argtypes = [i64, i64, P, P, P, P, P, f64, f64,
+                                             f64, f64, P, P, P, P, P, P, P]
+        lib.or_rings_from_events.restype = None
+        lib.or_angle.argtypes = [P, P]
+        lib.or_angle.restype = f64
+        lib.or_map.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i64, f64,
+                               i32, P]
+        lib.or_map.restype = None
+        lib.or_likelihood.argtypes = [i64, P, P, P, P, P, P, P, f64]
+        lib.or_likelihood.restype = f64
+        lib.or_argmax.argtypes = [i64, P]
+        lib.or_argmax.restype = i64
+        lib.or_seeds.argtypes = [i64, P, P, P, P, i32, f64, P]
+        lib.or_seeds.restype = i32
+        lib.or_refine.argtypes = [i64, P, P, P, P, P, P, P, i32, f64, i32, f64,
+                                  P, P, P]
+        lib.or_refine.restype = i32
+        lib.or_grid_fibonacci.argtypes = [i64, P, P, P]
+        lib.or_grid_fibonacci.restype = None
+        lib.or_grid_healpix_ring.argtypes = [i64, P, P, P]
+        lib.or_grid_healpix_ring.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+ME_KEV = 510.99895
+
+
+# --------------------------------------------------------------------------
+# Ordering
+# --------------------------------------------------------------------------
+def order_event(x, y, z, e):
+    """Ordering decision for one event (arrays of its k sites, binary32).
+
+    Returns (order tuple, lexicographic rank, chi2) or None when no order is
+    kinematically valid."""
+    x, y, z, e = (_f32(v) for v in (x, y, z, e))
+    k = len(x)
+    order = np.zeros(4, dtype=np.int32)
+    rank = C.c_int(0)
+    chi2 = C.c_float(0)
+    ok = _load().or_order_event(k, _p(x), _p(y), _p(z), _p(e), _p(order),
+                                C.addressof(rank), C.addressof(chi2))
+    if not ok:
+        return None
+    return tuple(int(v) for v in order[:k]), rank.value, chi2.value
+
+
+def order_chi2(x, y, z, e, order):
+    """Compton chi-square of one order (binary32); +inf when invalid."""
+    x, y, z, e = (_f32(v) for v in (x, y, z, e))
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    return _load().or_order_chi2(len(x), _p(x), _p(y), _p(z), _p(e), _p(o))
+
+
+def kn_weight_f32(P, cos_eta):
+    return _load().or_kn_weight_f32(float(P), float(cos_eta))
+
+
+# --------------------------------------------------------------------------
+# Rings
+# --------------------------------------------------------------------------
+def rings_from_events(ev, sigma_e_frac, sigma_pos_cm, deta_min, deta_max):
+    """Rings of an event set ``ev`` (dict with n[N] u8 and x, y, z, e as
+    [4, N] arrays).  Returns a dict of FP64 ring arrays + valid + perm."""
+    n = np.ascontiguousarray(ev["n"], dtype=np.uint8)
+    N = n.shape[0]
+    x, y, z, e = (_f64(ev[k]) for k in ("x", "y", "z", "e"))
+    stride = x.shape[1] if x.ndim == 2 else N
+    out = {k: np.zeros(N) for k in ("ax", "ay", "az", "eta", "deta")}
+    out["valid"] = np.zeros(N, dtype=np.uint8)
+    out["perm"] = np.zeros(N, dtype=np.uint8)
+    _load().or_rings_from_events(
+        N, stride, _p(n), _p(x), _p(y), _p(z), _p(e), sigma_e_frac,
+        sigma_pos_cm, deta_min, deta_max, _p(out["ax"]), _p(out["ay"]),
+        _p(out["az"]), _p(out["eta"]), _p(out["deta"]), _p(out["valid"]),
+        _p(out["perm"]))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Map, argmax, seeds
+# --------------------------------------------------------------------------
+def _rings64(r):
+    ax, ay, az, eta, deta = (_f64(r[k]) for k in ("ax", "ay", "az", "eta", "deta"))
+    v = r.get("valid")
+    valid = np.ones(ax.shape[0], np.uint8) if v is None else \
+        np.ascontiguousarray(v, dtype=np.uint8)
+    return ax, ay, az, eta, deta, valid
+
+
+def angle(a, c):
+    a, c = _f64(a), _f64(c)
+    return _load().or_angle(_p(a), _p(c))
+
+
+def likelihood_map(rings, grid, idx=None, k_cut=0.0, nthreads=None):
+    """L_j for the directions ``idx`` (all when None).  ``grid`` = (x, y, z)."""
+    ax, ay, az, eta, deta, valid = _rings64(rings)
+    cx, cy, cz = (_f64(v) for v in grid)
+    if idx is None:
+        idx_a, nidx = None, cx.shape[0]
+    else:
+        idx_a = np.ascontiguousarray(idx, dtype=np.int64)
+        nidx = idx_a.shape[0]
+    out = np.zeros(nidx)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    _load().or_map(ax.shape[0], _p(ax), _p(ay), _p(az), _p(eta), _p(deta),
+                   _p(valid), _p(cx), _p(cy), _p(cz), _p(idx_a), nidx,
+                   float(k_cut), int(nthreads), _p(out))
+    return out
+
+
+def likelihood(rings, s, k_cut=0.0):
+    ax, ay, az, eta, deta, valid = _rings64(rings)
+    s = _f64(s)
+    return _load().or_likelihood(ax.shape[0], _p(ax), _p(ay), _p(az), _p(eta),
+                                 _p(deta), _p(valid), _p(s), float(k_cut))
+
+
+def argmax(m):
+    m = _f64(m)
+    return int(_load().or_argmax(m.shape[0], _p(m)))
+
+
+def seeds(m, grid, topk, nms_rad):
+    m = _f64(m)
+    cx, cy, cz = (_f64(v) for v in grid)
+    out = np.zeros(topk, dtype=np.int64)
+    got = _load().or_seeds(m.shape[0], _p(m), _p(cx), _p(cy), _p(cz), topk,
+                           nms_rad, _p(out))
+    return out[:got]
+
+
+# --------------------------------------------------------------------------
+# Refinement
+# --------------------------------------------------------------------------
+def refine(rings, seed_dirs, k_cut=0.0, max_iter=50, tol_rad=1e-10):
+    """Returns (dir[3], objective, iterations, status)."""
+    ax, ay, az, eta, deta, valid = _rings64(rings)
+    sd = _f64(np.atleast_2d(seed_dirs))
+    out = np.zeros(3)
+    obj = C.c_double(0)
+    iters = C.c_int(0)
+    st = _load().or_refine(ax.shape[0], _p(ax), _p(ay), _p(az), _p(eta),
+                           _p(deta), _p(valid), _p(sd), sd.shape[0],
+                           float(k_cut), int(max_iter), float(tol_rad),
+                           _p(out), C.addressof(obj), C.addressof(iters))
+    return out, obj.value, iters.value, st
+
+
+# --------------------------------------------------------------------------
+# Grids
+# --------------------------------------------------------------------------
+def grid_fibonacci(n):
+    x, y, z = np.zeros(n), np.zeros(n), np.zeros(n)
+    _load().or_grid_fibonacci(n, _p(x), _p(y), _p(z))
+    return x, y, z
+
+
+def grid_healpix_ring(nside):
+    npix = 12 * nside * nside
+    x, y, z = np.zeros(npix), np.zeros(npix), np.zeros(npix)
+    if _load().or_grid_healpix_ring(nside, _p(x), _p(y), _p(z)) != 0:
+        raise ValueError("nside must be >= 1")
+    return x, y, z

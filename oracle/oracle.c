@@ -1,0 +1,674 @@
+/*
+ * oracle.c - plain, slow, obviously correct CPU oracle for the Compton
+ * ring-localisation hot path (Gameiro et al., "Towards Real Time Compton
+ * Imaging in Demanding Conditions", arXiv 2411.04785).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header,
+ * table or constant generator with the CUDA library, and it never reads a
+ * value the CUDA library produced.
+ *
+ * What follows the paper and what is a reading of it:
+ *  - Compton formula (Sec. 1.1, the displayed equation): the scattered photon
+ *    energy E' = E / (1 + (E / m_e c^2)(1 - cos theta)).  Solved for the cone
+ *    half-angle with E' = E2 (energy left after the first site) and
+ *    E = E0 = E1 + E2: cos eta = 1 - m_e c^2 (1/E2 - 1/E0).
+ *  - Cone from two interactions (Sec. 1.1): the axis joins the first two
+ *    sites; cones overlap at the source.  We point the axis from the second
+ *    site back through the first, a = unit(x1 - x2), so that a . s = cos eta
+ *    for the true source direction s.
+ *  - Back projection (Sec. 3): every (event, probe) pair contributes
+ *    independently a "probability the gamma-ray came from" the probe; the
+ *    contributions are summed per probe.  Far-field reading: probes are sky
+ *    directions c_j and the contribution is the unnormalised Gaussian of the
+ *    angular residual, exp(-r^2/2), r = (angle(a_i, c_j) - eta_i) / deta_i.
+ *  - Angular selection of voxels (Sec. 3, "Angular selection"): optional
+ *    cut, terms with |r| > k_cut are dropped (k_cut = 0 keeps every term).
+ *  - Site ordering for 3-4 sites, the ring width deta, the argmax/top-k seeds
+ *    and the Gauss-Newton refinement are not in the paper; each function
+ *    below states the reading it implements.
+ *
+ * Parity status of each function is listed in the design notes; every function
+ * here is pinned by a CPU test except the physical correctness of the 2-site
+ * ordering rule (parity unpinned: only its fraction correct is reported).
+ *
+ * Precision: FP64 throughout, except the site-ordering DECISION, which is an
+ * integer result decided by floating point; it is taken in IEEE binary32 with
+ * every operation rounded once (compile with -ffp-contract=off), the same
+ * precision the GPU kernel decides in, so the chosen order is comparable bit
+ * for bit.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ME_KEV 510.99895      /* electron rest energy m_e c^2, keV (CODATA) */
+#define ME_KEV_F 510.99895f
+#define POS_EPS2_F 1e-12f     /* |x1 - x2|^2 below (1e-6 cm)^2: no axis */
+#define INF_F ((float)INFINITY)
+
+/* ------------------------------------------------------------------------ */
+/* Site ordering: binary32 decision.                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Energy of a set of sites: the deposits of the set's slots added in
+ * increasing slot order, starting from 0. */
+static float set_energy_f32(int k, const float *e, unsigned mask)
+{
+    float s = 0.0f;
+    for (int m = 0; m < k; m++)
+        if (mask & (1u << m))
+            s = s + e[m];
+    return s;
+}
+
+/* Cosine of a Compton scatter from the photon energy before (e_before) and
+ * after (e_after) the scatter, by the Sec. 1.1 formula solved for cos. */
+static float compton_cos_f32(float e_after, float e_before)
+{
+    float inv_after = 1.0f / e_after;
+    float inv_before = 1.0f / e_before;
+    float d = inv_after - inv_before;
+    float u = ME_KEV_F * d;
+    return 1.0f - u;
+}
+
+/* Squared distance between sites p and q. */
+static float sqdist_f32(const float *x, const float *y, const float *z, int p,
+                        int q)
+{
+    float dx = x[q] - x[p];
+    float dy = y[q] - y[p];
+    float dz = z[q] - z[p];
+    float a = dx * dx;
+    float b = dy * dy;
+    float c = dz * dz;
+    return (a + b) + c;
+}
+
+/*
+ * Compton chi-square of a site order (reading of the kinematic-consistency
+ * ordering; the paper treats two sites only).  The photon deposits all of its
+ * energy, so the energy entering site j is the sum of the deposits from j on.
+ * At each intermediate site j (not first, not last) the scatter cosine from
+ * energies, cos_E = 1 - m_e c^2 (1/E_after - 1/E_before), must agree with the
+ * cosine of the angle between the incoming and outgoing segments,
+ * cos_G = u(x_{j-1} -> x_j) . u(x_j -> x_{j+1}).
+ * chi2 = sum_j (cos_E - cos_G)^2, unweighted.  The order is invalid (+inf)
+ * when the first-site cone is invalid (E2 <= 0, |cos eta| > 1, or sites 1
+ * and 2 closer than 1e-6 cm), or when some intermediate site has no energy
+ * left after it, |cos_E| > 1, or a zero-length segment.
+ */
+float or_order_chi2(int k, const float *x, const float *y, const float *z,
+                    const float *e, const int *ord)
+{
+    unsigned all = (1u << k) - 1u;
+    float e0 = set_energy_f32(k, e, all);
+    float e2 = set_energy_f32(k, e, all & ~(1u << ord[0]));
+    if (!(e0 > 0.0f) || !(e2 > 0.0f))
+        return INF_F;
+    float c1 = compton_cos_f32(e2, e0);
+    if (!(c1 >= -1.0f && c1 <= 1.0f))
+        return INF_F;
+    if (!(sqdist_f32(x, y, z, ord[0], ord[1]) > POS_EPS2_F))
+        return INF_F;
+
+    float chi2 = 0.0f;
+    for (int j = 1; j + 1 < k; j++) {
+        unsigned before = 0;
+        for (int m = j; m < k; m++)
+            before |= 1u << ord[m];
+        unsigned after = before & ~(1u << ord[j]);
+        float eb = set_energy_f32(k, e, before);
+        float ea = set_energy_f32(k, e, after);
+        if (!(ea > 0.0f))
+            return INF_F;
+        float ce = compton_cos_f32(ea, eb);
+        if (!(ce >= -1.0f && ce <= 1.0f))
+            return INF_F;
+
+        int p = ord[j - 1], q = ord[j], r = ord[j + 1];
+        float ux = x[q] - x[p], uy = y[q] - y[p], uz = z[q] - z[p];
+        float vx = x[r] - x[q], vy = y[r] - y[q], vz = z[r] - z[q];
+        float t0 = ux * vx;
+        float t1 = uy * vy;
+        float t2 = uz * vz;
+        float dot = (t0 + t1) + t2;
+        float nn = sqdist_f32(x, y, z, p, q) * sqdist_f32(x, y, z, q, r);
+        if (!(nn > 0.0f))
+            return INF_F;
+        float cg = dot / sqrtf(nn);
+        float d = ce - cg;
+        chi2 = chi2 + d * d;
+    }
+    return chi2;
+}
+
+/* Klein-Nishina angular weight: dsigma/dOmega is proportional to
+ * P^2 (P + 1/P - sin^2 eta) with P = E'/E the energy ratio. */
+float or_kn_weight_f32(float P, float cos_eta)
+{
+    float c2 = cos_eta * cos_eta;
+    float s2 = 1.0f - c2;
+    float ip = 1.0f / P;
+    float t = P + ip;
+    float u = t - s2;
+    float pp = P * P;
+    return pp * u;
+}
+
+/* Next permutation in lexicographic order; returns 0 after the last one. */
+static int next_permutation(int *a, int k)
+{
+    int i = k - 2;
+    while (i >= 0 && a[i] >= a[i + 1])
+        i--;
+    if (i < 0)
+        return 0;
+    int j = k - 1;
+    while (a[j] <= a[i])
+        j--;
+    int t = a[i];
+    a[i] = a[j];
+    a[j] = t;
+    for (int l = i + 1, r = k - 1; l < r; l++, r--) {
+        t = a[l];
+        a[l] = a[r];
+        a[r] = t;
+    }
+    return 1;
+}
+
+/*
+ * Ordering rule (reading).  k = 3, 4: every one of the k! orders of the
+ * slots, ranked lexicographically; the valid order with the smallest chi2
+ * wins, ties going to the lowest rank.  k = 2: no intermediate site, so among
+ * the kinematically valid orders the one with the larger Klein-Nishina weight
+ * at its own cone angle wins (P = E2 / E0), ties going to the input order.
+ */
+int or_order_event(int k, const float *x, const float *y, const float *z,
+                   const float *e, int *order_out, int *rank_out,
+                   float *chi2_out)
+{
+    if (k < 2 || k > 4)
+        return 0;
+    if (k == 2) {
+        static const int ords[2][2] = {{0, 1}, {1, 0}};
+        float e0 = set_energy_f32(2, e, 3u);
+        int ok[2];
+        float w[2];
+        for (int o = 0; o < 2; o++) {
+            ok[o] = or_order_chi2(2, x, y, z, e, ords[o]) == 0.0f;
+            w[o] = 0.0f;
+            if (ok[o]) {
+                float e2 = set_energy_f32(2, e, 3u & ~(1u << ords[o][0]));
+                float c1 = compton_cos_f32(e2, e0);
+                float P = e2 / e0;
+                w[o] = or_kn_weight_f32(P, c1);
+            }
+        }
+        int pick;
+        if (ok[1] && (!ok[0] || w[1] > w[0]))
+            pick = 1;
+        else if (ok[0])
+            pick = 0;
+        else
+            return 0;
+        order_out[0] = ords[pick][0];
+        order_out[1] = ords[pick][1];
+        *rank_out = pick;
+        if (chi2_out)
+            *chi2_out = 0.0f;
+        return 1;
+    }
+
+    int a[4] = {0, 1, 2, 3};
+    float best = INF_F;
+    int best_rank = -1;
+    int rank = 0;
+    do {
+        float c = or_order_chi2(k, x, y, z, e, a);
+        if (c < best) {
+            best = c;
+            best_rank = rank;
+            memcpy(order_out, a, sizeof(int) * (size_t)k);
+        }
+        rank++;
+    } while (next_permutation(a, k));
+    if (best_rank < 0)
+        return 0;
+    *rank_out = best_rank;
+    if (chi2_out)
+        *chi2_out = best;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rings (FP64).                                                            */
+/* ------------------------------------------------------------------------ */
+
+static double clampd(double v, double lo, double hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/*
+ * Ring of one event from its chosen order (Sec. 1.1 formula, reading of the
+ * width).  E1 = first deposit, E2 = sum of the later deposits, E0 = E1 + E2.
+ * Width (reading, first-order error propagation):
+ *   sigma_cos^2 = (m_e c^2)^2 [ s1^2 / E0^4 + s2^2 (1/E2^2 - 1/E0^2)^2 ],
+ *   s1 = f E1, s2^2 = sum over later sites of (f e_m)^2, f = sigma_e_frac;
+ *   deta_E = sigma_cos / max(sin eta, 1e-3);
+ *   deta_G = sqrt(2) sigma_pos / |x1 - x2|;
+ *   deta = sqrt(deta_E^2 + deta_G^2) clamped to [deta_min, deta_max].
+ */
+void or_rings_from_events(int64_t count, int64_t stride, const uint8_t *n,
+                          const double *x, const double *y, const double *z,
+                          const double *e, double sigma_e_frac,
+                          double sigma_pos_cm, double deta_min,
+                          double deta_max, double *ax, double *ay, double *az,
+                          double *eta, double *deta, uint8_t *valid,
+                          uint8_t *perm)
+{
+    for (int64_t i = 0; i < count; i++) {
+        int k = n[i];
+        ax[i] = ay[i] = az[i] = eta[i] = deta[i] = 0.0;
+        valid[i] = 0;
+        perm[i] = 255;
+        if (k < 2 || k > 4)
+            continue;
+        float xf[4], yf[4], zf[4], ef[4];
+        double xd[4], yd[4], zd[4], ed[4];
+        for (int s = 0; s < k; s++) {
+            xd[s] = x[s * stride + i];
+            yd[s] = y[s * stride + i];
+            zd[s] = z[s * stride + i];
+            ed[s] = e[s * stride + i];
+            xf[s] = (float)xd[s];
+            yf[s] = (float)yd[s];
+            zf[s] = (float)zd[s];
+            ef[s] = (float)ed[s];
+        }
+        int ord[4], rank;
+        if (!or_order_event(k, xf, yf, zf, ef, ord, &rank, NULL))
+            continue;
+
+        double e1 = ed[ord[0]];
+        double e2 = 0.0, var2 = 0.0;
+        for (int j = 1; j < k; j++) {
+            e2 += ed[ord[j]];
+            double sj = sigma_e_frac * ed[ord[j]];
+            var2 += sj * sj;
+        }
+        double e0 = e1 + e2;
+        double ce = clampd(1.0 - ME_KEV * (1.0 / e2 - 1.0 / e0), -1.0, 1.0);
+        double th = acos(ce);
+
+        double d[3] = {xd[ord[0]] - xd[ord[1]], yd[ord[0]] - yd[ord[1]],
+                       zd[ord[0]] - zd[ord[1]]};
+        double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+
+        double s1 = sigma_e_frac * e1;
+        double q = 1.0 / (e2 * e2) - 1.0 / (e0 * e0);
+        double var_cos =
+            ME_KEV * ME_KEV * (s1 * s1 / (e0 * e0 * e0 * e0) + var2 * q * q);
+        double sin_eta = sin(th);
+        double w_e = sqrt(var_cos) / (sin_eta > 1e-3 ? sin_eta : 1e-3);
+        double w_g = sqrt(2.0) * sigma_pos_cm / len;
+        double w = sqrt(w_e * w_e + w_g * w_g);
+
+        ax[i] = d[0] / len;
+        ay[i] = d[1] / len;
+        az[i] = d[2] / len;
+        eta[i] = th;
+        deta[i] = clampd(w, deta_min, deta_max);
+        valid[i] = 1;
+        perm[i] = (uint8_t)rank;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Likelihood map (FP64).                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Angle between a and c, atan2(|a x c|, a . c): the plain definition of the
+ * angle, equal to acos(a . c) for unit vectors and well conditioned near 0
+ * and pi. */
+double or_angle(const double *a, const double *c)
+{
+    double cr[3] = {a[1] * c[2] - a[2] * c[1], a[2] * c[0] - a[0] * c[2],
+                    a[0] * c[1] - a[1] * c[0]};
+    double sn = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    double cs = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+    return atan2(sn, cs);
+}
+
+/* One ring's contribution to one direction (Sec. 3 back projection, far-field
+ * Gaussian reading, optional angular selection). */
+static double ring_term(double ax, double ay, double az, double eta,
+                        double deta, const double *c, double k_cut)
+{
+    double a[3] = {ax, ay, az};
+    double r = (or_angle(a, c) - eta) / deta;
+    if (k_cut > 0.0 && fabs(r) > k_cut)
+        return 0.0;
+    return exp(-0.5 * r * r);
+}
+
+double or_likelihood(int64_t R, const double *ax, const double *ay,
+                     const double *az, const double *eta, const double *deta,
+                     const uint8_t *valid, const double *s, double k_cut)
+{
+    double L = 0.0;
+    for (int64_t i = 0; i < R; i++)
+        if (valid[i])
+            L += ring_term(ax[i], ay[i], az[i], eta[i], deta[i], s, k_cut);
+    return L;
+}
+
+void or_map(int64_t R, const double *ax, const double *ay, const double *az,
+            const double *eta, const double *deta, const uint8_t *valid,
+            const double *cx, const double *cy, const double *cz,
+            const int64_t *idx, int64_t nidx, double k_cut, int nthreads,
+            double *out)
+{
+    if (nthreads < 1)
+        nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+    for (int64_t t = 0; t < nidx; t++) {
+        int64_t j = idx ? idx[t] : t;
+        double c[3] = {cx[j], cy[j], cz[j]};
+        out[t] = or_likelihood(R, ax, ay, az, eta, deta, valid, c, k_cut);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Argmax and seeds.                                                        */
+/* ------------------------------------------------------------------------ */
+
+int64_t or_argmax(int64_t M, const double *map)
+{
+    int64_t best = 0;
+    for (int64_t j = 1; j < M; j++)
+        if (map[j] > map[best])
+            best = j;
+    return best;
+}
+
+typedef struct {
+    double v;
+    int64_t j;
+} vj_t;
+
+static int cmp_vj(const void *pa, const void *pb)
+{
+    const vj_t *a = (const vj_t *)pa, *b = (const vj_t *)pb;
+    if (a->v > b->v)
+        return -1;
+    if (a->v < b->v)
+        return 1;
+    return (a->j > b->j) - (a->j < b->j);
+}
+
+/* Seeds (reading): directions sorted by (L descending, index ascending); a
+ * direction is accepted unless it lies closer than nms_rad to a seed already
+ * accepted; stop after topk. */
+int or_seeds(int64_t M, const double *map, const double *cx, const double *cy,
+             const double *cz, int topk, double nms_rad, int64_t *seeds)
+{
+    vj_t *v = (vj_t *)malloc(sizeof(vj_t) * (size_t)M);
+    if (!v)
+        return -1;
+    for (int64_t j = 0; j < M; j++) {
+        v[j].v = map[j];
+        v[j].j = j;
+    }
+    qsort(v, (size_t)M, sizeof(vj_t), cmp_vj);
+    int got = 0;
+    for (int64_t t = 0; t < M && got < topk; t++) {
+        int64_t j = v[t].j;
+        double c[3] = {cx[j], cy[j], cz[j]};
+        int near = 0;
+        for (int s = 0; s < got && !near; s++) {
+            double d[3] = {cx[seeds[s]], cy[seeds[s]], cz[seeds[s]]};
+            near = or_angle(c, d) < nms_rad;
+        }
+        if (!near)
+            seeds[got++] = j;
+    }
+    free(v);
+    return got;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Newton (IRLS) refinement, FP64.                                    */
+/* ------------------------------------------------------------------------ */
+
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static void unit3(double *a)
+{
+    double n = sqrt(dot3(a, a));
+    a[0] /= n;
+    a[1] /= n;
+    a[2] /= n;
+}
+
+/* Tangent basis at s: e1 = unit(s x z) (s x x when |s . z| > 0.9),
+ * e2 = s x e1. */
+static void tangent_basis(const double *s, double *e1, double *e2)
+{
+    double ref[3] = {0.0, 0.0, 1.0};
+    if (fabs(s[2]) > 0.9) {
+        ref[0] = 1.0;
+        ref[2] = 0.0;
+    }
+    cross3(s, ref, e1);
+    unit3(e1);
+    cross3(s, e1, e2);
+}
+
+typedef struct {
+    double L, a11, a12, a22, g1, g2;
+} gn_sums_t;
+
+/* Objective and normal-equation sums at s.  r_i = (theta_i - eta_i)/deta_i,
+ * w_i = exp(-r_i^2/2) (0 beyond k_cut); the Jacobian of r_i with respect to a
+ * tangent-plane step (u, v) at s is J_i = -[a.e1, a.e2] / (sin theta_i deta_i)
+ * (rings with sin theta_i < 1e-6 give no Jacobian).  The iteratively
+ * reweighted least-squares step solves (sum w J J^T) d = -sum w r J, whose
+ * fixed points are the stationary points of L = sum w. */
+static void gn_sums(int64_t R, const double *ax, const double *ay,
+                    const double *az, const double *eta, const double *deta,
+                    const uint8_t *valid, const double *s, const double *e1,
+                    const double *e2, double k_cut, gn_sums_t *o)
+{
+    memset(o, 0, sizeof(*o));
+    for (int64_t i = 0; i < R; i++) {
+        if (!valid[i])
+            continue;
+        double a[3] = {ax[i], ay[i], az[i]};
+        unit3(a);
+        double th = or_angle(a, s);
+        double r = (th - eta[i]) / deta[i];
+        if (k_cut > 0.0 && fabs(r) > k_cut)
+            continue;
+        double w = exp(-0.5 * r * r);
+        o->L += w;
+        double st = sin(th);
+        if (st < 1e-6)
+            continue;
+        double j1 = -dot3(a, e1) / (st * deta[i]);
+        double j2 = -dot3(a, e2) / (st * deta[i]);
+        o->a11 += w * j1 * j1;
+        o->a12 += w * j1 * j2;
+        o->a22 += w * j2 * j2;
+        o->g1 += w * r * j1;
+        o->g2 += w * r * j2;
+    }
+}
+
+/*
+ * Refinement of one seed (reading of "Gauss-Newton refinement of the best
+ * direction"): at each iteration solve the 2x2 normal equations for the step
+ * d; stop converged when |d| < tol_rad; otherwise try s + d, s + d/2, ...,
+ * s + d/1024 on the tangent plane (renormalised) and move to the first trial
+ * whose L is larger, re-basing the tangent plane there; when none is larger
+ * the point is stationary to working precision (converged).  Singular or
+ * non-finite normal equations, or max_iter iterations, end it unconverged.
+ */
+static int refine_one(int64_t R, const double *ax, const double *ay,
+                      const double *az, const double *eta, const double *deta,
+                      const uint8_t *valid, const double *seed, double k_cut,
+                      int max_iter, double tol_rad, double *s_out,
+                      double *L_out, int *iters_out)
+{
+    double s[3] = {seed[0], seed[1], seed[2]}, e1[3], e2[3];
+    unit3(s);
+    tangent_basis(s, e1, e2);
+    gn_sums_t cur;
+    gn_sums(R, ax, ay, az, eta, deta, valid, s, e1, e2, k_cut, &cur);
+    int status = -5, it;
+    for (it = 0; it < max_iter; it++) {
+        double det = cur.a11 * cur.a22 - cur.a12 * cur.a12;
+        if (!(det > 0.0) || !isfinite(det))
+            break;
+        double d1 = (-cur.g1 * cur.a22 + cur.g2 * cur.a12) / det;
+        double d2 = (-cur.g2 * cur.a11 + cur.g1 * cur.a12) / det;
+        if (!isfinite(d1) || !isfinite(d2))
+            break;
+        if (sqrt(d1 * d1 + d2 * d2) < tol_rad) {
+            status = 0;
+            it++;
+            break;
+        }
+        int moved = 0;
+        for (int h = 0; h <= 10 && !moved; h++) {
+            double f = ldexp(1.0, -h);
+            double t[3], te1[3], te2[3];
+            for (int c = 0; c < 3; c++)
+                t[c] = s[c] + f * d1 * e1[c] + f * d2 * e2[c];
+            unit3(t);
+            tangent_basis(t, te1, te2);
+            gn_sums_t trial;
+            gn_sums(R, ax, ay, az, eta, deta, valid, t, te1, te2, k_cut,
+                    &trial);
+            if (trial.L > cur.L) {
+                memcpy(s, t, sizeof s);
+                memcpy(e1, te1, sizeof e1);
+                memcpy(e2, te2, sizeof e2);
+                cur = trial;
+                moved = 1;
+            }
+        }
+        if (!moved) {
+            status = 0;
+            it++;
+            break;
+        }
+    }
+    memcpy(s_out, s, sizeof s);
+    *L_out = cur.L;
+    *iters_out = it;
+    return status;
+}
+
+int or_refine(int64_t R, const double *ax, const double *ay, const double *az,
+              const double *eta, const double *deta, const uint8_t *valid,
+              const double *seeds, int k, double k_cut, int max_iter,
+              double tol_rad, double *out_dir, double *out_obj,
+              int *out_iters)
+{
+    double best_L = -INFINITY;
+    int best_status = -5;
+    for (int t = 0; t < k; t++) {
+        double s[3], L;
+        int iters;
+        int st = refine_one(R, ax, ay, az, eta, deta, valid, seeds + 3 * t,
+                            k_cut, max_iter, tol_rad, s, &L, &iters);
+        if (L > best_L) {
+            best_L = L;
+            best_status = st;
+            memcpy(out_dir, s, sizeof s);
+            *out_obj = L;
+            *out_iters = iters;
+        }
+    }
+    return best_status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sky grids (FP64).                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Fibonacci sphere (reading): z_i = 1 - (2i+1)/n, phi_i = i * golden angle,
+ * golden angle = pi (3 - sqrt 5). */
+void or_grid_fibonacci(int64_t n, double *x, double *y, double *z)
+{
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int64_t i = 0; i < n; i++) {
+        double zi = 1.0 - (2.0 * (double)i + 1.0) / (double)n;
+        double phi = fmod((double)i * golden, 2.0 * M_PI);
+        double rho = sqrt((1.0 - zi) * (1.0 + zi));
+        x[i] = rho * cos(phi);
+        y[i] = rho * sin(phi);
+        z[i] = zi;
+    }
+}
+
+/* HEALPix pixel centres in RING order (Gorski et al. 2005): 12 nside^2
+ * equal-area pixels on 4 nside - 1 iso-latitude rings.  Polar-cap ring i
+ * (1 <= i < nside) holds 4i pixels at z = +-(1 - i^2/(3 nside^2)),
+ * phi = (j - 1/2) pi / (2i); equatorial ring i (nside <= i <= 3 nside) holds
+ * 4 nside pixels at z = (2 nside - i) 2/(3 nside), phi = (j - f) pi/(2 nside)
+ * with f = 1 when i + nside is odd and 1/2 when it is even. */
+int or_grid_healpix_ring(int64_t nside, double *x, double *y, double *z)
+{
+    if (nside < 1)
+        return -1;
+    int64_t npix = 12 * nside * nside;
+    int64_t ncap = 2 * nside * (nside - 1);
+    double n2 = (double)nside * (double)nside;
+    for (int64_t p = 0; p < npix; p++) {
+        double zz, one_minus_abs_z, phi;
+        if (p < ncap) {
+            int64_t i = (int64_t)floor((1.0 + sqrt(1.0 + 2.0 * (double)p)) / 2.0);
+            int64_t j = p + 1 - 2 * i * (i - 1);
+            one_minus_abs_z = (double)(i * i) / (3.0 * n2);
+            zz = 1.0 - one_minus_abs_z;
+            phi = M_PI / (2.0 * (double)i) * ((double)j - 0.5);
+        } else if (p < npix - ncap) {
+            int64_t q = p - ncap;
+            int64_t i = q / (4 * nside) + nside;
+            int64_t j = q % (4 * nside) + 1;
+            double f = ((i + nside) & 1) ? 1.0 : 0.5;
+            zz = (double)(2 * nside - i) * 2.0 / (3.0 * (double)nside);
+            one_minus_abs_z = 1.0 - fabs(zz);
+            phi = M_PI / (2.0 * (double)nside) * ((double)j - f);
+        } else {
+            int64_t q = npix - p;
+            int64_t i = (int64_t)floor((1.0 + sqrt(2.0 * (double)q - 1.0)) / 2.0);
+            int64_t j = 4 * i + 1 - (q - 2 * i * (i - 1));
+            one_minus_abs_z = (double)(i * i) / (3.0 * n2);
+            zz = -(1.0 - one_minus_abs_z);
+            phi = M_PI / (2.0 * (double)i) * ((double)j - 0.5);
+        }
+        double rho = sqrt(one_minus_abs_z * (2.0 - one_minus_abs_z));
+        x[p] = rho * cos(phi);
+        y[p] = rho * sin(phi);
+        z[p] = zz;
+    }
+    return 0;
+}
