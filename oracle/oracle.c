@@ -481,15 +481,19 @@ static void tangent_basis(const double *s, double *e1, double *e2)
 }
 
 typedef struct {
-    double L, a11, a12, a22, g1, g2;
+    double L, n11, n12, n22, a11, a12, a22, g1, g2;
 } gn_sums_t;
 
 /* Objective and normal-equation sums at s.  r_i = (theta_i - eta_i)/deta_i,
  * w_i = exp(-r_i^2/2) (0 beyond k_cut); the Jacobian of r_i with respect to a
  * tangent-plane step (u, v) at s is J_i = -[a.e1, a.e2] / (sin theta_i deta_i)
- * (rings with sin theta_i < 1e-6 give no Jacobian).  The iteratively
- * reweighted least-squares step solves (sum w J J^T) d = -sum w r J, whose
- * fixed points are the stationary points of L = sum w. */
+ * (rings with sin theta_i < 1e-6 give no Jacobian).
+ *   gradient:            dL = -sum w r J            (g = sum w r J)
+ *   Gauss-Newton matrix: N  = sum w (1 - r^2) J J^T  (minus the Hessian of L
+ *                        without the second derivatives of r)
+ *   IRLS matrix:         A  = sum w J J^T            (always positive)
+ * Both steps d = -N^-1 g and d = -A^-1 g have the stationary points of L as
+ * their fixed points. */
 static void gn_sums(int64_t R, const double *ax, const double *ay,
                     const double *az, const double *eta, const double *deta,
                     const uint8_t *valid, const double *s, const double *e1,
@@ -512,6 +516,10 @@ static void gn_sums(int64_t R, const double *ax, const double *ay,
             continue;
         double j1 = -dot3(a, e1) / (st * deta[i]);
         double j2 = -dot3(a, e2) / (st * deta[i]);
+        double wn = w * (1.0 - r * r);
+        o->n11 += wn * j1 * j1;
+        o->n12 += wn * j1 * j2;
+        o->n22 += wn * j2 * j2;
         o->a11 += w * j1 * j1;
         o->a12 += w * j1 * j2;
         o->a22 += w * j2 * j2;
@@ -522,12 +530,17 @@ static void gn_sums(int64_t R, const double *ax, const double *ay,
 
 /*
  * Refinement of one seed (reading of "Gauss-Newton refinement of the best
- * direction"): at each iteration solve the 2x2 normal equations for the step
- * d; stop converged when |d| < tol_rad; otherwise try s + d, s + d/2, ...,
- * s + d/1024 on the tangent plane (renormalised) and move to the first trial
- * whose L is larger, re-basing the tangent plane there; when none is larger
- * the point is stationary to working precision (converged).  Singular or
- * non-finite normal equations, or max_iter iterations, end it unconverged.
+ * direction"): at each iteration solve the 2x2 normal equations N d = -g with
+ * the Gauss-Newton matrix N when it is positive definite (n11 > 0 and
+ * det N > 0), else with the IRLS matrix A (far from a maximum, where N is
+ * indefinite, A still gives an ascent direction); stop converged when
+ * |d| < tol_rad; otherwise try s + d, s + d/2, ..., s + d/1024 on the tangent
+ * plane (renormalised) and move to the first trial whose L is not smaller
+ * (a sum of many terms near 1 cannot resolve L within ~1e-8 rad of a
+ * maximum, so "not smaller" lets the Gauss-Newton steps finish), re-basing
+ * the tangent plane there; when every trial is smaller the point is
+ * stationary to working precision (converged).  Singular or non-finite
+ * normal equations, or max_iter iterations, end it unconverged.
  */
 static int refine_one(int64_t R, const double *ax, const double *ay,
                       const double *az, const double *eta, const double *deta,
@@ -542,11 +555,18 @@ static int refine_one(int64_t R, const double *ax, const double *ay,
     gn_sums(R, ax, ay, az, eta, deta, valid, s, e1, e2, k_cut, &cur);
     int status = -5, it;
     for (it = 0; it < max_iter; it++) {
-        double det = cur.a11 * cur.a22 - cur.a12 * cur.a12;
+        double m11 = cur.n11, m12 = cur.n12, m22 = cur.n22;
+        double det = m11 * m22 - m12 * m12;
+        if (!(m11 > 0.0) || !(det > 0.0) || !isfinite(det)) {
+            m11 = cur.a11;
+            m12 = cur.a12;
+            m22 = cur.a22;
+            det = m11 * m22 - m12 * m12;
+        }
         if (!(det > 0.0) || !isfinite(det))
             break;
-        double d1 = (-cur.g1 * cur.a22 + cur.g2 * cur.a12) / det;
-        double d2 = (-cur.g2 * cur.a11 + cur.g1 * cur.a12) / det;
+        double d1 = (-cur.g1 * m22 + cur.g2 * m12) / det;
+        double d2 = (-cur.g2 * m11 + cur.g1 * m12) / det;
         if (!isfinite(d1) || !isfinite(d2))
             break;
         if (sqrt(d1 * d1 + d2 * d2) < tol_rad) {
@@ -565,7 +585,7 @@ static int refine_one(int64_t R, const double *ax, const double *ay,
             gn_sums_t trial;
             gn_sums(R, ax, ay, az, eta, deta, valid, t, te1, te2, k_cut,
                     &trial);
-            if (trial.L > cur.L) {
+            if (trial.L >= cur.L) {
                 memcpy(s, t, sizeof s);
                 memcpy(e1, te1, sizeof e1);
                 memcpy(e2, te2, sizeof e2);
