@@ -1,0 +1,229 @@
+/*
+ * compton.h - C ABI of libcompton.so, the GB300 (sm_103a) hot path of
+ * far-field Compton ring localisation.
+ *
+ * The method (Gameiro et al., "Towards Real Time Compton Imaging in Demanding
+ * Conditions", arXiv 2411.04785):
+ *   - Sec. 1.1: a gamma ray scattering by theta keeps E' = E / (1 + (E/m_e c^2)
+ *     (1 - cos theta)); energies and positions of two interactions give a
+ *     Compton cone, and overlapping cones localise the source.
+ *   - Sec. 3: back projection - every (event, probe) pair contributes
+ *     independently the probability that the event came from the probe; the
+ *     contributions are summed per probe.  Angular selection drops pairs
+ *     whose geometric and energetic angles differ by more than a cut.
+ * Far-field restatement used here: probes are sky directions c_j, each event
+ * gives a ring (axis a, opening angle eta, width deta), and the map is
+ *   L_j = sum_i valid_i exp(-r_ij^2 / 2),  r_ij = (angle(a_i, c_j) - eta_i) / deta_i.
+ *
+ * Conventions (every entry point):
+ *   - Array pointers are DEVICE pointers owned by the caller, unless a
+ *     comment says otherwise; the library never allocates device memory.
+ *     Scratch comes from a caller-provided workspace sized by the matching
+ *     *_workspace_bytes() query.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) and is asynchronous: outputs are valid once
+ *     the caller synchronises the stream.
+ *   - Argument errors return CC_EINVAL synchronously and launch nothing; the
+ *     message is available from cc_last_error() (per host thread).  A failed
+ *     CUDA launch returns CC_ECUDA.
+ *   - Errors found on the device (a bounded wait that ran out, a refinement
+ *     that did not converge) are written to the `status` device word of the
+ *     call (CC_OK otherwise), readable after synchronisation.
+ *   - An event the method cannot turn into a ring is not an error: its ring
+ *     gets valid = 0 and is skipped by localisation and refinement.
+ *   - Units: keV, cm, radians.
+ */
+#ifndef COMPTON_H
+#define COMPTON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_ABI_VERSION 1
+
+typedef enum {
+    CC_OK = 0,
+    CC_EINVAL = -1,   /* bad argument; nothing launched */
+    CC_ECUDA = -2,    /* a CUDA call failed */
+    CC_ENOMEM = -3,   /* workspace smaller than the *_workspace_bytes() query */
+    CC_ETIMEOUT = -4, /* a device-side bounded wait gave up (device status) */
+    CC_ENOCONV = -5   /* refinement stopped before converging (device status) */
+} cc_status;
+
+/* Detector events, structure of arrays.  Event i has n[i] interaction sites
+ * (2..4 are reconstructed; any other count gives an invalid ring).  Site slot
+ * s < 4 of event i is at index s * stride + i of x, y, z (cm) and e (keV).
+ * Slots are in no particular order.  stride >= count. */
+typedef struct {
+    const uint8_t *n;
+    const float *x, *y, *z, *e;
+    int64_t count;
+    int64_t stride;
+} cc_events;
+
+/* Rings, structure of arrays, `count` entries.  (ax, ay, az) is the unit cone
+ * axis pointing from the second site through the first (so a . s = cos eta
+ * for the source direction s), eta the opening angle, deta the width (both
+ * radians).  valid = 1 for a usable ring.  perm is the lexicographic rank of
+ * the chosen site order among the n! orders of the event's slots (255 for an
+ * invalid event).  As an input, valid may be NULL (all rings valid) and perm
+ * is ignored. */
+typedef struct {
+    float *ax, *ay, *az, *eta, *deta;
+    uint8_t *valid;
+    uint8_t *perm;
+    int64_t count;
+} cc_rings;
+
+/* Sky grid: `count` unit direction vectors (x, y, z), structure of arrays. */
+typedef struct {
+    const float *x, *y, *z;
+    int64_t count;
+} cc_grid;
+
+/* Parameters.  cc_params_default() fills the documented defaults. */
+typedef struct {
+    float sigma_e_frac;   /* 1-sigma energy resolution, fraction of a deposit (0.05) */
+    float sigma_pos_cm;   /* 1-sigma position resolution per axis, cm (1.0) */
+    float deta_min;       /* ring width clamp, rad (0.5 deg) */
+    float deta_max;       /* ring width clamp, rad (20 deg) */
+    float k_cut;          /* angular selection: drop |r| > k_cut; 0 keeps every pair (0) */
+    int32_t topk;         /* number of seeds returned by cc_localize, 1..64 (1) */
+    float nms_rad;        /* seeds closer than this to an accepted seed are skipped (1 deg) */
+    int32_t max_iter;     /* refinement iteration limit, 1..1000 (50) */
+    double tol_rad;       /* refinement stops when its step is shorter (1e-7) */
+} cc_params;
+
+/* Library ABI version (CC_ABI_VERSION). */
+int32_t cc_abi_version(void);
+
+/* Message of the last error returned on this host thread ("" if none). */
+const char *cc_last_error(void);
+
+/* Fill `p` (host pointer) with the defaults listed in cc_params. */
+void cc_params_default(cc_params *p);
+
+/*
+ * Rings from events (Sec. 1.1 formula and two-interaction cone).
+ * Per event: the site order is chosen by Compton-kinematic consistency (for
+ * 3-4 sites the order minimising sum over intermediate sites of
+ * (cos_energy - cos_geometry)^2, for 2 sites the order of larger
+ * Klein-Nishina weight; ties to the lowest permutation rank), decided in IEEE
+ * binary32 with every operation rounded once.  Then
+ *   a = unit(x1 - x2), cos eta = 1 - m_e c^2 (1/E2 - 1/(E1 + E2)),
+ * E1 the first deposit and E2 the sum of the later ones, and the width
+ *   deta = clamp(sqrt(deta_E^2 + deta_G^2), deta_min, deta_max),
+ *   deta_E = sigma_cos / max(sin eta, 1e-3),
+ *   sigma_cos^2 = (m_e c^2)^2 [s1^2/E0^4 + s2^2 (1/E2^2 - 1/E0^2)^2],
+ *   deta_G = sqrt(2) sigma_pos / |x1 - x2|.
+ * `ev`, `out` and `p` are host pointers to structs of device pointers;
+ * out->count must equal ev->count.  count = 0 is valid (nothing launched).
+ */
+cc_status cc_rings_from_events(const cc_events *ev, const cc_rings *out,
+                               const cc_params *p, void *stream);
+
+/* Workspace bytes cc_localize needs for `rings` rings and `dirs` directions
+ * (0 on invalid sizes). */
+size_t cc_localize_workspace_bytes(int64_t rings, int64_t dirs,
+                                   const cc_params *p);
+
+/*
+ * Likelihood map, argmax and seeds (Sec. 3 back projection, far field).
+ *   map[j]   = sum over valid rings of exp(-r_ij^2/2) (FP32, Kahan-compensated
+ *              tile sums), r_ij as in the file header; |r| > k_cut dropped
+ *              when k_cut > 0;
+ *   argmax[0] = index of the largest map value (ties: lowest index);
+ *   seeds[0..topk) = greedy top-k: directions in (L desc, index asc) order,
+ *              skipping those within nms_rad of a seed already taken
+ *              (seeds[0] = argmax; unfilled slots are -1).
+ * rings->count >= 0 (0 gives an all-zero map), grid->count >= 1.
+ * `map` [grid->count] float, `argmax` [1] int32, `seeds` [p->topk] int32
+ * (may be NULL), `status` [1] int32 (may be NULL), `workspace` device
+ * memory of at least cc_localize_workspace_bytes() bytes, 256-byte aligned.
+ * Host pointers: rings, grid, p.
+ */
+cc_status cc_localize(const cc_rings *rings, const cc_grid *grid,
+                      const cc_params *p, float *map, int32_t *argmax,
+                      int32_t *seeds, int32_t *status, void *workspace,
+                      size_t ws_bytes, void *stream);
+
+/* Workspace bytes cc_refine needs for `rings` rings and `k` seeds. */
+size_t cc_refine_workspace_bytes(int64_t rings, int32_t k);
+
+/*
+ * Gauss-Newton refinement of the best direction (iteratively reweighted least
+ * squares on the tangent plane).  From each of the k seeds (seed_dirs, device,
+ * k x 3 doubles, row major): weights w_i = exp(-r_i^2/2) frozen per
+ * iteration, J_i = -[a_i.e1, a_i.e2] / (sin theta_i deta_i), step d from
+ * (sum w J J^T) d = -sum w r J solved in FP64; the step is tried at full,
+ * half, ..., 1/1024 length and the first trial that raises L is taken; stop
+ * when |d| < tol_rad or no trial raises L (converged), or after max_iter
+ * iterations or on singular normal equations (CC_ENOCONV in status).
+ * Per-ring terms are FP32; sums, the 2x2 solve and the final normalisation
+ * are FP64.  Of the refined seeds the one with the largest L wins (ties: lower
+ * seed index): out_dir [3] double (unit), out_obj [1] double (its L),
+ * out_iters [1] int32, status [1] int32 (device pointers).  1 <= k <= 64.
+ */
+cc_status cc_refine(const cc_rings *rings, const double *seed_dirs, int32_t k,
+                    const cc_params *p, double *out_dir, double *out_obj,
+                    int32_t *out_iters, int32_t *status, void *workspace,
+                    size_t ws_bytes, void *stream);
+
+/* Fibonacci sphere grid, n >= 1 directions: z_i = 1 - (2i+1)/n,
+ * phi_i = i pi (3 - sqrt 5) mod 2 pi.  x, y, z: [n] float device arrays. */
+cc_status cc_grid_fibonacci(int64_t n, float *x, float *y, float *z,
+                            void *stream);
+
+/* HEALPix pixel centres in RING order (Gorski et al. 2005), 12 nside^2
+ * directions, 1 <= nside <= 8192.  x, y, z: [12 nside^2] float device
+ * arrays. */
+cc_status cc_grid_healpix_ring(int32_t nside, float *x, float *y, float *z,
+                               void *stream);
+
+/* Gather k grid directions as FP64 unit vectors (e.g. seeds for
+ * cc_refine): out_dirs[3t..3t+2] = grid[idx[t]], renormalised.  Negative
+ * indices give (0, 0, 0).  idx [k] int32 and out_dirs [3k] double are device
+ * pointers, grid a host pointer.  1 <= k <= 64. */
+cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k,
+                         double *out_dirs, void *stream);
+
+/*
+ * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
+ * counted per stage; when tracing is enabled each launch is also bracketed by
+ * two CUDA events recorded on the launching stream, and cc_trace_read()
+ * waits for the recorded events and adds their elapsed time.  Host-side,
+ * process-wide, thread-safe.
+ */
+typedef enum {
+    CC_STAGE_RECON = 0,   /* rings from events */
+    CC_STAGE_PACK = 1,    /* ring repacking for the sweep */
+    CC_STAGE_SWEEP = 2,   /* ring x direction sweep (+ block argmax) */
+    CC_STAGE_REDUCE = 3,  /* split-ring partial-map reduction */
+    CC_STAGE_SELECT = 4,  /* argmax and seeds */
+    CC_STAGE_GATHER = 5,  /* grid gather */
+    CC_STAGE_REFINE = 6,  /* Gauss-Newton refinement */
+    CC_STAGE_GRID = 7,    /* grid generation */
+    CC_STAGE_COUNT = 8
+} cc_stage;
+
+typedef struct {
+    int64_t launches; /* kernels launched in this stage */
+    double ms;        /* summed event time (only while tracing is enabled) */
+} cc_stage_time;
+
+/* Enable (on != 0) or disable event timing. */
+cc_status cc_trace_enable(int32_t on);
+
+/* Copy min(n, CC_STAGE_COUNT) stage records into `out` (host array); with
+ * reset != 0 clear them afterwards.  Synchronises on pending events. */
+cc_status cc_trace_read(cc_stage_time *out, int32_t n, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMPTON_H */

@@ -1,0 +1,376 @@
+"""Python binding of libcompton.so (the C ABI declared in include/compton.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch provides device memory (tensors, workspaces) and the stream.  There is
+no CPU fallback: if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcompton.so")
+
+CC_OK, CC_EINVAL, CC_ECUDA, CC_ENOMEM, CC_ETIMEOUT, CC_ENOCONV = 0, -1, -2, -3, -4, -5
+STATUS_NAMES = {0: "CC_OK", -1: "CC_EINVAL", -2: "CC_ECUDA", -3: "CC_ENOMEM",
+                -4: "CC_ETIMEOUT", -5: "CC_ENOCONV"}
+
+_P = C.c_void_p
+
+
+class cc_params(C.Structure):
+    _fields_ = [("sigma_e_frac", C.c_float), ("sigma_pos_cm", C.c_float),
+                ("deta_min", C.c_float), ("deta_max", C.c_float),
+                ("k_cut", C.c_float), ("topk", C.c_int32), ("nms_rad", C.c_float),
+                ("max_iter", C.c_int32), ("tol_rad", C.c_double)]
+
+
+class cc_events(C.Structure):
+    _fields_ = [("n", _P), ("x", _P), ("y", _P), ("z", _P), ("e", _P),
+                ("count", C.c_int64), ("stride", C.c_int64)]
+
+
+class cc_rings(C.Structure):
+    _fields_ = [("ax", _P), ("ay", _P), ("az", _P), ("eta", _P), ("deta", _P),
+                ("valid", _P), ("perm", _P), ("count", C.c_int64)]
+
+
+class cc_grid(C.Structure):
+    _fields_ = [("x", _P), ("y", _P), ("z", _P), ("count", C.c_int64)]
+
+
+class cc_stage_time(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double)]
+
+
+STAGES = ("recon", "pack", "sweep", "reduce", "select", "gather", "refine", "grid")
+
+
+class CCError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libcompton.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -m paper_2411_04785_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        S = C.c_int
+        L.cc_abi_version.restype = C.c_int32
+        L.cc_last_error.restype = C.c_char_p
+        L.cc_params_default.argtypes = [C.POINTER(cc_params)]
+        L.cc_params_default.restype = None
+        L.cc_rings_from_events.argtypes = [C.POINTER(cc_events), C.POINTER(cc_rings),
+                                           C.POINTER(cc_params), _P]
+        L.cc_rings_from_events.restype = S
+        L.cc_localize_workspace_bytes.argtypes = [C.c_int64, C.c_int64, C.POINTER(cc_params)]
+        L.cc_localize_workspace_bytes.restype = C.c_size_t
+        L.cc_localize.argtypes = [C.POINTER(cc_rings), C.POINTER(cc_grid), C.POINTER(cc_params),
+                                  _P, _P, _P, _P, _P, C.c_size_t, _P]
+        L.cc_localize.restype = S
+        L.cc_refine_workspace_bytes.argtypes = [C.c_int64, C.c_int32]
+        L.cc_refine_workspace_bytes.restype = C.c_size_t
+        L.cc_refine.argtypes = [C.POINTER(cc_rings), _P, C.c_int32, C.POINTER(cc_params),
+                                _P, _P, _P, _P, _P, C.c_size_t, _P]
+        L.cc_refine.restype = S
+        L.cc_grid_fibonacci.argtypes = [C.c_int64, _P, _P, _P, _P]
+        L.cc_grid_fibonacci.restype = S
+        L.cc_grid_healpix_ring.argtypes = [C.c_int32, _P, _P, _P, _P]
+        L.cc_grid_healpix_ring.restype = S
+        L.cc_grid_gather.argtypes = [C.POINTER(cc_grid), _P, C.c_int32, _P, _P]
+        L.cc_grid_gather.restype = S
+        L.cc_trace_enable.argtypes = [C.c_int32]
+        L.cc_trace_enable.restype = S
+        L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
+        L.cc_trace_read.restype = S
+        if L.cc_abi_version() != 1:
+            raise RuntimeError("libcompton.so ABI version mismatch")
+        _lib = L
+    return _lib
+
+
+def _check(fn, st):
+    if st != CC_OK:
+        raise CCError(fn, st, lib().cc_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, name):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+# --------------------------------------------------------------------------
+# parameters
+# --------------------------------------------------------------------------
+@dataclass
+class Params:
+    sigma_e_frac: float = 0.05
+    sigma_pos_cm: float = 1.0
+    deta_min: float = math.radians(0.5)
+    deta_max: float = math.radians(20.0)
+    k_cut: float = 0.0
+    topk: int = 1
+    nms_rad: float = math.radians(1.0)
+    max_iter: int = 50
+    tol_rad: float = 1e-7
+
+    def c(self) -> cc_params:
+        return cc_params(self.sigma_e_frac, self.sigma_pos_cm, self.deta_min,
+                         self.deta_max, self.k_cut, self.topk, self.nms_rad,
+                         self.max_iter, self.tol_rad)
+
+
+def default_params() -> Params:
+    p = cc_params()
+    lib().cc_params_default(C.byref(p))
+    return Params(p.sigma_e_frac, p.sigma_pos_cm, p.deta_min, p.deta_max, p.k_cut,
+                  p.topk, p.nms_rad, p.max_iter, p.tol_rad)
+
+
+# --------------------------------------------------------------------------
+# rings
+# --------------------------------------------------------------------------
+RING_KEYS = ("ax", "ay", "az", "eta", "deta")
+
+
+def empty_rings(n: int, device) -> dict:
+    r = {k: torch.empty(n, dtype=torch.float32, device=device) for k in RING_KEYS}
+    r["valid"] = torch.empty(n, dtype=torch.uint8, device=device)
+    r["perm"] = torch.empty(n, dtype=torch.uint8, device=device)
+    return r
+
+
+def _rings_struct(r: dict) -> cc_rings:
+    n = r["ax"].numel()
+    for k in RING_KEYS:
+        _need(r[k], torch.float32, k)
+        if r[k].numel() != n:
+            raise ValueError("ring arrays differ in length")
+    for k in ("valid", "perm"):
+        if r.get(k) is not None:
+            _need(r[k], torch.uint8, k)
+    return cc_rings(*(_ptr(r[k]) for k in RING_KEYS), _ptr(r.get("valid")),
+                    _ptr(r.get("perm")), n)
+
+
+def rings_from_events(n, x, y, z, e, params: Params | None = None, out: dict | None = None,
+                      stream=None) -> dict:
+    """Rings from events.  ``n`` [N] uint8; x, y, z, e [4, S] float32 with
+    S >= N (slot s of event i at [s, i]).  Returns the ring dict."""
+    params = params or Params()
+    N = n.numel()
+    _need(n, torch.uint8, "n")
+    for t, nm in ((x, "x"), (y, "y"), (z, "z"), (e, "e")):
+        _need(t, torch.float32, nm)
+        if t.dim() != 2 or t.shape[0] != 4 or t.shape[1] < N:
+            raise ValueError(f"{nm} must be [4, S] with S >= N")
+    stride = x.shape[1]
+    if any(t.shape[1] != stride for t in (y, z, e)):
+        raise ValueError("x, y, z, e must share one stride")
+    out = out if out is not None else empty_rings(N, n.device)
+    ev = cc_events(_ptr(n), _ptr(x), _ptr(y), _ptr(z), _ptr(e), N, stride)
+    rs = _rings_struct(out)
+    if rs.count != N:
+        raise ValueError("out rings have the wrong length")
+    pc = params.c()
+    _check("cc_rings_from_events", lib().cc_rings_from_events(
+        C.byref(ev), C.byref(rs), C.byref(pc), _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------------
+# localisation
+# --------------------------------------------------------------------------
+def localize_workspace_bytes(R: int, M: int, params: Params | None = None) -> int:
+    pc = (params or Params()).c()
+    return int(lib().cc_localize_workspace_bytes(R, M, C.byref(pc)))
+
+
+def _grid_struct(grid) -> cc_grid:
+    gx, gy, gz = grid
+    for t, nm in ((gx, "grid x"), (gy, "grid y"), (gz, "grid z")):
+        _need(t, torch.float32, nm)
+    return cc_grid(_ptr(gx), _ptr(gy), _ptr(gz), gx.numel())
+
+
+def localize(rings: dict, grid, params: Params | None = None, workspace=None, out=None,
+             stream=None):
+    """Likelihood map, argmax and seeds.  Returns (map [M] f32, argmax [1]
+    i32, seeds [topk] i32, status [1] i32) as device tensors (asynchronous)."""
+    params = params or Params()
+    rs = _rings_struct(rings)
+    gs = _grid_struct(grid)
+    dev = grid[0].device
+    M = gs.count
+    need = localize_workspace_bytes(rs.count, M, params)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = (torch.empty(M, dtype=torch.float32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev),
+               torch.empty(params.topk, dtype=torch.int32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev))
+    m, am, sd, st = out
+    pc = params.c()
+    _check("cc_localize", lib().cc_localize(
+        C.byref(rs), C.byref(gs), C.byref(pc), _ptr(m), _ptr(am), _ptr(sd), _ptr(st),
+        _ptr(workspace), workspace.numel(), _stream(stream)))
+    return m, am, sd, st
+
+
+def refine_workspace_bytes(R: int, k: int) -> int:
+    return int(lib().cc_refine_workspace_bytes(R, k))
+
+
+def refine(rings: dict, seed_dirs, params: Params | None = None, workspace=None, out=None,
+           stream=None):
+    """Gauss-Newton refinement from seed_dirs [k, 3] float64 (device).
+    Returns (dir [3] f64, obj [1] f64, iters [1] i32, status [1] i32)."""
+    params = params or Params()
+    rs = _rings_struct(rings)
+    _need(seed_dirs, torch.float64, "seed_dirs")
+    k = seed_dirs.numel() // 3
+    dev = seed_dirs.device
+    need = refine_workspace_bytes(rs.count, k)
+    if need == 0:
+        raise ValueError("bad refine sizes")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    if out is None:
+        out = (torch.empty(3, dtype=torch.float64, device=dev),
+               torch.empty(1, dtype=torch.float64, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev))
+    d, obj, it, st = out
+    pc = params.c()
+    _check("cc_refine", lib().cc_refine(
+        C.byref(rs), _ptr(seed_dirs), k, C.byref(pc), _ptr(d), _ptr(obj), _ptr(it),
+        _ptr(st), _ptr(workspace), workspace.numel(), _stream(stream)))
+    return d, obj, it, st
+
+
+# --------------------------------------------------------------------------
+# grids
+# --------------------------------------------------------------------------
+def grid_fibonacci(n: int, device="cuda", stream=None):
+    g = [torch.empty(n, dtype=torch.float32, device=device) for _ in range(3)]
+    _check("cc_grid_fibonacci", lib().cc_grid_fibonacci(n, *(_ptr(t) for t in g),
+                                                        _stream(stream)))
+    return tuple(g)
+
+
+def grid_healpix_ring(nside: int, device="cuda", stream=None):
+    npix = 12 * nside * nside
+    g = [torch.empty(npix, dtype=torch.float32, device=device) for _ in range(3)]
+    _check("cc_grid_healpix_ring", lib().cc_grid_healpix_ring(nside, *(_ptr(t) for t in g),
+                                                              _stream(stream)))
+    return tuple(g)
+
+
+def grid_gather(grid, idx, out=None, stream=None):
+    """FP64 unit vectors of grid directions idx [k] int32 -> [k, 3]."""
+    gs = _grid_struct(grid)
+    _need(idx, torch.int32, "idx")
+    k = idx.numel()
+    out = out if out is not None else torch.empty((k, 3), dtype=torch.float64,
+                                                  device=idx.device)
+    _check("cc_grid_gather", lib().cc_grid_gather(C.byref(gs), _ptr(idx), k, _ptr(out),
+                                                  _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------------
+# the whole path
+# --------------------------------------------------------------------------
+class Localizer:
+    """Events (or rings) -> map, argmax, seeds, refined direction, with
+    workspaces and outputs allocated once and reused across calls."""
+
+    def __init__(self, grid, params: Params | None = None, max_rings: int = 0):
+        self.grid = grid
+        self.params = params or Params()
+        self.M = grid[0].numel()
+        self.dev = grid[0].device
+        self._ws_loc = None
+        self._ws_ref = None
+        self._rings = None
+        self.map = torch.empty(self.M, dtype=torch.float32, device=self.dev)
+        self.argmax = torch.empty(1, dtype=torch.int32, device=self.dev)
+        self.seeds = torch.empty(self.params.topk, dtype=torch.int32, device=self.dev)
+        self.loc_status = torch.empty(1, dtype=torch.int32, device=self.dev)
+        self.seed_dirs = torch.empty((self.params.topk, 3), dtype=torch.float64,
+                                     device=self.dev)
+        self.dir = torch.empty(3, dtype=torch.float64, device=self.dev)
+        self.obj = torch.empty(1, dtype=torch.float64, device=self.dev)
+        self.iters = torch.empty(1, dtype=torch.int32, device=self.dev)
+        self.ref_status = torch.empty(1, dtype=torch.int32, device=self.dev)
+        if max_rings:
+            self._reserve(max_rings)
+
+    def _reserve(self, R):
+        nl = localize_workspace_bytes(R, self.M, self.params)
+        if self._ws_loc is None or self._ws_loc.numel() < nl:
+            self._ws_loc = torch.empty(nl, dtype=torch.uint8, device=self.dev)
+        nr = refine_workspace_bytes(R, self.params.topk)
+        if self._ws_ref is None or self._ws_ref.numel() < nr:
+            self._ws_ref = torch.empty(nr, dtype=torch.uint8, device=self.dev)
+        if self._rings is None or self._rings["ax"].numel() != R:
+            self._rings = empty_rings(R, self.dev)
+
+    def from_rings(self, rings, stream=None):
+        R = rings["ax"].numel()
+        self._reserve(R)
+        localize(rings, self.grid, self.params, self._ws_loc,
+                 (self.map, self.argmax, self.seeds, self.loc_status), stream)
+        grid_gather(self.grid, self.seeds, self.seed_dirs, stream)
+        refine(rings, self.seed_dirs, self.params, self._ws_ref,
+               (self.dir, self.obj, self.iters, self.ref_status), stream)
+        return self
+
+    def from_events(self, n, x, y, z, e, stream=None):
+        self._reserve(n.numel())
+        rings_from_events(n, x, y, z, e, self.params, self._rings, stream)
+        return self.from_rings(self._rings, stream)
+
+
+# --------------------------------------------------------------------------
+# tracing
+# --------------------------------------------------------------------------
+def trace_enable(on: bool = True):
+    _check("cc_trace_enable", lib().cc_trace_enable(1 if on else 0))
+
+
+def trace_read(reset: bool = False) -> dict:
+    """Per-stage {launches, ms} since the last reset (waits for events)."""
+    arr = (cc_stage_time * len(STAGES))()
+    _check("cc_trace_read", lib().cc_trace_read(arr, len(STAGES), 1 if reset else 0))
+    return {n: {"launches": int(a.launches), "ms": float(a.ms)} for n, a in zip(STAGES, arr)}

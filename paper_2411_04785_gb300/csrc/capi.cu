@@ -1,0 +1,193 @@
+// capi.cu - the extern "C" entry points of libcompton.so: argument checks,
+// workspace planning, per-thread error messages.  Every entry point either
+// returns CC_EINVAL before launching anything, or enqueues its kernels on the
+// caller's stream and returns CC_OK / CC_ECUDA.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+
+static thread_local char g_err[512] = "";
+
+cc_status fail(cc_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cc_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(CC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
+static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static cc_status check_params(const cc_params *p) {
+    if (!p) return fail(CC_EINVAL, "params is NULL");
+    if (!(p->k_cut >= 0.0f)) return fail(CC_EINVAL, "k_cut must be >= 0");
+    if (p->topk < 1 || p->topk > 64) return fail(CC_EINVAL, "topk must be in 1..64");
+    if (!(p->nms_rad >= 0.0f)) return fail(CC_EINVAL, "nms_rad must be >= 0");
+    if (p->max_iter < 1 || p->max_iter > 1000)
+        return fail(CC_EINVAL, "max_iter must be in 1..1000");
+    if (!(p->tol_rad >= 0.0)) return fail(CC_EINVAL, "tol_rad must be >= 0");
+    if (!(p->deta_min > 0.0f) || !(p->deta_max >= p->deta_min))
+        return fail(CC_EINVAL, "need 0 < deta_min <= deta_max");
+    if (!(p->sigma_e_frac >= 0.0f) || !(p->sigma_pos_cm >= 0.0f))
+        return fail(CC_EINVAL, "resolutions must be >= 0");
+    return CC_OK;
+}
+
+static cc_status check_rings_in(const cc_rings *r) {
+    if (!r) return fail(CC_EINVAL, "rings is NULL");
+    if (r->count < 0) return fail(CC_EINVAL, "rings->count < 0");
+    if (r->count > 0 && (!r->ax || !r->ay || !r->az || !r->eta || !r->deta))
+        return fail(CC_EINVAL, "ring arrays must be non-NULL");
+    return CC_OK;
+}
+
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" {
+
+int32_t cc_abi_version(void) { return CC_ABI_VERSION; }
+
+const char *cc_last_error(void) { return g_err; }
+
+void cc_params_default(cc_params *p) {
+    if (!p) return;
+    const float deg = 3.14159265358979323846f / 180.0f;
+    p->sigma_e_frac = 0.05f;
+    p->sigma_pos_cm = 1.0f;
+    p->deta_min = 0.5f * deg;
+    p->deta_max = 20.0f * deg;
+    p->k_cut = 0.0f;
+    p->topk = 1;
+    p->nms_rad = 1.0f * deg;
+    p->max_iter = 50;
+    p->tol_rad = 1e-7;
+}
+
+cc_status cc_rings_from_events(const cc_events *ev, const cc_rings *out, const cc_params *p,
+                               void *stream) {
+    g_err[0] = 0;
+    cc_status st = check_params(p);
+    if (st != CC_OK) return st;
+    if (!ev || !out) return fail(CC_EINVAL, "events/rings is NULL");
+    if (ev->count < 0) return fail(CC_EINVAL, "events->count < 0");
+    if (ev->stride < ev->count) return fail(CC_EINVAL, "events->stride < count");
+    if (out->count != ev->count) return fail(CC_EINVAL, "rings->count != events->count");
+    if (ev->count == 0) return CC_OK;
+    if (!ev->n || !ev->x || !ev->y || !ev->z || !ev->e)
+        return fail(CC_EINVAL, "event arrays must be non-NULL");
+    if (!out->ax || !out->ay || !out->az || !out->eta || !out->deta || !out->valid ||
+        !out->perm)
+        return fail(CC_EINVAL, "ring output arrays must be non-NULL");
+    if (ev->stride > (INT64_MAX / 4)) return fail(CC_EINVAL, "events->stride too large");
+    cudaError_t e = launch_rings_from_events(*ev, *out, *p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rings_from_events launch");
+    return CC_OK;
+}
+
+size_t cc_localize_workspace_bytes(int64_t rings, int64_t dirs, const cc_params *p) {
+    cc_params d;
+    if (!p) { cc_params_default(&d); p = &d; }
+    SweepPlan plan;
+    if (!plan_sweep(rings, dirs, *p, &plan)) return 0;
+    return plan.bytes;
+}
+
+cc_status cc_localize(const cc_rings *rings, const cc_grid *grid, const cc_params *p,
+                      float *map, int32_t *argmax, int32_t *seeds, int32_t *status,
+                      void *workspace, size_t ws_bytes, void *stream) {
+    g_err[0] = 0;
+    cc_status st = check_params(p);
+    if (st != CC_OK) return st;
+    if ((st = check_rings_in(rings)) != CC_OK) return st;
+    if (!grid || grid->count < 1 || grid->count > INT32_MAX)
+        return fail(CC_EINVAL, "grid->count must be in 1..2^31-1");
+    if (!grid->x || !grid->y || !grid->z) return fail(CC_EINVAL, "grid arrays must be non-NULL");
+    if (!map || !argmax) return fail(CC_EINVAL, "map and argmax must be non-NULL");
+    if (!workspace || !aligned(workspace, 256))
+        return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    SweepPlan plan;
+    if (!plan_sweep(rings->count, grid->count, *p, &plan))
+        return fail(CC_EINVAL, "cannot plan the sweep (sizes or device)");
+    if (ws_bytes < plan.bytes)
+        return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, plan.bytes);
+    cudaError_t e = launch_localize(*rings, *grid, *p, plan, map, argmax, seeds, status,
+                                    (char *)workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "localize launch");
+    return CC_OK;
+}
+
+size_t cc_refine_workspace_bytes(int64_t rings, int32_t k) {
+    return refine_workspace_bytes(rings, k);
+}
+
+cc_status cc_refine(const cc_rings *rings, const double *seed_dirs, int32_t k,
+                    const cc_params *p, double *out_dir, double *out_obj, int32_t *out_iters,
+                    int32_t *status, void *workspace, size_t ws_bytes, void *stream) {
+    g_err[0] = 0;
+    cc_status st = check_params(p);
+    if (st != CC_OK) return st;
+    if ((st = check_rings_in(rings)) != CC_OK) return st;
+    if (k < 1 || k > 64) return fail(CC_EINVAL, "k must be in 1..64");
+    if (!seed_dirs || !out_dir || !out_obj || !out_iters || !status)
+        return fail(CC_EINVAL, "seed_dirs and outputs must be non-NULL");
+    if (!workspace || !aligned(workspace, 256))
+        return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    size_t need = refine_workspace_bytes(rings->count, k);
+    if (need == 0) return fail(CC_EINVAL, "cannot size the refinement workspace");
+    if (ws_bytes < need)
+        return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = launch_refine(*rings, seed_dirs, k, *p, out_dir, out_obj, out_iters, status,
+                                  (char *)workspace, ws_bytes, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "refine launch");
+    return CC_OK;
+}
+
+cc_status cc_grid_fibonacci(int64_t n, float *x, float *y, float *z, void *stream) {
+    g_err[0] = 0;
+    if (n < 1 || n > ((int64_t)1 << 31)) return fail(CC_EINVAL, "n must be in 1..2^31");
+    if (!x || !y || !z) return fail(CC_EINVAL, "output arrays must be non-NULL");
+    cudaError_t e = launch_grid_fibonacci(n, x, y, z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_fibonacci launch");
+    return CC_OK;
+}
+
+cc_status cc_grid_healpix_ring(int32_t nside, float *x, float *y, float *z, void *stream) {
+    g_err[0] = 0;
+    if (nside < 1 || nside > 8192) return fail(CC_EINVAL, "nside must be in 1..8192");
+    if (!x || !y || !z) return fail(CC_EINVAL, "output arrays must be non-NULL");
+    cudaError_t e = launch_grid_healpix(nside, x, y, z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_healpix_ring launch");
+    return CC_OK;
+}
+
+cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k, double *out_dirs,
+                         void *stream) {
+    g_err[0] = 0;
+    if (!grid || grid->count < 1 || !grid->x || !grid->y || !grid->z)
+        return fail(CC_EINVAL, "bad grid");
+    if (k < 1 || k > 64) return fail(CC_EINVAL, "k must be in 1..64");
+    if (!idx || !out_dirs) return fail(CC_EINVAL, "idx/out_dirs must be non-NULL");
+    cudaError_t e = launch_grid_gather(*grid, idx, k, out_dirs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_gather launch");
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// cc_internal.cuh - declarations shared by the CUDA translation units of
+// libcompton.so (kernels, launch planning, error state).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/compton.h"
+
+namespace cc {
+
+// electron rest energy m_e c^2, keV (CODATA)
+constexpr float kMeKeV = 510.99895f;
+constexpr float kPiF = 3.14159265358979323846f;
+
+// ---------------------------------------------------------------------------
+// error state (per host thread) - capi.cu
+// ---------------------------------------------------------------------------
+cc_status fail(cc_status st, const char *fmt, ...);
+cc_status cuda_fail(cudaError_t e, const char *what);
+int device_sm_count();
+
+// Bounded waits on the device give up after this long (ns) and report
+// CC_ETIMEOUT instead of hanging.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction - recon.cu
+// ---------------------------------------------------------------------------
+cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
+                                     const cc_params &p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// sweep / argmax / seeds - sweep.cu
+// ---------------------------------------------------------------------------
+// Packed ring record of the sweep, 32 bytes: axis pre-scaled by 1/sqrt(2),
+// k = sqrt(log2(e)/2)/deta, b = eta' k, b2 = (pi - eta') k, where
+// (axis, eta') is the ring mirrored to eta' <= pi/2 when needed.
+struct __align__(16) RingRec {
+    float ax, ay, az, k;
+    float b, b2, pad0, pad1;
+};
+
+struct BlockBest {
+    float v;
+    int32_t j;
+};
+
+struct SweepPlan {
+    int d;             // directions per thread (1, 2, 4, 8)
+    int threads;       // CTA size
+    int64_t tile;      // rings per shared-memory tile
+    int64_t tiles;     // tiles per split
+    int64_t nsplit;    // ring splits (partial maps when > 1)
+    int64_t ndb;       // direction blocks
+    int64_t rpad;      // padded ring count = tiles * nsplit * tile
+    int64_t nbb;       // block-best entries
+    // workspace byte offsets
+    size_t off_rec, off_part, off_bb, off_status, bytes;
+};
+
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan);
+cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid,
+                            const cc_params &p, const SweepPlan &plan,
+                            float *map, int32_t *argmax, int32_t *seeds,
+                            int32_t *status, char *ws, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// refinement - refine.cu
+// ---------------------------------------------------------------------------
+size_t refine_workspace_bytes(int64_t R, int k);
+cudaError_t launch_refine(const cc_rings &rings, const double *seeds, int k,
+                          const cc_params &p, double *out_dir, double *out_obj,
+                          int32_t *out_iters, int32_t *status, char *ws,
+                          size_t ws_bytes, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// grids - grid.cu
+// ---------------------------------------------------------------------------
+cudaError_t launch_grid_fibonacci(int64_t n, float *x, float *y, float *z,
+                                  cudaStream_t s);
+cudaError_t launch_grid_healpix(int32_t nside, float *x, float *y, float *z,
+                                cudaStream_t s);
+cudaError_t launch_grid_gather(const cc_grid &g, const int32_t *idx, int k,
+                               double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// stage tracing - trace.cu.  Construct before a launch, destroy after it.
+// ---------------------------------------------------------------------------
+class TraceScope {
+  public:
+    TraceScope(int stage, cudaStream_t s);
+    ~TraceScope();
+
+  private:
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace cc

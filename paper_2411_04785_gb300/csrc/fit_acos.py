@@ -1,0 +1,56 @@
+"""Fit of the polynomial Q(s) = acos(1 - s) / sqrt(s) on s in [0, 1] used by
+the sweep kernel (theta = sqrt(s) Q(s) for theta <= pi/2).
+
+Criterion: minimise the maximum absolute error of theta = sqrt(s) Q(s), i.e.
+max |sqrt(s) (P(s) - Q(s))|, by weighted least squares on Chebyshev nodes with
+Lawson-style reweighting toward the equioscillating minimax solution.  The
+printed coefficients (increasing powers, rounded to binary32) are the ones in
+sweep.cu; the report gives the error of the rounded coefficients evaluated
+with FP32 fused multiply-adds.
+
+Run: python paper_2411_04785_gb300/csrc/fit_acos.py [degree]
+"""
+import sys
+
+import numpy as np
+
+
+def target(s):
+    return np.arccos(1.0 - s) / np.sqrt(s)
+
+
+def fit(deg, n=4000, iters=60):
+    s = 0.5 - 0.5 * np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    w = np.sqrt(s)
+    lam = np.ones(n)
+    for _ in range(iters):
+        A = np.vander(s, deg + 1, increasing=True) * (w * lam)[:, None]
+        c, *_ = np.linalg.lstsq(A, target(s) * w * lam, rcond=None)
+        err = np.abs(w * (np.polynomial.polynomial.polyval(s, c) - target(s)))
+        lam = lam * (err / err.max()) ** 0.3 + 1e-12
+        lam /= lam.max()
+    return c
+
+
+def report(c):
+    s = np.linspace(1e-9, 1.0, 2_000_001)
+    exact = np.arccos(1.0 - s)
+    e64 = np.abs(np.sqrt(s) * np.polynomial.polynomial.polyval(s, c) - exact).max()
+    c32 = c.astype(np.float32)
+    s32 = s.astype(np.float32)
+    acc = np.full_like(s32, c32[-1])
+    for k in range(len(c32) - 2, -1, -1):   # FMA: one rounding per step
+        acc = (acc.astype(np.float64) * s32 + c32[k]).astype(np.float32)
+    th = (np.sqrt(s32.astype(np.float64)).astype(np.float32).astype(np.float64) * acc)
+    e32 = np.abs(th.astype(np.float32).astype(np.float64) - np.arccos(1.0 - s32.astype(np.float64)))
+    return e64, e32.max(), e32.mean(), c32
+
+
+if __name__ == "__main__":
+    deg = int(sys.argv[1]) if len(sys.argv) > 1 else 7
+    e64, e32max, e32mean, c32 = report(fit(deg))
+    print(f"degree {deg}: max |error| {e64:.3e} rad (exact coefficients), "
+          f"FP32 evaluation max {e32max:.3e} mean {e32mean:.3e}")
+    print("coefficients (increasing powers):")
+    for v in c32:
+        print(f"  {float(v):.8e}f")

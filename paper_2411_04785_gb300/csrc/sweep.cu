@@ -1,0 +1,481 @@
+// sweep.cu - the ring x direction likelihood sweep with fused block argmax,
+// the split-ring reduction, and argmax / top-k seed selection.
+//
+// Sec. 3 of the paper: every (event, probe) contribution is independent and
+// the contributions are summed per probe; here probes are sky directions and
+// the contribution of ring i to direction j is exp(-r^2/2),
+// r = (angle(a_i, c_j) - eta_i) / deta_i, optionally dropped for |r| > k_cut
+// (the paper's angular selection).
+//
+// Per pair the angle is evaluated from the chord, not from acos(a . c): with
+// both vectors pre-scaled by 1/sqrt(2), h = |a' - c'|^2 = 1 - cos(theta) to
+// relative (not absolute) FP32 accuracy, so small angles keep their precision.
+// For theta <= pi/2, theta = sqrt(h) Q(h); for theta > pi/2 the mirror
+// identity theta = pi - sqrt(2 - h) Q(2 - h) applies, with
+// Q(s) = acos(1 - s) / sqrt(s) a degree-7 polynomial fitted on [0, 1]
+// (fit_acos.py; |error| <= 1.3e-8 rad before FP32 rounding).  Rings with
+// eta > pi/2 are mirrored (a -> -a, eta -> pi - eta; the map is unchanged)
+// so that the ill-conditioned end theta -> pi only meets far tails.  The
+// Gaussian is exp2(-t^2) with t = theta k - eta k, k = sqrt(log2(e)/2)/deta,
+// on the MUFU ex2 unit.
+//
+// Layout: rings are repacked once per call into 32-byte records (axis', k,
+// b, b2) in the workspace and streamed through shared memory by
+// cp.async.bulk (TMA bulk copy) into a 4-stage mbarrier ring; every CTA owns
+// 256 x D directions held in registers (D per thread, coalesced loads and
+// stores) and a contiguous range of ring tiles.  Per direction the FP32 sum
+// of a 128-ring tile is added into a Kahan-compensated accumulator.  When the
+// grid has too few direction blocks to fill 152 SMs the rings are split over
+// CTAs and the partial maps are summed in a fixed order (deterministic).
+#include <float.h>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 128;    // rings per shared-memory tile (4 KB)
+constexpr int kStages = 4;
+constexpr float kInvSqrt2 = 0.70710678118654752f;
+constexpr float kGaussK = 0.84932180028801907f;   // sqrt(log2(e) / 2)
+constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
+
+__device__ __forceinline__ float acos_q(float s) {
+    // Q(s) = acos(1 - s)/sqrt(s) on [0, 1], coefficients from fit_acos.py
+    float p = 1.4414361e-03f;
+    p = fmaf(p, s, -2.8447455e-03f);
+    p = fmaf(p, s, 4.6071224e-03f);
+    p = fmaf(p, s, 5.2066805e-04f);
+    p = fmaf(p, s, 8.6035002e-03f);
+    p = fmaf(p, s, 2.6394552e-02f);
+    p = fmaf(p, s, 1.1786042e-01f);
+    p = fmaf(p, s, 1.4142133e+00f);
+    return p;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar) {
+    unsigned b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(b)
+        : "memory");
+}
+
+// Bounded wait for an mbarrier phase: false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    unsigned b = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 31) == 0) {
+            unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) return false;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void better(float &v, int &j, float v2, int j2) {
+    if (v2 > v || (v2 == v && j2 < j)) { v = v2; j = j2; }
+}
+
+// Block-wide argmax (ties: lowest index); result valid in thread 0.
+__device__ __forceinline__ void block_best(float &v, int &j) {
+    __shared__ float sv[32];
+    __shared__ int sj[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int j2 = __shfl_xor_sync(0xffffffffu, j, o);
+        better(v, j, v2, j2);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { sv[w] = v; sj[w] = j; }
+    __syncthreads();
+    if (w == 0) {
+        v = l < nw ? sv[l] : -FLT_MAX;
+        j = l < nw ? sj[l] : INT32_MAX;
+        if (l >= nw) v = -__builtin_huge_valf();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            int j2 = __shfl_xor_sync(0xffffffffu, j, o);
+            better(v, j, v2, j2);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// ring repacking
+// ---------------------------------------------------------------------------
+__global__ void k_pack_rings(const float *__restrict__ ax, const float *__restrict__ ay,
+                             const float *__restrict__ az, const float *__restrict__ eta,
+                             const float *__restrict__ deta, const uint8_t *__restrict__ valid,
+                             int64_t R, int64_t rpad, RingRec *__restrict__ rec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rpad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        RingRec r = {0.f, 0.f, 0.f, 0.f, kNullB, kNullB, 0.f, 0.f};
+        if (i < R && (valid == nullptr || valid[i])) {
+            float a0 = ax[i], a1 = ay[i], a2 = az[i], e = eta[i], de = deta[i];
+            bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(e) &&
+                       isfinite(de) && de > 0.0f;
+            if (fin) {
+                float k = kGaussK / de;
+                float b = e * k, b2 = (kPiF - e) * k;
+                if (e > 0.5f * kPiF) {      // mirror: same ring, eta' <= pi/2
+                    a0 = -a0; a1 = -a1; a2 = -a2;
+                    float t = b; b = b2; b2 = t;
+                }
+                r = {a0 * kInvSqrt2, a1 * kInvSqrt2, a2 * kInvSqrt2, k, b, b2, 0.f, 0.f};
+            }
+        }
+        rec[i] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the sweep
+// ---------------------------------------------------------------------------
+template <int D, bool KCUT>
+__global__ void __launch_bounds__(kThreads)
+k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
+        const float *__restrict__ cx, const float *__restrict__ cy,
+        const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
+        BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
+    __shared__ __align__(128) RingRec tile[kStages][kTile];
+    __shared__ __align__(8) unsigned long long full[kStages];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int64_t db = blockIdx.x % ndb;
+    const int64_t split = blockIdx.x / ndb;
+    const int64_t j0 = db * (int64_t)(kThreads * D) + tid;
+
+    float px[D], py[D], pz[D], acc[D], sum[D], comp[D];
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        int64_t j = j0 + (int64_t)d * kThreads;
+        int64_t jj = j < M ? j : M - 1;
+        px[d] = __ldg(cx + jj) * kInvSqrt2;
+        py[d] = __ldg(cy + jj) * kInvSqrt2;
+        pz[d] = __ldg(cz + jj) * kInvSqrt2;
+        acc[d] = sum[d] = comp[d] = 0.0f;
+    }
+
+    const RingRec *src = rec + split * tiles * kTile;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < kStages && s < tiles; s++)
+            tma_bulk_load(tile[s], src + (int64_t)s * kTile, kTile * sizeof(RingRec), &full[s]);
+    }
+
+    for (int64_t t = 0; t < tiles; t++) {
+        const int stage = (int)(t % kStages);
+        const unsigned parity = (unsigned)((t / kStages) & 1);
+        if (!mbar_wait(&full[stage], parity)) {
+            abort_flag = 1;
+        } else {
+            const RingRec *T = tile[stage];
+#pragma unroll 2
+            for (int r = 0; r < kTile; r++) {
+                const float4 A = *reinterpret_cast<const float4 *>(&T[r].ax);
+                const float2 B = *reinterpret_cast<const float2 *>(&T[r].b);
+#pragma unroll
+                for (int d = 0; d < D; d++) {
+                    float dx = A.x - px[d], dy = A.y - py[d], dz = A.z - pz[d];
+                    float h = dx * dx;
+                    h = fmaf(dy, dy, h);
+                    h = fmaf(dz, dz, h);
+                    float s = fminf(h, 2.0f - h);
+                    float th = sqrt_approx(s) * acos_q(s);
+                    float bs = (h <= 1.0f) ? B.x : B.y;
+                    float u = fmaf(th, A.w, -bs);
+                    float u2 = u * u;
+                    float e = ex2_approx(-u2);
+                    if (KCUT) e = (u2 > kc2) ? 0.0f : e;
+                    acc[d] += e;
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0 && t + kStages < tiles)
+            tma_bulk_load(tile[stage], src + (t + kStages) * kTile, kTile * sizeof(RingRec),
+                          &full[stage]);
+#pragma unroll
+        for (int d = 0; d < D; d++) {   // Kahan-compensated tile sums
+            float y = acc[d] - comp[d];
+            float tt = sum[d] + y;
+            comp[d] = (tt - sum[d]) - y;
+            sum[d] = tt;
+            acc[d] = 0.0f;
+        }
+    }
+    if (abort_flag) {
+        if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
+        return;
+    }
+
+    float bv = -__builtin_huge_valf();
+    int bj = INT32_MAX;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        int64_t j = j0 + (int64_t)d * kThreads;
+        float v = sum[d] - comp[d];
+        if (j < M) {
+            out[split * M + j] = v;
+            better(bv, bj, v, (int)j);
+        }
+    }
+    if (bb != nullptr) {
+        block_best(bv, bj);
+        if (tid == 0) bb[blockIdx.x] = BlockBest{bv, bj};
+    }
+}
+
+// Sum of the split partial maps, fixed order, Kahan; plus block argmax.
+__global__ void __launch_bounds__(256)
+k_reduce_splits(const float *__restrict__ part, int64_t nsplit, int64_t M,
+                float *__restrict__ map, BlockBest *__restrict__ bb) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float bv = -__builtin_huge_valf();
+    int bj = INT32_MAX;
+    if (j < M) {
+        float s = 0.0f, c = 0.0f;
+        for (int64_t k = 0; k < nsplit; k++) {
+            float y = part[k * M + j] - c;
+            float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
+        float v = s - c;
+        map[j] = v;
+        bv = v;
+        bj = (int)j;
+    }
+    block_best(bv, bj);
+    if (threadIdx.x == 0) bb[blockIdx.x] = BlockBest{bv, bj};
+}
+
+// Argmax from the block bests, then greedy top-k with angular suppression.
+__global__ void __launch_bounds__(1024)
+k_select(const float *__restrict__ map, const BlockBest *__restrict__ bb, int64_t nbb,
+         const float *__restrict__ cx, const float *__restrict__ cy,
+         const float *__restrict__ cz, int64_t M, int topk, float cos_nms,
+         int32_t *__restrict__ argmax, int32_t *__restrict__ seeds) {
+    __shared__ float sdir[64][3];
+    __shared__ int sidx[64];
+    __shared__ int nseed;
+    float v = -__builtin_huge_valf();
+    int j = INT32_MAX;
+    for (int64_t b = threadIdx.x; b < nbb; b += blockDim.x) better(v, j, bb[b].v, bb[b].j);
+    block_best(v, j);
+    if (threadIdx.x == 0) {
+        if (j < 0 || j >= M) j = 0;   // empty or all-NaN map
+        argmax[0] = j;
+        nseed = 1;
+        sidx[0] = j;
+        sdir[0][0] = cx[j];
+        sdir[0][1] = cy[j];
+        sdir[0][2] = cz[j];
+        if (seeds) {
+            seeds[0] = j;
+            for (int t = 1; t < topk; t++) seeds[t] = -1;
+        }
+    }
+    __syncthreads();
+    if (seeds == nullptr) return;
+    for (int t = 1; t < topk; t++) {
+        float bv = -__builtin_huge_valf();
+        int bj = INT32_MAX;
+        const int ns = nseed;
+        for (int64_t jj = threadIdx.x; jj < M; jj += blockDim.x) {
+            float c0 = cx[jj], c1 = cy[jj], c2 = cz[jj];
+            bool sup = false;
+            for (int s = 0; s < ns; s++) {
+                float dot = c0 * sdir[s][0] + c1 * sdir[s][1] + c2 * sdir[s][2];
+                sup = sup || (sidx[s] == (int)jj) || (dot > cos_nms);
+            }
+            if (!sup) better(bv, bj, map[jj], (int)jj);
+        }
+        block_best(bv, bj);
+        if (threadIdx.x == 0) {
+            if (bj >= 0 && bj < M) {
+                seeds[t] = bj;
+                sidx[t] = bj;
+                sdir[t][0] = cx[bj];
+                sdir[t][1] = cy[bj];
+                sdir[t][2] = cz[bj];
+                nseed = t + 1;
+            }
+        }
+        __syncthreads();
+        if (nseed != t + 1) break;
+    }
+}
+
+template <int D, bool KCUT>
+void *sweep_fn() {
+    return (void *)k_sweep<D, KCUT>;
+}
+
+void *pick_sweep(int d, bool kcut) {
+    switch (d) {
+        case 8: return kcut ? sweep_fn<8, true>() : sweep_fn<8, false>();
+        case 4: return kcut ? sweep_fn<4, true>() : sweep_fn<4, false>();
+        case 2: return kcut ? sweep_fn<2, true>() : sweep_fn<2, false>();
+        default: return kcut ? sweep_fn<1, true>() : sweep_fn<1, false>();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launch planning
+// ---------------------------------------------------------------------------
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
+    if (R < 0 || M < 1 || M > INT32_MAX) return false;
+    const int sms = device_sm_count();
+    if (sms <= 0) return false;
+    const bool kcut = p.k_cut > 0.0f;
+    const int64_t ring_tiles = R > 0 ? (R + kTile - 1) / kTile : 1;
+    const int64_t max_split = ring_tiles < 256 ? ring_tiles : 256;
+
+    int d = 1;
+    int64_t conc = 0;
+    for (int cand : {8, 4, 2, 1}) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_sweep(cand, kcut), kThreads, 0);
+        if (occ < 1) occ = 1;
+        int64_t c = (int64_t)sms * occ;
+        int64_t ndb = (M + (int64_t)kThreads * cand - 1) / ((int64_t)kThreads * cand);
+        d = cand;
+        conc = c;
+        if (ndb * max_split >= c) break;
+    }
+    const int64_t ndb = (M + (int64_t)kThreads * d - 1) / ((int64_t)kThreads * d);
+
+    // ring splits: enough CTAs to fill the machine, whole waves (>= 90 % of
+    // the last wave busy) when possible
+    int64_t best_ns = 1;
+    double best_eff = -1.0;
+    for (int64_t ns = 1; ns <= max_split; ns++) {
+        int64_t U = ndb * ns;
+        double waves = (double)U / (double)conc;
+        double eff = waves / std::ceil(waves);
+        if (U < conc) eff = waves;      // machine not full
+        if (eff > best_eff + 1e-9) { best_eff = eff; best_ns = ns; }
+        if (U >= conc && eff >= 0.9) break;
+    }
+    const int64_t tiles = (ring_tiles + best_ns - 1) / best_ns;
+
+    plan->d = d;
+    plan->threads = kThreads;
+    plan->tile = kTile;
+    plan->tiles = tiles;
+    plan->nsplit = best_ns;
+    plan->ndb = ndb;
+    plan->rpad = tiles * best_ns * kTile;
+    plan->nbb = best_ns > 1 ? (M + 255) / 256 : ndb;
+    size_t off = 0;
+    plan->off_rec = off;
+    off = align256(off + (size_t)plan->rpad * sizeof(RingRec));
+    plan->off_part = off;
+    if (best_ns > 1) off = align256(off + (size_t)best_ns * (size_t)M * sizeof(float));
+    plan->off_bb = off;
+    off = align256(off + (size_t)plan->nbb * sizeof(BlockBest));
+    plan->off_status = off;
+    off = align256(off + sizeof(int32_t));
+    plan->bytes = off;
+    return true;
+}
+
+cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc_params &p,
+                            const SweepPlan &plan, float *map, int32_t *argmax,
+                            int32_t *seeds, int32_t *status, char *ws, cudaStream_t s) {
+    RingRec *rec = reinterpret_cast<RingRec *>(ws + plan.off_rec);
+    float *part = reinterpret_cast<float *>(ws + plan.off_part);
+    BlockBest *bb = reinterpret_cast<BlockBest *>(ws + plan.off_bb);
+    int32_t *st = status ? status : reinterpret_cast<int32_t *>(ws + plan.off_status);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+
+    const int64_t R = rings.count, M = grid.count;
+    {
+        int64_t blocks = (plan.rpad + 255) / 256;
+        if (blocks > (int64_t)device_sm_count() * 16) blocks = (int64_t)device_sm_count() * 16;
+        TraceScope ts(CC_STAGE_PACK, s);
+        k_pack_rings<<<(unsigned)blocks, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta,
+                                                      rings.deta, rings.valid, R, plan.rpad, rec);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const bool kcut = p.k_cut > 0.0f;
+    const float kc = p.k_cut * kGaussK;
+    const float kc2 = kcut ? kc * kc : 0.0f;
+    float *out = plan.nsplit > 1 ? part : map;
+    BlockBest *bbk = plan.nsplit > 1 ? nullptr : bb;
+    const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
+    void *fn = pick_sweep(plan.d, kcut);
+    void *args[] = {(void *)&rec,  (void *)&plan.tiles, (void *)&plan.ndb, (void *)&grid.x,
+                    (void *)&grid.y, (void *)&grid.z,   (void *)&M,        (void *)&kc2,
+                    (void *)&out,  (void *)&bbk,        (void *)&st};
+    {
+        TraceScope ts(CC_STAGE_SWEEP, s);
+        e = cudaLaunchKernel(fn, dim3(grid_ctas), dim3(kThreads), args, 0, s);
+    }
+    if (e != cudaSuccess) return e;
+    if (plan.nsplit > 1) {
+        {
+            TraceScope ts(CC_STAGE_REDUCE, s);
+            k_reduce_splits<<<(unsigned)plan.nbb, 256, 0, s>>>(part, plan.nsplit, M, map, bb);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int topk = p.topk < 1 ? 1 : p.topk;
+    TraceScope ts(CC_STAGE_SELECT, s);
+    k_select<<<1, 1024, 0, s>>>(map, bb, plan.nbb, grid.x, grid.y, grid.z, M, topk,
+                                cosf(p.nms_rad), argmax, seeds);
+    return cudaGetLastError();
+}
+
+}  // namespace cc
