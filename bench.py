@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the Compton ring-localisation hot path on GB300.
+
+One step = one burst through the whole path: 200,000 simulated 2-4-site
+events -> rings (ordering, axis, eta, deta) -> ring x direction likelihood
+sweep over a 49,152-direction HEALPix (nside 64, RING) grid -> block argmax ->
+Gauss-Newton refinement of the best direction.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (256 MiB write) before every timed
+step.  The metric is ring x direction evaluations per second (rings x
+directions per step / step time); per-step latency percentiles are reported
+beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank localises its own burst
+(replicas, weak scaling); the barrier and the max-over-ranks time come from
+torch.distributed.  `--impl reference` times the CPU oracle instead (the
+reference arm of this build), on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ring×direction evals/s; burst localization p50/p99 ms at ≤0.5° error vs oracle"
+UNIT = "ring×direction evals/s"
+N_SRC, N_BKG, NSIDE = 18182, 181818, 64
+ALG_FP32_PER_PAIR, ALG_MUFU_SQRT, ALG_MUFU_EX2 = 16, 1, 1
+FP32_PER_CLK_SM, SQRT_PER_CLK_SM, EX2_PER_CLK_SM = 128, 16, 32
+
+
+def peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def alu_pairs_per_clk_sm():
+    """Algorithmic pairs per clock per SM: the tighter of the FP32 pipe
+    (16 FP32 ops per pair) and the MUFU pipe (one sqrt-class op at 16/clk and
+    one ex2 at 32/clk per pair)."""
+    fp32 = FP32_PER_CLK_SM / ALG_FP32_PER_PAIR
+    mufu = 1.0 / (ALG_MUFU_SQRT / SQRT_PER_CLK_SM + ALG_MUFU_EX2 / EX2_PER_CLK_SM)
+    return min(fp32, mufu)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 7]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        pw = [float(r[2]) for r in rows if re.match(r"^\s*[\d.]+\s*$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if "Active" in r[4 + k] and "Not" not in r[4 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# --------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v, dev=None):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# --------------------------------------------------------------------------
+def oracle_step(ev, rings_needed=True, n_dirs=None, budget_s=10.0, grid=None, threads=None):
+    """Time the oracle on a bounded sample of one step: rings of every event
+    (1 thread), the map of all rings over an evenly spread sample of
+    directions (OpenMP threads, time scaled to all directions), and the
+    refinement from the best sampled direction.  Returns (seconds per full
+    step, details)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    p = dict(sigma_e_frac=0.05, sigma_pos_cm=1.0, deta_min=math.radians(0.5),
+             deta_max=math.radians(20.0))
+    t0 = time.perf_counter()
+    r = oracle.rings_from_events(ev, *p.values())
+    t_recon = time.perf_counter() - t0
+    grid = grid or oracle.grid_healpix_ring(NSIDE)
+    M = grid[0].size
+    if n_dirs is None:   # calibrate: aim the map sample at budget_s
+        t0 = time.perf_counter()
+        oracle.likelihood_map(r, grid, idx=np.arange(16), nthreads=threads)
+        per_dir = max((time.perf_counter() - t0) / 16, 1e-6)
+        n_dirs = int(min(M, max(16, budget_s * 0.8 / per_dir)))
+    idx = np.linspace(0, M - 1, n_dirs).astype(np.int64)
+    t0 = time.perf_counter()
+    sampled = oracle.likelihood_map(r, grid, idx=idx, nthreads=threads)
+    t_map = (time.perf_counter() - t0) * M / n_dirs
+    j = int(idx[oracle.argmax(sampled)])     # seed: best sampled direction
+    t0 = time.perf_counter()
+    d, obj, iters, st = oracle.refine(r, [grid[0][j], grid[1][j], grid[2][j]],
+                                      tol_rad=1e-10)
+    t_ref = time.perf_counter() - t0
+    return t_recon + t_map + t_ref, {
+        "t_recon_s": t_recon, "t_map_s_scaled": t_map, "t_refine_s": t_ref,
+        "n_dirs": n_dirs, "threads": threads, "dir": d, "status": st, "iters": iters,
+        "rings": int(r["valid"].size)}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_2411_04785_gb300 import synth
+    ev = synth.simulate_events(n_src=N_SRC, n_bkg=N_BKG, seed=2)
+    pairs = (N_SRC + N_BKG) * 12 * NSIDE * NSIDE
+    times, info = [], None
+    n_dirs = None
+    for i in range(args.warmup + args.steps):
+        t, info = oracle_step(ev, n_dirs=n_dirs, budget_s=3.0)
+        n_dirs = info["n_dirs"]
+        if i >= args.warmup:
+            times.append(t)
+    ms = 1e3 * float(np.mean(times))
+    value = pairs / (ms / 1e3)
+    sample = (f"per step: oracle rings of all {N_SRC + N_BKG} events (1 thread) + map of all "
+              f"rings over {n_dirs} of {12 * NSIDE * NSIDE} directions ({info['threads']} "
+              f"threads, time scaled to all directions) + refinement from the best sampled direction")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "events200k_healpix64", "events": N_SRC + N_BKG,
+                   "directions": 12 * NSIDE * NSIDE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"],
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def sweep_traffic(dev_sha):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep source."""
+    path = os.path.join(ROOT, "profiles", "sweep_events200k_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != dev_sha:
+        return None
+    return float(t.group(1))
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    ev = synth.simulate_events(n_src=N_SRC, n_bkg=N_BKG, seed=2 + rank)
+    N = ev["n"].size
+    tn = torch.from_numpy(ev["n"]).to(dev)
+    tx, ty, tz, te = (torch.from_numpy(ev[k]).to(dev) for k in "xyze")
+    grid = cc.grid_healpix_ring(NSIDE, dev)
+    M = grid[0].numel()
+    params = cc.Params(topk=1)
+    loc = cc.Localizer(grid, params, max_rings=N)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        loc.from_events(tn, tx, ty, tz, te)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    cc.trace_read(reset=True)
+    cc.trace_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        time.sleep(0.5)                    # let nvidia-smi start sampling
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(pg)
+    cc.trace_enable(False)
+    trace = cc.trace_read(reset=True)
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    tot_s = max_over_ranks(pg, float(step_ms.sum()) / 1e3, dev)
+    ms_per_step = 1e3 * tot_s / args.steps
+    pairs_step = N * M
+    value = world * pairs_step * args.steps / tot_s
+    launches = sum(v["launches"] for v in trace.values())
+    assert int(loc.loc_status.item()) == 0 and int(loc.ref_status.item()) in (0, -5)
+
+    # dominant kernel: the sweep (ALU bound)
+    sw = trace["sweep"]
+    sweep_ms = sw["ms"] / max(sw["launches"], 1)
+    achieved = pairs_step / (sweep_ms / 1e3)
+    clocks = clk.summary()
+    pk = peaks_file()
+    sm_max = float(pk.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak = sms * sm_max * 1e6 * alu_pairs_per_clk_sm()
+    src = open(os.path.join(ROOT, "paper_2411_04785_gb300", "csrc", "sweep.cu"), "rb").read()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
+                "frac": achieved / peak, "traffic": sweep_traffic(hashlib.sha256(src).hexdigest()),
+                "kernel": "k_sweep", "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x "
+                f"{alu_pairs_per_clk_sm():.0f} pairs/clk/SM (16 FP32 ops at 128/clk; sqrt 16/clk "
+                f"+ ex2 32/clk)"}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (sms * clocks["sm_mhz"] * 1e6 *
+                                                        alu_pairs_per_clk_sm())
+    stages = {k: {"launches_per_step": v["launches"] / args.steps,
+                  "ms_per_step": v["ms"] / args.steps}
+              for k, v in trace.items() if v["launches"]}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "events200k_healpix64", "events": N,
+                      "valid_rings": int(loc._rings["valid"].sum().item()),
+                      "directions": M, "grid": "HEALPix nside 64 RING",
+                      "sites": "2/3/4 at 0.5/0.3/0.2", "source_to_background": "1:10",
+                      "l2": "flushed between timed steps (256 MiB write)",
+                      "parallelism": f"replicas x{world}"},
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                          "p99": float(np.percentile(step_ms, 99))},
+           "wall_s": wall, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+           "stages": stages}
+
+    if not args.quick:
+        # end to end through the public API with pinned host buffers
+        hn = torch.from_numpy(ev["n"]).pin_memory()
+        hx, hy, hz, he = (torch.from_numpy(ev[k]).pin_memory() for k in "xyze")
+        hmap = torch.empty(M, dtype=torch.float32).pin_memory()
+        hdir = torch.empty(3, dtype=torch.float64).pin_memory()
+        hst = torch.empty(2, dtype=torch.int32).pin_memory()
+        dn, dx, dy, dz, de = (torch.empty_like(t, device=dev) for t in (hn, hx, hy, hz, he))
+        h2d = sum(t.numel() * t.element_size() for t in (hn, hx, hy, hz, he))
+        d2h = hmap.numel() * 4 + 3 * 8 + 2 * 4
+
+        def e2e_step():
+            for d, h in ((dn, hn), (dx, hx), (dy, hy), (dz, hz), (de, he)):
+                d.copy_(h, non_blocking=True)
+            loc.from_events(dn, dx, dy, dz, de)
+            hmap.copy_(loc.map, non_blocking=True)
+            hdir.copy_(loc.dir, non_blocking=True)
+            hst[0:1].copy_(loc.loc_status, non_blocking=True)
+            hst[1:2].copy_(loc.ref_status, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            es[i].record(stream)
+            e2e_step()
+            ee[i].record(stream)
+            ee[i].synchronize()          # the host reads the result every step
+        e_ms = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])
+        e_tot = max_over_ranks(pg, float(e_ms.sum()) / 1e3, dev)
+        out["e2e"] = {"value": world * pairs_step * args.steps / e_tot, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": 1e3 * e_tot / args.steps,
+                      "latency_ms": {"p50": float(np.percentile(e_ms, 50)),
+                                     "p99": float(np.percentile(e_ms, 99))}}
+
+        # reconstruction on a pile of 16M events (HBM bound, larger than L2)
+        copies = 80
+        pile = synth.tile_events(ev, copies)
+        pn = torch.from_numpy(pile["n"]).to(dev)
+        px, py, pz, pe = (torch.from_numpy(pile[k]).to(dev) for k in "xyze")
+        rings = cc.empty_rings(pn.numel(), dev)
+        for _ in range(3):
+            cc.rings_from_events(pn, px, py, pz, pe, params, rings)
+        torch.cuda.synchronize()
+        cc.trace_read(reset=True)
+        cc.trace_enable(True)
+        for _ in range(5):
+            cc.rings_from_events(pn, px, py, pz, pe, params, rings)
+        cc.trace_enable(False)
+        rt = cc.trace_read(reset=True)["recon"]
+        k = ev["n"].astype(np.int64)
+        alg_bytes = copies * int((1 + 16 * k + 22).sum())
+        gbs = alg_bytes / (rt["ms"] / rt["launches"] / 1e3) / 1e9
+        hbm = float(pk.get("hbm_gbs") or 6760.9)
+        out["roofline_recon"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": gbs / hbm, "traffic": None, "kernel": "k_rings_from_events",
+                                 "events": int(pn.numel()),
+                                 "ms_per_launch": rt["ms"] / rt["launches"],
+                                 "bytes_basis": "1 + 16 k + 22 bytes per event (n, k sites, ring)"}
+        del pn, px, py, pz, pe, rings
+
+    # accuracy and the CPU baseline (rank 0, N = 1 only)
+    d = loc.dir.cpu().numpy()
+    s = ev["source"]
+    out["accuracy"] = {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s))))}
+    if rank == 0 and world == 1 and not args.quick:
+        t_cpu, info = oracle_step(ev, budget_s=args.cpu_budget)
+        dd = info.pop("dir")
+        out["accuracy"]["refined_vs_oracle_deg"] = math.degrees(
+            math.atan2(np.linalg.norm(np.cross(d, dd)), float(d @ dd)))
+        out["cpu_baseline"] = {
+            "value": pairs_step / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
+            "sample": (f"oracle (C, FP64) on the same burst: rings of all {N} events on 1 "
+                       f"thread ({info['t_recon_s']:.2f} s), map of all rings over "
+                       f"{info['n_dirs']} of {M} directions on {info['threads']} threads "
+                       f"(scaled to all: {info['t_map_s_scaled']:.1f} s), refinement "
+                       f"({info['t_refine_s']:.2f} s)"),
+            "s_per_step": t_cpu}
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--quick", action="store_true", help="skip e2e, recon pile and CPU baseline")
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle map work in the CPU baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -260,9 +260,7 @@ def refine(rings: dict, seed_dirs, params: Params | None = None, workspace=None,
     _need(seed_dirs, torch.float64, "seed_dirs")
     k = seed_dirs.numel() // 3
     dev = seed_dirs.device
-    need = refine_workspace_bytes(rs.count, k)
-    if need == 0:
-        raise ValueError("bad refine sizes")
+    need = max(refine_workspace_bytes(rs.count, k), 256)   # 0: bad sizes, the call says why
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     if out is None:
