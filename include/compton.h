@@ -151,6 +151,30 @@ cc_status cc_localize(const cc_rings *rings, const cc_grid *grid,
                       int32_t *seeds, int32_t *status, void *workspace,
                       size_t ws_bytes, void *stream);
 
+/*
+ * cc_localize without a workspace, for callers that cannot allocate device
+ * memory: a detector's real-time acquisition loop that must not allocate
+ * once running, or a host application whose own pool owns all device memory
+ * and hands out no scratch.  The paper has no counterpart; this is a
+ * deployment variant of cc_localize.
+ * Same arguments, results and status as cc_localize minus the workspace: the
+ * scratch is one static device array of CC_LOCALIZE_STATIC_SCRATCH_BYTES
+ * bytes inside libcompton.so, held on every GPU that loads the library until
+ * the process exits.  Sizes whose scratch (cc_localize_workspace_bytes) does
+ * not fit are rejected with CC_EINVAL and a message; nothing is launched.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array: calls that
+ * can overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  The call allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.
+ */
+#define CC_LOCALIZE_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+cc_status cc_localize_static(const cc_rings *rings, const cc_grid *grid,
+                             const cc_params *p, float *map, int32_t *argmax,
+                             int32_t *seeds, int32_t *status, void *stream);
+
 /* Workspace bytes cc_refine needs for `rings` rings and `k` seeds. */
 size_t cc_refine_workspace_bytes(int64_t rings, int32_t k);
 

@@ -93,6 +93,9 @@ def lib() -> C.CDLL:
         L.cc_grid_healpix_ring.restype = S
         L.cc_grid_gather.argtypes = [C.POINTER(cc_grid), _P, C.c_int32, _P, _P]
         L.cc_grid_gather.restype = S
+        L.cc_localize_static.argtypes = [C.POINTER(cc_rings), C.POINTER(cc_grid),
+                                         C.POINTER(cc_params), _P, _P, _P, _P, _P]
+        L.cc_localize_static.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -244,6 +247,31 @@ def localize(rings: dict, grid, params: Params | None = None, workspace=None, ou
     _check("cc_localize", lib().cc_localize(
         C.byref(rs), C.byref(gs), C.byref(pc), _ptr(m), _ptr(am), _ptr(sd), _ptr(st),
         _ptr(workspace), workspace.numel(), _stream(stream)))
+    return m, am, sd, st
+
+
+STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def localize_static(rings: dict, grid, params: Params | None = None, out=None, stream=None):
+    """cc_localize_static: localize without a workspace (the library's static
+    device scratch, STATIC_SCRATCH_BYTES; calls that overlap on the GPU race).
+    Returns (map, argmax, seeds, status) like localize()."""
+    params = params or Params()
+    rs = _rings_struct(rings)
+    gs = _grid_struct(grid)
+    dev = grid[0].device
+    M = gs.count
+    if out is None:
+        out = (torch.empty(M, dtype=torch.float32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev),
+               torch.empty(params.topk, dtype=torch.int32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev))
+    m, am, sd, st = out
+    pc = params.c()
+    _check("cc_localize_static", lib().cc_localize_static(
+        C.byref(rs), C.byref(gs), C.byref(pc), _ptr(m), _ptr(am), _ptr(sd), _ptr(st),
+        _stream(stream)))
     return m, am, sd, st
 
 

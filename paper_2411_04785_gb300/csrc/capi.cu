@@ -20,6 +20,8 @@ cc_status fail(cc_status st, const char *fmt, ...) {
     return st;
 }
 
+void clear_error() { g_err[0] = 0; }
+
 cc_status cuda_fail(cudaError_t e, const char *what) {
     return fail(CC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }

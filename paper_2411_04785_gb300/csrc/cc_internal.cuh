@@ -17,6 +17,7 @@ constexpr float kPiF = 3.14159265358979323846f;
 // error state (per host thread) - capi.cu
 // ---------------------------------------------------------------------------
 cc_status fail(cc_status st, const char *fmt, ...);
+void clear_error();
 cc_status cuda_fail(cudaError_t e, const char *what);
 int device_sm_count();
 
