@@ -535,10 +535,13 @@ static void gn_sums(int64_t R, const double *ax, const double *ay,
  * det N > 0), else with the IRLS matrix A (far from a maximum, where N is
  * indefinite, A still gives an ascent direction); stop converged when
  * |d| < tol_rad; otherwise try s + d, s + d/2, ..., s + d/1024 on the tangent
- * plane (renormalised) and move to the first trial whose L is not smaller
- * (a sum of many terms near 1 cannot resolve L within ~1e-8 rad of a
- * maximum, so "not smaller" lets the Gauss-Newton steps finish), re-basing
- * the tangent plane there; when every trial is smaller the point is
+ * plane (renormalised) and move to the first acceptable trial, re-basing the
+ * tangent plane there.  A trial t is acceptable when L(t) is not smaller than
+ * L(s), or when the slope of L along the step is still >= 0 at t, i.e. t lies
+ * before the maximum of L on the step's great circle, so that L(t) > L(s)
+ * for a unimodal L along it.  (A sum of many terms near 1 cannot resolve L
+ * differences close to a flat maximum; the slope comes from the gradient
+ * sums and stays resolvable.)  When no trial is acceptable the point is
  * stationary to working precision (converged).  Singular or non-finite
  * normal equations, or max_iter iterations, end it unconverged.
  */
@@ -585,7 +588,13 @@ static int refine_one(int64_t R, const double *ax, const double *ay,
             gn_sums_t trial;
             gn_sums(R, ax, ay, az, eta, deta, valid, t, te1, te2, k_cut,
                     &trial);
-            if (trial.L >= cur.L) {
+            /* slope of L along D = d1 e1 + d2 e2 at t, in t's tangent plane:
+             * grad L = -(g1, g2) there */
+            double D[3], slope;
+            for (int c = 0; c < 3; c++)
+                D[c] = d1 * e1[c] + d2 * e2[c];
+            slope = -(trial.g1 * dot3(D, te1) + trial.g2 * dot3(D, te2));
+            if (trial.L >= cur.L || slope >= 0.0) {
                 memcpy(s, t, sizeof s);
                 memcpy(e1, te1, sizeof e1);
                 memcpy(e2, te2, sizeof e2);
