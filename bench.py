@@ -212,19 +212,77 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-def sweep_traffic(dev_sha):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current sweep source."""
-    path = os.path.join(ROOT, "profiles", "sweep_events200k_ncu.md")
+def ncu_traffic(summary, source):
+    """DRAM bytes per launch (read + write) from a committed ncu summary under
+    profiles/, if it was taken on the current kernel source (same sha256)."""
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", summary)).read()
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2411_04785_gb300", "csrc", source),
+                                  "rb").read()).hexdigest()
     except OSError:
         return None
     m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != dev_sha:
+    if not m or not t or m.group(1) != sha:
         return None
     return float(t.group(1))
+
+
+def recon_pile(cc, synth, ev, params, dev, copies=80, warm=3, timed=5):
+    """Reconstruction of the event workload tiled `copies` times (16M events,
+    larger than L2): returns the HBM roofline record."""
+    import torch
+    pile = synth.tile_events(ev, copies)
+    pn = torch.from_numpy(pile["n"]).to(dev)
+    px, py, pz, pe = (torch.from_numpy(pile[k]).to(dev) for k in "xyze")
+    rings = cc.empty_rings(pn.numel(), dev)
+    for _ in range(warm):
+        cc.rings_from_events(pn, px, py, pz, pe, params, rings)
+    torch.cuda.synchronize()
+    cc.trace_read(reset=True)
+    cc.trace_enable(True)
+    for _ in range(timed):
+        cc.rings_from_events(pn, px, py, pz, pe, params, rings)
+    cc.trace_enable(False)
+    rt = cc.trace_read(reset=True)["recon"]
+    k = ev["n"].astype(np.int64)
+    alg_bytes = copies * int((1 + 16 * k + 22).sum())
+    ms = rt["ms"] / max(rt["launches"], 1)
+    gbs = alg_bytes / (ms / 1e3) / 1e9 if ms > 0 else None
+    hbm = float(peaks_file().get("hbm_gbs") or 6760.9)
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm if gbs else None,
+            "traffic": ncu_traffic("recon_pile16M_ncu.md", "recon.cu"),
+            "kernel": "k_rings_from_events", "events": int(pn.numel()), "ms_per_launch": ms,
+            "bytes_basis": "1 + 16 k + 22 bytes per event (n, k sites, ring)"}
+
+
+def run_alu_rates():
+    """Per-SM FP32 / MUFU issue rates behind the sweep's roofline."""
+    src = os.path.join(ROOT, "paper_2411_04785_gb300", "csrc", "alu_rates.cu")
+    exe = os.path.join(ROOT, "paper_2411_04785_gb300", "_build", "alu_rates")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", src, "-o", exe],
+                   check=True)
+    mhz = str(peaks_file().get("sm_max_mhz") or 2070)
+    with ClockSampler(0) as clk:
+        time.sleep(0.5)
+        out = subprocess.run([exe, mhz], capture_output=True, text=True, check=True).stdout
+    rec = json.loads(out)
+    rec["clocks"] = clk.summary()
+    print(json.dumps(rec))
+
+
+def run_recon_pile(args):
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ev = synth.simulate_events(n_src=N_SRC, n_bkg=N_BKG, seed=2)
+    print(json.dumps({"roofline_recon": recon_pile(cc, synth, ev, cc.Params(), dev,
+                                                   warm=args.warmup, timed=max(args.steps, 1))}))
 
 
 def run_gpu(args):
@@ -299,9 +357,9 @@ def run_gpu(args):
     pk = peaks_file()
     sm_max = float(pk.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     peak = sms * sm_max * 1e6 * alu_pairs_per_clk_sm()
-    src = open(os.path.join(ROOT, "paper_2411_04785_gb300", "csrc", "sweep.cu"), "rb").read()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                "frac": achieved / peak, "traffic": sweep_traffic(hashlib.sha256(src).hexdigest()),
+                "frac": achieved / peak,
+                "traffic": ncu_traffic("sweep_events200k_ncu.md", "sweep.cu"),
                 "kernel": "k_sweep", "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x "
                 f"{alu_pairs_per_clk_sm():.0f} pairs/clk/SM (16 FP32 ops at 128/clk; sqrt 16/clk "
                 f"+ ex2 32/clk)"}
@@ -367,35 +425,14 @@ def run_gpu(args):
                                      "p99": float(np.percentile(e_ms, 99))}}
 
         # reconstruction on a pile of 16M events (HBM bound, larger than L2)
-        copies = 80
-        pile = synth.tile_events(ev, copies)
-        pn = torch.from_numpy(pile["n"]).to(dev)
-        px, py, pz, pe = (torch.from_numpy(pile[k]).to(dev) for k in "xyze")
-        rings = cc.empty_rings(pn.numel(), dev)
-        for _ in range(3):
-            cc.rings_from_events(pn, px, py, pz, pe, params, rings)
-        torch.cuda.synchronize()
-        cc.trace_read(reset=True)
-        cc.trace_enable(True)
-        for _ in range(5):
-            cc.rings_from_events(pn, px, py, pz, pe, params, rings)
-        cc.trace_enable(False)
-        rt = cc.trace_read(reset=True)["recon"]
-        k = ev["n"].astype(np.int64)
-        alg_bytes = copies * int((1 + 16 * k + 22).sum())
-        gbs = alg_bytes / (rt["ms"] / rt["launches"] / 1e3) / 1e9
-        hbm = float(pk.get("hbm_gbs") or 6760.9)
-        out["roofline_recon"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                 "frac": gbs / hbm, "traffic": None, "kernel": "k_rings_from_events",
-                                 "events": int(pn.numel()),
-                                 "ms_per_launch": rt["ms"] / rt["launches"],
-                                 "bytes_basis": "1 + 16 k + 22 bytes per event (n, k sites, ring)"}
-        del pn, px, py, pz, pe, rings
+        out["roofline_recon"] = recon_pile(cc, synth, ev, params, dev)
 
     # accuracy and the CPU baseline (rank 0, N = 1 only)
     d = loc.dir.cpu().numpy()
     s = ev["source"]
-    out["accuracy"] = {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s))))}
+    out["accuracy"] = {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s)))),
+                       "refine_iterations": int(loc.iters.item()),
+                       "refine_status": int(loc.ref_status.item())}
     if rank == 0 and world == 1 and not args.quick:
         t_cpu, info = oracle_step(ev, budget_s=args.cpu_budget)
         dd = info.pop("dir")
@@ -422,6 +459,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--quick", action="store_true", help="skip e2e, recon pile and CPU baseline")
+    ap.add_argument("--alu-rates", action="store_true",
+                    help="build and run the FP32 / MUFU rate microbenchmark (csrc/alu_rates.cu)")
+    ap.add_argument("--profile-recon", action="store_true",
+                    help="only run reconstruction on the 16M-event pile (for ncu)")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle map work in the CPU baseline sample")
     args = ap.parse_args()
@@ -429,6 +470,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_recon:
+        run_recon_pile(args)
+    elif args.alu_rates:
+        run_alu_rates()
     else:
         run_gpu(args)
 

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcompton.so")
 SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu",
            "noalloc.cu"]
-HEADERS = ["cc_internal.cuh", os.path.join("..", "..", "include", "compton.h")]
+HEADERS = ["cc_internal.cuh", "cc_math.cuh", os.path.join("..", "..", "include", "compton.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

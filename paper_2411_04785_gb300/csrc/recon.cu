@@ -2,7 +2,8 @@
 // angle and width (Sec. 1.1 of the paper: the Compton formula and the cone of
 // two interactions; the ordering of 3-4 sites and the width are readings).
 //
-// One thread per event.  The ORDER is an integer decided by floating point,
+// One thread per event, events grouped by site count within each CTA (see
+// k_rings_from_events).  The ORDER is an integer decided by floating point,
 // so it is decided in IEEE binary32 with every operation rounded once
 // (__fadd_rn / __fmul_rn / __frcp_rn / __fdiv_rn / __fsqrt_rn: no
 // contraction into FMA), in a fixed sequence:
@@ -14,7 +15,7 @@
 // so any implementation of the same rule in binary32 picks the same order.
 // The ring itself (axis, eta, width) is computed in FP32 with
 // better-conditioned but mathematically equal formulas.
-#include "cc_internal.cuh"
+#include "cc_math.cuh"
 
 namespace cc {
 namespace {
@@ -47,42 +48,86 @@ __device__ __forceinline__ float sqdist(const float (&x)[4], const float (&y)[4]
 
 __device__ __forceinline__ bool in_unit(float c) { return c >= -1.0f && c <= 1.0f; }
 
-// Compton chi2 of the order o[0..K) (compile-time indices after unrolling);
-// +inf when the order is kinematically invalid.
+// Per-event tables of the binary32 decision sequence, built once and shared
+// by all k! orders (indices are compile-time constants after unrolling):
+// subset energies E[S] and their reciprocals 1/E[S], squared site distances,
+// and the geometric cosines cos_G(p -> q -> r) = dot(x_q - x_p, x_r - x_q) /
+// sqrt(|x_q - x_p|^2 |x_r - x_q|^2), which are bitwise symmetric in p and r.
 template <int K>
-__device__ __forceinline__ float order_chi2(const float (&x)[4], const float (&y)[4],
-                                            const float (&z)[4], const float (&e)[4],
-                                            const int (&o)[K]) {
+struct OrderTables {
+    float E[1 << K], inv[1 << K];
+    float nsq[K][K];
+    float cg[K][K][K];
+    bool cgok[K][K][K];   // |x_q - x_p|^2 |x_r - x_q|^2 > 0
+
+    __device__ __forceinline__ OrderTables(const float (&x)[4], const float (&y)[4],
+                                           const float (&z)[4], const float (&e)[4]) {
+#pragma unroll
+        for (unsigned m = 1; m < (1u << K); m++) {
+            E[m] = set_energy<K>(e, m);
+            inv[m] = __frcp_rn(E[m]);
+        }
+#pragma unroll
+        for (int p = 0; p < K; p++)
+#pragma unroll
+            for (int q = p + 1; q < K; q++) nsq[p][q] = nsq[q][p] = sqdist(x, y, z, p, q);
+#pragma unroll
+        for (int q = 0; q < K; q++)
+#pragma unroll
+            for (int p = 0; p < K; p++)
+#pragma unroll
+                for (int r = p + 1; r < K; r++) {
+                    if (p == q || r == q) continue;
+                    float ux = __fsub_rn(x[q], x[p]), uy = __fsub_rn(y[q], y[p]),
+                          uz = __fsub_rn(z[q], z[p]);
+                    float vx = __fsub_rn(x[r], x[q]), vy = __fsub_rn(y[r], y[q]),
+                          vz = __fsub_rn(z[r], z[q]);
+                    float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
+                                          __fmul_rn(uz, vz));
+                    float nn = __fmul_rn(nsq[p][q], nsq[q][r]);
+                    float c = __fdiv_rn(dot, __fsqrt_rn(nn));
+                    cg[p][q][r] = cg[r][q][p] = c;
+                    cgok[p][q][r] = cgok[r][q][p] = nn > 0.0f;
+                }
+    }
+
+    // 1 - m_e c^2 (1/E[after] - 1/E[before])
+    __device__ __forceinline__ float ccos(unsigned after, unsigned before) const {
+        return __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(inv[after], inv[before])));
+    }
+};
+
+// Compton chi2 of the order o[0..K) from the tables; +inf when invalid.
+template <int K>
+__device__ __forceinline__ float order_chi2_t(const OrderTables<K> &T, const int (&o)[K]) {
     constexpr unsigned all = (1u << K) - 1u;
-    float e0 = set_energy<K>(e, all);
-    float e2 = set_energy<K>(e, all & ~(1u << o[0]));
-    float c1 = compton_cos(e2, e0);
-    bool ok = (e0 > 0.0f) && (e2 > 0.0f) && in_unit(c1) &&
-              (sqdist(x, y, z, o[0], o[1]) > 1e-12f);
+    const unsigned m0 = all & ~(1u << o[0]);
+    float c1 = T.ccos(m0, all);
+    bool ok = (T.E[all] > 0.0f) && (T.E[m0] > 0.0f) && in_unit(c1) &&
+              (T.nsq[o[0]][o[1]] > 1e-12f);
     float chi2 = 0.0f;
 #pragma unroll
     for (int j = 1; j + 1 < K; j++) {
         unsigned before = 0;
 #pragma unroll
         for (int m = j; m < K; m++) before |= 1u << o[m];
-        unsigned after = before & ~(1u << o[j]);
-        float eb = set_energy<K>(e, before);
-        float ea = set_energy<K>(e, after);
-        float ce = compton_cos(ea, eb);
-        int p = o[j - 1], q = o[j], r = o[j + 1];
-        float ux = __fsub_rn(x[q], x[p]), uy = __fsub_rn(y[q], y[p]),
-              uz = __fsub_rn(z[q], z[p]);
-        float vx = __fsub_rn(x[r], x[q]), vy = __fsub_rn(y[r], y[q]),
-              vz = __fsub_rn(z[r], z[q]);
-        float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
-                              __fmul_rn(uz, vz));
-        float nn = __fmul_rn(sqdist(x, y, z, p, q), sqdist(x, y, z, q, r));
-        float cg = __fdiv_rn(dot, __fsqrt_rn(nn));
-        float d = __fsub_rn(ce, cg);
+        const unsigned after = before & ~(1u << o[j]);
+        float ce = T.ccos(after, before);
+        float d = __fsub_rn(ce, T.cg[o[j - 1]][o[j]][o[j + 1]]);
         chi2 = __fadd_rn(chi2, __fmul_rn(d, d));
-        ok = ok && (ea > 0.0f) && in_unit(ce) && (nn > 0.0f);
+        ok = ok && (T.E[after] > 0.0f) && in_unit(ce) && T.cgok[o[j - 1]][o[j]][o[j + 1]];
     }
     return ok ? chi2 : kInf;
+}
+
+// Two-site validity (no intermediate site): the first-site cone only.
+__device__ __forceinline__ bool two_site_valid(const float (&x)[4], const float (&y)[4],
+                                               const float (&z)[4], const float (&e)[4],
+                                               int p0) {
+    float e0 = set_energy<2>(e, 3u);
+    float e2 = set_energy<2>(e, 3u & ~(1u << p0));
+    float c1 = compton_cos(e2, e0);
+    return (e0 > 0.0f) && (e2 > 0.0f) && in_unit(c1) && (sqdist(x, y, z, 0, 1) > 1e-12f);
 }
 
 // Klein-Nishina angular weight P^2 (P + 1/P - sin^2 eta), binary32 sequence.
@@ -106,17 +151,17 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
                                             const float (&z)[4], const float (&e)[4],
                                             int &f0, int &f1) {
     if constexpr (K == 2) {
-        const int o01[2] = {0, 1}, o10[2] = {1, 0};
-        bool ok0 = order_chi2<2>(x, y, z, e, o01) == 0.0f;
-        bool ok1 = order_chi2<2>(x, y, z, e, o10) == 0.0f;
+        bool ok0 = two_site_valid(x, y, z, e, 0);
+        bool ok1 = two_site_valid(x, y, z, e, 1);
         float e0 = set_energy<2>(e, 3u);
+        // set_energy of a single slot is the deposit itself (0 + e = e)
         float w0 = kn_weight(__fdiv_rn(e[1], e0), compton_cos(e[1], e0));
         float w1 = kn_weight(__fdiv_rn(e[0], e0), compton_cos(e[0], e0));
-        // set_energy of a single slot is the deposit itself (0 + e = e)
         if (ok1 && (!ok0 || w1 > w0)) { f0 = 1; f1 = 0; return 1; }
         if (ok0) { f0 = 0; f1 = 1; return 0; }
         return -1;
     } else {
+        const OrderTables<K> T(x, y, z, e);
         float best = kInf;
         int best_rank = -1, rank = 0;
 #pragma unroll
@@ -126,7 +171,7 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
                 if (p1 == p0) continue;
                 if constexpr (K == 3) {
                     const int o[3] = {p0, p1, 3 - p0 - p1};
-                    float c = order_chi2<3>(x, y, z, e, o);
+                    float c = order_chi2_t<3>(T, o);
                     if (c < best) { best = c; best_rank = rank; f0 = p0; f1 = p1; }
                     rank++;
                 } else {
@@ -134,7 +179,7 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
                     for (int p2 = 0; p2 < 4; p2++) {
                         if (p2 == p0 || p2 == p1) continue;
                         const int o[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
-                        float c = order_chi2<4>(x, y, z, e, o);
+                        float c = order_chi2_t<4>(T, o);
                         if (c < best) { best = c; best_rank = rank; f0 = p0; f1 = p1; }
                         rank++;
                     }
@@ -144,61 +189,56 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
     }
 }
 
-__global__ void __launch_bounds__(128)
-k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
-                    const float *__restrict__ ys, const float *__restrict__ zs,
-                    const float *__restrict__ es, int64_t count, int64_t stride,
-                    float sig_e, float sig_pos, float deta_min, float deta_max,
-                    float *__restrict__ ax, float *__restrict__ ay,
-                    float *__restrict__ az, float *__restrict__ eta,
-                    float *__restrict__ deta, uint8_t *__restrict__ valid,
-                    uint8_t *__restrict__ perm) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const int k = n[i];
-    float x[4], y[4], z[4], e[4];
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        bool used = s < k;
-        int64_t o = s * stride + i;
-        x[s] = used ? __ldg(xs + o) : 0.0f;
-        y[s] = used ? __ldg(ys + o) : 0.0f;
-        z[s] = used ? __ldg(zs + o) : 0.0f;
-        e[s] = used ? __ldg(es + o) : 0.0f;
-    }
-    int f0 = 0, f1 = 1, rank = -1;
-    if (k == 2) rank = choose_order<2>(x, y, z, e, f0, f1);
-    else if (k == 3) rank = choose_order<3>(x, y, z, e, f0, f1);
-    else if (k == 4) rank = choose_order<4>(x, y, z, e, f0, f1);
+constexpr int kRThreads = 256;
+constexpr int kWin = 1024;            // events per CTA window
+constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
-    if (rank < 0) {
-        ax[i] = ay[i] = az[i] = eta[i] = deta[i] = 0.0f;
-        valid[i] = 0;
-        perm[i] = 255;
+struct ReconSmem {
+    float v[4][4][kWin];      // [x|y|z|e][slot][sorted position]
+    float o[5][kWin];         // ax, ay, az, eta, deta by window position
+    uint16_t win_of[kWin];    // sorted position -> window position
+    uint8_t k[kWin];          // site count by sorted position
+    uint8_t ov[kWin], op[kWin];
+    int cnt[4], start[4], fill[4], next;
+};
+
+// Ring of one event (FP32) from its chosen order; writes window position w.
+__device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const float (&x)[4],
+                                              const float (&y)[4], const float (&z)[4],
+                                              const float (&e)[4], float sig_e, float sig_pos,
+                                              float deta_min, float deta_max) {
+    int f0 = 0, f1 = 1, rk = -1;
+    if (kk == 2) rk = choose_order<2>(x, y, z, e, f0, f1);
+    else if (kk == 3) rk = choose_order<3>(x, y, z, e, f0, f1);
+    else if (kk == 4) rk = choose_order<4>(x, y, z, e, f0, f1);
+    if (rk < 0) {
+        S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
+        S.ov[w] = 0;
+        S.op[w] = 255;
         return;
     }
-    // ring of the chosen order: E1 first deposit, E2 the rest, E0 = E1 + E2
+    // E1 first deposit, E2 the rest, E0 = E1 + E2
     float e1 = pick(e, f0);
     float e2 = 0.0f, var2 = 0.0f;
 #pragma unroll
     for (int s = 0; s < 4; s++)
-        if (s < k && s != f0) {
+        if (s < kk && s != f0) {
             e2 += e[s];
             float sd = sig_e * e[s];
             var2 = fmaf(sd, sd, var2);
         }
     float e0 = e1 + e2;
     // 1/E2 - 1/E0 = E1 / (E2 E0): no cancellation for small E1
-    float u = kMeKeV * e1 / (e2 * e0);
-    float c = fminf(fmaxf(1.0f - u, -1.0f), 1.0f);
-    float th = acosf(c);
+    // u = 1 - cos(eta) in [0, 2] for a valid order; eta from u directly (the
+    // chord form of acos, no rounding of 1 - u)
+    float u = fminf(fmaxf(kMeKeV * e1 / (e2 * e0), 0.0f), 2.0f);
+    float th = angle_from_half_chord2(u);
     float sin_eta = sqrtf(fmaxf(u * (2.0f - u), 0.0f));   // sqrt((1-c)(1+c))
 
     float dx = pick(x, f0) - pick(x, f1);
     float dy = pick(y, f0) - pick(y, f1);
     float dz = pick(z, f0) - pick(z, f1);
-    float len = sqrtf(dx * dx + dy * dy + dz * dz);
-    float inv_len = 1.0f / len;
+    float inv_len = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
 
     float s1 = sig_e * e1;
     // 1/E2^2 - 1/E0^2 = E1 (E0 + E2) / (E2^2 E0^2)
@@ -207,15 +247,110 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     float var_cos = kMeKeV * kMeKeV * (t1 * t1 + var2 * q * q);
     float w_e = sqrtf(var_cos) / fmaxf(sin_eta, 1e-3f);
     float w_g = 1.41421356237f * sig_pos * inv_len;
-    float w = sqrtf(w_e * w_e + w_g * w_g);
+    float wd = sqrtf(w_e * w_e + w_g * w_g);
 
-    ax[i] = dx * inv_len;
-    ay[i] = dy * inv_len;
-    az[i] = dz * inv_len;
-    eta[i] = th;
-    deta[i] = fminf(fmaxf(w, deta_min), deta_max);
-    valid[i] = 1;
-    perm[i] = (uint8_t)rank;
+    S.o[0][w] = dx * inv_len;
+    S.o[1][w] = dy * inv_len;
+    S.o[2][w] = dz * inv_len;
+    S.o[3][w] = th;
+    S.o[4][w] = fminf(fmaxf(wd, deta_min), deta_max);
+    S.ov[w] = 1;
+    S.op[w] = (uint8_t)rk;
+}
+
+// One CTA takes a window of 1024 consecutive events.  It counting-sorts them
+// in shared memory by site count (4, 3, 2, other), then its warps take
+// 32-event chunks from a shared queue, the costly 4-site chunks first, so
+// that a warp runs one code path at a time and the warps finish together;
+// the rings are written back in the original order with coalesced stores.
+__global__ void __launch_bounds__(kRThreads, 2)
+k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
+                    const float *__restrict__ ys, const float *__restrict__ zs,
+                    const float *__restrict__ es, int64_t count, int64_t stride,
+                    float sig_e, float sig_pos, float deta_min, float deta_max,
+                    float *__restrict__ ax, float *__restrict__ ay,
+                    float *__restrict__ az, float *__restrict__ eta,
+                    float *__restrict__ deta, uint8_t *__restrict__ valid,
+                    uint8_t *__restrict__ perm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ReconSmem &S = *reinterpret_cast<ReconSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t base = blockIdx.x * (int64_t)kWin;
+    if (tid < 4) {
+        S.cnt[tid] = 0;
+        S.fill[tid] = 0;
+    }
+    if (tid == 0) S.next = 0;
+    __syncthreads();
+
+    constexpr int kPer = kWin / kRThreads;
+    int kk[kPer], cls[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int64_t i = base + tid + j * kRThreads;
+        kk[j] = i < count ? n[i] : 0;
+        cls[j] = kk[j] == 4 ? 0 : kk[j] == 3 ? 1 : kk[j] == 2 ? 2 : 3;
+        atomicAdd(&S.cnt[cls[j]], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int b = 0;
+        for (int c = 0; c < 4; c++) {
+            S.start[c] = b;
+            b += S.cnt[c];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int w = tid + j * kRThreads;
+        const int64_t i = base + w;
+        const int p = S.start[cls[j]] + atomicAdd(&S.fill[cls[j]], 1);
+        S.k[p] = (uint8_t)kk[j];
+        S.win_of[p] = (uint16_t)w;
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const bool used = s < kk[j];     // kk = 0 past the end
+            const int64_t off = s * stride + i;
+            S.v[0][s][p] = used ? __ldg(xs + off) : 0.0f;
+            S.v[1][s][p] = used ? __ldg(ys + off) : 0.0f;
+            S.v[2][s][p] = used ? __ldg(zs + off) : 0.0f;
+            S.v[3][s][p] = used ? __ldg(es + off) : 0.0f;
+        }
+    }
+    __syncthreads();
+
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&S.next, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= kChunks) break;
+        const int p = c * 32 + lane;
+        float x[4], y[4], z[4], e[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            x[s] = S.v[0][s][p];
+            y[s] = S.v[1][s][p];
+            z[s] = S.v[2][s][p];
+            e[s] = S.v[3][s][p];
+        }
+        ring_of_event(S, S.win_of[p], S.k[p], x, y, z, e, sig_e, sig_pos, deta_min, deta_max);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; j++) {
+        const int w = tid + j * kRThreads;
+        const int64_t i = base + w;
+        if (i < count) {
+            ax[i] = S.o[0][w];
+            ay[i] = S.o[1][w];
+            az[i] = S.o[2][w];
+            eta[i] = S.o[3][w];
+            deta[i] = S.o[4][w];
+            valid[i] = S.ov[w];
+            perm[i] = S.op[w];
+        }
+    }
 }
 
 }  // namespace
@@ -223,10 +358,13 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
 cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
                                      const cc_params &p, cudaStream_t s) {
     if (ev.count == 0) return cudaSuccess;
-    const int threads = 128;
-    int64_t blocks = (ev.count + threads - 1) / threads;
+    const size_t smem = sizeof(ReconSmem);   // > 48 KB: opt in (per device, so every call)
+    cudaError_t e = cudaFuncSetAttribute(k_rings_from_events,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (ev.count + kWin - 1) / kWin;
     TraceScope ts(CC_STAGE_RECON, s);
-    k_rings_from_events<<<(unsigned)blocks, threads, 0, s>>>(
+    k_rings_from_events<<<(unsigned)blocks, kRThreads, smem, s>>>(
         ev.n, ev.x, ev.y, ev.z, ev.e, ev.count, ev.stride, p.sigma_e_frac,
         p.sigma_pos_cm, p.deta_min, p.deta_max, out.ax, out.ay, out.az, out.eta,
         out.deta, out.valid, out.perm);

@@ -1,18 +1,20 @@
-// refine.cu - Gauss-Newton (iteratively reweighted least squares) refinement
-// of the best direction on the tangent plane, all seeds at once, in one
-// persistent cooperative kernel.
+// refine.cu - Gauss-Newton refinement of the best direction on the tangent
+// plane, all seeds at once, in one persistent cooperative kernel.
 //
 // Each pass evaluates, for every active seed, the objective L and the 2x2
 // normal-equation sums at that seed's current candidate point: per ring in
-// FP32 (angle from the chord, Gaussian weight, Jacobian), per CTA summed in
-// FP64 and written to a double-buffered workspace slot; one bounded grid
-// barrier; then every CTA reduces all CTA partials in the same fixed order and
-// runs the same FP64 update (accept / halve / solve / stop), so every CTA
-// holds identical state without a second barrier.  No host round trip per
-// iteration; the step rule and stopping rule are those of the header.
+// FP32 (angle from the chord, Gaussian weight, Jacobian); within the CTA and
+// across CTAs the sums are carried as double-float pairs (two FP32 values,
+// ~48-bit significand, error-free TwoSum additions), because FP64 arithmetic
+// on GB300 runs at 1/64 of the FP32 rate.  One bounded grid barrier per pass;
+// then every CTA reduces all CTA partials in the same fixed order and runs the
+// same update (accept / halve / solve / stop), so every CTA holds identical
+// state without a second barrier.  FP64 is used only for the 2x2 solve, the
+// step on the sphere and its normalisation.  No host round trip per
+// iteration; the step and stopping rules are those of the C header.
 #include <float.h>
 
-#include "cc_internal.cuh"
+#include "cc_math.cuh"
 
 namespace cc {
 namespace {
@@ -23,31 +25,60 @@ constexpr int kGroup = 4;          // seeds evaluated per pass over the rings
 constexpr int kMaxHalvings = 10;
 constexpr int kSums = 9;           // L, n11, n12, n22, a11, a12, a22, g1, g2
 
+// ---------------------------------------------------------------------------
+// double-float arithmetic (pairs hi + lo of FP32 values)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    float e = s.y + (a.y + b.y);
+    float h = s.x + e;
+    return make_float2(h, e - (h - s.x));
+}
+
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                       __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// ---------------------------------------------------------------------------
+// seed state (identical in every CTA)
+// ---------------------------------------------------------------------------
 struct SeedState {
     double s[3], e1[3], e2[3];     // accepted point and tangent basis
     double c[3], ce1[3], ce2[3];   // candidate under evaluation
-    double cur[kSums];             // sums at s (see kSums)
+    double cur[kSums];             // sums at s
     double d1, d2;
     int h, iter, phase, st;        // phase 0: first evaluation, 1: trial, 2: done
 };
 
-__device__ __forceinline__ void unit3(double *a) {
-    double n = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    a[0] /= n;
-    a[1] /= n;
-    a[2] /= n;
+// Tangent basis at c (FP32: it only orients the step and the FP32 per-ring
+// Jacobian): e1 = unit(c x z) (c x x when |c_z| > 0.9), e2 = c x e1.
+__device__ __forceinline__ void basis(const double *c, double *e1, double *e2) {
+    float s0 = (float)c[0], s1 = (float)c[1], s2 = (float)c[2];
+    float r0 = 0.0f, r1 = 0.0f, r2 = 1.0f;
+    if (fabsf(s2) > 0.9f) { r0 = 1.0f; r2 = 0.0f; }
+    float a0 = s1 * r2 - s2 * r1, a1 = s2 * r0 - s0 * r2, a2 = s0 * r1 - s1 * r0;
+    float inv = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+    a0 *= inv; a1 *= inv; a2 *= inv;
+    e1[0] = a0; e1[1] = a1; e1[2] = a2;
+    e2[0] = s1 * a2 - s2 * a1;
+    e2[1] = s2 * a0 - s0 * a2;
+    e2[2] = s0 * a1 - s1 * a0;
 }
 
-__device__ __forceinline__ void basis(const double *s, double *e1, double *e2) {
-    double r0 = 0.0, r1 = 0.0, r2 = 1.0;
-    if (fabs(s[2]) > 0.9) { r0 = 1.0; r2 = 0.0; }
-    e1[0] = s[1] * r2 - s[2] * r1;
-    e1[1] = s[2] * r0 - s[0] * r2;
-    e1[2] = s[0] * r1 - s[1] * r0;
-    unit3(e1);
-    e2[0] = s[1] * e1[2] - s[2] * e1[1];
-    e2[1] = s[2] * e1[0] - s[0] * e1[2];
-    e2[2] = s[0] * e1[1] - s[1] * e1[0];
+// Final normalisation (FP64).
+__device__ __forceinline__ void unit3(double *a) {
+    double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    a[0] *= inv;
+    a[1] *= inv;
+    a[2] *= inv;
 }
 
 // Candidate s + f (d1 e1 + d2 e2), renormalised, with its tangent basis.
@@ -71,11 +102,12 @@ __device__ void next_step(SeedState &S, int max_iter, double tol) {
         det = a11 * a22 - a12 * a12;
     }
     if (!(det > 0.0) || !isfinite(det)) { S.phase = 2; S.st = CC_ENOCONV; return; }
-    double d1 = (-g1 * a22 + g2 * a12) / det;
-    double d2 = (-g2 * a11 + g1 * a12) / det;
+    double idet = 1.0 / det;
+    double d1 = (-g1 * a22 + g2 * a12) * idet;
+    double d2 = (-g2 * a11 + g1 * a12) * idet;
     if (!isfinite(d1) || !isfinite(d2)) { S.phase = 2; S.st = CC_ENOCONV; return; }
     S.iter++;
-    if (sqrt(d1 * d1 + d2 * d2) < tol) { S.phase = 2; S.st = CC_OK; return; }
+    if (d1 * d1 + d2 * d2 < tol * tol) { S.phase = 2; S.st = CC_OK; return; }
     S.d1 = d1;
     S.d2 = d2;
     S.h = 0;
@@ -90,12 +122,19 @@ __device__ void update(SeedState &S, const double *sums, int max_iter, double to
         for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
         next_step(S, max_iter, tol);
     } else if (S.phase == 1) {
-        if (sums[0] >= S.cur[0]) {       // first trial that does not lower L
+        // acceptable: L not lower, or the slope of L along the step is still
+        // >= 0 at the trial (before the maximum on the step's great circle)
+        double slope = 0.0;
+        for (int c = 0; c < 3; c++) {
+            double Dc = S.d1 * S.e1[c] + S.d2 * S.e2[c];
+            slope -= Dc * (sums[7] * S.ce1[c] + sums[8] * S.ce2[c]);
+        }
+        if (sums[0] >= S.cur[0] || slope >= 0.0) {
             for (int c = 0; c < 3; c++) { S.s[c] = S.c[c]; S.e1[c] = S.ce1[c]; S.e2[c] = S.ce2[c]; }
             for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
             next_step(S, max_iter, tol);
         } else if (++S.h > kMaxHalvings) {
-            S.phase = 2;                 // every trial lowers L: stationary
+            S.phase = 2;                 // no acceptable trial: stationary
             S.st = CC_OK;
         } else {
             set_candidate(S, ldexp(1.0, -S.h));
@@ -121,7 +160,7 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks) {
             unsigned long long t0 = globaltimer_ns();
             unsigned it = 0;
             while (*vgen == g) {
-                __nanosleep(64);
+                __nanosleep(32);
                 if ((++it & 255) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
                     ok = 0;
                     break;
@@ -134,20 +173,52 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks) {
     return ok != 0;
 }
 
+// One ring's FP32 terms at a candidate point C = (s, e1, e2): the weight w
+// (into the double-float L) and the normal-equation terms.  The angle comes
+// from the chord as in the sweep; sin(theta) = sqrt(h (2 - h)).
+__device__ __forceinline__ void ring_terms(float a0, float a1, float a2, float eta, float inv_de,
+                                           const float *C, float kcut, float2 &L, float *acc) {
+    float dx = a0 - C[0], dy = a1 - C[1], dz = a2 - C[2];
+    float h = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // 1 - cos(theta)
+    float th = angle_from_half_chord2(h);
+    float r = (th - eta) * inv_de;
+    if (kcut > 0.0f && fabsf(r) > kcut) return;
+    float w = ex2_approx(-0.72134752f * r * r);              // exp(-r^2 / 2)
+    L = df_add(L, make_float2(w, 0.0f));
+    float st2 = h * (2.0f - h);                              // sin^2(theta)
+    if (st2 < 1e-12f) return;                                // sin(theta) < 1e-6
+    float f = -inv_de * rsqrt_approx(st2);                   // -1 / (sin(theta) deta)
+    float j1 = f * fmaf(a0, C[3], fmaf(a1, C[4], a2 * C[5]));
+    float j2 = f * fmaf(a0, C[6], fmaf(a1, C[7], a2 * C[8]));
+    float wj1 = w * j1, wj2 = w * j2;
+    float nf = fmaf(-r, r, 1.0f);
+    acc[1] = fmaf(nf * wj1, j1, acc[1]);
+    acc[2] = fmaf(nf * wj1, j2, acc[2]);
+    acc[3] = fmaf(nf * wj2, j2, acc[3]);
+    acc[4] = fmaf(wj1, j1, acc[4]);
+    acc[5] = fmaf(wj1, j2, acc[5]);
+    acc[6] = fmaf(wj2, j2, acc[6]);
+    acc[7] = fmaf(wj1, r, acc[7]);
+    acc[8] = fmaf(wj2, r, acc[8]);
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
          const float *__restrict__ az, const float *__restrict__ eta,
          const float *__restrict__ deta, const uint8_t *__restrict__ valid, int64_t R,
          const double *__restrict__ seeds, int k, float k_cut, int max_iter, double tol,
-         unsigned *bar, double *partials, double *out_dir, double *out_obj,
+         unsigned *bar, float2 *partials, double *out_dir, double *out_obj,
          int32_t *out_iters, int32_t *status) {
     __shared__ SeedState S[kMaxSeeds];
-    __shared__ float cf[kMaxSeeds][9];      // FP32 copy of candidate + basis
-    __shared__ double red[kThreads / 32][kGroup * kSums];
+    __shared__ float cf[kMaxSeeds][9];                  // FP32 candidate + basis
+    __shared__ float2 red[kThreads / 32][kGroup * kSums];
+    __shared__ float2 part[kThreads];
+    __shared__ double sums[kMaxSeeds * kSums];
     __shared__ int active_any;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned G = gridDim.x;
+    const int P = k * kSums;                            // partial sums per CTA
     if (tid < k) {
         SeedState &T = S[tid];
         for (int c = 0; c < 3; c++) T.c[c] = seeds[3 * tid + c];
@@ -162,9 +233,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     }
     __syncthreads();
 
-    const float kcut = k_cut;
     for (int pass = 0;; pass++) {
-        // FP32 copies of the candidates
         if (tid < k) {
             for (int c = 0; c < 3; c++) {
                 cf[tid][c] = (float)S[tid].c[c];
@@ -173,73 +242,58 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             }
         }
         __syncthreads();
-        double *slot = partials + (size_t)(pass & 1) * G * k * kSums;
+        float2 *slot = partials + (size_t)(pass & 1) * G * P;
+
+        // this CTA's sums, seeds in groups of kGroup
         for (int g0 = 0; g0 < k; g0 += kGroup) {
-            float acc[kGroup][kSums];
+            bool act[kGroup];
+            bool any = false;
 #pragma unroll
-            for (int g = 0; g < kGroup; g++)
+            for (int g = 0; g < kGroup; g++) {
+                act[g] = (g0 + g < k) && S[g0 + g].phase != 2;
+                any = any || act[g];
+            }
+            if (!any) continue;                         // uniform across the CTA
+            float acc[kGroup][kSums];
+            float2 L[kGroup];
+#pragma unroll
+            for (int g = 0; g < kGroup; g++) {
+                L[g] = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int q = 0; q < kSums; q++) acc[g][q] = 0.0f;
-            bool act[kGroup];
-#pragma unroll
-            for (int g = 0; g < kGroup; g++) act[g] = (g0 + g < k) && S[g0 + g].phase != 2;
+            }
             for (int64_t i = blockIdx.x * (int64_t)kThreads + tid; i < R;
                  i += (int64_t)G * kThreads) {
                 if (valid != nullptr && !valid[i]) continue;
                 float a0 = ax[i], a1 = ay[i], a2 = az[i];
-                float inv = rsqrtf(a0 * a0 + a1 * a1 + a2 * a2);
-                a0 *= inv; a1 *= inv; a2 *= inv;
-                const float et = eta[i], de = deta[i];
+                float inv = rsqrt_approx(fmaf(a0, a0, fmaf(a1, a1, a2 * a2)));
+                a0 *= inv;
+                a1 *= inv;
+                a2 *= inv;
+                const float et = eta[i], inv_de = __frcp_rn(deta[i]);
 #pragma unroll
-                for (int g = 0; g < kGroup; g++) {
-                    if (!act[g]) continue;
-                    const float *C = cf[g0 + g];
-                    float dx = a0 - C[0], dy = a1 - C[1], dz = a2 - C[2];
-                    float sx = a0 + C[0], sy = a1 + C[1], sz = a2 + C[2];
-                    float qm = dx * dx + dy * dy + dz * dz;   // |a - s|^2
-                    float qp = sx * sx + sy * sy + sz * sz;   // |a + s|^2
-                    float th = qm <= qp ? 2.0f * asinf(0.5f * sqrtf(qm))
-                                        : kPiF - 2.0f * asinf(0.5f * sqrtf(qp));
-                    float r = (th - et) / de;
-                    if (kcut > 0.0f && fabsf(r) > kcut) continue;
-                    float w = expf(-0.5f * r * r);
-                    acc[g][0] += w;
-                    float st = 0.5f * sqrtf(qm * qp);          // sin(theta)
-                    if (st < 1e-6f) continue;
-                    float f = -1.0f / (st * de);
-                    float j1 = f * (a0 * C[3] + a1 * C[4] + a2 * C[5]);
-                    float j2 = f * (a0 * C[6] + a1 * C[7] + a2 * C[8]);
-                    float wj1 = w * j1, wj2 = w * j2;
-                    float nf = 1.0f - r * r;
-                    acc[g][1] += nf * wj1 * j1;
-                    acc[g][2] += nf * wj1 * j2;
-                    acc[g][3] += nf * wj2 * j2;
-                    acc[g][4] += wj1 * j1;
-                    acc[g][5] += wj1 * j2;
-                    acc[g][6] += wj2 * j2;
-                    acc[g][7] += wj1 * r;
-                    acc[g][8] += wj2 * r;
-                }
+                for (int g = 0; g < kGroup; g++)
+                    if (act[g])
+                        ring_terms(a0, a1, a2, et, inv_de, cf[g0 + g], k_cut, L[g], acc[g]);
             }
-            // block sums in FP64
-            const int w = tid >> 5, l = tid & 31;
+            // warp and CTA sums in double-float
 #pragma unroll
-            for (int g = 0; g < kGroup; g++)
+            for (int g = 0; g < kGroup; g++) {
+                if (!act[g]) continue;
 #pragma unroll
                 for (int q = 0; q < kSums; q++) {
-                    double v = (double)acc[g][q];
+                    float2 v = q == 0 ? L[g] : make_float2(acc[g][q], 0.0f);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (l == 0) red[w][g * kSums + q] = v;
+                    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+                    if (lane == 0) red[wid][g * kSums + q] = v;
                 }
+            }
             __syncthreads();
-            if (tid < kGroup * kSums) {
-                int g = tid / kSums;
-                if (g0 + g < k) {
-                    double v = 0.0;
-                    for (int ww = 0; ww < kThreads / 32; ww++) v += red[ww][tid];
-                    slot[((size_t)blockIdx.x * k + g0 + g) * kSums + (tid % kSums)] = v;
-                }
+            if (tid < kGroup * kSums && g0 + tid / kSums < k) {
+                float2 v = make_float2(0.0f, 0.0f);
+                if (act[tid / kSums])
+                    for (int ww = 0; ww < kThreads / 32; ww++) v = df_add(v, red[ww][tid]);
+                slot[(size_t)blockIdx.x * P + g0 * kSums + tid] = v;
             }
             __syncthreads();
         }
@@ -247,15 +301,25 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
             return;
         }
-        // every CTA: reduce all partials (fixed order) and update the seeds
-        if (tid < k && S[tid].phase != 2) {
-            double sums[kSums];
-            for (int q = 0; q < kSums; q++) sums[q] = 0.0;
-            for (unsigned b = 0; b < G; b++)
-                for (int q = 0; q < kSums; q++)
-                    sums[q] += __ldcg(slot + ((size_t)b * k + tid) * kSums + q);
-            update(S[tid], sums, max_iter, tol);
+        // every CTA reduces all CTA partials, all threads, in one fixed order
+        for (int u0 = 0; u0 < P; u0 += kThreads) {
+            const int nu = (P - u0) < kThreads ? (P - u0) : kThreads;
+            const int T = kThreads / nu;                // threads per sum
+            const int u = tid % nu, v = tid / nu;
+            float2 a = make_float2(0.0f, 0.0f);
+            if (v < T && S[(u0 + u) / kSums].phase != 2)
+                for (unsigned b = v; b < G; b += T)
+                    a = df_add(a, __ldcg(slot + (size_t)b * P + u0 + u));
+            part[tid] = a;
+            __syncthreads();
+            if (tid < nu) {
+                float2 t = make_float2(0.0f, 0.0f);
+                for (int vv = 0; vv < T; vv++) t = df_add(t, part[vv * nu + tid]);
+                sums[u0 + tid] = (double)t.x + (double)t.y;
+            }
+            __syncthreads();
         }
+        if (tid < k && S[tid].phase != 2) update(S[tid], sums + tid * kSums, max_iter, tol);
         if (tid == 0) active_any = 0;
         __syncthreads();
         if (tid < k && S[tid].phase != 2) active_any = 1;
@@ -285,7 +349,7 @@ int refine_grid(int64_t R) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refine, kThreads, 0);
     if (occ < 1) occ = 1;
     int64_t cap = (int64_t)sms * occ;
-    int64_t want = (R + kThreads * 4 - 1) / (kThreads * 4);
+    int64_t want = (R + 2047) / 2048;                  // ~8 rings per thread per seed
     if (want < 1) want = 1;
     return (int)(want < cap ? want : cap);
 }
@@ -296,7 +360,7 @@ size_t refine_workspace_bytes(int64_t R, int k) {
     if (R < 0 || k < 1 || k > kMaxSeeds) return 0;
     int G = refine_grid(R);
     if (G <= 0) return 0;
-    return 256 + align256((size_t)2 * G * k * kSums * sizeof(double));
+    return 256 + align256((size_t)2 * G * k * kSums * sizeof(float2));
 }
 
 cudaError_t launch_refine(const cc_rings &rings, const double *seeds, int k,
@@ -310,7 +374,7 @@ cudaError_t launch_refine(const cc_rings &rings, const double *seeds, int k,
     if (e != cudaSuccess) return e;
     int G = refine_grid(rings.count);
     unsigned *bar = reinterpret_cast<unsigned *>(ws);
-    double *partials = reinterpret_cast<double *>(ws + 256);
+    float2 *partials = reinterpret_cast<float2 *>(ws + 256);
     int64_t R = rings.count;
     float kc = p.k_cut;
     int mi = p.max_iter;

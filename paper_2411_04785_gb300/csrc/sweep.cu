@@ -19,17 +19,21 @@
 // Gaussian is exp2(-t^2) with t = theta k - eta k, k = sqrt(log2(e)/2)/deta,
 // on the MUFU ex2 unit.
 //
-// Layout: rings are repacked once per call into 32-byte records (axis', k,
-// b, b2) in the workspace and streamed through shared memory by
-// cp.async.bulk (TMA bulk copy) into a 4-stage mbarrier ring; every CTA owns
-// 256 x D directions held in registers (D per thread, coalesced loads and
-// stores) and a contiguous range of ring tiles.  Per direction the FP32 sum
+// Layout: rings are repacked once per call into 48-byte records (axis', k,
+// -b, -b2, duplicated where they meet a direction pair) in the workspace and
+// streamed through shared memory by cp.async.bulk (TMA bulk copy) into a
+// 4-stage mbarrier ring; every CTA owns 256 x D directions held in registers
+// (D per thread, coalesced loads and stores) and a contiguous range of ring
+// tiles.  Directions are processed in pairs with the packed FP32x2 FMA / add
+// / multiply of sm_100+ (one instruction issue per two lanes of FP32 work),
+// which leaves the FP32 pipe, not instruction issue, as the limit.  Per
+// direction the FP32 sum
 // of a 128-ring tile is added into a Kahan-compensated accumulator.  When the
 // grid has too few direction blocks to fill 152 SMs the rings are split over
 // CTAs and the partial maps are summed in a fixed order (deterministic).
 #include <float.h>
 
-#include "cc_internal.cuh"
+#include "cc_math.cuh"
 
 namespace cc {
 namespace {
@@ -41,30 +45,8 @@ constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr float kGaussK = 0.84932180028801907f;   // sqrt(log2(e) / 2)
 constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
 
-__device__ __forceinline__ float acos_q(float s) {
-    // Q(s) = acos(1 - s)/sqrt(s) on [0, 1], coefficients from fit_acos.py
-    float p = 1.4414361e-03f;
-    p = fmaf(p, s, -2.8447455e-03f);
-    p = fmaf(p, s, 4.6071224e-03f);
-    p = fmaf(p, s, 5.2066805e-04f);
-    p = fmaf(p, s, 8.6035002e-03f);
-    p = fmaf(p, s, 2.6394552e-02f);
-    p = fmaf(p, s, 1.1786042e-01f);
-    p = fmaf(p, s, 1.4142133e+00f);
-    return p;
-}
-
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+// Coefficients of acos_q (cc_math.cuh) as FP32x2 pairs.
+__device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -149,7 +131,7 @@ __global__ void k_pack_rings(const float *__restrict__ ax, const float *__restri
                              int64_t R, int64_t rpad, RingRec *__restrict__ rec) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rpad;
          i += (int64_t)gridDim.x * blockDim.x) {
-        RingRec r = {0.f, 0.f, 0.f, 0.f, kNullB, kNullB, 0.f, 0.f};
+        RingRec r = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, 0.f, 0.f};
         if (i < R && (valid == nullptr || valid[i])) {
             float a0 = ax[i], a1 = ay[i], a2 = az[i], e = eta[i], de = deta[i];
             bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(e) &&
@@ -161,7 +143,8 @@ __global__ void k_pack_rings(const float *__restrict__ ax, const float *__restri
                     a0 = -a0; a1 = -a1; a2 = -a2;
                     float t = b; b = b2; b2 = t;
                 }
-                r = {a0 * kInvSqrt2, a1 * kInvSqrt2, a2 * kInvSqrt2, k, b, b2, 0.f, 0.f};
+                float s0 = a0 * kInvSqrt2, s1 = a1 * kInvSqrt2, s2 = a2 * kInvSqrt2;
+                r = {s0, s0, s1, s1, s2, s2, k, k, -b, -b2, 0.f, 0.f};
             }
         }
         rec[i] = r;
@@ -177,6 +160,8 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
         const float *__restrict__ cx, const float *__restrict__ cy,
         const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
         BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
+    static_assert(D % 2 == 0, "directions are processed in FP32x2 pairs");
+    constexpr int DP = D / 2;
     __shared__ __align__(128) RingRec tile[kStages][kTile];
     __shared__ __align__(8) unsigned long long full[kStages];
     __shared__ int abort_flag;
@@ -186,15 +171,17 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
     const int64_t split = blockIdx.x / ndb;
     const int64_t j0 = db * (int64_t)(kThreads * D) + tid;
 
-    float px[D], py[D], pz[D], acc[D], sum[D], comp[D];
+    // direction d of this thread: j0 + d * kThreads; pair p holds d = 2p, 2p+1
+    float2 ncx[DP], ncy[DP], ncz[DP], acc[DP], sum[DP], comp[DP];
 #pragma unroll
-    for (int d = 0; d < D; d++) {
-        int64_t j = j0 + (int64_t)d * kThreads;
-        int64_t jj = j < M ? j : M - 1;
-        px[d] = __ldg(cx + jj) * kInvSqrt2;
-        py[d] = __ldg(cy + jj) * kInvSqrt2;
-        pz[d] = __ldg(cz + jj) * kInvSqrt2;
-        acc[d] = sum[d] = comp[d] = 0.0f;
+    for (int q = 0; q < DP; q++) {
+        int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        ja = ja < M ? ja : M - 1;
+        jb = jb < M ? jb : M - 1;
+        ncx[q] = make_float2(-__ldg(cx + ja) * kInvSqrt2, -__ldg(cx + jb) * kInvSqrt2);
+        ncy[q] = make_float2(-__ldg(cy + ja) * kInvSqrt2, -__ldg(cy + jb) * kInvSqrt2);
+        ncz[q] = make_float2(-__ldg(cz + ja) * kInvSqrt2, -__ldg(cz + jb) * kInvSqrt2);
+        acc[q] = sum[q] = comp[q] = make_float2(0.0f, 0.0f);
     }
 
     const RingRec *src = rec + split * tiles * kTile;
@@ -209,6 +196,7 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
             tma_bulk_load(tile[s], src + (int64_t)s * kTile, kTile * sizeof(RingRec), &full[s]);
     }
 
+    const float2 one2 = pair(1.0f), m1 = pair(-1.0f), two2 = pair(2.0f);
     for (int64_t t = 0; t < tiles; t++) {
         const int stage = (int)(t % kStages);
         const unsigned parity = (unsigned)((t / kStages) & 1);
@@ -218,22 +206,40 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
             const RingRec *T = tile[stage];
 #pragma unroll 2
             for (int r = 0; r < kTile; r++) {
-                const float4 A = *reinterpret_cast<const float4 *>(&T[r].ax);
-                const float2 B = *reinterpret_cast<const float2 *>(&T[r].b);
+                const float4 P0 = *reinterpret_cast<const float4 *>(&T[r].ax);
+                const float4 P1 = *reinterpret_cast<const float4 *>(&T[r].az);
+                const float2 P2 = *reinterpret_cast<const float2 *>(&T[r].nb);
+                const float2 ax2 = make_float2(P0.x, P0.y), ay2 = make_float2(P0.z, P0.w);
+                const float2 az2 = make_float2(P1.x, P1.y), k2 = make_float2(P1.z, P1.w);
 #pragma unroll
-                for (int d = 0; d < D; d++) {
-                    float dx = A.x - px[d], dy = A.y - py[d], dz = A.z - pz[d];
-                    float h = dx * dx;
-                    h = fmaf(dy, dy, h);
-                    h = fmaf(dz, dz, h);
-                    float s = fminf(h, 2.0f - h);
-                    float th = sqrt_approx(s) * acos_q(s);
-                    float bs = (h <= 1.0f) ? B.x : B.y;
-                    float u = fmaf(th, A.w, -bs);
-                    float u2 = u * u;
-                    float e = ex2_approx(-u2);
-                    if (KCUT) e = (u2 > kc2) ? 0.0f : e;
-                    acc[d] += e;
+                for (int q = 0; q < DP; q++) {
+                    float2 dx = __fadd2_rn(ax2, ncx[q]);
+                    float2 dy = __fadd2_rn(ay2, ncy[q]);
+                    float2 dz = __fadd2_rn(az2, ncz[q]);
+                    float2 h = __fmul2_rn(dx, dx);
+                    h = __ffma2_rn(dy, dy, h);
+                    h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
+                    float2 g = __ffma2_rn(h, m1, two2);             // 2 - h
+                    float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+                    float2 p = pair(1.4414361e-03f);                // acos_q, FP32x2
+                    p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
+                    p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
+                    p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
+                    p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
+                    p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
+                    p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
+                    p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+                    float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
+                    float2 th = __fmul2_rn(rt, p);
+                    float2 nbs = make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
+                    float2 u = __ffma2_rn(th, k2, nbs);
+                    float2 u2 = __fmul2_rn(u, u);
+                    float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+                    if (KCUT) {
+                        e.x = u2.x > kc2 ? 0.0f : e.x;
+                        e.y = u2.y > kc2 ? 0.0f : e.y;
+                    }
+                    acc[q] = __fadd2_rn(acc[q], e);
                 }
             }
         }
@@ -243,14 +249,15 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
             tma_bulk_load(tile[stage], src + (t + kStages) * kTile, kTile * sizeof(RingRec),
                           &full[stage]);
 #pragma unroll
-        for (int d = 0; d < D; d++) {   // Kahan-compensated tile sums
-            float y = acc[d] - comp[d];
-            float tt = sum[d] + y;
-            comp[d] = (tt - sum[d]) - y;
-            sum[d] = tt;
-            acc[d] = 0.0f;
+        for (int q = 0; q < DP; q++) {   // Kahan-compensated tile sums
+            float2 y = make_float2(acc[q].x - comp[q].x, acc[q].y - comp[q].y);
+            float2 tt = make_float2(sum[q].x + y.x, sum[q].y + y.y);
+            comp[q] = make_float2((tt.x - sum[q].x) - y.x, (tt.y - sum[q].y) - y.y);
+            sum[q] = tt;
+            acc[q] = make_float2(0.0f, 0.0f);
         }
     }
+    (void)one2;
     if (abort_flag) {
         if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
         return;
@@ -259,12 +266,16 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
     float bv = -__builtin_huge_valf();
     int bj = INT32_MAX;
 #pragma unroll
-    for (int d = 0; d < D; d++) {
-        int64_t j = j0 + (int64_t)d * kThreads;
-        float v = sum[d] - comp[d];
-        if (j < M) {
-            out[split * M + j] = v;
-            better(bv, bj, v, (int)j);
+    for (int q = 0; q < DP; q++) {
+        const int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
+        if (ja < M) {
+            out[split * M + ja] = va;
+            better(bv, bj, va, (int)ja);
+        }
+        if (jb < M) {
+            out[split * M + jb] = vb;
+            better(bv, bj, vb, (int)jb);
         }
     }
     if (bb != nullptr) {
@@ -363,8 +374,7 @@ void *pick_sweep(int d, bool kcut) {
     switch (d) {
         case 8: return kcut ? sweep_fn<8, true>() : sweep_fn<8, false>();
         case 4: return kcut ? sweep_fn<4, true>() : sweep_fn<4, false>();
-        case 2: return kcut ? sweep_fn<2, true>() : sweep_fn<2, false>();
-        default: return kcut ? sweep_fn<1, true>() : sweep_fn<1, false>();
+        default: return kcut ? sweep_fn<2, true>() : sweep_fn<2, false>();
     }
 }
 
@@ -381,9 +391,9 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
     const int64_t ring_tiles = R > 0 ? (R + kTile - 1) / kTile : 1;
     const int64_t max_split = ring_tiles < 256 ? ring_tiles : 256;
 
-    int d = 1;
+    int d = 2;
     int64_t conc = 0;
-    for (int cand : {8, 4, 2, 1}) {
+    for (int cand : {4, 8, 2}) {
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_sweep(cand, kcut), kThreads, 0);
         if (occ < 1) occ = 1;
@@ -395,7 +405,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
     }
     const int64_t ndb = (M + (int64_t)kThreads * d - 1) / ((int64_t)kThreads * d);
 
-    // ring splits: enough CTAs to fill the machine, whole waves (>= 90 % of
+    // ring splits: enough CTAs to fill the machine, whole waves (>= 97 % of
     // the last wave busy) when possible
     int64_t best_ns = 1;
     double best_eff = -1.0;
@@ -405,7 +415,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
         double eff = waves / std::ceil(waves);
         if (U < conc) eff = waves;      // machine not full
         if (eff > best_eff + 1e-9) { best_eff = eff; best_ns = ns; }
-        if (U >= conc && eff >= 0.9) break;
+        if (U >= conc && eff >= 0.97) break;
     }
     const int64_t tiles = (ring_tiles + best_ns - 1) / best_ns;
 
