@@ -218,6 +218,66 @@ cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k,
                          double *out_dirs, void *stream);
 
 /*
+ * Learned ring filter (an extension beyond the paper: the paper's imaging
+ * has no learned part).  An MLP 16 -> 128 -> 128 -> 128 -> 2 with ReLU scores
+ * each ring before the sweep: out[i] = (z, v), z the source/background logit
+ * and v the log of a predicted ring width.  Weights, layer inputs and
+ * backward signals are BF16 (tensor cores, FP32 accumulation); biases,
+ * gradients and the Adam state are FP32.  Parameters are one flat FP32 vector
+ * of CC_MLP_PARAMS values, W1[128][16] b1[128] W2[128][128] b2[128]
+ * W3[128][128] b3[128] W4[2][128] b4[2], with a BF16 copy (uint16_t bit
+ * patterns) that the products read.  Loss per ring, averaged over the batch
+ * rows (rows with weight 0 contribute 0):
+ *   BCE(z, is_source) + is_source (v + residual^2 exp(-2 v) / 2),
+ * the residual being the ring's angular residual to the true source.
+ */
+#define CC_MLP_FEATURES 16
+#define CC_MLP_PARAMS 35458
+#define CC_MLP_MAX_BATCH 65536
+
+/* 16 BF16 features per ring (row-major [count][16]) from its event and its
+ * ring (valid, perm, eta, deta, az): eta/pi, cos eta, sin eta, log(deta)/4,
+ * [k=2], [k=3], [k=4], log(E0/500 keV), E1/E0, E_2nd/E0, E_last/E0,
+ * log(|x1-x2|/5 cm), a_z, z1/30 cm, z2/30 cm, sqrt(2) sigma_pos/|x1-x2|/deta.
+ * Invalid rings get zeros.  rings->count == ev->count. */
+cc_status cc_ring_features(const cc_events *ev, const cc_rings *rings,
+                           const cc_params *p, uint16_t *features, void *stream);
+
+/* Workspace bytes of cc_mlp_forward / cc_mlp_grad for `rows` rows. */
+size_t cc_mlp_workspace_bytes(int64_t rows);
+
+/* out [rows][2] = MLP(features); any number of rows (processed in chunks). */
+cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
+                         const uint16_t *features, int64_t rows, float *out,
+                         void *workspace, size_t ws_bytes, void *stream);
+
+/* Loss (device [1]) and its gradient (device [CC_MLP_PARAMS]) for one batch
+ * of 1..CC_MLP_MAX_BATCH rows: is_source [rows] u8, residual [rows] f32 (rad),
+ * weight [rows] u8 (0 excludes a row).  Deterministic (fixed-order sums). */
+cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16,
+                      const uint16_t *features, const uint8_t *is_source,
+                      const float *residual, const uint8_t *weight,
+                      int64_t rows, float *grad, float *loss, void *workspace,
+                      size_t ws_bytes, void *stream);
+
+/* One Adam step (step >= 1) on params with moments m, v; refreshes the BF16
+ * copy. */
+cc_status cc_mlp_adam(float *params, float *m, float *v, const float *grad,
+                      uint16_t *params_bf16, int32_t step, float lr,
+                      float beta1, float beta2, float eps, void *stream);
+
+/* params_bf16 = bf16(params). */
+cc_status cc_mlp_params_to_bf16(const float *params, uint16_t *params_bf16,
+                                void *stream);
+
+/* Filter rings in place with the MLP output: a valid ring stays valid when
+ * sigmoid(z) >= tau, and its width becomes clamp(exp(v), deta_min,
+ * deta_max). */
+cc_status cc_mlp_apply_filter(const float *out, const cc_rings *rings,
+                              float tau, float deta_min, float deta_max,
+                              void *stream);
+
+/*
  * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
  * counted per stage; when tracing is enabled each launch is also bracketed by
  * two CUDA events recorded on the launching stream, and cc_trace_read()
@@ -233,7 +293,8 @@ typedef enum {
     CC_STAGE_GATHER = 5,  /* grid gather */
     CC_STAGE_REFINE = 6,  /* Gauss-Newton refinement */
     CC_STAGE_GRID = 7,    /* grid generation */
-    CC_STAGE_COUNT = 8
+    CC_STAGE_MLP = 8,     /* learned ring filter (features, MLP, training, filter) */
+    CC_STAGE_COUNT = 9
 } cc_stage;
 
 typedef struct {

@@ -5,4 +5,5 @@ seeds, Gauss-Newton refinement - CUDA kernels for sm_103a behind the C ABI of
 from .api import (CCError, Localizer, Params, default_params, empty_rings,  # noqa: F401
                   grid_fibonacci, grid_gather, grid_healpix_ring, lib,
                   localize, localize_static, localize_workspace_bytes, refine, refine_workspace_bytes,
-                  rings_from_events, trace_enable, trace_read)
+                  rings_from_events, trace_enable, trace_read,
+                  RingFilter, ring_features, ring_residuals)

@@ -48,7 +48,7 @@ class cc_stage_time(C.Structure):
     _fields_ = [("launches", C.c_int64), ("ms", C.c_double)]
 
 
-STAGES = ("recon", "pack", "sweep", "reduce", "select", "gather", "refine", "grid")
+STAGES = ("recon", "pack", "sweep", "reduce", "select", "gather", "refine", "grid", "mlp")
 
 
 class CCError(RuntimeError):
@@ -96,6 +96,23 @@ def lib() -> C.CDLL:
         L.cc_localize_static.argtypes = [C.POINTER(cc_rings), C.POINTER(cc_grid),
                                          C.POINTER(cc_params), _P, _P, _P, _P, _P]
         L.cc_localize_static.restype = S
+        L.cc_ring_features.argtypes = [C.POINTER(cc_events), C.POINTER(cc_rings),
+                                       C.POINTER(cc_params), _P, _P]
+        L.cc_ring_features.restype = S
+        L.cc_mlp_workspace_bytes.argtypes = [C.c_int64]
+        L.cc_mlp_workspace_bytes.restype = C.c_size_t
+        L.cc_mlp_forward.argtypes = [_P, _P, _P, C.c_int64, _P, _P, C.c_size_t, _P]
+        L.cc_mlp_forward.restype = S
+        L.cc_mlp_grad.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]
+        L.cc_mlp_grad.restype = S
+        L.cc_mlp_adam.argtypes = [_P, _P, _P, _P, _P, C.c_int32, C.c_float, C.c_float,
+                                  C.c_float, C.c_float, _P]
+        L.cc_mlp_adam.restype = S
+        L.cc_mlp_params_to_bf16.argtypes = [_P, _P, _P]
+        L.cc_mlp_params_to_bf16.restype = S
+        L.cc_mlp_apply_filter.argtypes = [_P, C.POINTER(cc_rings), C.c_float, C.c_float,
+                                          C.c_float, _P]
+        L.cc_mlp_apply_filter.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -400,3 +417,125 @@ def trace_read(reset: bool = False) -> dict:
     arr = (cc_stage_time * len(STAGES))()
     _check("cc_trace_read", lib().cc_trace_read(arr, len(STAGES), 1 if reset else 0))
     return {n: {"launches": int(a.launches), "ms": float(a.ms)} for n, a in zip(STAGES, arr)}
+
+
+# --------------------------------------------------------------------------
+# learned ring filter
+# --------------------------------------------------------------------------
+MLP_FEATURES = 16
+MLP_PARAMS = 35458
+MLP_MAX_BATCH = 65536
+MLP_SIZES = ((128, 16), (128, 128), (128, 128), (2, 128))
+
+
+def ring_features(n, x, y, z, e, rings: dict, params: Params | None = None, out=None,
+                  stream=None):
+    """[N, 16] BF16 features of the rings of an event set (cc_ring_features)."""
+    params = params or Params()
+    N = n.numel()
+    stride = x.shape[1]
+    ev = cc_events(_ptr(n), _ptr(x), _ptr(y), _ptr(z), _ptr(e), N, stride)
+    rs = _rings_struct(rings)
+    out = out if out is not None else torch.empty((N, MLP_FEATURES), dtype=torch.bfloat16,
+                                                  device=n.device)
+    pc = params.c()
+    _check("cc_ring_features", lib().cc_ring_features(C.byref(ev), C.byref(rs), C.byref(pc),
+                                                      _ptr(out), _stream(stream)))
+    return out
+
+
+class RingFilter:
+    """The MLP of the learned ring filter with its FP32 parameters, BF16 copy
+    and Adam state on the device; every product runs in libcompton.so."""
+
+    def __init__(self, device, seed: int = 0, params=None):
+        import numpy as np
+        self.dev = torch.device(device)
+        if params is None:
+            rng = np.random.default_rng(seed)
+            parts = []
+            for o, i in MLP_SIZES:        # He-uniform weights, zero biases
+                lim = math.sqrt(6.0 / i)
+                parts += [rng.uniform(-lim, lim, o * i), np.zeros(o)]
+            params = np.concatenate(parts).astype(np.float32)
+            params[-1] = math.log(0.3)    # initial predicted width ~17 deg
+        self.p = torch.as_tensor(params, dtype=torch.float32).to(self.dev).contiguous()
+        assert self.p.numel() == MLP_PARAMS
+        self.wb = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=self.dev)
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.grad_buf = torch.zeros_like(self.p)
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        self.step = 0
+        self._ws = None
+        _check("cc_mlp_params_to_bf16", lib().cc_mlp_params_to_bf16(
+            _ptr(self.p), _ptr(self.wb), _stream(None)))
+
+    def _workspace(self, rows):
+        need = max(int(lib().cc_mlp_workspace_bytes(rows)), 256)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.dev)
+        return self._ws
+
+    def forward(self, feats, out=None, stream=None):
+        R = feats.shape[0]
+        out = out if out is not None else torch.empty((R, 2), dtype=torch.float32,
+                                                      device=self.dev)
+        ws = self._workspace(R)
+        _check("cc_mlp_forward", lib().cc_mlp_forward(
+            _ptr(self.p), _ptr(self.wb), _ptr(feats), R, _ptr(out), _ptr(ws), ws.numel(),
+            _stream(stream)))
+        return out
+
+    def grad(self, feats, is_source, residual, weight, stream=None):
+        """Loss and gradient of one batch (<= MLP_MAX_BATCH rows)."""
+        B = feats.shape[0]
+        ws = self._workspace(B)
+        _check("cc_mlp_grad", lib().cc_mlp_grad(
+            _ptr(self.p), _ptr(self.wb), _ptr(feats), _ptr(is_source), _ptr(residual),
+            _ptr(weight), B, _ptr(self.grad_buf), _ptr(self.loss_buf), _ptr(ws), ws.numel(),
+            _stream(stream)))
+        return self.loss_buf, self.grad_buf
+
+    def adam(self, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        _check("cc_mlp_adam", lib().cc_mlp_adam(
+            _ptr(self.p), _ptr(self.m), _ptr(self.v), _ptr(self.grad_buf), _ptr(self.wb),
+            self.step, lr, beta1, beta2, eps, _stream(stream)))
+
+    def train(self, feats, is_source, residual, weight, epochs=4, batch=MLP_MAX_BATCH,
+              lr=2e-3, seed=0):
+        """Adam over shuffled batches; returns the mean loss of each epoch."""
+        R = feats.shape[0]
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        losses = []
+        for _ in range(epochs):
+            order = torch.randperm(R, generator=g).to(self.dev)
+            tot = torch.zeros(1, device=self.dev)
+            nb = 0
+            for b0 in range(0, R, batch):
+                ix = order[b0:b0 + batch]
+                loss, _ = self.grad(feats[ix].contiguous(), is_source[ix].contiguous(),
+                                    residual[ix].contiguous(), weight[ix].contiguous())
+                tot += loss
+                self.adam(lr)
+                nb += 1
+            losses.append(float(tot.item()) / nb)
+        return losses
+
+    def apply(self, rings: dict, out, tau: float, deta_min: float, deta_max: float,
+              stream=None):
+        """Filter rings in place: keep sigmoid(z) >= tau, width exp(v)."""
+        rs = _rings_struct(rings)
+        _check("cc_mlp_apply_filter", lib().cc_mlp_apply_filter(
+            _ptr(out), C.byref(rs), tau, deta_min, deta_max, _stream(stream)))
+
+
+def ring_residuals(rings: dict, sources):
+    """Angle between each ring's axis and its true source minus eta (training
+    labels; sources [N, 3] device float)."""
+    a = torch.stack([rings["ax"], rings["ay"], rings["az"]], 1).double()
+    s = sources.double()
+    cr = torch.linalg.cross(a, s, dim=1).norm(dim=1)
+    th = torch.atan2(cr, (a * s).sum(1))
+    return (th - rings["eta"].double()).float().contiguous()

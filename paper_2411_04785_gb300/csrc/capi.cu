@@ -193,3 +193,103 @@ cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k, dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned ring filter
+// ---------------------------------------------------------------------------
+extern "C" {
+
+cc_status cc_ring_features(const cc_events *ev, const cc_rings *rings, const cc_params *p,
+                           uint16_t *features, void *stream) {
+    g_err[0] = 0;
+    cc_status st = check_params(p);
+    if (st != CC_OK) return st;
+    if (!ev || !rings || !features) return fail(CC_EINVAL, "events/rings/features is NULL");
+    if (ev->count < 0 || ev->stride < ev->count || rings->count != ev->count)
+        return fail(CC_EINVAL, "bad counts (need 0 <= count <= stride, rings->count == count)");
+    if (ev->count == 0) return CC_OK;
+    if (!ev->n || !ev->x || !ev->y || !ev->z || !ev->e || !rings->az || !rings->eta ||
+        !rings->deta || !rings->valid || !rings->perm)
+        return fail(CC_EINVAL, "event and ring arrays must be non-NULL");
+    cudaError_t e = mlp_features(*ev, *rings, p->sigma_pos_cm, features, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ring_features launch");
+    return CC_OK;
+}
+
+size_t cc_mlp_workspace_bytes(int64_t rows) {
+    if (rows < 0) return 0;
+    return mlp_workspace_bytes(rows);
+}
+
+cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
+                         const uint16_t *features, int64_t rows, float *out, void *workspace,
+                         size_t ws_bytes, void *stream) {
+    g_err[0] = 0;
+    if (rows < 0) return fail(CC_EINVAL, "rows < 0");
+    if (rows == 0) return CC_OK;
+    if (!params || !params_bf16 || !features || !out)
+        return fail(CC_EINVAL, "params/features/out must be non-NULL");
+    if (!workspace || !aligned(workspace, 256))
+        return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    size_t need = mlp_workspace_bytes(rows);
+    if (ws_bytes < need) return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = mlp_forward(params, params_bf16, features, rows, out, (char *)workspace,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_forward launch");
+    return CC_OK;
+}
+
+cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16, const uint16_t *features,
+                      const uint8_t *is_source, const float *residual, const uint8_t *weight,
+                      int64_t rows, float *grad, float *loss, void *workspace, size_t ws_bytes,
+                      void *stream) {
+    g_err[0] = 0;
+    if (rows < 1 || rows > CC_MLP_MAX_BATCH)
+        return fail(CC_EINVAL, "rows must be in 1..%d", CC_MLP_MAX_BATCH);
+    if (!params || !params_bf16 || !features || !is_source || !residual || !weight || !grad ||
+        !loss)
+        return fail(CC_EINVAL, "arguments must be non-NULL");
+    if (!workspace || !aligned(workspace, 256))
+        return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+    size_t need = mlp_workspace_bytes(rows);
+    if (ws_bytes < need) return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+    cudaError_t e = mlp_grad(params, params_bf16, features, is_source, residual, weight, rows,
+                             grad, loss, (char *)workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_grad launch");
+    return CC_OK;
+}
+
+cc_status cc_mlp_adam(float *params, float *m, float *v, const float *grad, uint16_t *params_bf16,
+                      int32_t step, float lr, float beta1, float beta2, float eps, void *stream) {
+    g_err[0] = 0;
+    if (!params || !m || !v || !grad || !params_bf16) return fail(CC_EINVAL, "NULL argument");
+    if (step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(CC_EINVAL, "need step >= 1, lr > 0, 0 <= beta < 1, eps > 0");
+    cudaError_t e = mlp_adam(params, m, v, grad, params_bf16, step, lr, beta1, beta2, eps,
+                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_adam launch");
+    return CC_OK;
+}
+
+cc_status cc_mlp_params_to_bf16(const float *params, uint16_t *params_bf16, void *stream) {
+    g_err[0] = 0;
+    if (!params || !params_bf16) return fail(CC_EINVAL, "NULL argument");
+    cudaError_t e = mlp_params_to_bf16(params, params_bf16, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_params_to_bf16 launch");
+    return CC_OK;
+}
+
+cc_status cc_mlp_apply_filter(const float *out, const cc_rings *rings, float tau, float deta_min,
+                              float deta_max, void *stream) {
+    g_err[0] = 0;
+    if (!out || !rings || rings->count < 0) return fail(CC_EINVAL, "bad arguments");
+    if (rings->count > 0 && (!rings->valid || !rings->deta))
+        return fail(CC_EINVAL, "rings->valid and rings->deta must be non-NULL");
+    if (!(deta_min > 0.0f) || !(deta_max >= deta_min)) return fail(CC_EINVAL, "bad deta clamp");
+    cudaError_t e = mlp_apply_filter(out, *rings, tau, deta_min, deta_max, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_apply_filter launch");
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -95,6 +95,23 @@ cudaError_t launch_grid_gather(const cc_grid &g, const int32_t *idx, int k,
                                double *out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// learned ring filter - mlp.cu
+// ---------------------------------------------------------------------------
+size_t mlp_workspace_bytes(int64_t rows);
+cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, uint16_t *F,
+                         cudaStream_t s);
+cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
+                        float *out, char *ws, cudaStream_t s);
+cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
+                     const uint8_t *y, const float *res, const uint8_t *wv, int64_t B,
+                     float *grad, float *loss, char *ws, cudaStream_t s);
+cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, uint16_t *wb, int32_t t,
+                     float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t mlp_params_to_bf16(const float *p, uint16_t *wb, cudaStream_t s);
+cudaError_t mlp_apply_filter(const float *out, const cc_rings &r, float tau, float dmin,
+                             float dmax, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // stage tracing - trace.cu.  Construct before a launch, destroy after it.
 // ---------------------------------------------------------------------------
 class TraceScope {

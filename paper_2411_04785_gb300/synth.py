@@ -282,3 +282,27 @@ def tile_events(ev: dict, copies: int) -> dict:
     for k in ("x", "y", "z", "e"):
         out[k] = np.ascontiguousarray(np.tile(ev[k], (1, copies)))
     return out
+
+
+def training_events(n_events: int, seed: int, bkg_ratio: float = 3.0, chunk: int = 20000):
+    """Training data of the learned ring filter: chunks of simulated events,
+    each chunk with its own random source direction (so that no direction is
+    learned), background bkg_ratio times the source.  Returns the event dict
+    of simulate_events over all chunks plus 'sources' [N, 3] (the true source
+    of each event's chunk; meaningful for source events)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for c in range((n_events + chunk - 1) // chunk):
+        m = min(chunk, n_events - c * chunk)
+        s = random_units(rng, 1)[0]
+        n_src = int(round(m / (1.0 + bkg_ratio)))
+        ev = simulate_events(n_src=n_src, n_bkg=m - n_src, seed=seed * 100003 + c, source=s)
+        ev["sources"] = np.repeat(s[None, :], m, axis=0)
+        parts.append(ev)
+    out = {"n": np.concatenate([p["n"] for p in parts]),
+           "is_source": np.concatenate([p["is_source"] for p in parts]),
+           "sources": np.concatenate([p["sources"] for p in parts]),
+           "order": np.concatenate([p["order"] for p in parts])}
+    for k in ("x", "y", "z", "e"):
+        out[k] = np.ascontiguousarray(np.concatenate([p[k] for p in parts], axis=1))
+    return out
