@@ -175,6 +175,30 @@ cc_status cc_localize_static(const cc_rings *rings, const cc_grid *grid,
                              const cc_params *p, float *map, int32_t *argmax,
                              int32_t *seeds, int32_t *status, void *stream);
 
+/*
+ * Several bursts in one call (continuous batching of a serving loop): the
+ * sweep of all of them runs in one persistent launch whose CTAs take work
+ * units of every burst from a shared counter; each burst keeps its own plan,
+ * rings, map and outputs, and its results do not depend on the other bursts
+ * of the batch (the same burst gives the same map alone or in any batch).
+ * rings [n] is a host array of ring structs; maps, argmax, seeds (may be
+ * NULL), status (may be NULL) and workspaces are host arrays of n device
+ * pointers; ws_bytes [n] host.  Workspace i needs
+ * cc_localize_batch_workspace_bytes(rings[i].count, grid->count, p) bytes.
+ * 1 <= n <= CC_BATCH_MAX.
+ */
+#define CC_BATCH_MAX 64
+
+size_t cc_localize_batch_workspace_bytes(int64_t rings, int64_t dirs,
+                                         const cc_params *p);
+
+cc_status cc_localize_batch(int32_t n, const cc_rings *rings,
+                            const cc_grid *grid, const cc_params *p,
+                            float *const *maps, int32_t *const *argmax,
+                            int32_t *const *seeds, int32_t *const *status,
+                            void *const *workspaces, const size_t *ws_bytes,
+                            void *stream);
+
 /* Workspace bytes cc_refine needs for `rings` rings and `k` seeds. */
 size_t cc_refine_workspace_bytes(int64_t rings, int32_t k);
 

@@ -113,6 +113,11 @@ def lib() -> C.CDLL:
         L.cc_mlp_apply_filter.argtypes = [_P, C.POINTER(cc_rings), C.c_float, C.c_float,
                                           C.c_float, _P]
         L.cc_mlp_apply_filter.restype = S
+        L.cc_localize_batch_workspace_bytes.argtypes = [C.c_int64, C.c_int64, C.POINTER(cc_params)]
+        L.cc_localize_batch_workspace_bytes.restype = C.c_size_t
+        L.cc_localize_batch.argtypes = [C.c_int32, C.POINTER(cc_rings), C.POINTER(cc_grid),
+                                        C.POINTER(cc_params), _P, _P, _P, _P, _P, _P, _P]
+        L.cc_localize_batch.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -477,11 +482,13 @@ class RingFilter:
             self._ws = torch.empty(need, dtype=torch.uint8, device=self.dev)
         return self._ws
 
-    def forward(self, feats, out=None, stream=None):
+    def forward(self, feats, out=None, stream=None, workspace=None):
+        """MLP outputs [R, 2].  Calls that may run concurrently (other streams)
+        must each pass their own workspace (mlp_workspace_bytes)."""
         R = feats.shape[0]
         out = out if out is not None else torch.empty((R, 2), dtype=torch.float32,
                                                       device=self.dev)
-        ws = self._workspace(R)
+        ws = workspace if workspace is not None else self._workspace(R)
         _check("cc_mlp_forward", lib().cc_mlp_forward(
             _ptr(self.p), _ptr(self.wb), _ptr(feats), R, _ptr(out), _ptr(ws), ws.numel(),
             _stream(stream)))
@@ -529,6 +536,10 @@ class RingFilter:
         rs = _rings_struct(rings)
         _check("cc_mlp_apply_filter", lib().cc_mlp_apply_filter(
             _ptr(out), C.byref(rs), tau, deta_min, deta_max, _stream(stream)))
+
+
+def mlp_workspace_bytes(rows: int) -> int:
+    return max(int(lib().cc_mlp_workspace_bytes(rows)), 256)
 
 
 def ring_residuals(rings: dict, sources):

@@ -136,6 +136,46 @@ cc_status cc_localize(const cc_rings *rings, const cc_grid *grid, const cc_param
     return CC_OK;
 }
 
+size_t cc_localize_batch_workspace_bytes(int64_t rings, int64_t dirs, const cc_params *p) {
+    cc_params d;
+    if (!p) { cc_params_default(&d); p = &d; }
+    SweepPlan plan;
+    if (!plan_sweep(rings, dirs, *p, &plan, kBatchD)) return 0;
+    return plan.bytes;
+}
+
+cc_status cc_localize_batch(int32_t n, const cc_rings *rings, const cc_grid *grid,
+                            const cc_params *p, float *const *maps, int32_t *const *argmax,
+                            int32_t *const *seeds, int32_t *const *status,
+                            void *const *workspaces, const size_t *ws_bytes, void *stream) {
+    g_err[0] = 0;
+    cc_status st = check_params(p);
+    if (st != CC_OK) return st;
+    if (n < 1 || n > CC_BATCH_MAX) return fail(CC_EINVAL, "n must be in 1..%d", CC_BATCH_MAX);
+    if (!rings || !maps || !argmax || !workspaces || !ws_bytes)
+        return fail(CC_EINVAL, "rings, maps, argmax, workspaces, ws_bytes must be non-NULL");
+    if (!grid || grid->count < 1 || grid->count > INT32_MAX || !grid->x || !grid->y || !grid->z)
+        return fail(CC_EINVAL, "bad grid");
+    SweepPlan plans[CC_BATCH_MAX];
+    char *ws[CC_BATCH_MAX];
+    for (int b = 0; b < n; b++) {
+        if ((st = check_rings_in(&rings[b])) != CC_OK) return st;
+        if (!maps[b] || !argmax[b]) return fail(CC_EINVAL, "burst %d: map/argmax NULL", b);
+        if (!workspaces[b] || !aligned(workspaces[b], 256))
+            return fail(CC_EINVAL, "burst %d: workspace NULL or not 256-byte aligned", b);
+        if (!plan_sweep(rings[b].count, grid->count, *p, &plans[b], kBatchD))
+            return fail(CC_EINVAL, "burst %d: cannot plan the sweep", b);
+        if (ws_bytes[b] < plans[b].bytes)
+            return fail(CC_ENOMEM, "burst %d: workspace of %zu bytes < %zu needed", b,
+                        ws_bytes[b], plans[b].bytes);
+        ws[b] = (char *)workspaces[b];
+    }
+    cudaError_t e = launch_localize_batch(n, rings, *grid, *p, plans, maps, argmax, seeds, status,
+                                          ws, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "localize_batch launch");
+    return CC_OK;
+}
+
 size_t cc_refine_workspace_bytes(int64_t rings, int32_t k) {
     return refine_workspace_bytes(rings, k);
 }

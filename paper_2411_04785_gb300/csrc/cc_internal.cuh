@@ -66,14 +66,21 @@ struct SweepPlan {
     int64_t rpad;      // padded ring count = tiles * nsplit * tile
     int64_t nbb;       // block-best entries
     // workspace byte offsets
-    size_t off_rec, off_part, off_bb, off_status, bytes;
+    size_t off_rec, off_part, off_bb, off_status, off_counter, bytes;
 };
 
-bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan);
+// force_d = 0 lets the planner pick the directions per thread; the batched
+// path fixes it so that bursts share one kernel instantiation.
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d = 0);
 cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid,
                             const cc_params &p, const SweepPlan &plan,
                             float *map, int32_t *argmax, int32_t *seeds,
                             int32_t *status, char *ws, cudaStream_t s);
+constexpr int kBatchD = 4;   // directions per thread of the batched sweep
+cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &grid,
+                                  const cc_params &p, const SweepPlan *plans, float *const *maps,
+                                  int32_t *const *argmax, int32_t *const *seeds,
+                                  int32_t *const *status, char *const *ws, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // refinement - refine.cu

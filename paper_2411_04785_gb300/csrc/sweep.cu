@@ -154,21 +154,31 @@ __global__ void k_pack_rings(const float *__restrict__ ax, const float *__restri
 // ---------------------------------------------------------------------------
 // the sweep
 // ---------------------------------------------------------------------------
+struct SweepSmem {
+    RingRec tile[kStages][kTile];
+    unsigned long long full[kStages];
+    int abort_flag;
+};
+
+// One work unit of the sweep: the 256 x D directions of direction block db
+// against the ring tiles [split * tiles, (split + 1) * tiles).  Writes the
+// unit's partial (or full) map row and, when bb_slot is set, its block best.
+// Returns false when a bounded wait gave up (status set to CC_ETIMEOUT).
 template <int D, bool KCUT>
-__global__ void __launch_bounds__(kThreads)
-k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
-        const float *__restrict__ cx, const float *__restrict__ cy,
-        const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
-        BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
+__device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restrict__ rec,
+                                           int64_t tiles, int64_t db, int64_t split,
+                                           const float *__restrict__ cx,
+                                           const float *__restrict__ cy,
+                                           const float *__restrict__ cz, int64_t M, float kc2,
+                                           float *__restrict__ out, BlockBest *bb_slot,
+                                           int32_t *__restrict__ status) {
     static_assert(D % 2 == 0, "directions are processed in FP32x2 pairs");
     constexpr int DP = D / 2;
-    __shared__ __align__(128) RingRec tile[kStages][kTile];
-    __shared__ __align__(8) unsigned long long full[kStages];
-    __shared__ int abort_flag;
+    auto &tile = S.tile;
+    auto &full = S.full;
+    int &abort_flag = S.abort_flag;
 
     const int tid = threadIdx.x;
-    const int64_t db = blockIdx.x % ndb;
-    const int64_t split = blockIdx.x / ndb;
     const int64_t j0 = db * (int64_t)(kThreads * D) + tid;
 
     // direction d of this thread: j0 + d * kThreads; pair p holds d = 2p, 2p+1
@@ -260,7 +270,7 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
     (void)one2;
     if (abort_flag) {
         if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
-        return;
+        return false;
     }
 
     float bv = -__builtin_huge_valf();
@@ -278,9 +288,65 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
             better(bv, bj, vb, (int)jb);
         }
     }
-    if (bb != nullptr) {
+    if (bb_slot != nullptr) {
         block_best(bv, bj);
-        if (tid == 0) bb[blockIdx.x] = BlockBest{bv, bj};
+        if (tid == 0) *bb_slot = BlockBest{bv, bj};
+    }
+    __syncthreads();   // the tiles and barriers may be reused by the next unit
+    return true;
+}
+
+
+template <int D, bool KCUT>
+__global__ void __launch_bounds__(kThreads)
+k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
+        const float *__restrict__ cx, const float *__restrict__ cy,
+        const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
+        BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
+    __shared__ __align__(128) SweepSmem S;
+    sweep_unit<D, KCUT>(S, rec, tiles, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, M, kc2,
+                        out, bb ? bb + blockIdx.x : nullptr, status);
+}
+
+// Several bursts in one persistent launch: CTAs take work units of all the
+// bursts from a shared counter until none is left.  A unit is computed
+// exactly as in k_sweep, so each burst's map does not depend on the others.
+struct BurstDesc {
+    const RingRec *rec;
+    int64_t tiles, ndb;
+    float *out;
+    BlockBest *bb;
+    int32_t *status;
+};
+
+struct MultiArgs {
+    int n;
+    BurstDesc b[CC_BATCH_MAX];
+    int64_t unit_begin[CC_BATCH_MAX + 1];
+    const float *cx, *cy, *cz;
+    int64_t M;
+    float kc2;
+    unsigned long long *counter;
+};
+
+template <int D, bool KCUT>
+__global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant__ MultiArgs a) {
+    __shared__ __align__(128) SweepSmem S;
+    __shared__ long long unit_s;
+    const long long total = a.unit_begin[a.n];
+    for (;;) {
+        if (threadIdx.x == 0) unit_s = (long long)atomicAdd(a.counter, 1ull);
+        __syncthreads();
+        const long long u = unit_s;
+        __syncthreads();
+        if (u >= total) break;
+        int b = 0;
+        while (u >= a.unit_begin[b + 1]) b++;
+        const BurstDesc &d = a.b[b];
+        const int64_t lu = u - a.unit_begin[b];
+        if (!sweep_unit<D, KCUT>(S, d.rec, d.tiles, lu % d.ndb, lu / d.ndb, a.cx, a.cy, a.cz,
+                                 a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr, d.status))
+            break;
     }
 }
 
@@ -383,7 +449,7 @@ void *pick_sweep(int d, bool kcut) {
 // ---------------------------------------------------------------------------
 // launch planning
 // ---------------------------------------------------------------------------
-bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d) {
     if (R < 0 || M < 1 || M > INT32_MAX) return false;
     const int sms = device_sm_count();
     if (sms <= 0) return false;
@@ -394,6 +460,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
     int d = 2;
     int64_t conc = 0;
     for (int cand : {4, 8, 2}) {
+        if (force_d > 0) cand = force_d;
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_sweep(cand, kcut), kThreads, 0);
         if (occ < 1) occ = 1;
@@ -401,7 +468,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
         int64_t ndb = (M + (int64_t)kThreads * cand - 1) / ((int64_t)kThreads * cand);
         d = cand;
         conc = c;
-        if (ndb * max_split >= c) break;
+        if (force_d > 0 || ndb * max_split >= c) break;
     }
     const int64_t ndb = (M + (int64_t)kThreads * d - 1) / ((int64_t)kThreads * d);
 
@@ -436,8 +503,48 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan) {
     off = align256(off + (size_t)plan->nbb * sizeof(BlockBest));
     plan->off_status = off;
     off = align256(off + sizeof(int32_t));
+    plan->off_counter = off;
+    off = align256(off + sizeof(unsigned long long));
     plan->bytes = off;
     return true;
+}
+
+// Pack one burst's rings into the plan's records (and zero its status).
+cudaError_t pack_for_plan(const cc_rings &rings, const SweepPlan &plan, int32_t *status, char *ws,
+                          cudaStream_t s) {
+    RingRec *rec = reinterpret_cast<RingRec *>(ws + plan.off_rec);
+    int32_t *st = status ? status : reinterpret_cast<int32_t *>(ws + plan.off_status);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (plan.rpad + 255) / 256;
+    if (blocks > (int64_t)device_sm_count() * 16) blocks = (int64_t)device_sm_count() * 16;
+    TraceScope ts(CC_STAGE_PACK, s);
+    k_pack_rings<<<(unsigned)blocks, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta,
+                                                  rings.deta, rings.valid, rings.count,
+                                                  plan.rpad, rec);
+    return cudaGetLastError();
+}
+
+// After the sweep of one burst: the split reduction and argmax / seeds.
+cudaError_t finish_localize(const cc_grid &grid, const cc_params &p, const SweepPlan &plan,
+                            float *map, int32_t *argmax, int32_t *seeds, char *ws,
+                            cudaStream_t s) {
+    float *part = reinterpret_cast<float *>(ws + plan.off_part);
+    BlockBest *bb = reinterpret_cast<BlockBest *>(ws + plan.off_bb);
+    cudaError_t e;
+    if (plan.nsplit > 1) {
+        {
+            TraceScope ts(CC_STAGE_REDUCE, s);
+            k_reduce_splits<<<(unsigned)plan.nbb, 256, 0, s>>>(part, plan.nsplit, grid.count,
+                                                               map, bb);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int topk = p.topk < 1 ? 1 : p.topk;
+    TraceScope ts(CC_STAGE_SELECT, s);
+    k_select<<<1, 1024, 0, s>>>(map, bb, plan.nbb, grid.x, grid.y, grid.z, grid.count, topk,
+                                cosf(p.nms_rad), argmax, seeds);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc_params &p,
@@ -447,18 +554,9 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     float *part = reinterpret_cast<float *>(ws + plan.off_part);
     BlockBest *bb = reinterpret_cast<BlockBest *>(ws + plan.off_bb);
     int32_t *st = status ? status : reinterpret_cast<int32_t *>(ws + plan.off_status);
-    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+    cudaError_t e = pack_for_plan(rings, plan, status, ws, s);
     if (e != cudaSuccess) return e;
-
-    const int64_t R = rings.count, M = grid.count;
-    {
-        int64_t blocks = (plan.rpad + 255) / 256;
-        if (blocks > (int64_t)device_sm_count() * 16) blocks = (int64_t)device_sm_count() * 16;
-        TraceScope ts(CC_STAGE_PACK, s);
-        k_pack_rings<<<(unsigned)blocks, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta,
-                                                      rings.deta, rings.valid, R, plan.rpad, rec);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    const int64_t M = grid.count;
     const bool kcut = p.k_cut > 0.0f;
     const float kc = p.k_cut * kGaussK;
     const float kc2 = kcut ? kc * kc : 0.0f;
@@ -474,18 +572,57 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
         e = cudaLaunchKernel(fn, dim3(grid_ctas), dim3(kThreads), args, 0, s);
     }
     if (e != cudaSuccess) return e;
-    if (plan.nsplit > 1) {
-        {
-            TraceScope ts(CC_STAGE_REDUCE, s);
-            k_reduce_splits<<<(unsigned)plan.nbb, 256, 0, s>>>(part, plan.nsplit, M, map, bb);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return finish_localize(grid, p, plan, map, argmax, seeds, ws, s);
+}
+
+cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &grid,
+                                  const cc_params &p, const SweepPlan *plans, float *const *maps,
+                                  int32_t *const *argmax, int32_t *const *seeds,
+                                  int32_t *const *status, char *const *ws, cudaStream_t s) {
+    MultiArgs a{};
+    a.n = n;
+    a.cx = grid.x;
+    a.cy = grid.y;
+    a.cz = grid.z;
+    a.M = grid.count;
+    const bool kcut = p.k_cut > 0.0f;
+    const float kc = p.k_cut * kGaussK;
+    a.kc2 = kcut ? kc * kc : 0.0f;
+    a.counter = reinterpret_cast<unsigned long long *>(ws[0] + plans[0].off_counter);
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    a.unit_begin[0] = 0;
+    for (int b = 0; b < n; b++) {
+        const SweepPlan &pl = plans[b];
+        if ((e = pack_for_plan(rings[b], pl, status ? status[b] : nullptr, ws[b], s))) return e;
+        BurstDesc &d = a.b[b];
+        d.rec = reinterpret_cast<const RingRec *>(ws[b] + pl.off_rec);
+        d.tiles = pl.tiles;
+        d.ndb = pl.ndb;
+        d.out = pl.nsplit > 1 ? reinterpret_cast<float *>(ws[b] + pl.off_part) : maps[b];
+        d.bb = pl.nsplit > 1 ? nullptr : reinterpret_cast<BlockBest *>(ws[b] + pl.off_bb);
+        d.status = (status && status[b]) ? status[b]
+                                         : reinterpret_cast<int32_t *>(ws[b] + pl.off_status);
+        a.unit_begin[b + 1] = a.unit_begin[b] + pl.ndb * pl.nsplit;
     }
-    int topk = p.topk < 1 ? 1 : p.topk;
-    TraceScope ts(CC_STAGE_SELECT, s);
-    k_select<<<1, 1024, 0, s>>>(map, bb, plan.nbb, grid.x, grid.y, grid.z, M, topk,
-                                cosf(p.nms_rad), argmax, seeds);
-    return cudaGetLastError();
+    int occ = 0;
+    void *fn = kcut ? (void *)k_sweep_multi<kBatchD, true> : (void *)k_sweep_multi<kBatchD, false>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, 0);
+    if (occ < 1) occ = 1;
+    int64_t ctas = (int64_t)device_sm_count() * occ;
+    if (ctas > a.unit_begin[n]) ctas = a.unit_begin[n];
+    if (ctas < 1) ctas = 1;
+    void *args[] = {(void *)&a};
+    {
+        TraceScope ts(CC_STAGE_SWEEP, s);
+        e = cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(kThreads), args, 0, s);
+    }
+    if (e != cudaSuccess) return e;
+    for (int b = 0; b < n; b++)
+        if ((e = finish_localize(grid, p, plans[b], maps[b], argmax[b], seeds ? seeds[b] : nullptr,
+                                 ws[b], s)))
+            return e;
+    return cudaSuccess;
 }
 
 }  // namespace cc

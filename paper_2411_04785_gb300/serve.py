@@ -1,0 +1,235 @@
+"""Serving loop for burst localisation with continuous batching.
+
+Bursts (event sets of uneven size) arrive over time.  A burst is admitted as
+soon as a slot and its device-memory budget are free; its events are copied
+to the device and reconstructed into rings (and, on the learned path, scored
+and re-widthed by the ring filter) on a stream of its own.  Every pass of the
+loop sweeps ALL admitted bursts whose rings are ready in one batched launch
+(cc_localize_batch: one persistent kernel over the work units of every
+burst), on one of two sweep streams, so a new batch overlaps a running one on
+the GPU; each burst's refinement and result read-back then run on its own
+stream again.  The host only polls events; it never waits for the GPU while
+bursts remain.
+
+A burst's results do not depend on the batch it was swept in (the batched
+sweep keeps each burst's own plan), which the tests check against the same
+burst served alone.  Host code here only schedules and moves buffers: every
+step of the localisation runs in libcompton.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import api
+
+BATCH_MAX = 64
+
+
+@dataclass
+class Burst:
+    """One request: events on the host (pinned), arrival time in seconds."""
+    bid: int
+    arrival: float
+    n: torch.Tensor
+    x: torch.Tensor
+    y: torch.Tensor
+    z: torch.Tensor
+    e: torch.Tensor
+    source: np.ndarray | None = None
+
+    @property
+    def count(self):
+        return self.n.numel()
+
+
+@dataclass
+class _Active:
+    burst: Burst
+    stream: torch.cuda.Stream
+    bytes: int
+    t_admit: float
+    dev: dict = field(default_factory=dict)
+    ready: torch.cuda.Event | None = None
+    swept: bool = False
+    done: torch.cuda.Event | None = None
+    out_host: dict = field(default_factory=dict)
+
+
+def burst_bytes(N: int, M: int, params: api.Params, learned: bool) -> int:
+    """Device bytes one burst holds while in flight."""
+    b = N * (1 + 4 * 4 * 4) + N * (5 * 4 + 2)                 # events + rings
+    b += api.lib().cc_localize_batch_workspace_bytes(N, M, C.byref(params.c()))
+    b += api.refine_workspace_bytes(N, params.topk) + M * 4 + 1024
+    if learned:
+        b += N * (api.MLP_FEATURES * 2 + 8) + api.lib().cc_mlp_workspace_bytes(N)
+    return int(b)
+
+
+class Server:
+    """Continuous-batching server over one GPU."""
+
+    def __init__(self, grid, params: api.Params | None = None, hbm_budget: int = 2 << 30,
+                 max_active: int = 48, ring_filter: api.RingFilter | None = None,
+                 tau: float = 0.0, filter_deta_max: float | None = None):
+        self.grid = grid
+        self.M = grid[0].numel()
+        self.dev = grid[0].device
+        self.params = params or api.Params()
+        self.budget = hbm_budget
+        self.max_active = max_active
+        self.filter = ring_filter
+        self.tau = tau
+        self.filter_deta_max = filter_deta_max or self.params.deta_max
+        self.sweep_streams = [torch.cuda.Stream(self.dev) for _ in range(2)]
+        self._ss = 0
+        self._gs = api._grid_struct(grid)
+
+    # -- per-burst front end ------------------------------------------------
+    def _admit(self, b: Burst, now: float) -> _Active:
+        s = torch.cuda.Stream(self.dev)
+        a = _Active(b, s, burst_bytes(b.count, self.M, self.params, self.filter is not None), now)
+        d = a.dev
+        with torch.cuda.stream(s):
+            d["n"] = b.n.to(self.dev, non_blocking=True)
+            for k in "xyze":
+                d[k] = getattr(b, k).to(self.dev, non_blocking=True)
+            d["rings"] = api.rings_from_events(d["n"], d["x"], d["y"], d["z"], d["e"],
+                                               self.params, stream=s)
+            if self.filter is not None:
+                F = api.ring_features(d["n"], d["x"], d["y"], d["z"], d["e"], d["rings"],
+                                      self.params, stream=s)
+                mws = torch.empty(api.mlp_workspace_bytes(b.count), dtype=torch.uint8,
+                                  device=self.dev)
+                out = self.filter.forward(F, stream=s, workspace=mws)
+                self.filter.apply(d["rings"], out, self.tau, self.params.deta_min,
+                                  self.filter_deta_max, stream=s)
+            ws_b = api.lib().cc_localize_batch_workspace_bytes(b.count, self.M,
+                                                               C.byref(self.params.c()))
+            d["ws"] = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=self.dev)
+            d["map"] = torch.empty(self.M, dtype=torch.float32, device=self.dev)
+            d["argmax"] = torch.empty(1, dtype=torch.int32, device=self.dev)
+            d["seeds"] = torch.empty(self.params.topk, dtype=torch.int32, device=self.dev)
+            d["status"] = torch.empty(1, dtype=torch.int32, device=self.dev)
+            a.ready = torch.cuda.Event()
+            a.ready.record(s)
+        return a
+
+    # -- one batched sweep ----------------------------------------------------
+    def _sweep(self, batch: list[_Active]):
+        n = len(batch)
+        stream = self.sweep_streams[self._ss]
+        self._ss = (self._ss + 1) % len(self.sweep_streams)
+        rings = (api.cc_rings * n)(*[api._rings_struct(a.dev["rings"]) for a in batch])
+        P = C.c_void_p
+        maps = (P * n)(*[a.dev["map"].data_ptr() for a in batch])
+        am = (P * n)(*[a.dev["argmax"].data_ptr() for a in batch])
+        sd = (P * n)(*[a.dev["seeds"].data_ptr() for a in batch])
+        st = (P * n)(*[a.dev["status"].data_ptr() for a in batch])
+        ws = (P * n)(*[a.dev["ws"].data_ptr() for a in batch])
+        wsb = (C.c_size_t * n)(*[a.dev["ws"].numel() for a in batch])
+        for a in batch:
+            stream.wait_event(a.ready)
+        pc = self.params.c()
+        api._check("cc_localize_batch", api.lib().cc_localize_batch(
+            n, rings, C.byref(self._gs), C.byref(pc), maps, am, sd, st, ws, wsb,
+            C.c_void_p(stream.cuda_stream)))
+        swept = torch.cuda.Event()
+        swept.record(stream)
+        for a in batch:                       # refine + read-back on the burst's stream
+            s = a.stream
+            s.wait_event(swept)
+            d = a.dev
+            with torch.cuda.stream(s):
+                seeds_dir = api.grid_gather(self.grid, d["seeds"], stream=s)
+                res = api.refine(d["rings"], seeds_dir, self.params, stream=s)
+                a.out_host = {"dir": res[0].to("cpu", non_blocking=True),
+                              "obj": res[1].to("cpu", non_blocking=True),
+                              "status": torch.cat([d["status"], res[3]]).to("cpu", non_blocking=True),
+                              "argmax": d["argmax"].to("cpu", non_blocking=True)}
+                if self.keep_maps:
+                    a.out_host["map"] = d["map"].to("cpu", non_blocking=True)
+                a.done = torch.cuda.Event()
+                a.done.record(s)
+            a.swept = True
+
+    # -- the loop -------------------------------------------------------------
+    def run(self, bursts: list[Burst], realtime: bool = True, keep_maps: bool = False):
+        """Serve the bursts; returns per-burst results and latencies (s).
+        With realtime, bursts become available at their arrival times;
+        otherwise all are available at once (arrivals then only order them)."""
+        self.keep_maps = keep_maps
+        pending = deque(sorted(bursts, key=lambda b: b.arrival))
+        active: list[_Active] = []
+        used = 0
+        results = {}
+        batches = []
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            progressed = False
+            # admit
+            while pending and (not realtime or pending[0].arrival <= now) and \
+                    len(active) < self.max_active:
+                need = burst_bytes(pending[0].count, self.M, self.params, self.filter is not None)
+                if used + need > self.budget and active:
+                    break                                   # wait for memory to free up
+                b = pending.popleft()
+                active.append(self._admit(b, now))
+                used += active[-1].bytes
+                progressed = True
+            # sweep everything whose rings are ready, in one batched launch
+            ready = [a for a in active if not a.swept and a.ready.query()]
+            for i in range(0, len(ready), BATCH_MAX):
+                self._sweep(ready[i:i + BATCH_MAX])
+                batches.append(len(ready[i:i + BATCH_MAX]))
+                progressed = True
+            # complete
+            still = []
+            for a in active:
+                if a.swept and a.done.query():
+                    t = time.perf_counter() - t0
+                    b = a.burst
+                    arrival = b.arrival if realtime else 0.0
+                    results[b.bid] = {"latency": t - arrival, "t_done": t,
+                                      "dir": a.out_host["dir"].numpy(),
+                                      "obj": float(a.out_host["obj"][0]),
+                                      "status": a.out_host["status"].numpy(),
+                                      "argmax": int(a.out_host["argmax"][0]),
+                                      "rings": b.count}
+                    if keep_maps:
+                        results[b.bid]["map"] = a.out_host["map"].numpy()
+                    used -= a.bytes
+                    progressed = True
+                else:
+                    still.append(a)
+            active = still
+            if not progressed:
+                if realtime and pending and not active:
+                    time.sleep(max(0.0, min(pending[0].arrival - now, 0.002)))
+                else:
+                    time.sleep(20e-6)
+        wall = time.perf_counter() - t0
+        return results, {"wall_s": wall, "batches": batches}
+
+
+def to_bursts(items) -> list[Burst]:
+    """Bursts (pinned host tensors) from synth.serving_bursts items."""
+    out = []
+    for i, it in enumerate(items):
+        ev = it["events"]
+        out.append(Burst(i, it["arrival"], torch.from_numpy(ev["n"]).pin_memory(),
+                         *(torch.from_numpy(ev[k]).pin_memory() for k in "xyze"),
+                         source=it["source"]))
+    return out
+
+
+def make_bursts(n_bursts: int, rate_hz: float, seed: int, **kw) -> list[Burst]:
+    from . import synth
+    return to_bursts(synth.serving_bursts(n_bursts, rate_hz, seed, **kw))

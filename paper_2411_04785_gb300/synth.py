@@ -306,3 +306,42 @@ def training_events(n_events: int, seed: int, bkg_ratio: float = 3.0, chunk: int
     for k in ("x", "y", "z", "e"):
         out[k] = np.ascontiguousarray(np.concatenate([p[k] for p in parts], axis=1))
     return out
+
+
+def serving_bursts(n_bursts: int = 2000, rate_hz: float = 50.0, seed: int = 5,
+                   median: int = 20000, sigma: float = 1.0, lo: int = 500, hi: int = 300000,
+                   bkg_lo: float = 1.0, bkg_hi: float = 50.0, n_dirs: int = 16,
+                   pool_src: int = 160000, pool_bkg: int = 320000):
+    """The serving workload: Poisson arrivals at rate_hz; event counts
+    log-normal (median, sigma) truncated to [lo, hi]; background ratio uniform
+    in [bkg_lo, bkg_hi]; the source direction one of n_dirs random directions.
+    Events are drawn without replacement (within a burst) from pools simulated
+    once: pool_src source events per direction and pool_bkg isotropic
+    background events.  Returns a list of dicts: arrival (s), source, and the
+    event arrays n [N], x, y, z, e [4, N] float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dirs = random_units(rng, n_dirs)
+    src_pools = [simulate_events(n_src=pool_src, n_bkg=0, seed=seed * 7919 + d, source=dirs[d])
+                 for d in range(n_dirs)]
+    bkg = simulate_events(n_src=0, n_bkg=pool_bkg, seed=seed * 7919 + n_dirs)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_bursts))
+    out = []
+    for i in range(n_bursts):
+        while True:
+            N = int(round(median * math.exp(sigma * rng.standard_normal())))
+            if lo <= N <= hi:
+                break
+        ratio = rng.uniform(bkg_lo, bkg_hi)
+        n_src = min(pool_src, max(1, int(round(N / (1.0 + ratio)))))
+        n_bkg = min(pool_bkg, N - n_src)
+        d = int(rng.integers(n_dirs))
+        si = rng.choice(pool_src, n_src, replace=False)
+        bi = rng.choice(pool_bkg, n_bkg, replace=False)
+        order = rng.permutation(n_src + n_bkg)
+        ev = {"n": np.concatenate([src_pools[d]["n"][si], bkg["n"][bi]])[order]}
+        for k in ("x", "y", "z", "e"):
+            ev[k] = np.ascontiguousarray(
+                np.concatenate([src_pools[d][k][:, si], bkg[k][:, bi]], axis=1)[:, order])
+        ev["is_source"] = np.concatenate([np.ones(n_src, bool), np.zeros(n_bkg, bool)])[order]
+        out.append({"arrival": float(t[i]), "source": dirs[d], "events": ev})
+    return out

@@ -1,0 +1,91 @@
+"""The serving path: batched sweeps give each burst the same result as when
+it is swept alone, and the continuous-batching server returns, for every
+burst of a mixed stream, the same map and direction as serving it alone."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_04785_gb300 import synth
+from tests.helpers import grid_to_dev, rings_to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_04785_gb300 as m
+    m.lib()
+    return m
+
+
+def batch_localize(cc, ring_sets, grid, params):
+    from paper_2411_04785_gb300 import api
+    dev = grid[0].device
+    n = len(ring_sets)
+    M = grid[0].numel()
+    outs = []
+    for r in ring_sets:
+        nb = api.lib().cc_localize_batch_workspace_bytes(r["ax"].numel(), M, C.byref(params.c()))
+        outs.append({"map": torch.empty(M, device=dev), "am": torch.empty(1, dtype=torch.int32, device=dev),
+                     "sd": torch.empty(params.topk, dtype=torch.int32, device=dev),
+                     "st": torch.empty(1, dtype=torch.int32, device=dev),
+                     "ws": torch.empty(nb, dtype=torch.uint8, device=dev)})
+    P = C.c_void_p
+    rings = (api.cc_rings * n)(*[api._rings_struct(r) for r in ring_sets])
+    arr = lambda k: (P * n)(*[o[k].data_ptr() for o in outs])
+    wsb = (C.c_size_t * n)(*[o["ws"].numel() for o in outs])
+    st = api.lib().cc_localize_batch(n, rings, C.byref(api._grid_struct(grid)), C.byref(params.c()),
+                                     arr("map"), arr("am"), arr("sd"), arr("st"), arr("ws"), wsb,
+                                     None)
+    assert st == 0, api.lib().cc_last_error()
+    torch.cuda.synchronize()
+    return [{k: o[k].cpu().numpy() for k in ("map", "am", "sd", "st")} for o in outs]
+
+
+def test_batched_sweep_equals_alone_and_matches_oracle(cc):
+    dev = torch.device("cuda:0")
+    grid_np = oracle.grid_healpix_ring(32)
+    grid = grid_to_dev(grid_np, dev)
+    p = cc.Params(topk=3, nms_rad=math.radians(5))
+    sets_np = [synth.rings_burst(n=n, seed=s)[0] for n, s in ((500, 1), (3000, 2), (20000, 3),
+                                                             (129, 4), (150000, 5))]
+    sets = [rings_to_dev(r, dev) for r in sets_np]
+    mixed = batch_localize(cc, sets, grid, p)
+    for r, r_np, m in zip(sets, sets_np, mixed):
+        alone = batch_localize(cc, [r], grid, p)[0]
+        np.testing.assert_array_equal(m["map"], alone["map"])      # bit for bit
+        assert m["am"][0] == alone["am"][0] and (m["sd"] == alone["sd"]).all()
+        assert m["st"][0] == 0
+        # and the batched map satisfies the parity rule against the oracle
+        idx = np.arange(0, grid_np[0].size, 7)
+        want = oracle.likelihood_map({k: np.asarray(r_np[k], np.float32) for k in
+                                      ("ax", "ay", "az", "eta", "deta")}, grid_np, idx=idx)
+        bound = 1e-5 * np.maximum(want, 1e-3 * want.max())
+        assert (np.abs(m["map"][idx] - want) <= bound).all()
+
+
+def test_server_mixed_stream_equals_alone(cc):
+    from paper_2411_04785_gb300 import serve
+    dev = torch.device("cuda:0")
+    grid = cc.grid_healpix_ring(32, dev)
+    p = cc.Params()
+    bursts = serve.make_bursts(16, rate_hz=400.0, seed=7, median=4000, hi=60000, n_dirs=3,
+                               pool_src=30000, pool_bkg=60000)
+    srv = serve.Server(grid, p, hbm_budget=256 << 20, max_active=8)
+    mixed, stats = srv.run(bursts, realtime=True, keep_maps=True)
+    assert len(mixed) == 16 and max(stats["batches"]) > 1        # bursts were batched
+    for b in bursts:
+        alone, _ = serve.Server(grid, p).run([b], realtime=False, keep_maps=True)
+        a, m = alone[b.bid], mixed[b.bid]
+        np.testing.assert_array_equal(m["map"], a["map"])
+        assert m["argmax"] == a["argmax"]
+        np.testing.assert_array_equal(m["dir"], a["dir"])
+        assert (m["status"] == 0).all() or m["status"][1] == -5
+    lat = np.array([r["latency"] for r in mixed.values()])
+    assert (lat > 0).all()
