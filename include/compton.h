@@ -140,7 +140,10 @@ size_t cc_localize_workspace_bytes(int64_t rings, int64_t dirs,
  *   seeds[0..topk) = greedy top-k: directions in (L desc, index asc) order,
  *              skipping those within nms_rad of a seed already taken
  *              (seeds[0] = argmax; unfilled slots are -1).
- * rings->count >= 0 (0 gives an all-zero map), grid->count >= 1.
+ * Only valid rings with finite values and deta > 0 are swept: they are
+ * compacted (in index order) before the sweep, so the sweep's time follows
+ * the number of such rings, not rings->count.
+ * 0 <= rings->count <= 2^31 - 1 (0 gives an all-zero map), grid->count >= 1.
  * `map` [grid->count] float, `argmax` [1] int32, `seeds` [p->topk] int32
  * (may be NULL), `status` [1] int32 (may be NULL), `workspace` device
  * memory of at least cc_localize_workspace_bytes() bytes, 256-byte aligned.

@@ -54,6 +54,7 @@ static cc_status check_params(const cc_params *p) {
 static cc_status check_rings_in(const cc_rings *r) {
     if (!r) return fail(CC_EINVAL, "rings is NULL");
     if (r->count < 0) return fail(CC_EINVAL, "rings->count < 0");
+    if (r->count > INT32_MAX) return fail(CC_EINVAL, "rings->count > 2^31 - 1");
     if (r->count > 0 && (!r->ax || !r->ay || !r->az || !r->eta || !r->deta))
         return fail(CC_EINVAL, "ring arrays must be non-NULL");
     return CC_OK;

@@ -60,13 +60,14 @@ struct SweepPlan {
     int d;             // directions per thread (1, 2, 4, 8)
     int threads;       // CTA size
     int64_t tile;      // rings per shared-memory tile
-    int64_t tiles;     // tiles per split
+    int64_t tiles;     // tiles per split at most (split s takes tiles s, s + nsplit, ...)
     int64_t nsplit;    // ring splits (partial maps when > 1)
     int64_t ndb;       // direction blocks
     int64_t rpad;      // padded ring count = tiles * nsplit * tile
     int64_t nbb;       // block-best entries
+    int64_t npack;     // blocks of the ring compaction
     // workspace byte offsets
-    size_t off_rec, off_part, off_bb, off_status, off_counter, bytes;
+    size_t off_rec, off_part, off_bb, off_status, off_counter, off_nkept, off_packcnt, bytes;
 };
 
 // force_d = 0 lets the planner pick the directions per thread; the batched

@@ -125,29 +125,120 @@ __device__ __forceinline__ void block_best(float &v, int &j) {
 // ---------------------------------------------------------------------------
 // ring repacking
 // ---------------------------------------------------------------------------
-__global__ void k_pack_rings(const float *__restrict__ ax, const float *__restrict__ ay,
-                             const float *__restrict__ az, const float *__restrict__ eta,
-                             const float *__restrict__ deta, const uint8_t *__restrict__ valid,
-                             int64_t R, int64_t rpad, RingRec *__restrict__ rec) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rpad;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        RingRec r = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, 0.f, 0.f};
-        if (i < R && (valid == nullptr || valid[i])) {
-            float a0 = ax[i], a1 = ay[i], a2 = az[i], e = eta[i], de = deta[i];
-            bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(e) &&
-                       isfinite(de) && de > 0.0f;
-            if (fin) {
-                float k = kGaussK / de;
-                float b = e * k, b2 = (kPiF - e) * k;
-                if (e > 0.5f * kPiF) {      // mirror: same ring, eta' <= pi/2
-                    a0 = -a0; a1 = -a1; a2 = -a2;
-                    float t = b; b = b2; b2 = t;
-                }
-                float s0 = a0 * kInvSqrt2, s1 = a1 * kInvSqrt2, s2 = a2 * kInvSqrt2;
-                r = {s0, s0, s1, s1, s2, s2, k, k, -b, -b2, 0.f, 0.f};
-            }
+constexpr int kPackChunk = 2048;   // rings per pack block (8 per thread)
+
+// A ring enters the sweep when it is valid and its numbers are usable.
+__device__ __forceinline__ bool ring_kept(const float *__restrict__ ax,
+                                          const float *__restrict__ ay,
+                                          const float *__restrict__ az,
+                                          const float *__restrict__ eta,
+                                          const float *__restrict__ deta,
+                                          const uint8_t *__restrict__ valid, int64_t i,
+                                          int64_t R) {
+    if (i >= R || (valid != nullptr && !valid[i])) return false;
+    float de = deta[i];
+    return isfinite(ax[i]) && isfinite(ay[i]) && isfinite(az[i]) && isfinite(eta[i]) &&
+           isfinite(de) && de > 0.0f;
+}
+
+__device__ __forceinline__ RingRec make_rec(float a0, float a1, float a2, float e, float de) {
+    float k = kGaussK / de;
+    float b = e * k, b2 = (kPiF - e) * k;
+    if (e > 0.5f * kPiF) {      // mirror: same ring, eta' <= pi/2
+        a0 = -a0; a1 = -a1; a2 = -a2;
+        float t = b; b = b2; b2 = t;
+    }
+    float s0 = a0 * kInvSqrt2, s1 = a1 * kInvSqrt2, s2 = a2 * kInvSqrt2;
+    return RingRec{s0, s0, s1, s1, s2, s2, k, k, -b, -b2, 0.f, 0.f};
+}
+
+// Kept rings are compacted, in index order, to the front of the record
+// array, so the sweep's cost follows the rings that count (a filter that
+// drops rings shortens the sweep).  Three passes: per-block counts, one scan
+// of the counts, and the scatter.
+__global__ void __launch_bounds__(256)
+k_pack_count(const float *__restrict__ ax, const float *__restrict__ ay,
+             const float *__restrict__ az, const float *__restrict__ eta,
+             const float *__restrict__ deta, const uint8_t *__restrict__ valid, int64_t R,
+             int32_t *__restrict__ blockcnt) {
+    const int64_t base = blockIdx.x * (int64_t)kPackChunk;
+    int n = 0;
+    for (int r = 0; r < kPackChunk / 256; r++)
+        n += __syncthreads_count(ring_kept(ax, ay, az, eta, deta, valid,
+                                           base + r * 256 + threadIdx.x, R));
+    if (threadIdx.x == 0) blockcnt[blockIdx.x] = n;
+}
+
+__global__ void __launch_bounds__(1024)
+k_pack_scan(int32_t *__restrict__ blockcnt, int64_t nblk, int64_t *__restrict__ nkept) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t c = 0; c < nblk; c += 1024) {
+        const int64_t i = c + threadIdx.x;
+        int64_t v = i < nblk ? blockcnt[i] : 0, x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (l >= o) x += y;
         }
-        rec[i] = r;
+        if (l == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t s = wsum[l], t = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (l >= o) t += y;
+            }
+            wsum[l] = t - s;                  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const int64_t excl = carry + wsum[w] + x - v;
+        if (i < nblk) blockcnt[i] = (int32_t)excl;   // offsets fit: R < 2^31
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nkept = carry;
+}
+
+__global__ void __launch_bounds__(256)
+k_pack_scatter(const float *__restrict__ ax, const float *__restrict__ ay,
+               const float *__restrict__ az, const float *__restrict__ eta,
+               const float *__restrict__ deta, const uint8_t *__restrict__ valid, int64_t R,
+               const int32_t *__restrict__ offs, const int64_t *__restrict__ nkept,
+               RingRec *__restrict__ rec) {
+    __shared__ int wcnt[8];
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = blockIdx.x * (int64_t)kPackChunk;
+    int64_t pos = offs[blockIdx.x];
+    for (int r = 0; r < kPackChunk / 256; r++) {
+        const int64_t i = base + r * 256 + threadIdx.x;
+        const bool keep = ring_kept(ax, ay, az, eta, deta, valid, i, R);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (l == 0) wcnt[w] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            before += k < w ? wcnt[k] : 0;
+            total += wcnt[k];
+        }
+        if (keep)
+            rec[pos + before + __popc(m & ((1u << l) - 1u))] =
+                make_rec(ax[i], ay[i], az[i], eta[i], deta[i]);
+        pos += total;
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x < kTile) {   // null records up to the tile end
+        const int64_t n = *nkept;
+        const int64_t end = (n + kTile - 1) / kTile * kTile;
+        if (n + threadIdx.x < end)
+            rec[n + threadIdx.x] =
+                RingRec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, 0.f, 0.f};
     }
 }
 
@@ -161,12 +252,14 @@ struct SweepSmem {
 };
 
 // One work unit of the sweep: the 256 x D directions of direction block db
-// against the ring tiles [split * tiles, (split + 1) * tiles).  Writes the
-// unit's partial (or full) map row and, when bb_slot is set, its block best.
-// Returns false when a bounded wait gave up (status set to CC_ETIMEOUT).
+// against the ring tiles split, split + nsplit, split + 2 nsplit, ... of the
+// *nkept packed rings.  Writes the unit's partial (or full) map row and, when
+// bb_slot is set, its block best.  Returns false when a bounded wait gave up
+// (status set to CC_ETIMEOUT).
 template <int D, bool KCUT>
 __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restrict__ rec,
-                                           int64_t tiles, int64_t db, int64_t split,
+                                           const int64_t *__restrict__ nkept, int64_t nsplit,
+                                           int64_t db, int64_t split,
                                            const float *__restrict__ cx,
                                            const float *__restrict__ cy,
                                            const float *__restrict__ cz, int64_t M, float kc2,
@@ -194,7 +287,10 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         acc[q] = sum[q] = comp[q] = make_float2(0.0f, 0.0f);
     }
 
-    const RingRec *src = rec + split * tiles * kTile;
+    const int64_t ntk = (*nkept + kTile - 1) / kTile;
+    const int64_t tiles = split < ntk ? (ntk - split + nsplit - 1) / nsplit : 0;
+    const RingRec *src = rec + split * kTile;
+    const int64_t stride = nsplit * kTile;
     if (tid == 0) {
         for (int s = 0; s < kStages; s++) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -203,7 +299,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < kStages && s < tiles; s++)
-            tma_bulk_load(tile[s], src + (int64_t)s * kTile, kTile * sizeof(RingRec), &full[s]);
+            tma_bulk_load(tile[s], src + (int64_t)s * stride, kTile * sizeof(RingRec), &full[s]);
     }
 
     const float2 one2 = pair(1.0f), m1 = pair(-1.0f), two2 = pair(2.0f);
@@ -256,7 +352,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         __syncthreads();
         if (abort_flag) break;
         if (tid == 0 && t + kStages < tiles)
-            tma_bulk_load(tile[stage], src + (t + kStages) * kTile, kTile * sizeof(RingRec),
+            tma_bulk_load(tile[stage], src + (t + kStages) * stride, kTile * sizeof(RingRec),
                           &full[stage]);
 #pragma unroll
         for (int q = 0; q < DP; q++) {   // Kahan-compensated tile sums
@@ -299,12 +395,14 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
 
 template <int D, bool KCUT>
 __global__ void __launch_bounds__(kThreads)
-k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
+k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
+        int64_t ndb,
         const float *__restrict__ cx, const float *__restrict__ cy,
         const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
         BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
     __shared__ __align__(128) SweepSmem S;
-    sweep_unit<D, KCUT>(S, rec, tiles, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, M, kc2,
+    sweep_unit<D, KCUT>(S, rec, nkept, nsplit, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, M,
+                        kc2,
                         out, bb ? bb + blockIdx.x : nullptr, status);
 }
 
@@ -313,7 +411,8 @@ k_sweep(const RingRec *__restrict__ rec, int64_t tiles, int64_t ndb,
 // exactly as in k_sweep, so each burst's map does not depend on the others.
 struct BurstDesc {
     const RingRec *rec;
-    int64_t tiles, ndb;
+    const int64_t *nkept;
+    int64_t nsplit, ndb;
     float *out;
     BlockBest *bb;
     int32_t *status;
@@ -344,8 +443,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant_
         while (u >= a.unit_begin[b + 1]) b++;
         const BurstDesc &d = a.b[b];
         const int64_t lu = u - a.unit_begin[b];
-        if (!sweep_unit<D, KCUT>(S, d.rec, d.tiles, lu % d.ndb, lu / d.ndb, a.cx, a.cy, a.cz,
-                                 a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr, d.status))
+        if (!sweep_unit<D, KCUT>(S, d.rec, d.nkept, d.nsplit, lu % d.ndb, lu / d.ndb, a.cx, a.cy,
+                                 a.cz, a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr, d.status))
             break;
     }
 }
@@ -505,6 +604,11 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     off = align256(off + sizeof(int32_t));
     plan->off_counter = off;
     off = align256(off + sizeof(unsigned long long));
+    plan->off_nkept = off;
+    off = align256(off + sizeof(int64_t));
+    plan->npack = R > 0 ? (R + kPackChunk - 1) / kPackChunk : 1;
+    plan->off_packcnt = off;
+    off = align256(off + (size_t)plan->npack * sizeof(int32_t));
     plan->bytes = off;
     return true;
 }
@@ -516,12 +620,15 @@ cudaError_t pack_for_plan(const cc_rings &rings, const SweepPlan &plan, int32_t 
     int32_t *st = status ? status : reinterpret_cast<int32_t *>(ws + plan.off_status);
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (plan.rpad + 255) / 256;
-    if (blocks > (int64_t)device_sm_count() * 16) blocks = (int64_t)device_sm_count() * 16;
+    int32_t *cnt = reinterpret_cast<int32_t *>(ws + plan.off_packcnt);
+    int64_t *nkept = reinterpret_cast<int64_t *>(ws + plan.off_nkept);
     TraceScope ts(CC_STAGE_PACK, s);
-    k_pack_rings<<<(unsigned)blocks, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta,
-                                                  rings.deta, rings.valid, rings.count,
-                                                  plan.rpad, rec);
+    const unsigned nb = (unsigned)plan.npack;
+    k_pack_count<<<nb, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta, rings.deta,
+                                    rings.valid, rings.count, cnt);
+    k_pack_scan<<<1, 1024, 0, s>>>(cnt, plan.npack, nkept);
+    k_pack_scatter<<<nb, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta, rings.deta,
+                                      rings.valid, rings.count, cnt, nkept, rec);
     return cudaGetLastError();
 }
 
@@ -564,9 +671,10 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     BlockBest *bbk = plan.nsplit > 1 ? nullptr : bb;
     const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
     void *fn = pick_sweep(plan.d, kcut);
-    void *args[] = {(void *)&rec,  (void *)&plan.tiles, (void *)&plan.ndb, (void *)&grid.x,
-                    (void *)&grid.y, (void *)&grid.z,   (void *)&M,        (void *)&kc2,
-                    (void *)&out,  (void *)&bbk,        (void *)&st};
+    const int64_t *nkept = reinterpret_cast<const int64_t *>(ws + plan.off_nkept);
+    void *args[] = {(void *)&rec,    (void *)&nkept, (void *)&plan.nsplit, (void *)&plan.ndb,
+                    (void *)&grid.x, (void *)&grid.y, (void *)&grid.z,     (void *)&M,
+                    (void *)&kc2,    (void *)&out,   (void *)&bbk,         (void *)&st};
     {
         TraceScope ts(CC_STAGE_SWEEP, s);
         e = cudaLaunchKernel(fn, dim3(grid_ctas), dim3(kThreads), args, 0, s);
@@ -597,7 +705,8 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
         if ((e = pack_for_plan(rings[b], pl, status ? status[b] : nullptr, ws[b], s))) return e;
         BurstDesc &d = a.b[b];
         d.rec = reinterpret_cast<const RingRec *>(ws[b] + pl.off_rec);
-        d.tiles = pl.tiles;
+        d.nkept = reinterpret_cast<const int64_t *>(ws[b] + pl.off_nkept);
+        d.nsplit = pl.nsplit;
         d.ndb = pl.ndb;
         d.out = pl.nsplit > 1 ? reinterpret_cast<float *>(ws[b] + pl.off_part) : maps[b];
         d.bb = pl.nsplit > 1 ? nullptr : reinterpret_cast<BlockBest *>(ws[b] + pl.off_bb);

@@ -34,19 +34,17 @@ BATCH_MAX = 64
 
 @dataclass
 class Burst:
-    """One request: events on the host (pinned), arrival time in seconds."""
+    """One request: its events on the host as one or more parts, each
+    (n [k] uint8, x, y, z, e [4, k] float32) pinned tensors or views of
+    pinned tensors whose rows are contiguous; arrival time in seconds."""
     bid: int
     arrival: float
-    n: torch.Tensor
-    x: torch.Tensor
-    y: torch.Tensor
-    z: torch.Tensor
-    e: torch.Tensor
+    parts: list
     source: np.ndarray | None = None
 
     @property
     def count(self):
-        return self.n.numel()
+        return sum(p[0].numel() for p in self.parts)
 
 
 @dataclass
@@ -96,10 +94,19 @@ class Server:
         s = torch.cuda.Stream(self.dev)
         a = _Active(b, s, burst_bytes(b.count, self.M, self.params, self.filter is not None), now)
         d = a.dev
+        N = b.count
         with torch.cuda.stream(s):
-            d["n"] = b.n.to(self.dev, non_blocking=True)
+            d["n"] = torch.empty(N, dtype=torch.uint8, device=self.dev)
             for k in "xyze":
-                d[k] = getattr(b, k).to(self.dev, non_blocking=True)
+                d[k] = torch.empty((4, N), dtype=torch.float32, device=self.dev)
+            off = 0
+            for part in b.parts:                 # one copy per contiguous row segment
+                k = part[0].numel()
+                d["n"][off:off + k].copy_(part[0], non_blocking=True)
+                for name, h in zip("xyze", part[1:]):
+                    for slot in range(4):
+                        d[name][slot, off:off + k].copy_(h[slot], non_blocking=True)
+                off += k
             d["rings"] = api.rings_from_events(d["n"], d["x"], d["y"], d["z"], d["e"],
                                                self.params, stream=s)
             if self.filter is not None:
@@ -219,17 +226,29 @@ class Server:
         return results, {"wall_s": wall, "batches": batches}
 
 
-def to_bursts(items) -> list[Burst]:
-    """Bursts (pinned host tensors) from synth.serving_bursts items."""
+def pin_pools(pools):
+    """The serving pools as pinned host tensors."""
+    conv = lambda ev: {k: torch.from_numpy(np.ascontiguousarray(ev[k])).pin_memory()
+                       for k in ("n", "x", "y", "z", "e")}
+    return {"src": [conv(p) for p in pools["src"]], "bkg": conv(pools["bkg"])}
+
+
+def to_bursts(pinned, specs) -> list[Burst]:
+    """Bursts from synth.serving_bursts specs over pinned pools: two parts
+    each (the source slice and the background slice), no copies on the host."""
     out = []
-    for i, it in enumerate(items):
-        ev = it["events"]
-        out.append(Burst(i, it["arrival"], torch.from_numpy(ev["n"]).pin_memory(),
-                         *(torch.from_numpy(ev[k]).pin_memory() for k in "xyze"),
-                         source=it["source"]))
+    for i, sp in enumerate(specs):
+        parts = []
+        for pool, (a, n) in ((pinned["src"][sp["dir"]], sp["src"]), (pinned["bkg"], sp["bkg"])):
+            if n > 0:
+                parts.append((pool["n"][a:a + n],) +
+                             tuple(pool[k][:, a:a + n] for k in ("x", "y", "z", "e")))
+        out.append(Burst(i, sp["arrival"], parts, source=sp["source"]))
     return out
 
 
 def make_bursts(n_bursts: int, rate_hz: float, seed: int, **kw) -> list[Burst]:
+    """Bursts of the serving workload (synth.serving_bursts)."""
     from . import synth
-    return to_bursts(synth.serving_bursts(n_bursts, rate_hz, seed, **kw))
+    pools, specs = synth.serving_bursts(n_bursts, rate_hz, seed, **kw)
+    return to_bursts(pin_pools(pools), specs)

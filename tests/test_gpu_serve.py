@@ -89,3 +89,55 @@ def test_server_mixed_stream_equals_alone(cc):
         assert (m["status"] == 0).all() or m["status"][1] == -5
     lat = np.array([r["latency"] for r in mixed.values()])
     assert (lat > 0).all()
+
+
+def test_sweep_compacts_to_the_kept_rings(cc):
+    """Rings that are invalid, non-finite or of zero width are left out of
+    the sweep (compacted away before it): the map equals the oracle's over
+    the kept rings, and the localisation of the kept subset alone."""
+    dev = torch.device("cuda:0")
+    grid_np = oracle.grid_healpix_ring(32)
+    grid = grid_to_dev(grid_np, dev)
+    p = cc.Params()
+    r_np = synth.rings_burst(n=40000, seed=9)[0]
+    rng = np.random.default_rng(9)
+    valid = (rng.uniform(size=40000) < 0.6).astype(np.uint8)
+    deta = np.asarray(r_np["deta"], np.float32).copy()
+    bad = rng.choice(40000, 300, replace=False)
+    deta[bad[:100]] = np.nan
+    deta[bad[100:200]] = 0.0
+    deta[bad[200:]] = -1.0
+    r_np = dict(r_np, deta=deta, valid=valid)
+    keep = (valid == 1) & np.isfinite(deta) & (deta > 0)
+    full = cc.localize(rings_to_dev(r_np, dev), grid, p)
+    sub = cc.localize(rings_to_dev({k: np.asarray(v)[keep] for k, v in r_np.items()}, dev), grid, p)
+    torch.cuda.synchronize()
+    got, want_sub = full[0].cpu().numpy(), sub[0].cpu().numpy()
+    np.testing.assert_allclose(got, want_sub, rtol=2e-6, atol=1e-6 * want_sub.max())
+    idx = np.arange(0, grid_np[0].size, 5)
+    want = oracle.likelihood_map({k: np.asarray(r_np[k], np.float32)[keep] for k in
+                                  ("ax", "ay", "az", "eta", "deta")}, grid_np, idx=idx)
+    bound = 1e-5 * np.maximum(want, 1e-3 * want.max())
+    assert (np.abs(got[idx] - want) <= bound).all()
+
+
+def test_server_learned_path_mixed_equals_alone(cc):
+    """The learned path (features, MLP, filter with tau > 0, then the sweep)
+    served in a mixed stream gives every burst its alone result."""
+    from paper_2411_04785_gb300 import serve
+    dev = torch.device("cuda:0")
+    grid = cc.grid_healpix_ring(32, dev)
+    p = cc.Params()
+    f = cc.RingFilter(dev, seed=3)
+    bursts = serve.make_bursts(12, rate_hz=400.0, seed=8, median=4000, hi=60000, n_dirs=2,
+                               pool_src=30000, pool_bkg=60000)
+    kw = dict(ring_filter=f, tau=0.3)
+    mixed, stats = serve.Server(grid, p, hbm_budget=256 << 20, max_active=8, **kw).run(
+        bursts, realtime=True, keep_maps=True)
+    assert len(mixed) == 12 and max(stats["batches"]) > 1
+    for b in bursts:
+        alone, _ = serve.Server(grid, p, **kw).run([b], realtime=False, keep_maps=True)
+        a, m = alone[b.bid], mixed[b.bid]
+        np.testing.assert_array_equal(m["map"], a["map"])
+        assert m["argmax"] == a["argmax"]
+        np.testing.assert_array_equal(m["dir"], a["dir"])
