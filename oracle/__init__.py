@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cluster.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -31,10 +32,10 @@ CFLAGS = ["-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to the source (gcc, a few seconds)."""
     if force or not os.path.exists(_LIB) or \
-            os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
-                                         os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            os.path.getmtime(_LIB) < max([os.path.getmtime(s) for s in _SRCS] +
+                                         [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        subprocess.run(["gcc", *CFLAGS, *_SRCS, "-o", tmp, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,6 +74,14 @@ def _load():
         lib.or_grid_fibonacci.restype = None
         lib.or_grid_healpix_ring.argtypes = [i64, P, P, P]
         lib.or_grid_healpix_ring.restype = i32
+        lib.or_maxstep_edges.argtypes = [P, i64, i64, P]
+        lib.or_maxstep_edges.restype = None
+        lib.or_events_from_edges.argtypes = [P, P, i64, P, P, P, P]
+        lib.or_events_from_edges.restype = i64
+        lib.or_fixed_window.argtypes = [P, P, i64, i64, i64, C.c_uint64, P, P, P, P]
+        lib.or_fixed_window.restype = i64
+        lib.or_spectrum.argtypes = [P, i64, C.c_uint64, i32, P]
+        lib.or_spectrum.restype = None
         _lib = lib
     return _lib
 
@@ -231,3 +240,52 @@ def grid_healpix_ring(nside):
     if _load().or_grid_healpix_ring(nside, _p(x), _p(y), _p(z)) != 0:
         raise ValueError("nside must be >= 1")
     return x, y, z
+
+
+# --------------------------------------------------------------------------
+# Event clustering of detections (cluster.c, Sec. 2)
+# --------------------------------------------------------------------------
+def _events_out(N):
+    K = N // 2 + 1
+    return (np.empty(N, np.int32), np.empty(K, np.int64), np.empty(K, np.int32),
+            np.empty(K, np.uint64))
+
+
+def maxstep_edges(t, dt_max):
+    """The edge array E of the max-step clustering (uint8 [N])."""
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    edge = np.empty(t.size, np.uint8)
+    _load().or_maxstep_edges(_p(t), t.size, int(dt_max), _p(edge))
+    return edge
+
+
+def maxstep_events(t, adc, dt_max):
+    """Max-step clustering: dict of edge [N], event_id [N] (-1 isolated),
+    first [K], count [K], adc [K] (uint64 sums)."""
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    adc = np.ascontiguousarray(adc, dtype=np.uint32)
+    edge = maxstep_edges(t, dt_max)
+    eid, first, count, s = _events_out(t.size)
+    K = _load().or_events_from_edges(_p(edge), _p(adc), t.size, _p(eid), _p(first),
+                                     _p(count), _p(s))
+    return {"edge": edge, "event_id": eid, "first": first[:K], "count": count[:K],
+            "adc": s[:K]}
+
+
+def fixed_window_events(t, adc, window, n_min, adc_min):
+    """The prior-art fixed-length non-overlapping window (sequential)."""
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    adc = np.ascontiguousarray(adc, dtype=np.uint32)
+    N = t.size
+    eid, first, count, s = (np.empty(N, np.int32), np.empty(N + 1, np.int64),
+                            np.empty(N + 1, np.int32), np.empty(N + 1, np.uint64))
+    K = _load().or_fixed_window(_p(t), _p(adc), N, int(window), int(n_min), int(adc_min),
+                                _p(eid), _p(first), _p(count), _p(s))
+    return {"event_id": eid, "first": first[:K], "count": count[:K], "adc": s[:K]}
+
+
+def spectrum(adc_sum, bin_width, nbins):
+    a = np.ascontiguousarray(adc_sum, dtype=np.uint64)
+    h = np.empty(nbins, np.uint64)
+    _load().or_spectrum(_p(a), a.size, int(bin_width), int(nbins), _p(h))
+    return h

@@ -80,4 +80,17 @@ int or_refine(int64_t R, const double *ax, const double *ay, const double *az,
 void or_grid_fibonacci(int64_t n, double *x, double *y, double *z);
 int or_grid_healpix_ring(int64_t nside, double *x, double *y, double *z);
 
+/* Event clustering of time-sorted detections (cluster.c, Sec. 2). */
+void or_maxstep_edges(const int64_t *t, int64_t N, int64_t dt_max, uint8_t *edge);
+int64_t or_events_from_edges(const uint8_t *edge, const uint32_t *adc, int64_t N,
+                             int32_t *event_id, int64_t *first, int32_t *count,
+                             uint64_t *adc_sum);
+int64_t or_fixed_window(const int64_t *t, const uint32_t *adc, int64_t N, int64_t window,
+                        int64_t n_min, uint64_t adc_min, int32_t *event_id, int64_t *first,
+                        int32_t *count, uint64_t *adc_sum);
+/* Histogram of event amplitudes: bin = adc / bin_width, the last bin also
+ * takes everything above it. */
+void or_spectrum(const uint64_t *adc_sum, int64_t K, uint64_t bin_width, int32_t nbins,
+                 uint64_t *hist);
+
 #endif

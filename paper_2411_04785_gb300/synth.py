@@ -308,24 +308,29 @@ def training_events(n_events: int, seed: int, bkg_ratio: float = 3.0, chunk: int
     return out
 
 
+
 def serving_bursts(n_bursts: int = 2000, rate_hz: float = 50.0, seed: int = 5,
                    median: int = 20000, sigma: float = 1.0, lo: int = 500, hi: int = 300000,
                    bkg_lo: float = 1.0, bkg_hi: float = 50.0, n_dirs: int = 16,
                    pool_src: int = 160000, pool_bkg: int = 320000):
     """The serving workload: Poisson arrivals at rate_hz; event counts
     log-normal (median, sigma) truncated to [lo, hi]; background ratio uniform
-    in [bkg_lo, bkg_hi]; the source direction one of n_dirs random directions.
-    Events are drawn without replacement (within a burst) from pools simulated
-    once: pool_src source events per direction and pool_bkg isotropic
-    background events.  Returns a list of dicts: arrival (s), source, and the
-    event arrays n [N], x, y, z, e [4, N] float32."""
+    in [bkg_lo, bkg_hi]; the source one of n_dirs random directions.
+
+    Events come from pools simulated once (pool_src source events per
+    direction, pool_bkg isotropic background events, each pool in random
+    order): a burst is a contiguous slice of its direction's source pool plus
+    a contiguous slice of the background pool, at random offsets.  Returns
+    (pools, specs): pools = {"src": [event dict per direction], "bkg": event
+    dict}; specs = list of {"arrival" (s), "dir", "source", "src": (offset,
+    count), "bkg": (offset, count)}."""
     rng = np.random.Generator(np.random.PCG64(seed))
     dirs = random_units(rng, n_dirs)
-    src_pools = [simulate_events(n_src=pool_src, n_bkg=0, seed=seed * 7919 + d, source=dirs[d])
-                 for d in range(n_dirs)]
-    bkg = simulate_events(n_src=0, n_bkg=pool_bkg, seed=seed * 7919 + n_dirs)
+    pools = {"src": [simulate_events(n_src=pool_src, n_bkg=0, seed=seed * 7919 + d,
+                                     source=dirs[d]) for d in range(n_dirs)],
+             "bkg": simulate_events(n_src=0, n_bkg=pool_bkg, seed=seed * 7919 + n_dirs)}
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n_bursts))
-    out = []
+    specs = []
     for i in range(n_bursts):
         while True:
             N = int(round(median * math.exp(sigma * rng.standard_normal())))
@@ -335,13 +340,62 @@ def serving_bursts(n_bursts: int = 2000, rate_hz: float = 50.0, seed: int = 5,
         n_src = min(pool_src, max(1, int(round(N / (1.0 + ratio)))))
         n_bkg = min(pool_bkg, N - n_src)
         d = int(rng.integers(n_dirs))
-        si = rng.choice(pool_src, n_src, replace=False)
-        bi = rng.choice(pool_bkg, n_bkg, replace=False)
-        order = rng.permutation(n_src + n_bkg)
-        ev = {"n": np.concatenate([src_pools[d]["n"][si], bkg["n"][bi]])[order]}
-        for k in ("x", "y", "z", "e"):
-            ev[k] = np.ascontiguousarray(
-                np.concatenate([src_pools[d][k][:, si], bkg[k][:, bi]], axis=1)[:, order])
-        ev["is_source"] = np.concatenate([np.ones(n_src, bool), np.zeros(n_bkg, bool)])[order]
-        out.append({"arrival": float(t[i]), "source": dirs[d], "events": ev})
-    return out
+        a = int(rng.integers(pool_src - n_src + 1))
+        b = int(rng.integers(pool_bkg - n_bkg + 1))
+        specs.append({"arrival": float(t[i]), "dir": d, "source": dirs[d],
+                      "src": (a, n_src), "bkg": (b, n_bkg)})
+    return pools, specs
+
+
+def burst_events(pools, spec):
+    """The events of one serving burst as one event dict (source slice then
+    background slice), with is_source."""
+    (a, ns), (b, nb) = spec["src"], spec["bkg"]
+    S, B = pools["src"][spec["dir"]], pools["bkg"]
+    ev = {"n": np.concatenate([S["n"][a:a + ns], B["n"][b:b + nb]]),
+          "is_source": np.concatenate([np.ones(ns, bool), np.zeros(nb, bool)]),
+          "source": spec["source"]}
+    for k in ("x", "y", "z", "e"):
+        ev[k] = np.ascontiguousarray(np.concatenate([S[k][:, a:a + ns], B[k][:, b:b + nb]], 1))
+    return ev
+
+
+def detection_stream(n_events: int = 400_000, seed: int = 21, event_rate_hz: float = 2.0e5,
+                     mean_det: float = 12.0, tau_ns: float = 28.0, jitter_ns: float = 0.5,
+                     dark_rate_hz: float = 1.0e6, adc_per_kev: float = 10.0,
+                     pe_adc: int = 8, photopeak_frac: float = 0.35):
+    """Time-sorted detections of a monolithic scintillator read out by a
+    pixelated photodetector under a 662 keV (137Cs-like) source.
+
+    Events arrive as a Poisson process at event_rate_hz; each gives
+    1 + Poisson(mean_det - 1) detections, delayed from the event time by the
+    scintillation decay (exponential, tau_ns) plus Gaussian jitter
+    (jitter_ns).  Its energy is the 662 keV photopeak (photopeak_frac of
+    events) or the Compton continuum (uniform below the 477 keV edge), split
+    among its detections by a flat Dirichlet draw.  Dark counts (single
+    detections of 1-3 photoelectrons, pe_adc channels each) arrive as a
+    Poisson process at dark_rate_hz.  Times are int64 picoseconds from 0,
+    amplitudes uint32 ADC channels.
+
+    Returns (t [N] int64 sorted, adc [N] uint32, truth [N] int64: the
+    generating event of each detection, -1 for dark counts)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t_ev = np.cumsum(rng.exponential(1e12 / event_rate_hz, n_events))     # ps
+    span = t_ev[-1] + 1e6 if n_events else 0.0
+    k = 1 + rng.poisson(mean_det - 1.0, n_events)
+    e_kev = np.where(rng.uniform(size=n_events) < photopeak_frac, 662.0,
+                     rng.uniform(0.0, 477.0, n_events))
+    owner = np.repeat(np.arange(n_events), k)
+    delay = rng.exponential(tau_ns * 1e3, owner.size) + rng.normal(0.0, jitter_ns * 1e3, owner.size)
+    t_det = t_ev[owner] + np.abs(delay)
+    share = rng.exponential(1.0, owner.size)                 # flat Dirichlet per event
+    tot = np.bincount(owner, weights=share, minlength=n_events)
+    adc_det = np.maximum(1, np.round(share / tot[owner] * e_kev[owner] * adc_per_kev))
+    n_dark = rng.poisson(dark_rate_hz * span * 1e-12)
+    t_dark = rng.uniform(0.0, span, n_dark)
+    adc_dark = pe_adc * rng.integers(1, 4, n_dark)
+    t = np.concatenate([t_det, t_dark])
+    adc = np.concatenate([adc_det, adc_dark])
+    truth = np.concatenate([owner, -np.ones(n_dark, np.int64)])
+    order = np.argsort(t, kind="stable")
+    return (np.round(t[order]).astype(np.int64), adc[order].astype(np.uint32), truth[order])
