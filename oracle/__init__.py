@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "cluster.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "cluster.c"), os.path.join(_HERE, "nearfield.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -82,6 +82,13 @@ def _load():
         lib.or_fixed_window.restype = i64
         lib.or_spectrum.argtypes = [P, i64, C.c_uint64, i32, P]
         lib.or_spectrum.restype = None
+        lib.or_ring_apex.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
+        lib.or_ring_apex.restype = None
+        lib.or_backproject.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, P, P, i64, f64,
+                                       i32, P]
+        lib.or_backproject.restype = None
+        lib.or_universe.argtypes = [i32, i64, f64, f64, f64, f64, P, P, P]
+        lib.or_universe.restype = i64
         _lib = lib
     return _lib
 
@@ -289,3 +296,50 @@ def spectrum(adc_sum, bin_width, nbins):
     h = np.empty(nbins, np.uint64)
     _load().or_spectrum(_p(a), a.size, int(bin_width), int(nbins), _p(h))
     return h
+
+
+# --------------------------------------------------------------------------
+# Near-field back projection (nearfield.c, Sec. 3)
+# --------------------------------------------------------------------------
+UNIVERSES = {"cube": 0, "cylinder": 1, "sphere": 2}
+
+
+def ring_apex(ev, rings):
+    """Apex (first interaction site) of each valid ring: [N, 3] float64."""
+    n = np.ascontiguousarray(ev["n"], dtype=np.uint8)
+    N = n.size
+    x, y, z = (_f64(ev[k]) for k in ("x", "y", "z"))
+    stride = x.shape[1] if x.ndim == 2 else N
+    out = [np.zeros(N) for _ in range(3)]
+    _load().or_ring_apex(N, stride, _p(n), _p(x), _p(y), _p(z),
+                         _p(np.ascontiguousarray(rings["perm"], dtype=np.uint8)),
+                         _p(np.ascontiguousarray(rings["valid"], dtype=np.uint8)), *map(_p, out))
+    return np.stack(out, 1)
+
+
+def backproject(rings, apex, vox, idx=None, k_cut=0.0, nthreads=None):
+    """Image value at voxels vox[idx] (all voxels when idx is None)."""
+    ax, ay, az, eta, deta, valid = _rings64(rings)
+    p = _f64(apex)
+    px, py, pz = (np.ascontiguousarray(p[:, c]) for c in range(3))
+    vx, vy, vz = (_f64(v) for v in vox)
+    idx = np.arange(vx.size, dtype=np.int64) if idx is None else \
+        np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(idx.size)
+    _load().or_backproject(ax.size, _p(px), _p(py), _p(pz), _p(ax), _p(ay),
+                           _p(az), _p(eta), _p(deta), _p(valid), _p(vx), _p(vy),
+                           _p(vz), _p(idx), idx.size, float(k_cut),
+                           int(nthreads or os.cpu_count() or 1), _p(out))
+    return out
+
+
+def universe(shape, n, pitch, center=(0.0, 0.0, 0.0), count_only=False):
+    """Voxel centres of the image universe ('cube', 'cylinder', 'sphere')."""
+    L = _load()
+    s = UNIVERSES[shape]
+    m = L.or_universe(s, n, pitch, *center, None, None, None)
+    if count_only:
+        return m
+    out = [np.zeros(m) for _ in range(3)]
+    L.or_universe(s, n, pitch, *center, *map(_p, out))
+    return tuple(out)

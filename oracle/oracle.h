@@ -93,4 +93,18 @@ int64_t or_fixed_window(const int64_t *t, const uint32_t *adc, int64_t N, int64_
 void or_spectrum(const uint64_t *adc_sum, int64_t K, uint64_t bin_width, int32_t nbins,
                  uint64_t *hist);
 
+/* Near-field back projection (nearfield.c, Sec. 3). */
+void or_ring_apex(int64_t count, int64_t stride, const uint8_t *n, const double *x,
+                  const double *y, const double *z, const uint8_t *perm, const uint8_t *valid,
+                  double *px, double *py, double *pz);
+void or_backproject(int64_t R, const double *px, const double *py, const double *pz,
+                    const double *ax, const double *ay, const double *az, const double *eta,
+                    const double *deta, const uint8_t *valid, const double *vx,
+                    const double *vy, const double *vz, const int64_t *idx, int64_t nidx,
+                    double k_cut, int nthreads, double *out);
+/* shape 0 cube, 1 cylinder (axis z), 2 sphere; x/y/z may be NULL (count
+ * only).  Returns the number of voxels. */
+int64_t or_universe(int shape, int64_t n, double pitch, double cx, double cy, double cz,
+                    double *x, double *y, double *z);
+
 #endif
