@@ -305,6 +305,121 @@ cc_status cc_mlp_apply_filter(const float *out, const cc_rings *rings,
                               void *stream);
 
 /*
+ * Event clustering of monolithic-scintillator detections (Sec. 2 of the
+ * paper: events delimited by a maximum step between consecutive detections).
+ *
+ * Detections, sorted by time (non-decreasing t): t [count] int64 time stamps
+ * in any tick unit, 8-byte aligned; adc [count] uint32 amplitudes (ADC
+ * channels), 4-byte aligned, may be NULL when no amplitude sums are asked for.
+ * Device pointers, owned by the caller.
+ */
+typedef struct {
+    const int64_t *t;
+    const uint32_t *adc;
+    int64_t count;
+} cc_detections;
+
+/* Workspace bytes of cc_cluster_maxstep for `count` detections. */
+size_t cc_cluster_workspace_bytes(int64_t count);
+
+/*
+ * Max-step clustering (Sec. 2): with M_i = (t[i+1] - t[i] < dt_max) the mask
+ * of the step after detection i (no step before the first or after the last
+ * detection: false), the edge of detection i is
+ *   edge[i] = M_{i-1} XOR M_i                      (uint8, the paper's E)
+ * and a run of detections joined by masked steps is one event.  Events are
+ * numbered 0, 1, ... in time order:
+ *   event_id[i]  event of detection i, -1 for an isolated detection (int32)
+ *   ev_first[k]  index of event k's first detection (int64)
+ *   ev_count[k]  its number of detections, >= 2 (int32)
+ *   ev_adc[k]    the sum of its amplitudes (uint64, exact)
+ *   n_events[0]  the number of events (int64, written on the device)
+ * Steps are taken in wrapping 64-bit arithmetic (meaningful for |step| <
+ * 2^63); unsorted input is not an error, a negative step simply counts as
+ * below dt_max.  Every output pointer may be NULL (not written); the per-event
+ * arrays hold ev_capacity >= count / 2 entries (the most events count
+ * detections can make).  status [1] int32 (may be NULL) receives
+ * CC_ETIMEOUT if a bounded wait between CTAs gave up (no result is then
+ * valid).  0 <= count <= 2^31 - 1; count = 0 writes n_events = 0.  Workspace:
+ * cc_cluster_workspace_bytes(count) bytes, 256-byte aligned.  One kernel
+ * launch; asynchronous on `stream`.
+ */
+cc_status cc_cluster_maxstep(const cc_detections *d, int64_t dt_max, uint8_t *edge,
+                             int32_t *event_id, int64_t *ev_first, int32_t *ev_count,
+                             uint64_t *ev_adc, int64_t ev_capacity, int64_t *n_events,
+                             int32_t *status, void *workspace, size_t ws_bytes,
+                             void *stream);
+
+/*
+ * Amplitude spectrum of the events (the validation of Sec. 2): hist[b]
+ * (uint64 [nbins], device) counts the events with ev_adc / bin_width == b,
+ * the last bin also those above it.  n_events is the device count written by
+ * cc_cluster_maxstep.  bin_width >= 1, nbins >= 1.
+ */
+cc_status cc_cluster_spectrum(const uint64_t *ev_adc, const int64_t *n_events,
+                              uint64_t bin_width, int32_t nbins, uint64_t *hist,
+                              void *stream);
+
+/*
+ * Near-field 3D back projection (Sec. 3 of the paper): every (gamma-ray,
+ * voxel) pair contributes "the probability the gamma-ray came from the voxel
+ * centre", summed per voxel into an image.
+ *
+ * A gamma-ray is its ring (cone axis a, energetic half angle eta, width deta,
+ * as cc_rings_from_events builds them) plus the cone's apex p, the first
+ * interaction site of the chosen order.  For voxel centre v the geometric
+ * Compton angle is theta = angle(v - p, a), the angle between the incoming
+ * direction (voxel -> first site) and the outgoing one (first -> second
+ * site), and the contribution is exp(-r^2/2), r = (theta - eta)/deta, left
+ * out for |r| > k_cut when p->k_cut > 0 (the angular selection of voxels).
+ */
+
+/* Apex of every ring: (px, py, pz)[i] = position of the first site of ring
+ * i's chosen order (rings->perm); 0 for invalid rings.  Device arrays of
+ * ev->count floats; rings->count == ev->count. */
+cc_status cc_ring_apex(const cc_events *ev, const cc_rings *rings, float *px,
+                       float *py, float *pz, void *stream);
+
+/* Image universes (Sec. 3, spatial optimisation): the n^3 voxels of side
+ * `pitch` of a cube centred on (cx, cy, cz) (shape 0), or those whose centres
+ * lie in the inscribed cylinder with axis along z (shape 1, about pi/4 of the
+ * cube) or the inscribed sphere (shape 2, about pi/6).  Voxel (i, j, k) has
+ * centre c + pitch/2 (2i+1-n, 2j+1-n, 2k+1-n), computed in FP64 and rounded
+ * once to FP32; "inside" is the exact integer test on those odd offsets
+ * (sum of squares <= n^2).  Voxels are listed z-major, then y, then x.
+ * cc_voxel_count returns their number (host arithmetic, no GPU; -1 for bad
+ * arguments); cc_voxel_universe writes them to device arrays x, y, z of that
+ * length.  1 <= n <= CC_VOXEL_MAX_N. */
+#define CC_VOXEL_MAX_N 1024
+int64_t cc_voxel_count(int32_t shape, int32_t n);
+cc_status cc_voxel_universe(int32_t shape, int32_t n, float pitch, float cx,
+                            float cy, float cz, float *x, float *y, float *z,
+                            void *stream);
+
+/* Workspace bytes of cc_backproject (0 for bad arguments or no device). */
+size_t cc_backproject_workspace_bytes(int64_t rings, int64_t voxels,
+                                      const cc_params *p);
+
+/*
+ * The back projection: image[v] = sum over valid rings with finite values
+ * and deta > 0 of exp(-r^2/2) (FP32, Kahan-compensated 128-ring tile sums,
+ * fixed-order split reduction), r as above; argmax[0] = the voxel with the
+ * largest value (ties: lowest index).  Rings are compacted before the sweep,
+ * so its time follows the kept rings.  rings: as from cc_rings_from_events;
+ * px, py, pz: apexes [rings->count]; voxels: centres (any layout, e.g. from
+ * cc_voxel_universe), 1 <= voxels->count <= 2^31 - 1; image [voxels->count]
+ * float, argmax [1] int32, status [1] int32 (may be NULL; CC_ETIMEOUT if a
+ * bounded wait gave up).  A voxel centre that coincides with an apex is a
+ * degenerate pair with a finite but unspecified contribution.  Workspace:
+ * cc_backproject_workspace_bytes() bytes, 256-byte aligned.  All pointers
+ * but rings, voxels and p are device pointers; asynchronous on `stream`.
+ */
+cc_status cc_backproject(const cc_rings *rings, const float *px, const float *py,
+                         const float *pz, const cc_grid *voxels, const cc_params *p,
+                         float *image, int32_t *argmax, int32_t *status,
+                         void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
  * counted per stage; when tracing is enabled each launch is also bracketed by
  * two CUDA events recorded on the launching stream, and cc_trace_read()
@@ -321,7 +436,9 @@ typedef enum {
     CC_STAGE_REFINE = 6,  /* Gauss-Newton refinement */
     CC_STAGE_GRID = 7,    /* grid generation */
     CC_STAGE_MLP = 8,     /* learned ring filter (features, MLP, training, filter) */
-    CC_STAGE_COUNT = 9
+    CC_STAGE_CLUSTER = 9, /* event clustering of detections and its spectrum */
+    CC_STAGE_VOXEL = 10,  /* near-field back projection (apex, universe, sweep) */
+    CC_STAGE_COUNT = 11
 } cc_stage;
 
 typedef struct {

@@ -6,4 +6,6 @@ from .api import (CCError, Localizer, Params, default_params, empty_rings,  # no
                   grid_fibonacci, grid_gather, grid_healpix_ring, lib,
                   localize, localize_static, localize_workspace_bytes, refine, refine_workspace_bytes,
                   rings_from_events, trace_enable, trace_read,
-                  RingFilter, ring_features, ring_residuals)
+                  RingFilter, ring_features, ring_residuals,
+                  cluster_maxstep, cluster_spectrum, cluster_workspace_bytes,
+                  ring_apex, voxel_count, voxel_universe, backproject, backproject_workspace_bytes)

@@ -44,11 +44,16 @@ class cc_grid(C.Structure):
     _fields_ = [("x", _P), ("y", _P), ("z", _P), ("count", C.c_int64)]
 
 
+class cc_detections(C.Structure):
+    _fields_ = [("t", _P), ("adc", _P), ("count", C.c_int64)]
+
+
 class cc_stage_time(C.Structure):
     _fields_ = [("launches", C.c_int64), ("ms", C.c_double)]
 
 
-STAGES = ("recon", "pack", "sweep", "reduce", "select", "gather", "refine", "grid", "mlp")
+STAGES = ("recon", "pack", "sweep", "reduce", "select", "gather", "refine", "grid", "mlp",
+          "cluster", "voxel")
 
 
 class CCError(RuntimeError):
@@ -118,6 +123,25 @@ def lib() -> C.CDLL:
         L.cc_localize_batch.argtypes = [C.c_int32, C.POINTER(cc_rings), C.POINTER(cc_grid),
                                         C.POINTER(cc_params), _P, _P, _P, _P, _P, _P, _P]
         L.cc_localize_batch.restype = S
+        L.cc_cluster_workspace_bytes.argtypes = [C.c_int64]
+        L.cc_cluster_workspace_bytes.restype = C.c_size_t
+        L.cc_cluster_maxstep.argtypes = [C.POINTER(cc_detections), C.c_int64, _P, _P, _P, _P, _P,
+                                         C.c_int64, _P, _P, _P, C.c_size_t, _P]
+        L.cc_cluster_maxstep.restype = S
+        L.cc_cluster_spectrum.argtypes = [_P, _P, C.c_uint64, C.c_int32, _P, _P]
+        L.cc_cluster_spectrum.restype = S
+        L.cc_ring_apex.argtypes = [C.POINTER(cc_events), C.POINTER(cc_rings), _P, _P, _P, _P]
+        L.cc_ring_apex.restype = S
+        L.cc_voxel_count.argtypes = [C.c_int32, C.c_int32]
+        L.cc_voxel_count.restype = C.c_int64
+        L.cc_voxel_universe.argtypes = [C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_float,
+                                        C.c_float, _P, _P, _P, _P]
+        L.cc_voxel_universe.restype = S
+        L.cc_backproject_workspace_bytes.argtypes = [C.c_int64, C.c_int64, C.POINTER(cc_params)]
+        L.cc_backproject_workspace_bytes.restype = C.c_size_t
+        L.cc_backproject.argtypes = [C.POINTER(cc_rings), _P, _P, _P, C.POINTER(cc_grid),
+                                     C.POINTER(cc_params), _P, _P, _P, _P, C.c_size_t, _P]
+        L.cc_backproject.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -550,3 +574,123 @@ def ring_residuals(rings: dict, sources):
     cr = torch.linalg.cross(a, s, dim=1).norm(dim=1)
     th = torch.atan2(cr, (a * s).sum(1))
     return (th - rings["eta"].double()).float().contiguous()
+
+
+# --------------------------------------------------------------------------
+# event clustering of detections (Sec. 2)
+# --------------------------------------------------------------------------
+CLUSTER_OUTPUTS = ("edge", "event_id", "first", "count", "adc")
+
+
+def cluster_workspace_bytes(n: int) -> int:
+    return int(lib().cc_cluster_workspace_bytes(n))
+
+
+def cluster_maxstep(t, adc, dt_max: int, outputs=CLUSTER_OUTPUTS, out: dict | None = None,
+                    workspace=None, stream=None) -> dict:
+    """Max-step clustering of time-sorted detections: t [N] int64, adc [N]
+    uint32 (or None) device tensors.  Returns device tensors: the requested
+    outputs among edge [N] u8, event_id [N] i32, first / count / adc
+    [N // 2 + 1] (i64 / i32 / u64; the first n_events entries are events), and
+    n_events [1] i64, status [1] i32 (asynchronous)."""
+    _need(t, torch.int64, "t")
+    _need(adc, torch.uint32, "adc")
+    N = t.numel()
+    dev = t.device
+    K = N // 2 + 1
+    shapes = {"edge": (N, torch.uint8), "event_id": (N, torch.int32), "first": (K, torch.int64),
+              "count": (K, torch.int32), "adc": (K, torch.uint64)}
+    o = dict(out or {})
+    for k in outputs:
+        if k not in o:
+            n, dt = shapes[k]
+            o[k] = torch.empty(n, dtype=dt, device=dev)
+    o.setdefault("n_events", torch.empty(1, dtype=torch.int64, device=dev))
+    o.setdefault("status", torch.empty(1, dtype=torch.int32, device=dev))
+    need = cluster_workspace_bytes(N)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    d = cc_detections(t.data_ptr() if N else None, adc.data_ptr() if adc is not None and N else None, N)
+    g = lambda k: _ptr(o.get(k)) if k in outputs else None
+    _check("cc_cluster_maxstep", lib().cc_cluster_maxstep(
+        C.byref(d), int(dt_max), g("edge"), g("event_id"), g("first"), g("count"), g("adc"), K,
+        _ptr(o["n_events"]), _ptr(o["status"]), _ptr(workspace), workspace.numel(),
+        _stream(stream)))
+    return o
+
+
+def cluster_spectrum(ev_adc, n_events, bin_width: int, nbins: int, out=None, stream=None):
+    """Histogram (uint64 [nbins], device) of event amplitude sums."""
+    h = out if out is not None else torch.empty(nbins, dtype=torch.uint64, device=ev_adc.device)
+    _check("cc_cluster_spectrum", lib().cc_cluster_spectrum(
+        _ptr(ev_adc), _ptr(n_events), int(bin_width), int(nbins), _ptr(h), _stream(stream)))
+    return h
+
+
+# --------------------------------------------------------------------------
+# near-field back projection (Sec. 3)
+# --------------------------------------------------------------------------
+UNIVERSES = {"cube": 0, "cylinder": 1, "sphere": 2}
+
+
+def ring_apex(n, x, y, z, rings: dict, out=None, stream=None):
+    """Apex (first site of the chosen order) of every ring: (px, py, pz)."""
+    N = n.numel()
+    dev = n.device
+    o = out if out is not None else tuple(torch.empty(N, dtype=torch.float32, device=dev)
+                                          for _ in range(3))
+    _need(n, torch.uint8, "n")
+    for t, nm in ((x, "x"), (y, "y"), (z, "z")):
+        _need(t, torch.float32, nm)
+        if t.dim() != 2 or t.shape[0] != 4 or t.shape[1] < N or t.shape[1] != x.shape[1]:
+            raise ValueError(f"{nm} must be [4, S] with S >= N, one stride for x, y, z")
+    ev = cc_events(_ptr(n), _ptr(x), _ptr(y), _ptr(z), None, N, x.shape[1])
+    _check("cc_ring_apex", lib().cc_ring_apex(C.byref(ev), C.byref(_rings_struct(rings)),
+                                               *(_ptr(t) for t in o), _stream(stream)))
+    return o
+
+
+def voxel_count(shape: str, n: int) -> int:
+    c = int(lib().cc_voxel_count(UNIVERSES[shape], n))
+    if c < 0:
+        raise ValueError(f"bad universe ({shape}, {n})")
+    return c
+
+
+def voxel_universe(shape: str, n: int, pitch: float, center=(0.0, 0.0, 0.0), device="cuda",
+                   stream=None):
+    """Voxel centres of the image universe as (x, y, z) device tensors."""
+    m = voxel_count(shape, n)
+    out = tuple(torch.empty(m, dtype=torch.float32, device=device) for _ in range(3))
+    _check("cc_voxel_universe", lib().cc_voxel_universe(
+        UNIVERSES[shape], n, float(pitch), *(float(c) for c in center), *(_ptr(t) for t in out),
+        _stream(stream)))
+    return out
+
+
+def backproject_workspace_bytes(R: int, V: int, params: Params | None = None) -> int:
+    params = params or Params()
+    return int(lib().cc_backproject_workspace_bytes(R, V, C.byref(params.c())))
+
+
+def backproject(rings: dict, apex, voxels, params: Params | None = None, workspace=None,
+                out=None, stream=None):
+    """Near-field image over the voxels.  Returns (image [V] f32, argmax [1]
+    i32, status [1] i32) device tensors (asynchronous)."""
+    params = params or Params()
+    rs = _rings_struct(rings)
+    vs = _grid_struct(voxels)
+    dev = voxels[0].device
+    V = vs.count
+    need = backproject_workspace_bytes(rs.count, V, params)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = (torch.empty(V, dtype=torch.float32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev),
+               torch.empty(1, dtype=torch.int32, device=dev))
+    _check("cc_backproject", lib().cc_backproject(
+        C.byref(rs), *(_ptr(t) for t in apex), C.byref(vs), C.byref(params.c()),
+        _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(workspace), workspace.numel(),
+        _stream(stream)))
+    return out

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcompton.so")
-SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu",
+SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu", "cluster.cu", "voxel.cu",
            "noalloc.cu", "mlp.cu"]
 HEADERS = ["cc_internal.cuh", "cc_math.cuh", os.path.join("..", "..", "include", "compton.h")]
 

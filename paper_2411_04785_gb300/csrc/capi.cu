@@ -2,6 +2,7 @@
 // workspace planning, per-thread error messages.  Every entry point either
 // returns CC_EINVAL before launching anything, or enqueues its kernels on the
 // caller's stream and returns CC_OK / CC_ECUDA.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -330,6 +331,115 @@ cc_status cc_mlp_apply_filter(const float *out, const cc_rings *rings, float tau
     if (!(deta_min > 0.0f) || !(deta_max >= deta_min)) return fail(CC_EINVAL, "bad deta clamp");
     cudaError_t e = mlp_apply_filter(out, *rings, tau, deta_min, deta_max, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_apply_filter launch");
+    return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// event clustering of detections (Sec. 2)
+// ---------------------------------------------------------------------------
+size_t cc_cluster_workspace_bytes(int64_t count) {
+    return count < 0 ? 0 : cluster_workspace_bytes(count);
+}
+
+cc_status cc_cluster_maxstep(const cc_detections *d, int64_t dt_max, uint8_t *edge,
+                             int32_t *event_id, int64_t *ev_first, int32_t *ev_count,
+                             uint64_t *ev_adc, int64_t ev_capacity, int64_t *n_events,
+                             int32_t *status, void *workspace, size_t ws_bytes, void *stream) {
+    g_err[0] = 0;
+    if (!d) return fail(CC_EINVAL, "detections is NULL");
+    if (d->count < 0 || d->count > INT32_MAX)
+        return fail(CC_EINVAL, "need 0 <= detections->count <= 2^31 - 1");
+    if (d->count > 0 && !d->t) return fail(CC_EINVAL, "detections->t is NULL");
+    if (ev_adc && d->count > 0 && !d->adc) return fail(CC_EINVAL, "ev_adc needs detections->adc");
+    if ((ev_first || ev_count || ev_adc) && ev_capacity < d->count / 2)
+        return fail(CC_EINVAL, "ev_capacity < count / 2 (the most events count detections make)");
+    if (!workspace || ws_bytes < cluster_workspace_bytes(d->count))
+        return fail(CC_EINVAL, "workspace too small (cc_cluster_workspace_bytes)");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(CC_EINVAL, "workspace not 256-byte aligned");
+    if (((uintptr_t)d->t & 7u) != 0 || ((uintptr_t)d->adc & 3u) != 0)
+        return fail(CC_EINVAL, "misaligned detection arrays");
+    cudaError_t e = launch_cluster(d->t, d->adc, d->count, dt_max, edge, event_id, ev_first,
+                                   ev_count, ev_adc, n_events, status, (char *)workspace,
+                                   (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
+    return CC_OK;
+}
+
+cc_status cc_cluster_spectrum(const uint64_t *ev_adc, const int64_t *n_events, uint64_t bin_width,
+                              int32_t nbins, uint64_t *hist, void *stream) {
+    g_err[0] = 0;
+    if (!ev_adc || !n_events || !hist) return fail(CC_EINVAL, "NULL argument");
+    if (bin_width < 1 || nbins < 1) return fail(CC_EINVAL, "need bin_width >= 1 and nbins >= 1");
+    cudaError_t e = launch_spectrum(ev_adc, n_events, bin_width, nbins, hist, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
+    return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// near-field back projection (Sec. 3)
+// ---------------------------------------------------------------------------
+cc_status cc_ring_apex(const cc_events *ev, const cc_rings *rings, float *px, float *py,
+                       float *pz, void *stream) {
+    g_err[0] = 0;
+    if (!ev || !rings) return fail(CC_EINVAL, "events/rings is NULL");
+    if (ev->count < 0 || ev->stride < ev->count || rings->count != ev->count)
+        return fail(CC_EINVAL, "bad counts (need 0 <= count <= stride, rings->count == count)");
+    if (ev->stride > (INT64_MAX / 4)) return fail(CC_EINVAL, "events->stride too large");
+    if (ev->count == 0) return CC_OK;
+    if (!ev->n || !ev->x || !ev->y || !ev->z || !rings->perm || !rings->valid || !px || !py ||
+        !pz)
+        return fail(CC_EINVAL, "event, ring and apex arrays must be non-NULL");
+    cudaError_t e = launch_ring_apex(*ev, *rings, px, py, pz, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ring_apex launch");
+    return CC_OK;
+}
+
+int64_t cc_voxel_count(int32_t shape, int32_t n) {
+    if (shape < 0 || shape > 2 || n < 1 || n > CC_VOXEL_MAX_N) return -1;
+    return universe_count(shape, n);
+}
+
+cc_status cc_voxel_universe(int32_t shape, int32_t n, float pitch, float cx, float cy, float cz,
+                            float *x, float *y, float *z, void *stream) {
+    g_err[0] = 0;
+    if (shape < 0 || shape > 2) return fail(CC_EINVAL, "shape must be 0 (cube), 1 (cylinder) or 2 (sphere)");
+    if (n < 1 || n > CC_VOXEL_MAX_N) return fail(CC_EINVAL, "need 1 <= n <= CC_VOXEL_MAX_N");
+    if (!(pitch > 0.0f) || !isfinite(cx) || !isfinite(cy) || !isfinite(cz))
+        return fail(CC_EINVAL, "need pitch > 0 and a finite centre");
+    if (!x || !y || !z) return fail(CC_EINVAL, "x, y, z must be non-NULL");
+    cudaError_t e = launch_universe(shape, n, pitch, cx, cy, cz, x, y, z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "universe launch");
+    return CC_OK;
+}
+
+size_t cc_backproject_workspace_bytes(int64_t rings, int64_t voxels, const cc_params *p) {
+    if (!p || rings < 0 || voxels < 1 || voxels > INT32_MAX) return 0;
+    SweepPlan plan;
+    if (!plan_backproject(rings, voxels, *p, &plan)) return 0;
+    return plan.bytes;
+}
+
+cc_status cc_backproject(const cc_rings *rings, const float *px, const float *py, const float *pz,
+                         const cc_grid *voxels, const cc_params *p, float *image, int32_t *argmax,
+                         int32_t *status, void *workspace, size_t ws_bytes, void *stream) {
+    g_err[0] = 0;
+    cc_status st;
+    if ((st = check_rings_in(rings)) != CC_OK) return st;
+    if (rings->count > 0 && (!px || !py || !pz)) return fail(CC_EINVAL, "apex arrays must be non-NULL");
+    if (!voxels || voxels->count < 1 || voxels->count > INT32_MAX || !voxels->x || !voxels->y ||
+        !voxels->z)
+        return fail(CC_EINVAL, "need 1 <= voxels->count <= 2^31 - 1 and voxel arrays");
+    if ((st = check_params(p)) != CC_OK) return st;
+    if (!image || !argmax) return fail(CC_EINVAL, "image and argmax must be non-NULL");
+    SweepPlan plan;
+    if (!plan_backproject(rings->count, voxels->count, *p, &plan))
+        return fail(CC_ECUDA, "no CUDA device for planning");
+    if (!workspace || ws_bytes < plan.bytes)
+        return fail(CC_EINVAL, "workspace too small (cc_backproject_workspace_bytes)");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(CC_EINVAL, "workspace not 256-byte aligned");
+    cudaError_t e = launch_backproject(*rings, px, py, pz, *voxels, *p, plan, image, argmax, status,
+                                       (char *)workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "backproject launch");
     return CC_OK;
 }
 

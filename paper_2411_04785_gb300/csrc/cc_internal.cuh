@@ -72,7 +72,20 @@ struct SweepPlan {
 
 // force_d = 0 lets the planner pick the directions per thread; the batched
 // path fixes it so that bursts share one kernel instantiation.
-bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d = 0);
+// `pick` returns the sweep kernel for (directions per thread, k_cut on) whose
+// occupancy the plan sizes the grid for (NULL: the far-field sweep).
+typedef void *(*SweepPick)(int d, bool kcut);
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d = 0,
+                SweepPick pick = nullptr, size_t rec_bytes = 48);
+// Ring compaction shared by the sweeps: blocks of kPackChunk rings are
+// counted, the counts are scanned into block offsets (in place) and the total
+// is written to *nkept; the plan's split reduction, argmax and seeds follow a
+// sweep through finish_localize (probe coordinates in `grid`).
+constexpr int kPackChunk = 2048;
+cudaError_t launch_pack_scan(int32_t *blockcnt, int64_t nblk, int64_t *nkept, cudaStream_t s);
+cudaError_t finish_localize(const cc_grid &grid, const cc_params &p, const SweepPlan &plan,
+                            float *map, int32_t *argmax, int32_t *seeds, char *ws,
+                            cudaStream_t s);
 cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid,
                             const cc_params &p, const SweepPlan &plan,
                             float *map, int32_t *argmax, int32_t *seeds,
@@ -118,6 +131,31 @@ cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, uint16_t *wb,
 cudaError_t mlp_params_to_bf16(const float *p, uint16_t *wb, cudaStream_t s);
 cudaError_t mlp_apply_filter(const float *out, const cc_rings &r, float tau, float dmin,
                              float dmax, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// event clustering of detections - cluster.cu
+// ---------------------------------------------------------------------------
+size_t cluster_workspace_bytes(int64_t n);
+cudaError_t launch_cluster(const int64_t *t, const uint32_t *adc, int64_t n, int64_t dt_max,
+                           uint8_t *edge, int32_t *event_id, int64_t *ev_first, int32_t *ev_count,
+                           uint64_t *ev_adc, int64_t *n_events, int32_t *status, char *ws,
+                           cudaStream_t s);
+cudaError_t launch_spectrum(const uint64_t *ev_adc, const int64_t *n_events, uint64_t bin_width,
+                            int32_t nbins, uint64_t *hist, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// near-field back projection - voxel.cu
+// ---------------------------------------------------------------------------
+bool plan_backproject(int64_t R, int64_t V, const cc_params &p, SweepPlan *plan);
+int64_t universe_count(int shape, int n);
+cudaError_t launch_ring_apex(const cc_events &ev, const cc_rings &r, float *px, float *py,
+                             float *pz, cudaStream_t s);
+cudaError_t launch_universe(int shape, int n, float pitch, float cx, float cy, float cz,
+                            float *x, float *y, float *z, cudaStream_t s);
+cudaError_t launch_backproject(const cc_rings &rings, const float *px, const float *py,
+                               const float *pz, const cc_grid &vox, const cc_params &p,
+                               const SweepPlan &plan, float *image, int32_t *argmax,
+                               int32_t *status, char *ws, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // stage tracing - trace.cu.  Construct before a launch, destroy after it.

@@ -34,6 +34,7 @@
 #include <float.h>
 
 #include "cc_math.cuh"
+#include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
@@ -48,85 +49,9 @@ constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
 // Coefficients of acos_q (cc_math.cuh) as FP32x2 pairs.
 __device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, unsigned bytes,
-                                              unsigned long long *bar) {
-    unsigned b = smem_u32(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(b)
-        : "memory");
-}
-
-// Bounded wait for an mbarrier phase: false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    unsigned b = smem_u32(bar);
-    unsigned long long t0 = 0;
-    for (unsigned it = 0; it < (1u << 30); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(b), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 31) == 0) {
-            unsigned long long now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitLimitNs) return false;
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ void better(float &v, int &j, float v2, int j2) {
-    if (v2 > v || (v2 == v && j2 < j)) { v = v2; j = j2; }
-}
-
-// Block-wide argmax (ties: lowest index); result valid in thread 0.
-__device__ __forceinline__ void block_best(float &v, int &j) {
-    __shared__ float sv[32];
-    __shared__ int sj[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        int j2 = __shfl_xor_sync(0xffffffffu, j, o);
-        better(v, j, v2, j2);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0) { sv[w] = v; sj[w] = j; }
-    __syncthreads();
-    if (w == 0) {
-        v = l < nw ? sv[l] : -FLT_MAX;
-        j = l < nw ? sj[l] : INT32_MAX;
-        if (l >= nw) v = -__builtin_huge_valf();
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            int j2 = __shfl_xor_sync(0xffffffffu, j, o);
-            better(v, j, v2, j2);
-        }
-    }
-    __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // ring repacking
 // ---------------------------------------------------------------------------
-constexpr int kPackChunk = 2048;   // rings per pack block (8 per thread)
-
 // A ring enters the sweep when it is valid and its numbers are usable.
 __device__ __forceinline__ bool ring_kept(const float *__restrict__ ax,
                                           const float *__restrict__ ay,
@@ -548,7 +473,9 @@ void *pick_sweep(int d, bool kcut) {
 // ---------------------------------------------------------------------------
 // launch planning
 // ---------------------------------------------------------------------------
-bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d) {
+bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d,
+                SweepPick pick, size_t rec_bytes) {
+    if (pick == nullptr) pick = pick_sweep;
     if (R < 0 || M < 1 || M > INT32_MAX) return false;
     const int sms = device_sm_count();
     if (sms <= 0) return false;
@@ -561,7 +488,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     for (int cand : {4, 8, 2}) {
         if (force_d > 0) cand = force_d;
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_sweep(cand, kcut), kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick(cand, kcut), kThreads, 0);
         if (occ < 1) occ = 1;
         int64_t c = (int64_t)sms * occ;
         int64_t ndb = (M + (int64_t)kThreads * cand - 1) / ((int64_t)kThreads * cand);
@@ -595,7 +522,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     plan->nbb = best_ns > 1 ? (M + 255) / 256 : ndb;
     size_t off = 0;
     plan->off_rec = off;
-    off = align256(off + (size_t)plan->rpad * sizeof(RingRec));
+    off = align256(off + (size_t)plan->rpad * rec_bytes);
     plan->off_part = off;
     if (best_ns > 1) off = align256(off + (size_t)best_ns * (size_t)M * sizeof(float));
     plan->off_bb = off;
@@ -611,6 +538,11 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     off = align256(off + (size_t)plan->npack * sizeof(int32_t));
     plan->bytes = off;
     return true;
+}
+
+cudaError_t launch_pack_scan(int32_t *blockcnt, int64_t nblk, int64_t *nkept, cudaStream_t s) {
+    k_pack_scan<<<1, 1024, 0, s>>>(blockcnt, nblk, nkept);
+    return cudaGetLastError();
 }
 
 // Pack one burst's rings into the plan's records (and zero its status).

@@ -399,3 +399,12 @@ def detection_stream(n_events: int = 400_000, seed: int = 21, event_rate_hz: flo
     truth = np.concatenate([owner, -np.ones(n_dark, np.int64)])
     order = np.argsort(t, kind="stable")
     return (np.round(t[order]).astype(np.int64), adc[order].astype(np.uint32), truth[order])
+
+
+def tile_stream(t, adc, copies: int, gap_ps: int = 1_000_000):
+    """A longer sorted stream made of `copies` copies of (t, adc), each
+    shifted past the end of the previous one by gap_ps."""
+    t = np.asarray(t, np.int64)
+    span = int(t[-1] - t[0]) + gap_ps if t.size else gap_ps
+    off = (np.arange(copies, dtype=np.int64) * span)[:, None]
+    return (t[None, :] + off).ravel(), np.tile(np.asarray(adc, np.uint32), copies)

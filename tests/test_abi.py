@@ -61,3 +61,35 @@ def test_host_side_calls_without_gpu(libpath):
                          None, 0, None) == -1
     assert b"topk" in L.cc_last_error()
     assert L.cc_refine_workspace_bytes(-1, 1) == 0
+
+
+def test_cluster_argument_checks_without_gpu(libpath):
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import api
+    L = cc.lib()
+    ws = L.cc_cluster_workspace_bytes(10_000)
+    assert ws >= 256 and L.cc_cluster_workspace_bytes(-1) == 0
+    fake = C.c_void_p(1 << 20)                     # never dereferenced: checks come first
+    call = lambda d, cap=5000, wsb=ws, ev=None: L.cc_cluster_maxstep(
+        d, 10, None, None, ev, None, None, cap, None, None, fake, wsb, None)
+    assert call(None) == -1 and b"NULL" in L.cc_last_error()
+    assert call(C.byref(api.cc_detections(fake, fake, 1 << 31))) == -1
+    assert call(C.byref(api.cc_detections(None, None, 10))) == -1            # t NULL
+    d = C.byref(api.cc_detections(fake, fake, 10_000))
+    assert call(d, cap=4999, ev=fake) == -1 and b"capacity" in L.cc_last_error()
+    assert call(d, wsb=ws - 1) == -1 and b"workspace" in L.cc_last_error()
+    assert L.cc_cluster_spectrum(fake, fake, 0, 10, fake, None) == -1
+    assert L.cc_cluster_spectrum(fake, fake, 4, 0, fake, None) == -1
+
+
+def test_voxel_universe_counts_without_gpu(libpath):
+    import oracle
+    import paper_2411_04785_gb300 as cc
+    L = cc.lib()
+    for shape, s in (("cube", 0), ("cylinder", 1), ("sphere", 2)):
+        for n in (1, 2, 5, 16, 37):
+            assert L.cc_voxel_count(s, n) == oracle.universe(shape, n, 1.0, count_only=True)
+    assert L.cc_voxel_count(3, 4) == -1 and L.cc_voxel_count(0, 0) == -1
+    assert L.cc_voxel_count(0, 1025) == -1
+    assert L.cc_voxel_universe(1, 0, 1.0, 0, 0, 0, None, None, None, None) == -1
+    assert L.cc_voxel_universe(1, 8, 0.0, 0, 0, 0, None, None, None, None) == -1
