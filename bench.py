@@ -174,7 +174,7 @@ def oracle_step(ev, rings_needed=True, n_dirs=None, budget_s=10.0, grid=None, th
     return t_recon + t_map + t_ref, {
         "t_recon_s": t_recon, "t_map_s_scaled": t_map, "t_refine_s": t_ref,
         "n_dirs": n_dirs, "threads": threads, "dir": d, "status": st, "iters": iters,
-        "rings": int(r["valid"].size)}
+        "rings": int(r["valid"].size), "valid": int(r["valid"].sum())}
 
 
 def run_reference(args):
@@ -183,7 +183,6 @@ def run_reference(args):
         return
     from paper_2411_04785_gb300 import synth
     ev = synth.simulate_events(n_src=N_SRC, n_bkg=N_BKG, seed=2)
-    pairs = (N_SRC + N_BKG) * 12 * NSIDE * NSIDE
     times, info = [], None
     n_dirs = None
     for i in range(args.warmup + args.steps):
@@ -192,6 +191,7 @@ def run_reference(args):
         if i >= args.warmup:
             times.append(t)
     ms = 1e3 * float(np.mean(times))
+    pairs = info["valid"] * 12 * NSIDE * NSIDE     # valid rings x directions
     value = pairs / (ms / 1e3)
     sample = (f"per step: oracle rings of all {N_SRC + N_BKG} events (1 thread) + map of all "
               f"rings over {n_dirs} of {12 * NSIDE * NSIDE} directions ({info['threads']} "
@@ -202,6 +202,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "events200k_healpix64", "events": N_SRC + N_BKG,
+                   "valid_rings": info["valid"], "evals": "valid rings x directions",
                    "directions": 12 * NSIDE * NSIDE},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"],
                          "kind": "oracle", "sample": sample},
@@ -416,7 +417,10 @@ def run_gpu(args):
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     tot_s = max_over_ranks(pg, float(step_ms.sum()) / 1e3, dev)
     ms_per_step = 1e3 * tot_s / args.steps
-    pairs_step = N * M
+    # evaluations = valid rings x directions: invalid rings are compacted away
+    # before the sweep and cost nothing
+    n_valid = int(loc._rings["valid"].sum().item())
+    pairs_step = n_valid * M
     value = world * pairs_step * args.steps / tot_s
     launches = sum(v["launches"] for v in trace.values())
     assert int(loc.loc_status.item()) == 0 and int(loc.ref_status.item()) in (0, -5)
@@ -447,7 +451,7 @@ def run_gpu(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": "events200k_healpix64", "events": N,
-                      "valid_rings": int(loc._rings["valid"].sum().item()),
+                      "valid_rings": n_valid, "evals": "valid rings x directions",
                       "directions": M, "grid": "HEALPix nside 64 RING",
                       "sites": "2/3/4 at 0.5/0.3/0.2", "source_to_background": "1:10",
                       "l2": "flushed between timed steps (256 MiB write)",
@@ -524,14 +528,124 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving: Poisson bursts (50/s; log-normal ring counts, median 20k,
+    500-300k; background 1-50x; random source among 16 directions) served in
+    real time by the continuous-batching server, first on the plain path,
+    then on the learned path (ring filter trained here on the GPU).  Reports
+    per-burst latency p50/p99 (arrival to result on the host), the ring x
+    direction evaluations per second over the run, and the localisation error
+    against the true source; the plain path's results are checked against
+    the oracle on a sample of small bursts."""
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import serve, synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = cc.Params()
+    # the learned path's filter, trained on the GPU by the library's kernels
+    t0 = time.perf_counter()
+    tr = synth.training_events(args.train_events, seed=11 + rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    n = to(tr["n"])
+    x, y, z, e = (to(np.asarray(tr[k], np.float32)) for k in "xyze")
+    rings = cc.rings_from_events(n, x, y, z, e, p)
+    F = cc.ring_features(n, x, y, z, e, rings, p)
+    res = cc.ring_residuals(rings, to(tr["sources"]))
+    filt = cc.RingFilter(dev, seed=0)
+    losses = filt.train(F, to(tr["is_source"].astype(np.uint8)), res, rings["valid"], epochs=8,
+                        batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del n, x, y, z, e, rings, F, res, tr
+
+    pools, specs = synth.serving_bursts(args.bursts, 50.0, seed=5 + rank)
+    bursts = serve.to_bursts(serve.pin_pools(pools), specs)
+    grid = cc.grid_healpix_ring(NSIDE, dev)
+    M = grid[0].numel()
+    arms = {"plain": {}, "learned": {"ring_filter": filt, "tau": args.tau}}
+    out_arms = {}
+    gpu_index = local
+    for name, kw in arms.items():
+        srv = serve.Server(grid, p, hbm_budget=8 << 30, max_active=48, **kw)
+        srv.run(bursts[:args.warmup * 4], realtime=False)              # warm-up
+        torch.cuda.synchronize()
+        cc.trace_read(reset=True)
+        barrier(pg)
+        with ClockSampler(gpu_index) as clk:
+            time.sleep(0.5)
+            res_arm, stats = srv.run(bursts, realtime=True)
+        launches = sum(v["launches"] for v in cc.trace_read(reset=True).values())
+        lat = np.array([res_arm[b.bid]["latency"] for b in bursts]) * 1e3
+        err = np.array([math.degrees(math.atan2(np.linalg.norm(np.cross(res_arm[b.bid]["dir"], b.source)),
+                                                float(res_arm[b.bid]["dir"] @ b.source))) for b in bursts])
+        rings_total = sum(b.count for b in bursts)
+        out_arms[name] = {
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "evals_per_s": rings_total * M / stats["wall_s"], "wall_s": stats["wall_s"],
+            "bursts_per_s": len(bursts) / stats["wall_s"],
+            "batches": {"count": len(stats["batches"]), "mean_size": float(np.mean(stats["batches"])),
+                        "max_size": int(max(stats["batches"]))},
+            "error_vs_source_deg": {"p50": float(np.percentile(err, 50)),
+                                    "p90": float(np.percentile(err, 90)),
+                                    "within_0.5": float((err <= 0.5).mean())},
+            "gpu_launches": launches, "clocks": clk.summary()}
+        if name == "plain":
+            plain_res = res_arm
+    # oracle parity of the plain path on the smallest bursts (rank 0)
+    parity = None
+    if rank == 0 and not args.quick:
+        import oracle
+        g64 = oracle.grid_healpix_ring(NSIDE)
+        small = sorted(bursts, key=lambda b: b.count)[:3]
+        worst = 0.0
+        for b in small:
+            ev = synth.burst_events(pools, specs[b.bid])
+            r = oracle.rings_from_events(ev, p.sigma_e_frac, p.sigma_pos_cm, p.deta_min, p.deta_max)
+            m = oracle.likelihood_map(r, g64)
+            j = oracle.argmax(m)
+            d, _, _, _ = oracle.refine(r, [g64[0][j], g64[1][j], g64[2][j]], tol_rad=1e-10)
+            gd = plain_res[b.bid]["dir"]
+            worst = max(worst, math.degrees(math.atan2(np.linalg.norm(np.cross(gd, d)), float(gd @ d))))
+        parity = {"bursts": [b.count for b in small], "max_refined_vs_oracle_deg": worst}
+    pl, le = out_arms["plain"], out_arms["learned"]
+    out = {"metric": METRIC, "value": world * pl["evals_per_s"], "unit": UNIT, "n_gpus": world,
+           "steps": len(bursts), "warmup": args.warmup * 4,
+           "ms_per_step": pl["wall_s"] * 1e3 / len(bursts), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serve_poisson50", "bursts": len(bursts), "rate_hz": 50.0,
+                      "rings": "log-normal median 20k sigma 1 in [500, 300k]",
+                      "background": "uniform 1-50x", "directions": M,
+                      "grid": "HEALPix nside 64 RING", "hbm_budget_gb": 8, "max_active": 48,
+                      "arrivals": "real time (Poisson)",
+                      "filter": {"train_events": args.train_events, "train_s": t_train,
+                                 "loss_first_last": [losses[0], losses[-1]], "tau": args.tau}},
+           "latency_ms": {"plain": pl["latency_ms"], "learned": le["latency_ms"]},
+           "arms": out_arms, "gpu_launches": pl["gpu_launches"], "clocks": pl["clocks"],
+           "oracle_parity": parity}
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["events200k", "burst1m"], default="events200k",
-                    help="events200k (default, the headline) or the 1M-ring x 786k-direction burst")
+    ap.add_argument("--workload", choices=["events200k", "burst1m", "serve"], default="events200k",
+                    help="events200k (default, the headline), the 1M-ring x 786k-direction "
+                         "burst, or the serving stream (plain and learned paths)")
+    ap.add_argument("--bursts", type=int, default=2000, help="serve: bursts in the stream")
+    ap.add_argument("--train-events", type=int, default=1_000_000,
+                    help="serve: events simulated to train the ring filter")
+    ap.add_argument("--tau", type=float, default=0.0, help="serve: ring filter score threshold")
     ap.add_argument("--quick", action="store_true", help="skip e2e, recon pile and CPU baseline")
     ap.add_argument("--alu-rates", action="store_true",
                     help="build and run the FP32 / MUFU rate microbenchmark (csrc/alu_rates.cu)")
@@ -550,6 +664,8 @@ def main():
         run_alu_rates()
     elif args.workload == "burst1m":
         run_burst(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 
