@@ -74,6 +74,8 @@ def _load():
         lib.or_grid_fibonacci.restype = None
         lib.or_grid_healpix_ring.argtypes = [i64, P, P, P]
         lib.or_grid_healpix_ring.restype = i32
+        lib.or_grid_healpix_nest.argtypes = [i64, P, P, P]
+        lib.or_grid_healpix_nest.restype = i32
         lib.or_maxstep_edges.argtypes = [P, i64, i64, P]
         lib.or_maxstep_edges.restype = None
         lib.or_events_from_edges.argtypes = [P, P, i64, P, P, P, P]
@@ -246,6 +248,15 @@ def grid_healpix_ring(nside):
     x, y, z = np.zeros(npix), np.zeros(npix), np.zeros(npix)
     if _load().or_grid_healpix_ring(nside, _p(x), _p(y), _p(z)) != 0:
         raise ValueError("nside must be >= 1")
+    return x, y, z
+
+
+def grid_healpix_nest(nside):
+    """HEALPix pixel centres in NESTED order (nside a power of two)."""
+    npix = 12 * nside * nside
+    x, y, z = np.zeros(npix), np.zeros(npix), np.zeros(npix)
+    if _load().or_grid_healpix_nest(nside, _p(x), _p(y), _p(z)) != 0:
+        raise ValueError("nside must be a power of two")
     return x, y, z
 
 

@@ -701,3 +701,55 @@ int or_grid_healpix_ring(int64_t nside, double *x, double *y, double *z)
     }
     return 0;
 }
+
+/*
+ * HEALPix in NESTED order (Gorski et al. 2005): pixel p lies in base face
+ * f = p / nside^2; the remaining index interleaves the bits of the face
+ * coordinates (ix in the even bits, iy in the odd ones).  From (f, ix, iy):
+ * ring number jr = jr0(f) nside - ix - iy - 1 counted from the north pole,
+ * the pixel's place in its ring jp = (jp0(f) nr + ix - iy + 1 + shift) / 2
+ * with nr pixels-per-quarter-ring and shift the equatorial half-pixel
+ * offset, and from those z and phi as in the RING layout.  Consecutive
+ * NESTED pixels form compact patches (4^k pixels = a 2^k x 2^k block).
+ */
+int or_grid_healpix_nest(int64_t nside, double *x, double *y, double *z)
+{
+    static const int jr0[12] = {2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4};
+    static const int jp0[12] = {1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7};
+    if (nside < 1 || (nside & (nside - 1)) != 0)
+        return -1;                                   /* a power of two */
+    int64_t npface = nside * nside, npix = 12 * npface;
+    double n2 = (double)nside * (double)nside;
+    for (int64_t p = 0; p < npix; p++) {
+        int64_t f = p / npface, q = p % npface, ix = 0, iy = 0;
+        for (int b = 0; (int64_t)1 << (2 * b) < npface; b++) {
+            ix |= ((q >> (2 * b)) & 1) << b;
+            iy |= ((q >> (2 * b + 1)) & 1) << b;
+        }
+        int64_t jr = jr0[f] * nside - ix - iy - 1, nr, shift = 0;
+        double zz, omz;
+        if (jr < nside) {
+            nr = jr;
+            omz = (double)(nr * nr) / (3.0 * n2);
+            zz = 1.0 - omz;
+        } else if (jr > 3 * nside) {
+            nr = 4 * nside - jr;
+            omz = (double)(nr * nr) / (3.0 * n2);
+            zz = omz - 1.0;
+        } else {
+            nr = nside;
+            zz = (double)(2 * nside - jr) * 2.0 / (3.0 * (double)nside);
+            omz = 1.0 - fabs(zz);
+            shift = (jr - nside) & 1;
+        }
+        int64_t jp = (jp0[f] * nr + ix - iy + 1 + shift) / 2;
+        if (jp > 4 * nside) jp -= 4 * nside;
+        if (jp < 1) jp += 4 * nside;
+        double phi = ((double)jp - 0.5 * (double)(shift + 1)) * M_PI / (2.0 * (double)nr);
+        double rho = sqrt(omz * (2.0 - omz));
+        x[p] = rho * cos(phi);
+        y[p] = rho * sin(phi);
+        z[p] = zz;
+    }
+    return 0;
+}

@@ -79,6 +79,7 @@ int or_refine(int64_t R, const double *ax, const double *ay, const double *az,
 /* Sky grids. */
 void or_grid_fibonacci(int64_t n, double *x, double *y, double *z);
 int or_grid_healpix_ring(int64_t nside, double *x, double *y, double *z);
+int or_grid_healpix_nest(int64_t nside, double *x, double *y, double *z);
 
 /* Event clustering of time-sorted detections (cluster.c, Sec. 2). */
 void or_maxstep_edges(const int64_t *t, int64_t N, int64_t dt_max, uint8_t *edge);

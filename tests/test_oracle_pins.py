@@ -471,3 +471,42 @@ def test_fibonacci_grid_properties():
     spacing = math.sqrt(4 * math.pi / n)
     assert d.min(1).min() > 0.5 * spacing
     assert np.linalg.norm(c.sum(0)) < 1e-4 * n
+
+
+# --------------------------------------------------------------------------
+# HEALPix NESTED: the same pixels as RING, ordered hierarchically
+# --------------------------------------------------------------------------
+def test_healpix_nest_is_a_permutation_of_ring():
+    assert np.array_equal(np.stack(oracle.grid_healpix_nest(1)), np.stack(oracle.grid_healpix_ring(1)))
+    for nside in (2, 4, 8, 16):
+        nv = np.stack(oracle.grid_healpix_nest(nside), 1)
+        rv = np.stack(oracle.grid_healpix_ring(nside), 1)
+        d = nv @ rv.T                                     # cosines, nest x ring
+        best = d.argmax(1)
+        assert np.unique(best).size == nv.shape[0]        # a bijection
+        assert (1.0 - d[np.arange(nv.shape[0]), best]).max() < 1e-12
+
+
+def test_healpix_nest_hierarchy():
+    """NESTED index p at nside n has children 4p .. 4p+3 at nside 2n: each
+    child's nearest pixel centre at nside n is its parent's."""
+    for n in (1, 2, 4, 8):
+        par = np.stack(oracle.grid_healpix_nest(n), 1)
+        kid = np.stack(oracle.grid_healpix_nest(2 * n), 1)
+        nearest = (kid @ par.T).argmax(1)
+        np.testing.assert_array_equal(nearest, np.arange(kid.shape[0]) // 4)
+
+
+def test_healpix_nest_patches_are_compact():
+    # 1024 consecutive NESTED pixels at nside 64 form a 32 x 32 block of one
+    # base face (radius <= 26 deg); 1024 consecutive RING pixels are
+    # latitude strips around the sphere (wide except near the poles)
+    def radius(blk):
+        c = blk.sum(0)
+        c /= np.linalg.norm(c)
+        return np.degrees(np.arccos(np.clip(blk @ c, -1, 1)).max())
+    v = np.stack(oracle.grid_healpix_nest(64), 1)
+    r = np.stack(oracle.grid_healpix_ring(64), 1)
+    rn = [radius(v[b * 1024:(b + 1) * 1024]) for b in range(48)]
+    rr = [radius(r[b * 1024:(b + 1) * 1024]) for b in range(48)]
+    assert max(rn) < 26.0 and np.mean(rr) > 2.0 * np.mean(rn)
