@@ -633,13 +633,222 @@ def run_serve(args):
         pg.destroy_process_group()
 
 
+def timed_loop(step, steps, stream, flush=None):
+    """CUDA-event time of every step on `stream` (ms)."""
+    import torch
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        st[i].record(stream)
+        step()
+        en[i].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in zip(st, en)])
+
+
+def run_cluster(args):
+    """Max-step clustering (Sec. 2) of a 137Cs-like detection stream: 12
+    copies of a 400k-event segment (81.7M detections, 15 ns step), every
+    output (edges, event ids, per-event first / size / amplitude sum) plus
+    the amplitude spectrum per step.  HBM bound; inputs (981 MB) are larger
+    than L2."""
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    t0, a0, _ = synth.detection_stream(seed=21 + rank)
+    t_np, adc_np = synth.tile_stream(t0, a0, 12)
+    N = t_np.size
+    DT = 15_000
+    td = torch.from_numpy(t_np).to(dev)
+    ad = torch.from_numpy(adc_np).to(dev)
+    o = cc.cluster_maxstep(td, ad, DT)
+    hist = cc.cluster_spectrum(o["adc"], o["n_events"], 64, 256)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        cc.cluster_maxstep(td, ad, DT, out=o)
+        cc.cluster_spectrum(o["adc"], o["n_events"], 64, 256, out=hist)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = int(o["n_events"].item())
+    cc.trace_read(reset=True)
+    cc.trace_enable(True)
+    barrier(pg)
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)
+        ms = timed_loop(step, args.steps, stream)
+    barrier(pg)
+    cc.trace_enable(False)
+    trace = cc.trace_read(reset=True)
+    tot_s = max_over_ranks(pg, float(ms.sum()) / 1e3, dev)
+    # dominant kernel: k_cluster (launch 1 of 2 per step); its own time by events
+    kms = timed_loop(lambda: cc.cluster_maxstep(td, ad, DT, out=o), args.steps, stream)
+    alg = N * (8 + 4 + 1 + 4) + K * (8 + 4 + 8)
+    pk = peaks_file()
+    peak = float(pk.get("hbm_gbs") or 6800.0) * 1e9
+    achieved = alg / (float(np.mean(kms)) / 1e3)
+    out = {"metric": "detections clustered/s (max-step, Sec. 2)", "value": world * N * args.steps / tot_s,
+           "unit": "detections/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": "cluster_cs137_81M", "detections": N, "events": K,
+                      "dt_max_ps": DT, "l2": "inputs (981 MB) larger than L2"},
+           "gpu_launches": sum(v["launches"] for v in trace.values()), "clocks": clk.summary(),
+           "roofline": {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                        "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": ncu_traffic("cluster_cs137_81M_ncu.md", "cluster.cu"),
+                        "kernel": "k_cluster",
+                        "algorithmic_bytes": f"{N} x 17 B (t, adc in; edge, id out) + "
+                                             f"{K} events x 20 B = {alg}"}}
+    if not args.quick:
+        ht = torch.from_numpy(t_np).pin_memory()
+        ha = torch.from_numpy(adc_np).pin_memory()
+        hh = torch.empty(256, dtype=torch.uint64).pin_memory()
+        hk = torch.empty(1, dtype=torch.int64).pin_memory()
+
+        def e2e():
+            td.copy_(ht, non_blocking=True)
+            ad.copy_(ha, non_blocking=True)
+            step()
+            hh.copy_(hist, non_blocking=True)
+            hk.copy_(o["n_events"], non_blocking=True)
+
+        e_ms = []
+        for i in range(args.warmup + args.steps):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            e2e()
+            s1.record(stream)
+            s1.synchronize()
+            if i >= args.warmup:
+                e_ms.append(s0.elapsed_time(s1))
+        e_tot = max_over_ranks(pg, float(np.sum(e_ms)) / 1e3, dev)
+        out["e2e"] = {"value": world * N * args.steps / e_tot, "unit": "detections/s",
+                      "h2d_bytes_per_step": N * 12, "d2h_bytes_per_step": 256 * 8 + 8,
+                      "ms_per_step": 1e3 * e_tot / args.steps}
+        if rank == 0 and world == 1:
+            import oracle
+            c0 = time.perf_counter()
+            want = oracle.maxstep_events(t_np, adc_np, DT)
+            c1 = time.perf_counter() - c0
+            got_ok = (int(o["n_events"].item()) == want["count"].size and
+                      np.array_equal(o["event_id"].cpu().numpy(), want["event_id"]))
+            out["cpu_baseline"] = {"value": N / c1, "unit": "detections/s", "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": f"the whole {N}-detection stream, oracle (C) on 1 thread"}
+            out["parity"] = {"event_ids_bit_exact": bool(got_ok)}
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_voxel(args):
+    """Near-field back projection (Sec. 3): 200,000 events from a point
+    source 20 cm above the 4-layer detector (background 10:1) -> rings ->
+    apexes -> image over the sphere universe inscribed in a 64^3 cube of
+    0.3125 cm voxels (137,376 voxels); the cube and cylinder universes are
+    timed beside it."""
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    S = (1.3, -0.7, 20.2)
+    ev = synth.simulate_events(n_src=18182, n_bkg=181818, seed=12 + rank, source_point=S)
+    N = ev["n"].size
+    tn = torch.from_numpy(ev["n"]).to(dev)
+    tx, ty, tz, te = (torch.from_numpy(ev[k]).to(dev) for k in "xyze")
+    p = cc.Params()
+    unis = {u: cc.voxel_universe(u, 64, 0.3125, (0.0, 0.0, 20.0), dev)
+            for u in ("sphere", "cylinder", "cube")}
+    rings = cc.rings_from_events(tn, tx, ty, tz, te, p)
+    apex = cc.ring_apex(tn, tx, ty, tz, rings)
+    vox = unis["sphere"]
+    V = vox[0].numel()
+    ws = torch.empty(max(cc.backproject_workspace_bytes(N, unis["cube"][0].numel(), p), 256),
+                     dtype=torch.uint8, device=dev)
+    img = cc.backproject(rings, apex, vox, p, workspace=ws)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        cc.rings_from_events(tn, tx, ty, tz, te, p, out=rings)
+        cc.ring_apex(tn, tx, ty, tz, rings, out=apex)
+        cc.backproject(rings, apex, vox, p, workspace=ws, out=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_valid = int(rings["valid"].sum().item())
+    cc.trace_read(reset=True)
+    cc.trace_enable(True)
+    barrier(pg)
+    with ClockSampler(local) as clk:
+        time.sleep(0.5)
+        ms = timed_loop(step, args.steps, stream)
+    barrier(pg)
+    cc.trace_enable(False)
+    trace = cc.trace_read(reset=True)
+    tot_s = max_over_ranks(pg, float(ms.sum()) / 1e3, dev)
+    vt = trace["voxel"]
+    sweep_ms = (vt["ms"] - 0.0) / max(args.steps, 1)   # apex + sweep per step
+    pairs = n_valid * V
+    sm_max = float(peaks_file().get("sm_max_mhz") or 2070.0)
+    per_clk = 128.0 / 26.0        # 26 FP32 ops per pair at 128 lanes/clk/SM (MUFU: 3 ops, not binding)
+    peak = sms * sm_max * 1e6 * per_clk
+    achieved = pairs / (sweep_ms / 1e3)
+    j = int(img[1].item())
+    vj = np.array([vox[c][j].item() for c in range(3)])
+    others = {}
+    for u in ("cube", "cylinder"):
+        o2 = cc.backproject(rings, apex, unis[u], p, workspace=ws)
+        torch.cuda.synchronize()
+        t_u = timed_loop(lambda: cc.backproject(rings, apex, unis[u], p, workspace=ws, out=o2),
+                         max(3, args.steps // 4), stream)
+        others[u] = {"voxels": unis[u][0].numel(), "ms": float(np.mean(t_u))}
+    out = {"metric": "ring×voxel evals/s (near-field back projection, Sec. 3)",
+           "value": world * pairs * args.steps / tot_s, "unit": "ring×voxel evals/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "voxel_point_source_200k_sphere64", "events": N,
+                      "valid_rings": n_valid, "voxels": V,
+                      "universe": "sphere in a 64^3 cube, 0.3125 cm voxels, centre (0,0,20) cm",
+                      "source_point_cm": S, "l2": "working set re-read each step (no flush)"},
+           "gpu_launches": sum(v["launches"] for v in trace.values()), "clocks": clk.summary(),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
+                        "frac": achieved / peak, "traffic": None, "kernel": "k_backproject",
+                        "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x 128/26 pairs/clk/SM"},
+           "universes_ms": dict(others, sphere={"voxels": V, "ms": float(np.mean(ms))}),
+           "accuracy": {"argmax_voxel_cm": vj.tolist(),
+                        "argmax_to_source_cm": float(np.linalg.norm(vj - np.array(S)))}}
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["events200k", "burst1m", "serve"], default="events200k",
+    ap.add_argument("--workload", choices=["events200k", "burst1m", "serve", "cluster", "voxel"],
+                    default="events200k",
                     help="events200k (default, the headline), the 1M-ring x 786k-direction "
                          "burst, or the serving stream (plain and learned paths)")
     ap.add_argument("--bursts", type=int, default=2000, help="serve: bursts in the stream")
@@ -666,6 +875,10 @@ def main():
         run_burst(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "cluster":
+        run_cluster(args)
+    elif args.workload == "voxel":
+        run_voxel(args)
     else:
         run_gpu(args)
 

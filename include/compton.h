@@ -237,6 +237,13 @@ cc_status cc_grid_fibonacci(int64_t n, float *x, float *y, float *z,
 cc_status cc_grid_healpix_ring(int32_t nside, float *x, float *y, float *z,
                                void *stream);
 
+/* The same pixels in NESTED order (nside a power of two, 1..8192): pixel
+ * p's centre is RING pixel nest_to_ring(p)'s, bit for bit.  Consecutive
+ * NESTED pixels form compact patches, so sweep blocks of them can be skipped
+ * by the angular selection (p->k_cut > 0) where no ring reaches them. */
+cc_status cc_grid_healpix_nest(int32_t nside, float *x, float *y, float *z,
+                               void *stream);
+
 /* Gather k grid directions as FP64 unit vectors (e.g. seeds for
  * cc_refine): out_dirs[3t..3t+2] = grid[idx[t]], renormalised.  Negative
  * indices give (0, 0, 0).  idx [k] int32 and out_dirs [3k] double are device
@@ -437,7 +444,7 @@ typedef enum {
     CC_STAGE_GRID = 7,    /* grid generation */
     CC_STAGE_MLP = 8,     /* learned ring filter (features, MLP, training, filter) */
     CC_STAGE_CLUSTER = 9, /* event clustering of detections and its spectrum */
-    CC_STAGE_VOXEL = 10,  /* near-field back projection (apex, universe, sweep) */
+    CC_STAGE_VOXEL = 10,  /* near-field back-projection sweep */
     CC_STAGE_COUNT = 11
 } cc_stage;
 

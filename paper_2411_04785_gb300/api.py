@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         L.cc_grid_fibonacci.restype = S
         L.cc_grid_healpix_ring.argtypes = [C.c_int32, _P, _P, _P, _P]
         L.cc_grid_healpix_ring.restype = S
+        L.cc_grid_healpix_nest.argtypes = [C.c_int32, _P, _P, _P, _P]
+        L.cc_grid_healpix_nest.restype = S
         L.cc_grid_gather.argtypes = [C.POINTER(cc_grid), _P, C.c_int32, _P, _P]
         L.cc_grid_gather.restype = S
         L.cc_localize_static.argtypes = [C.POINTER(cc_rings), C.POINTER(cc_grid),
@@ -364,6 +366,16 @@ def grid_healpix_ring(nside: int, device="cuda", stream=None):
     npix = 12 * nside * nside
     g = [torch.empty(npix, dtype=torch.float32, device=device) for _ in range(3)]
     _check("cc_grid_healpix_ring", lib().cc_grid_healpix_ring(nside, *(_ptr(t) for t in g),
+                                                              _stream(stream)))
+    return tuple(g)
+
+
+def grid_healpix_nest(nside: int, device="cuda", stream=None):
+    """HEALPix pixel centres in NESTED order (compact blocks for the angular
+    selection's block skipping)."""
+    npix = 12 * nside * nside
+    g = [torch.empty(npix, dtype=torch.float32, device=device) for _ in range(3)]
+    _check("cc_grid_healpix_nest", lib().cc_grid_healpix_nest(nside, *(_ptr(t) for t in g),
                                                               _stream(stream)))
     return tuple(g)
 

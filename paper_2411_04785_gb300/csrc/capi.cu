@@ -222,6 +222,16 @@ cc_status cc_grid_healpix_ring(int32_t nside, float *x, float *y, float *z, void
     return CC_OK;
 }
 
+cc_status cc_grid_healpix_nest(int32_t nside, float *x, float *y, float *z, void *stream) {
+    g_err[0] = 0;
+    if (nside < 1 || nside > 8192 || (nside & (nside - 1)) != 0)
+        return fail(CC_EINVAL, "nside must be a power of two in 1..8192");
+    if (!x || !y || !z) return fail(CC_EINVAL, "output arrays must be non-NULL");
+    cudaError_t e = launch_grid_healpix_nest(nside, x, y, z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_healpix_nest launch");
+    return CC_OK;
+}
+
 cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k, double *out_dirs,
                          void *stream) {
     g_err[0] = 0;

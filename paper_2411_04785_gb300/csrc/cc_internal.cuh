@@ -112,6 +112,8 @@ cudaError_t launch_grid_fibonacci(int64_t n, float *x, float *y, float *z,
                                   cudaStream_t s);
 cudaError_t launch_grid_healpix(int32_t nside, float *x, float *y, float *z,
                                 cudaStream_t s);
+cudaError_t launch_grid_healpix_nest(int32_t nside, float *x, float *y, float *z,
+                                     cudaStream_t s);
 cudaError_t launch_grid_gather(const cc_grid &g, const int32_t *idx, int k,
                                double *out, cudaStream_t s);
 

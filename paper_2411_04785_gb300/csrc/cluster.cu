@@ -23,11 +23,14 @@
 // amplitude sum is the difference of two prefix sums taken at its two edges
 // with no per-event atomics.  All arithmetic is integer: results are exact.
 //
-// Layout inside a tile: warp w owns 512 consecutive detections as 16 rows of
-// 32 (lane l of row r holds detection base + 32 r + l), so every row is one
-// coalesced 256-byte load of t and 128-byte load of adc, and the row-level
+// Layout inside a tile: the tile's t (32 KB) and adc (16 KB) are staged in
+// shared memory by two bulk copies (TMA) completing on one mbarrier, so no
+// thread holds the tile in registers and four CTAs fit an SM; warp w then
+// reads its 512 consecutive detections as 16 rows of 32 (lane l of row r
+// holds detection base + 512 w + 32 r + l), conflict-free, and the row-level
 // prefix counts are ballots.
 #include "cc_internal.cuh"
+#include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
@@ -107,6 +110,25 @@ __device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long l
     return v;
 }
 
+// Shared memory of one CTA: the tile's time stamps and amplitudes (staged
+// by two bulk copies), the neighbours just outside it, and the scan state.
+struct ClusterSmem {
+    long long ts[kTileSpan];
+    unsigned as[kTileSpan];
+    long long t_prev, t_next;
+    unsigned long long bar;
+    long long tile;
+};
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __global__ void __launch_bounds__(kCThreads)
 k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, long long N,
           long long dt_max, unsigned char *__restrict__ edge, int *__restrict__ event_id,
@@ -114,48 +136,75 @@ k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, lon
           unsigned long long *__restrict__ ev_adc, long long *__restrict__ n_events,
           TileState *__restrict__ tiles, unsigned long long *__restrict__ ticket,
           int *__restrict__ status) {
-    __shared__ long long tile_s;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(smem_raw);
     __shared__ Carry warp_agg[kCWarps];
     __shared__ Carry warp_excl[kCWarps];
     __shared__ Carry tile_excl;
+    __shared__ int load_failed;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) tile_s = (long long)atomicAdd(ticket, 1ull);
-    __syncthreads();
-    const long long tile = tile_s;
-    const long long seg = tile * kTileSpan + (long long)w * kWarpSpan;
-
-    // ---- load: row r of this warp = detections seg + 32 r + lane
-    long long tv[kRows];
-    unsigned av[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const long long i = seg + 32 * r + lane;
-        tv[r] = i < N ? __ldcs(t + i) : 0;
-        av[r] = (adc != nullptr && i < N) ? __ldcs(adc + i) : 0u;
+    if (threadIdx.x == 0) {
+        S.tile = (long long)atomicAdd(ticket, 1ull);
+        mbar_init(&S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        load_failed = 0;
     }
-    // the detections just outside the warp's span
-    const long long t_next = (seg + kWarpSpan < N) ? __ldg(t + seg + kWarpSpan) : 0;
-    const long long t_prev = (seg > 0 && seg - 1 < N) ? __ldg(t + seg - 1) : 0;
+    __syncthreads();
+    const long long tile = S.tile;
+    const long long base = tile * kTileSpan;
+    const long long n_here = N - base < kTileSpan ? N - base : kTileSpan;
+
+    // ---- stage the tile: whole aligned tiles by two bulk copies on one
+    // mbarrier, the ragged last tile by plain loads
+    const bool bulk = n_here == kTileSpan && ((reinterpret_cast<uintptr_t>(t) & 15u) == 0) &&
+                      (adc == nullptr || (reinterpret_cast<uintptr_t>(adc) & 15u) == 0);
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            const unsigned bytes = kTileSpan * 8u + (adc ? kTileSpan * 4u : 0u);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                             smem_u32(&S.bar)), "r"(bytes)
+                         : "memory");
+            bulk_copy(S.ts, t + base, kTileSpan * 8u, &S.bar);
+            if (adc) bulk_copy(S.as, adc + base, kTileSpan * 4u, &S.bar);
+        }
+        if (adc == nullptr)
+            for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) S.as[i] = 0u;
+    } else {
+        for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) {
+            const long long g = base + i;
+            S.ts[i] = g < N ? __ldcs(t + g) : 0;
+            S.as[i] = (adc != nullptr && g < N) ? __ldcs(adc + g) : 0u;
+        }
+    }
+    if (threadIdx.x == 32) {
+        S.t_prev = base > 0 ? __ldg(t + base - 1) : 0;
+        S.t_next = base + kTileSpan < N ? __ldg(t + base + kTileSpan) : 0;
+    }
+    if (bulk && threadIdx.x == 0 && !mbar_wait(&S.bar, 0)) load_failed = 1;
+    __syncthreads();
+    if (load_failed) {              // a bounded wait gave up: report, publish, go on
+        if (threadIdx.x == 0) atomicExch(status, (int)CC_ETIMEOUT);
+        for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) {
+            S.ts[i] = 0;
+            S.as[i] = 0u;
+        }
+        __syncthreads();
+    }
 
     // ---- masks: bit r of m_after = "step from this detection to the next
     // is below dt_max", bit r of m_before = the same for the step before
+    const int wl = w * kWarpSpan + lane;                // local index of row 0
+    const long long seg = base + (long long)w * kWarpSpan;
     unsigned m_after = 0, m_before = 0;
-    bool carry_after = false;   // m_after of lane 31 of the previous row
-    if (lane == 0 && seg > 0 && seg < N) carry_after = step_of(t_prev, tv[0]) < dt_max;
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
-        const long long i = seg + 32 * r + lane;
-        long long tn = __shfl_down_sync(0xffffffffu, tv[r], 1);
-        const long long tn_row = r + 1 < kRows ? __shfl_sync(0xffffffffu, tv[r + 1 < kRows ? r + 1 : r], 0)
-                                               : t_next;
-        if (lane == 31) tn = tn_row;
-        const bool ma = (i + 1 < N) && step_of(tv[r], tn) < dt_max;
-        bool mb = __shfl_up_sync(0xffffffffu, ma, 1);
-        // lane 31's mask of the previous row: the step into this row's lane 0
-        const bool prev_row_last = __shfl_sync(0xffffffffu, carry_after, 31);
-        if (lane == 0) mb = r == 0 ? carry_after : prev_row_last;
-        if (i >= N) mb = false;
-        carry_after = ma;
+        const int li = wl + 32 * r;
+        const long long i = base + li;
+        const long long ti = S.ts[li];
+        const long long tn = li + 1 < kTileSpan ? S.ts[li + 1] : S.t_next;
+        const long long tp = li > 0 ? S.ts[li - 1] : S.t_prev;
+        const bool ma = (i + 1 < N) && step_of(ti, tn) < dt_max;
+        const bool mb = (i > 0) && (i < N) && step_of(tp, ti) < dt_max;
         m_after |= (unsigned)ma << r;
         m_before |= (unsigned)mb << r;
     }
@@ -172,8 +221,9 @@ k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, lon
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
         const long long i = seg + 32 * r + lane;
-        own += av[r];
-        if (i < last) own_before += av[r];
+        const unsigned a = S.as[wl + 32 * r];
+        own += a;
+        if (i < last) own_before += a;
     }
     Carry wa{cnt, last, warp_sum_u64(own), warp_sum_u64(own_before)};
     if (last < 0) wa.sum_before = 0;
@@ -257,8 +307,9 @@ k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, lon
         const bool ma = (m_after >> r) & 1u, mb = (m_before >> r) & 1u;
         const bool st = ma && !mb, en = mb && !ma;
         const unsigned s = __ballot_sync(0xffffffffu, st);
-        const unsigned long long incl = warp_incl_scan_u64(av[r], lane);
-        const unsigned long long excl_here = incl - av[r];
+        const unsigned a = S.as[wl + 32 * r];
+        const unsigned long long incl = warp_incl_scan_u64(a, lane);
+        const unsigned long long excl_here = incl - a;
         const unsigned s_le = s & lane_le;
         const int sl = s_le ? 31 - __clz((int)s_le) : 0;
         const unsigned long long before_sl = __shfl_sync(0xffffffffu, excl_here, sl);
@@ -333,8 +384,13 @@ cudaError_t launch_cluster(const int64_t *t, const uint32_t *adc, int64_t n, int
         if (n_events) return cudaMemsetAsync(n_events, 0, sizeof(int64_t), s);
         return cudaSuccess;
     }
+    // the staged tile needs more than 48 KB of shared memory (set per call:
+    // the attribute belongs to the current device)
+    e = cudaFuncSetAttribute((const void *)k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ClusterSmem));
+    if (e != cudaSuccess) return e;
     TraceScope ts(CC_STAGE_CLUSTER, s);
-    k_cluster<<<(unsigned)tiles, kCThreads, 0, s>>>(
+    k_cluster<<<(unsigned)tiles, kCThreads, sizeof(ClusterSmem), s>>>(
         reinterpret_cast<const long long *>(t), adc, (long long)n, (long long)dt_max, edge,
         event_id, reinterpret_cast<long long *>(ev_first), ev_count,
         reinterpret_cast<unsigned long long *>(ev_adc), reinterpret_cast<long long *>(n_events),

@@ -31,12 +31,12 @@ __global__ void k_fibonacci(int64_t n, float *__restrict__ x, float *__restrict_
     z[i] = (float)(n - 2 * i - 1) / fn;
 }
 
-__global__ void k_healpix_ring(int64_t nside, float *__restrict__ x, float *__restrict__ y,
-                               float *__restrict__ z) {
+// Centre of RING pixel p (0 <= p < 12 nside^2) into out[o].
+__device__ __forceinline__ void ring_pixel(int64_t nside, int64_t p, int64_t o,
+                                           float *__restrict__ x, float *__restrict__ y,
+                                           float *__restrict__ z) {
     const int64_t npix = 12 * nside * nside;
     const int64_t ncap = 2 * nside * (nside - 1);
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= npix) return;
     float zz, omz, num, den;   // omz = 1 - |z|; phi = pi * num / den
     if (p < ncap || p >= npix - ncap) {
         const bool north = p < ncap;
@@ -64,9 +64,61 @@ __global__ void k_healpix_ring(int64_t nside, float *__restrict__ x, float *__re
     float rho = sqrtf(fmaxf(omz * (2.0f - omz), 0.0f));
     float s, c;
     sincospif(num / den, &s, &c);
-    x[p] = rho * c;
-    y[p] = rho * s;
-    z[p] = zz;
+    x[o] = rho * c;
+    y[o] = rho * s;
+    z[o] = zz;
+}
+
+__global__ void k_healpix_ring(int64_t nside, float *__restrict__ x, float *__restrict__ y,
+                               float *__restrict__ z) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < 12 * nside * nside) ring_pixel(nside, p, p, x, y, z);
+}
+
+// The even bits of v packed together (bit 2b -> bit b).
+__device__ __forceinline__ int64_t even_bits(uint64_t v) {
+    v &= 0x5555555555555555ull;
+    v = (v | (v >> 1)) & 0x3333333333333333ull;
+    v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v >> 16)) & 0x00000000FFFFFFFFull;
+    return (int64_t)v;
+}
+
+// NESTED pixel p -> RING pixel (Gorski et al. 2005): base face f, face
+// coordinates (ix, iy) from the interleaved bits, then the ring counted from
+// the north pole and the place in that ring.
+__device__ __forceinline__ int64_t nest_to_ring(int64_t nside, int64_t p) {
+    const int64_t npface = nside * nside, npix = 12 * npface, ncap = 2 * nside * (nside - 1);
+    const int f = (int)(p / npface);
+    const int64_t q = p - (int64_t)f * npface;
+    const int64_t ix = even_bits((uint64_t)q), iy = even_bits((uint64_t)q >> 1);
+    const int row = f >> 2;                                  // 0 north, 1 equator, 2 south
+    const int64_t jr = (2 + row) * nside - ix - iy - 1;      // ring, 1 .. 4 nside - 1
+    const int64_t jp0 = 2 * (f & 3) + (row == 1 ? 0 : 1);
+    int64_t nr, start, shift = 0;
+    if (jr < nside) {
+        nr = jr;
+        start = 2 * nr * (nr - 1);
+    } else if (jr > 3 * nside) {
+        nr = 4 * nside - jr;
+        start = npix - 2 * nr * (nr + 1);
+    } else {
+        nr = nside;
+        start = ncap + (jr - nside) * 4 * nside;
+        shift = (jr - nside) & 1;
+    }
+    int64_t jp = (jp0 * nr + ix - iy + 1 + shift) / 2;
+    if (jp > 4 * nside) jp -= 4 * nside;
+    if (jp < 1) jp += 4 * nside;
+    return start + jp - 1;
+}
+
+__global__ void k_healpix_nest(int64_t nside, float *__restrict__ x, float *__restrict__ y,
+                               float *__restrict__ z) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < 12 * nside * nside) ring_pixel(nside, nest_to_ring(nside, p), p, x, y, z);
 }
 
 __global__ void k_gather(const float *__restrict__ gx, const float *__restrict__ gy,
@@ -104,6 +156,15 @@ cudaError_t launch_grid_healpix(int32_t nside, float *x, float *y, float *z, cud
     int64_t blocks = (npix + 255) / 256;
     TraceScope ts(CC_STAGE_GRID, s);
     k_healpix_ring<<<(unsigned)blocks, 256, 0, s>>>(nside, x, y, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_healpix_nest(int32_t nside, float *x, float *y, float *z,
+                                    cudaStream_t s) {
+    int64_t npix = 12 * (int64_t)nside * nside;
+    int64_t blocks = (npix + 255) / 256;
+    TraceScope ts(CC_STAGE_GRID, s);
+    k_healpix_nest<<<(unsigned)blocks, 256, 0, s>>>(nside, x, y, z);
     return cudaGetLastError();
 }
 

@@ -176,9 +176,73 @@ struct SweepSmem {
     int abort_flag;
 };
 
+// The pair term for one ring and DP direction pairs (see the file header).
+template <int DP, bool KCUT>
+__device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
+                                           const float2 (&ncy)[DP], const float2 (&ncz)[DP],
+                                           float2 (&acc)[DP], float kc2) {
+    const float4 P0 = *reinterpret_cast<const float4 *>(&R.ax);
+    const float4 P1 = *reinterpret_cast<const float4 *>(&R.az);
+    const float2 P2 = *reinterpret_cast<const float2 *>(&R.nb);
+    const float2 ax2 = make_float2(P0.x, P0.y), ay2 = make_float2(P0.z, P0.w);
+    const float2 az2 = make_float2(P1.x, P1.y), k2 = make_float2(P1.z, P1.w);
+    const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
+#pragma unroll
+    for (int q = 0; q < DP; q++) {
+        float2 dx = __fadd2_rn(ax2, ncx[q]);
+        float2 dy = __fadd2_rn(ay2, ncy[q]);
+        float2 dz = __fadd2_rn(az2, ncz[q]);
+        float2 h = __fmul2_rn(dx, dx);
+        h = __ffma2_rn(dy, dy, h);
+        h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
+        float2 g = __ffma2_rn(h, m1, two2);             // 2 - h
+        float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+        float2 p = pair(1.4414361e-03f);                // acos_q, FP32x2
+        p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
+        p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
+        p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
+        p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
+        p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
+        p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
+        p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+        float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
+        float2 th = __fmul2_rn(rt, p);
+        float2 nbs = make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
+        float2 u = __ffma2_rn(th, k2, nbs);
+        float2 u2 = __fmul2_rn(u, u);
+        float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+        if (KCUT) {
+            e.x = u2.x > kc2 ? 0.0f : e.x;
+            e.y = u2.y > kc2 ? 0.0f : e.y;
+        }
+        acc[q] = __fadd2_rn(acc[q], e);
+    }
+}
+
+// Angular selection of a ring against a warp's cap (centre c' = c/sqrt(2),
+// radius rho): false when every direction within rho of c lies more than
+// k_cut widths from the ring, |theta - eta| > k_cut deta, so that all its
+// terms there are 0.  |alpha - eta| k comes from the pair formula at the
+// centre; by the triangle inequality no direction of the cap is closer to
+// the ring than |alpha - eta| - rho.  rho carries a margin for the FP32
+// error of both angles, so a skipped ring contributes exactly 0.
+__device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float cy, float cz,
+                                             float rho, float kc) {
+    const float dx = R.ax - cx, dy = R.ay - cy, dz = R.az - cz;
+    const float h = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float sv = fminf(h, fabsf(2.0f - h));
+    const float th = sqrt_approx(sv) * acos_q(sv);
+    const float u = fmaf(th, R.k, h <= 1.0f ? R.nb : R.nb2);
+    const float lim = fmaf(rho, R.k, kc);
+    return fabsf(u) <= lim;
+}
+
 // One work unit of the sweep: the 256 x D directions of direction block db
-// against the ring tiles split, split + nsplit, split + 2 nsplit, ... of the
-// *nkept packed rings.  Writes the unit's partial (or full) map row and, when
+// (warp w owns the 32 D consecutive ones from db 256 D + 32 D w; lane l the
+// directions l, l + 32, ...) against the ring tiles split, split + nsplit,
+// split + 2 nsplit, ... of the *nkept packed rings.  With the angular
+// selection on, each warp skips, tile by tile, the rings that cannot reach
+// its directions.  Writes the unit's partial (or full) map row and, when
 // bb_slot is set, its block best.  Returns false when a bounded wait gave up
 // (status set to CC_ETIMEOUT).
 template <int D, bool KCUT>
@@ -196,20 +260,56 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     auto &full = S.full;
     int &abort_flag = S.abort_flag;
 
-    const int tid = threadIdx.x;
-    const int64_t j0 = db * (int64_t)(kThreads * D) + tid;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t j0 = db * (int64_t)(kThreads * D) + (int64_t)(tid >> 5) * (32 * D) + lane;
 
-    // direction d of this thread: j0 + d * kThreads; pair p holds d = 2p, 2p+1
+    // direction d of this thread: j0 + 32 d; pair q holds d = 2q, 2q+1
     float2 ncx[DP], ncy[DP], ncz[DP], acc[DP], sum[DP], comp[DP];
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         ja = ja < M ? ja : M - 1;
         jb = jb < M ? jb : M - 1;
         ncx[q] = make_float2(-__ldg(cx + ja) * kInvSqrt2, -__ldg(cx + jb) * kInvSqrt2);
         ncy[q] = make_float2(-__ldg(cy + ja) * kInvSqrt2, -__ldg(cy + jb) * kInvSqrt2);
         ncz[q] = make_float2(-__ldg(cz + ja) * kInvSqrt2, -__ldg(cz + jb) * kInvSqrt2);
         acc[q] = sum[q] = comp[q] = make_float2(0.0f, 0.0f);
+    }
+
+    // the warp's cap: centre (scaled by 1/sqrt 2) and angular radius
+    float capx = 0.f, capy = 0.f, capz = 0.f, rho = 0.f, kc = 0.f;
+    if (KCUT) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            sx -= ncx[q].x + ncx[q].y;
+            sy -= ncy[q].x + ncy[q].y;
+            sz -= ncz[q].x + ncz[q].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        const float inv = kInvSqrt2 * rsqrtf(fmaxf(fmaf(sz, sz, fmaf(sy, sy, sx * sx)), 1e-30f));
+        capx = sx * inv;
+        capy = sy * inv;
+        capz = sz * inv;
+        float h = 0.f;                                  // largest |c' - cap'|^2 = chord^2 / 2
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            const float ax = ncx[q].x + capx, ay = ncy[q].x + capy, az = ncz[q].x + capz;
+            const float bx = ncx[q].y + capx, by = ncy[q].y + capy, bz = ncz[q].y + capz;
+            h = fmaxf(h, fmaf(az, az, fmaf(ay, ay, ax * ax)));
+            h = fmaxf(h, fmaf(bz, bz, fmaf(by, by, bx * bx)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+        // rho = 2 asin(chord / 2), chord = sqrt(2 h); plus 2e-5 rad for the
+        // rounding of the centre, the chords and both angles
+        rho = 2.0f * asinf(fminf(sqrtf(0.5f * h), 1.0f)) + 2.0e-5f;
+        kc = sqrtf(kc2);
     }
 
     const int64_t ntk = (*nkept + kTile - 1) / kTile;
@@ -227,7 +327,6 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
             tma_bulk_load(tile[s], src + (int64_t)s * stride, kTile * sizeof(RingRec), &full[s]);
     }
 
-    const float2 one2 = pair(1.0f), m1 = pair(-1.0f), two2 = pair(2.0f);
     for (int64_t t = 0; t < tiles; t++) {
         const int stage = (int)(t % kStages);
         const unsigned parity = (unsigned)((t / kStages) & 1);
@@ -235,43 +334,21 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
             abort_flag = 1;
         } else {
             const RingRec *T = tile[stage];
-#pragma unroll 2
-            for (int r = 0; r < kTile; r++) {
-                const float4 P0 = *reinterpret_cast<const float4 *>(&T[r].ax);
-                const float4 P1 = *reinterpret_cast<const float4 *>(&T[r].az);
-                const float2 P2 = *reinterpret_cast<const float2 *>(&T[r].nb);
-                const float2 ax2 = make_float2(P0.x, P0.y), ay2 = make_float2(P0.z, P0.w);
-                const float2 az2 = make_float2(P1.x, P1.y), k2 = make_float2(P1.z, P1.w);
+            if (KCUT) {
 #pragma unroll
-                for (int q = 0; q < DP; q++) {
-                    float2 dx = __fadd2_rn(ax2, ncx[q]);
-                    float2 dy = __fadd2_rn(ay2, ncy[q]);
-                    float2 dz = __fadd2_rn(az2, ncz[q]);
-                    float2 h = __fmul2_rn(dx, dx);
-                    h = __ffma2_rn(dy, dy, h);
-                    h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
-                    float2 g = __ffma2_rn(h, m1, two2);             // 2 - h
-                    float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
-                    float2 p = pair(1.4414361e-03f);                // acos_q, FP32x2
-                    p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
-                    p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
-                    p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
-                    p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
-                    p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
-                    p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
-                    p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
-                    float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
-                    float2 th = __fmul2_rn(rt, p);
-                    float2 nbs = make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
-                    float2 u = __ffma2_rn(th, k2, nbs);
-                    float2 u2 = __fmul2_rn(u, u);
-                    float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
-                    if (KCUT) {
-                        e.x = u2.x > kc2 ? 0.0f : e.x;
-                        e.y = u2.y > kc2 ? 0.0f : e.y;
+                for (int g = 0; g < kTile / 32; g++) {
+                    unsigned m = __ballot_sync(0xffffffffu,
+                                               ring_reaches(T[32 * g + lane], capx, capy, capz,
+                                                            rho, kc));
+                    while (m) {                        // warp-uniform: the rings that reach
+                        const int r = 32 * g + __ffs(m) - 1;
+                        m &= m - 1;
+                        ring_pairs<DP, KCUT>(T[r], ncx, ncy, ncz, acc, kc2);
                     }
-                    acc[q] = __fadd2_rn(acc[q], e);
                 }
+            } else {
+#pragma unroll 2
+                for (int r = 0; r < kTile; r++) ring_pairs<DP, KCUT>(T[r], ncx, ncy, ncz, acc, kc2);
             }
         }
         __syncthreads();
@@ -288,7 +365,6 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
             acc[q] = make_float2(0.0f, 0.0f);
         }
     }
-    (void)one2;
     if (abort_flag) {
         if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
         return false;
@@ -298,7 +374,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     int bj = INT32_MAX;
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        const int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        const int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
         if (ja < M) {
             out[split * M + ja] = va;

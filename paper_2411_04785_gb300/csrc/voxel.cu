@@ -421,14 +421,14 @@ cudaError_t launch_ring_apex(const cc_events &ev, const cc_rings &r, float *px, 
     if (ev.count == 0) return cudaSuccess;
     int64_t blocks = (ev.count + 255) / 256;
     if (blocks > (int64_t)device_sm_count() * 16) blocks = (int64_t)device_sm_count() * 16;
-    TraceScope ts(CC_STAGE_VOXEL, s);
+    TraceScope ts(CC_STAGE_RECON, s);
     k_ring_apex<<<(unsigned)blocks, 256, 0, s>>>(ev, r.perm, r.valid, px, py, pz);
     return cudaGetLastError();
 }
 
 cudaError_t launch_universe(int shape, int n, float pitch, float cx, float cy, float cz,
                             float *x, float *y, float *z, cudaStream_t s) {
-    TraceScope ts(CC_STAGE_VOXEL, s);
+    TraceScope ts(CC_STAGE_GRID, s);
     k_universe<<<(unsigned)n, 1024, 0, s>>>(shape, n, pitch, cx, cy, cz, x, y, z);
     return cudaGetLastError();
 }

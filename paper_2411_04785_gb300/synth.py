@@ -168,16 +168,21 @@ def _first_points(rng, n):
                     axis=1)
 
 
-def _simulate_tracks(rng, e0, u0, k, max_tries=64):
+def _simulate_tracks(rng, e0, u0, k, max_tries=64, point=None, from_point=None):
     """Forward Compton tracks: k-1 Klein-Nishina scatters then full
-    absorption.  Returns positions [n,4,3], deposits [n,4] and a mask of the
-    tracks whose every site fell inside a layer."""
+    absorption.  Rows in ``from_point`` come from the point ``point`` (their
+    direction is the one from it to their first site) instead of u0.
+    Returns positions [n,4,3], deposits [n,4] and a mask of the tracks whose
+    every site fell inside a layer."""
     n = e0.shape[0]
     pos = np.zeros((n, 4, 3))
     dep = np.zeros((n, 4))
     ok = np.ones(n, bool)
     p = _first_points(rng, n)
     u = u0.copy()
+    if point is not None and from_point is not None and from_point.any():
+        d = p[from_point] - np.asarray(point, float)[None, :]
+        u[from_point] = d / np.linalg.norm(d, axis=1, keepdims=True)
     e = e0.copy()
     pos[:, 0] = p
     for j in range(3):
@@ -211,12 +216,15 @@ def _simulate_tracks(rng, e0, u0, k, max_tries=64):
 def simulate_events(n_src: int = 18182, n_bkg: int = 181818, seed: int = 2,
                     theta_deg: float = 30.0, phi_deg: float = 45.0,
                     sigma_e_frac: float = 0.05, sigma_pos_cm: float = 1.0,
-                    source=None, dtype=np.float32):
+                    source=None, dtype=np.float32, source_point=None):
     """Detector events: source photons (Band spectrum, alpha -1, beta -2.3,
     E_peak 300 keV, 50 keV - 2 MeV) from one direction and isotropic
     background photons (E^-2, 50 keV - 2 MeV); k = 2/3/4 sites with
     probabilities 0.5/0.3/0.2; Gaussian noise sigma_e_frac of each deposit and
-    sigma_pos_cm per axis.  Sites are stored in a random slot order.
+    sigma_pos_cm per axis.  Sites are stored in a random slot order.  With
+    ``source_point`` (cm) the source is a point at that position instead of a
+    direction at infinity (near field): each source photon travels from it to
+    its first site.
 
     Returns a dict: n [N] u8; x, y, z, e [4, N] ``dtype`` (slot-major, unused
     slots 0); truth: order [N, 4] (slot of the j-th true site), is_source [N],
@@ -238,7 +246,8 @@ def simulate_events(n_src: int = 18182, n_bkg: int = 181818, seed: int = 2,
         e0 = np.where(src, _sample_band(rng, m), _sample_power_m2(rng, m))
         u0 = np.where(src[:, None], -s[None, :], -random_units(rng, m))
         k = rng.choice(np.array([2, 3, 4]), size=m, p=SITE_PROBS)
-        p_, d_, ok = _simulate_tracks(rng, e0, u0, k)
+        p_, d_, ok = _simulate_tracks(rng, e0, u0, k, point=source_point,
+                                      from_point=src if source_point is not None else None)
         done = todo[ok]
         pos[done], dep[done], kk[done], energy[done] = p_[ok], d_[ok], k[ok], e0[ok]
         todo = todo[~ok]

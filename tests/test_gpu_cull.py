@@ -1,0 +1,88 @@
+"""Angular selection with block skipping: on a NESTED HEALPix grid the
+sweep skips, per warp and tile, rings that cannot reach the warp's compact
+patch.  A skipped ring's terms are all cut to 0 anyway, so the map must be
+bit for bit the map of the same pixels in RING order (where patches are wide
+and little is skipped), and within the oracle's k_cut bracket."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_04785_gb300 import synth
+from tests.helpers import rings_to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2411_04785_gb300 as m
+    m.lib()
+    return m
+
+
+def nest_to_ring_perm(nside):
+    """RING index of every NESTED pixel, from the two oracle grids."""
+    nv = np.stack(oracle.grid_healpix_nest(nside), 1)
+    rv = np.stack(oracle.grid_healpix_ring(nside), 1)
+    out = np.empty(nv.shape[0], np.int64)
+    for a in range(0, nv.shape[0], 4096):
+        out[a:a + 4096] = (nv[a:a + 4096] @ rv.T).argmax(1)
+    return out
+
+
+@pytest.mark.parametrize("nside", [1, 2, 16, 64])
+def test_nest_grid_is_the_ring_grid_permuted(cc, nside):
+    perm = nest_to_ring_perm(nside)
+    gn = [t.cpu().numpy() for t in cc.grid_healpix_nest(nside, "cuda:0")]
+    gr = [t.cpu().numpy() for t in cc.grid_healpix_ring(nside, "cuda:0")]
+    for a, b in zip(gn, gr):
+        np.testing.assert_array_equal(a, b[perm])
+    on = oracle.grid_healpix_nest(nside)
+    for a, b in zip(gn, on):
+        assert np.abs(a - b).max() < 3e-7
+
+
+@pytest.mark.parametrize("dmax_deg,kcut", [(2.0, 5.0), (10.0, 3.0), (0.6, 8.0)])
+def test_skipping_is_exact(cc, dmax_deg, kcut):
+    nside = 64
+    perm = nest_to_ring_perm(nside)
+    rng = np.random.default_rng(int(dmax_deg * 10))
+    r, s, _ = synth.rings_burst(n=30000, seed=int(kcut))
+    r = dict(r)
+    lo, hi = math.log(math.radians(0.5)), math.log(math.radians(dmax_deg))
+    r["deta"] = np.exp(rng.uniform(lo, hi, 30000)).astype(np.float32)
+    rd = rings_to_dev(r, "cuda:0")
+    p = cc.Params(k_cut=kcut)
+    m_nest = cc.localize(rd, cc.grid_healpix_nest(nside, "cuda:0"), p)[0].cpu().numpy()
+    m_ring = cc.localize(rd, cc.grid_healpix_ring(nside, "cuda:0"), p)[0].cpu().numpy()
+    np.testing.assert_array_equal(m_nest, m_ring[perm])
+    # and within the oracle's bracket of the cut
+    g = oracle.grid_healpix_nest(nside)
+    idx = np.arange(0, g[0].size, 97)
+    r32 = {k: np.asarray(r[k], np.float32) for k in ("ax", "ay", "az", "eta", "deta")}
+    lo_m = oracle.likelihood_map(r32, g, idx=idx, k_cut=kcut * (1 - 1e-4))
+    hi_m = oracle.likelihood_map(r32, g, idx=idx, k_cut=kcut * (1 + 1e-4))
+    b = 1e-5 * np.maximum(hi_m, 1e-3 * hi_m.max()) + 1e-6
+    assert ((m_nest[idx] >= lo_m - b) & (m_nest[idx] <= hi_m + b)).all()
+
+
+def test_batched_sweep_with_skipping_equals_alone(cc):
+    from tests.test_gpu_serve import batch_localize
+    g = cc.grid_healpix_nest(32, "cuda:0")
+    p = cc.Params(k_cut=5.0, topk=2, nms_rad=math.radians(5))
+    sets = []
+    for n, seed in ((3000, 1), (20000, 2), (700, 3)):
+        r = dict(synth.rings_burst(n=n, seed=seed)[0])
+        r["deta"] = np.full(n, math.radians(1.5), np.float32)
+        sets.append(rings_to_dev(r, "cuda:0"))
+    mixed = batch_localize(cc, sets, g, p)
+    for rs, m in zip(sets, mixed):
+        alone = batch_localize(cc, [rs], g, p)[0]
+        np.testing.assert_array_equal(m["map"], alone["map"])
+        single = cc.localize(rs, g, p)[0].cpu().numpy()
+        np.testing.assert_allclose(m["map"], single, rtol=2e-6, atol=1e-6 * single.max())

@@ -140,3 +140,24 @@ def test_apex_is_the_first_site_of_the_chosen_order():
         # the first rank-th permutation's first slot is rank // (k-1)!
         assert order[0] == rank // math.factorial(k - 1)
     del rng
+
+
+def test_noise_free_near_field_cones_pass_through_the_point_source():
+    """Sec. 1.1 in the near field: noise-free events from a point source give
+    cones (oracle rings and apexes) through the source point, except where
+    the chosen order is not the true one."""
+    from paper_2411_04785_gb300 import synth
+    S = np.array([1.0, -2.0, 20.0])
+    ev = synth.simulate_events(n_src=2000, n_bkg=0, seed=3, sigma_e_frac=0.0, sigma_pos_cm=0.0,
+                               dtype=np.float64, source_point=tuple(S))
+    r = oracle.rings_from_events(ev, 0.05, 1.0, math.radians(0.5), math.radians(20))
+    v = r["valid"] == 1
+    ap = oracle.ring_apex(ev, r)[v]
+    a = np.stack([r["ax"], r["ay"], r["az"]], 1)[v]
+    d = S[None, :] - ap
+    th = np.arctan2(np.linalg.norm(np.cross(d, a), axis=1), np.sum(d * a, 1))
+    hit = np.abs(th - r["eta"][v]) < 1e-9
+    assert v.mean() > 0.99 and hit.mean() > 0.95
+    img = oracle.backproject({k: np.asarray(r[k])[v] for k in ("ax", "ay", "az", "eta", "deta")},
+                             ap, tuple(np.array([S[c], S[c] + 2.0]) for c in range(3)))
+    assert img[0] >= hit.sum() - 1e-6 and img[0] > img[1]
