@@ -95,7 +95,8 @@ static float sqdist_f32(const float *x, const float *y, const float *z, int p,
  * At each intermediate site j (not first, not last) the scatter cosine from
  * energies, cos_E = 1 - m_e c^2 (1/E_after - 1/E_before), must agree with the
  * cosine of the angle between the incoming and outgoing segments,
- * cos_G = u(x_{j-1} -> x_j) . u(x_j -> x_{j+1}).
+ * cos_G = u(x_{j-1} -> x_j) . u(x_j -> x_{j+1}), in binary32 as
+ * dot(d1, d2) * ((1/sqrt|d1|^2) * (1/sqrt|d2|^2)).
  * chi2 = sum_j (cos_E - cos_G)^2, unweighted.  The order is invalid (+inf)
  * when the first-site cone is invalid (E2 <= 0, |cos eta| > 1, or sites 1
  * and 2 closer than 1e-6 cm), or when some intermediate site has no energy
@@ -136,10 +137,13 @@ float or_order_chi2(int k, const float *x, const float *y, const float *z,
         float t1 = uy * vy;
         float t2 = uz * vz;
         float dot = (t0 + t1) + t2;
-        float nn = sqdist_f32(x, y, z, p, q) * sqdist_f32(x, y, z, q, r);
-        if (!(nn > 0.0f))
+        float npq = sqdist_f32(x, y, z, p, q), nqr = sqdist_f32(x, y, z, q, r);
+        if (!(npq > 0.0f) || !(nqr > 0.0f))
             return INF_F;
-        float cg = dot / sqrtf(nn);
+        /* inverse segment lengths, each 1/sqrt rounded once per operation;
+         * their product is the same in either direction of the path */
+        float il_pq = 1.0f / sqrtf(npq), il_qr = 1.0f / sqrtf(nqr);
+        float cg = dot * (il_pq * il_qr);
         float d = ce - cg;
         chi2 = chi2 + d * d;
     }
