@@ -427,6 +427,15 @@ cc_status cc_backproject(const cc_rings *rings, const float *px, const float *py
                          void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Self-check of the correctly rounded reciprocal and square root that the
+ * ordering decision uses (no counterpart in the paper; it backs the bit-exact
+ * ordering): on every float of [1, 4), mismatches[0] counts results that
+ * differ from __frcp_rn, mismatches[1] from __fsqrt_rn.  mismatches: device
+ * uint64 [2].  Asynchronous on `stream`.
+ */
+cc_status cc_selftest_exact_ops(uint64_t *mismatches, void *stream);
+
+/*
  * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
  * counted per stage; when tracing is enabled each launch is also bracketed by
  * two CUDA events recorded on the launching stream, and cc_trace_read()

@@ -144,6 +144,8 @@ def lib() -> C.CDLL:
         L.cc_backproject.argtypes = [C.POINTER(cc_rings), _P, _P, _P, C.POINTER(cc_grid),
                                      C.POINTER(cc_params), _P, _P, _P, _P, C.c_size_t, _P]
         L.cc_backproject.restype = S
+        L.cc_selftest_exact_ops.argtypes = [_P, _P]
+        L.cc_selftest_exact_ops.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -705,4 +707,12 @@ def backproject(rings: dict, apex, voxels, params: Params | None = None, workspa
         C.byref(rs), *(_ptr(t) for t in apex), C.byref(vs), C.byref(params.c()),
         _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(workspace), workspace.numel(),
         _stream(stream)))
+    return out
+
+
+def selftest_exact_ops(device="cuda", stream=None):
+    """Mismatches of the decision's correctly rounded reciprocal and square
+    root against the CUDA intrinsics over [1, 4): (rcp, sqrt)."""
+    out = torch.empty(2, dtype=torch.uint64, device=device)
+    _check("cc_selftest_exact_ops", lib().cc_selftest_exact_ops(_ptr(out), _stream(stream)))
     return out

@@ -385,6 +385,14 @@ cc_status cc_cluster_spectrum(const uint64_t *ev_adc, const int64_t *n_events, u
     return CC_OK;
 }
 
+cc_status cc_selftest_exact_ops(uint64_t *mismatches, void *stream) {
+    g_err[0] = 0;
+    if (!mismatches) return fail(CC_EINVAL, "mismatches is NULL");
+    cudaError_t e = launch_selftest_exact(mismatches, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest launch");
+    return CC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // near-field back projection (Sec. 3)
 // ---------------------------------------------------------------------------

@@ -134,6 +134,8 @@ cudaError_t mlp_params_to_bf16(const float *p, uint16_t *wb, cudaStream_t s);
 cudaError_t mlp_apply_filter(const float *out, const cc_rings &r, float tau, float dmin,
                              float dmax, cudaStream_t s);
 
+cudaError_t launch_selftest_exact(uint64_t *bad, cudaStream_t s);   // recon.cu
+
 // ---------------------------------------------------------------------------
 // event clustering of detections - cluster.cu
 // ---------------------------------------------------------------------------

@@ -5,16 +5,18 @@
 // One thread per event, events grouped by site count within each CTA (see
 // k_rings_from_events).  The ORDER is an integer decided by floating point,
 // so it is decided in IEEE binary32 with every operation rounded once
-// (__fadd_rn / __fmul_rn / __frcp_rn / __fdiv_rn / __fsqrt_rn: no
-// contraction into FMA), in a fixed sequence:
+// (__fadd_rn / __fmul_rn / __fdiv_rn and the correctly rounded rcp_exact /
+// sqrt_exact of cc_math.cuh: no contraction into FMA), in a fixed sequence:
 //   E(S)        = deposits of the slots in set S added in increasing slot order
 //   cos(Ea, Eb) = 1 - m_e c^2 * (1/Ea - 1/Eb)
 //   |x_q - x_p|^2 = ((dx*dx) + (dy*dy)) + (dz*dz), d = x_q - x_p
-//   cos_G(p,q,r)  = dot(x_q - x_p, x_r - x_q) / sqrt(|x_q-x_p|^2 * |x_r-x_q|^2)
+//   il(p,q)     = 1 / sqrt(|x_q - x_p|^2)       (one per site pair)
+//   cos_G(p,q,r)  = dot(x_q - x_p, x_r - x_q) * (il(p,q) * il(q,r))
 //   chi2        = sum over intermediate positions (ascending) of (cos_E - cos_G)^2
 // so any implementation of the same rule in binary32 picks the same order.
-// The ring itself (axis, eta, width) is computed in FP32 with
-// better-conditioned but mathematically equal formulas.
+// The ring itself (axis, eta, width) is not a decision: it is computed in
+// FP32 with better-conditioned but mathematically equal formulas, using the
+// MUFU approximations.
 #include "cc_math.cuh"
 
 namespace cc {
@@ -32,8 +34,8 @@ __device__ __forceinline__ float set_energy(const float (&e)[4], unsigned mask) 
 }
 
 __device__ __forceinline__ float compton_cos(float e_after, float e_before) {
-    float ia = __frcp_rn(e_after);
-    float ib = __frcp_rn(e_before);
+    float ia = rcp_exact(e_after);
+    float ib = rcp_exact(e_before);
     return __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(ia, ib)));
 }
 
@@ -50,27 +52,31 @@ __device__ __forceinline__ bool in_unit(float c) { return c >= -1.0f && c <= 1.0
 
 // Per-event tables of the binary32 decision sequence, built once and shared
 // by all k! orders (indices are compile-time constants after unrolling):
-// subset energies E[S] and their reciprocals 1/E[S], squared site distances,
-// and the geometric cosines cos_G(p -> q -> r) = dot(x_q - x_p, x_r - x_q) /
-// sqrt(|x_q - x_p|^2 |x_r - x_q|^2), which are bitwise symmetric in p and r.
+// subset energies E[S] and their reciprocals 1/E[S], squared site distances
+// and inverse lengths, and the geometric cosines cos_G(p -> q -> r) =
+// dot(x_q - x_p, x_r - x_q) * (il(p,q) * il(q,r)), bitwise symmetric in p, r.
 template <int K>
 struct OrderTables {
     float E[1 << K], inv[1 << K];
     float nsq[K][K];
     float cg[K][K][K];
-    bool cgok[K][K][K];   // |x_q - x_p|^2 |x_r - x_q|^2 > 0
+    bool cgok[K][K][K];   // |x_q - x_p|^2 > 0 and |x_r - x_q|^2 > 0
 
     __device__ __forceinline__ OrderTables(const float (&x)[4], const float (&y)[4],
                                            const float (&z)[4], const float (&e)[4]) {
 #pragma unroll
         for (unsigned m = 1; m < (1u << K); m++) {
             E[m] = set_energy<K>(e, m);
-            inv[m] = __frcp_rn(E[m]);
+            inv[m] = rcp_exact(E[m]);
         }
+        float il[K][K];
 #pragma unroll
         for (int p = 0; p < K; p++)
 #pragma unroll
-            for (int q = p + 1; q < K; q++) nsq[p][q] = nsq[q][p] = sqdist(x, y, z, p, q);
+            for (int q = p + 1; q < K; q++) {
+                nsq[p][q] = nsq[q][p] = sqdist(x, y, z, p, q);
+                il[p][q] = il[q][p] = rcp_exact(sqrt_exact(nsq[p][q]));
+            }
 #pragma unroll
         for (int q = 0; q < K; q++)
 #pragma unroll
@@ -84,10 +90,9 @@ struct OrderTables {
                           vz = __fsub_rn(z[r], z[q]);
                     float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
                                           __fmul_rn(uz, vz));
-                    float nn = __fmul_rn(nsq[p][q], nsq[q][r]);
-                    float c = __fdiv_rn(dot, __fsqrt_rn(nn));
+                    float c = __fmul_rn(dot, __fmul_rn(il[p][q], il[q][r]));
                     cg[p][q][r] = cg[r][q][p] = c;
-                    cgok[p][q][r] = cgok[r][q][p] = nn > 0.0f;
+                    cgok[p][q][r] = cgok[r][q][p] = nsq[p][q] > 0.0f && nsq[q][r] > 0.0f;
                 }
     }
 
@@ -133,7 +138,7 @@ __device__ __forceinline__ bool two_site_valid(const float (&x)[4], const float 
 // Klein-Nishina angular weight P^2 (P + 1/P - sin^2 eta), binary32 sequence.
 __device__ __forceinline__ float kn_weight(float P, float c) {
     float s2 = __fsub_rn(1.0f, __fmul_rn(c, c));
-    float t = __fsub_rn(__fadd_rn(P, __frcp_rn(P)), s2);
+    float t = __fsub_rn(__fadd_rn(P, rcp_exact(P)), s2);
     return __fmul_rn(__fmul_rn(P, P), t);
 }
 
@@ -190,7 +195,7 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
 }
 
 constexpr int kRThreads = 256;
-constexpr int kWin = 1024;            // events per CTA window
+constexpr int kWin = 768;             // events per CTA window (3 CTAs per SM)
 constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
 struct ReconSmem {
@@ -231,23 +236,25 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const
     // 1/E2 - 1/E0 = E1 / (E2 E0): no cancellation for small E1
     // u = 1 - cos(eta) in [0, 2] for a valid order; eta from u directly (the
     // chord form of acos, no rounding of 1 - u)
-    float u = fminf(fmaxf(kMeKeV * e1 / (e2 * e0), 0.0f), 2.0f);
+    const float ie0 = rcp_approx(e0), ie2 = rcp_approx(e2);
+    float u = fminf(fmaxf(kMeKeV * e1 * (ie2 * ie0), 0.0f), 2.0f);
     float th = angle_from_half_chord2(u);
-    float sin_eta = sqrtf(fmaxf(u * (2.0f - u), 0.0f));   // sqrt((1-c)(1+c))
+    float sin_eta = sqrt_approx(fmaxf(u * (2.0f - u), 0.0f));   // sqrt((1-c)(1+c))
 
     float dx = pick(x, f0) - pick(x, f1);
     float dy = pick(y, f0) - pick(y, f1);
     float dz = pick(z, f0) - pick(z, f1);
-    float inv_len = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    float inv_len = rsqrt_approx(dx * dx + dy * dy + dz * dz);
 
     float s1 = sig_e * e1;
     // 1/E2^2 - 1/E0^2 = E1 (E0 + E2) / (E2^2 E0^2)
-    float q = e1 * (e0 + e2) / ((e2 * e2) * (e0 * e0));
-    float t1 = s1 / (e0 * e0);
+    const float ie02 = ie0 * ie0;
+    float q = e1 * (e0 + e2) * ((ie2 * ie2) * ie02);
+    float t1 = s1 * ie02;
     float var_cos = kMeKeV * kMeKeV * (t1 * t1 + var2 * q * q);
-    float w_e = sqrtf(var_cos) / fmaxf(sin_eta, 1e-3f);
+    float w_e = sqrt_approx(var_cos) * rcp_approx(fmaxf(sin_eta, 1e-3f));
     float w_g = 1.41421356237f * sig_pos * inv_len;
-    float wd = sqrtf(w_e * w_e + w_g * w_g);
+    float wd = sqrt_approx(w_e * w_e + w_g * w_g);
 
     S.o[0][w] = dx * inv_len;
     S.o[1][w] = dy * inv_len;
@@ -263,7 +270,7 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const
 // 32-event chunks from a shared queue, the costly 4-site chunks first, so
 // that a warp runs one code path at a time and the warps finish together;
 // the rings are written back in the original order with coalesced stores.
-__global__ void __launch_bounds__(kRThreads, 2)
+__global__ void __launch_bounds__(kRThreads, 3)
 k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
                     const float *__restrict__ ys, const float *__restrict__ zs,
                     const float *__restrict__ es, int64_t count, int64_t stride,
@@ -354,6 +361,29 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
 }
 
 }  // namespace
+
+// Every float of [1, 4) (all mantissas, both exponent parities): the
+// correctly rounded rcp_exact / sqrt_exact against the CUDA intrinsics.
+__global__ void k_selftest_exact(unsigned long long *__restrict__ bad) {
+    const uint32_t lo = 0x3F800000u, hi = 0x40800000u;
+    unsigned long long b0 = 0, b1 = 0;
+    for (uint32_t u = lo + blockIdx.x * blockDim.x + threadIdx.x; u < hi;
+         u += gridDim.x * blockDim.x) {
+        const float x = __uint_as_float(u);
+        b0 += __float_as_uint(rcp_exact(x)) != __float_as_uint(__frcp_rn(x));
+        b1 += __float_as_uint(sqrt_exact(x)) != __float_as_uint(__fsqrt_rn(x));
+    }
+    if (b0) atomicAdd(bad, b0);
+    if (b1) atomicAdd(bad + 1, b1);
+}
+
+cudaError_t launch_selftest_exact(uint64_t *bad, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, 2 * sizeof(uint64_t), s);
+    if (e != cudaSuccess) return e;
+    k_selftest_exact<<<(unsigned)device_sm_count() * 8, 256, 0, s>>>(
+        reinterpret_cast<unsigned long long *>(bad));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
                                      const cc_params &p, cudaStream_t s) {

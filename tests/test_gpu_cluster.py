@@ -47,7 +47,7 @@ def test_stream_matches_oracle(cc, dt_max):
     assert_same(got, oracle.maxstep_events(t, adc, dt_max))
 
 
-@pytest.mark.parametrize("N", [1, 2, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 12289])
+@pytest.mark.parametrize("N", [1, 2, 31, 32, 33, 511, 512, 513, 2047, 2048, 2049, 4095, 4096, 4097, 12289])
 def test_sizes_and_tile_boundaries(cc, N):
     rng = np.random.default_rng(N)
     t = np.cumsum(rng.integers(0, 20, N))

@@ -442,3 +442,13 @@ def test_abi_rejects_bad_arguments(cc, dev):
     with pytest.raises(cc.CCError):
         cc.refine(rd, torch.zeros((65, 3), dtype=torch.float64, device=dev))
     torch.cuda.synchronize()
+
+
+def test_exact_reciprocal_and_root_match_the_intrinsics(cc):
+    """The ordering decision's correctly rounded reciprocal and square root
+    equal __frcp_rn / __fsqrt_rn on every float of [1, 4), hence (the result
+    depending only on mantissa and exponent parity there) on [2^-100, 2^100]."""
+    from paper_2411_04785_gb300 import api
+    out = api.selftest_exact_ops("cuda:0")
+    torch.cuda.synchronize()
+    assert out.view(torch.int64).cpu().tolist() == [0, 0]
