@@ -31,6 +31,18 @@ __device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, unsign
         : "memory");
 }
 
+// A bulk copy completing on `bar` whose expected bytes were already
+// announced (several copies may share one arrive.expect_tx).  Both addresses
+// 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Bounded wait for an mbarrier phase: false after kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
     unsigned b = smem_u32(bar);

@@ -121,15 +121,6 @@ struct ClusterSmem {
     long long tile;
 };
 
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
-                                          unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 __global__ void __launch_bounds__(kCThreads)
 k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, long long N,
           long long dt_max, unsigned char *__restrict__ edge, int *__restrict__ event_id,

@@ -18,6 +18,7 @@
 // FP32 with better-conditioned but mathematically equal formulas, using the
 // MUFU approximations.
 #include "cc_math.cuh"
+#include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
@@ -199,12 +200,14 @@ constexpr int kWin = 768;             // events per CTA window (3 CTAs per SM)
 constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
 struct ReconSmem {
-    float v[4][4][kWin];      // [x|y|z|e][slot][sorted position]
+    float v[4][4][kWin];      // [x|y|z|e][slot][window position]
     float o[5][kWin];         // ax, ay, az, eta, deta by window position
-    uint16_t win_of[kWin];    // sorted position -> window position
-    uint8_t k[kWin];          // site count by sorted position
+    uint16_t order[kWin];     // sorted position -> window position
+    uint8_t k[kWin];          // site count by window position
     uint8_t ov[kWin], op[kWin];
     int cnt[4], start[4], fill[4], next;
+    unsigned long long bar;
+    int load_failed;
 };
 
 // Ring of one event (FP32) from its chosen order; writes window position w.
@@ -265,39 +268,74 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const
     S.op[w] = (uint8_t)rk;
 }
 
-// One CTA takes a window of 1024 consecutive events.  It counting-sorts them
-// in shared memory by site count (4, 3, 2, other), then its warps take
-// 32-event chunks from a shared queue, the costly 4-site chunks first, so
-// that a warp runs one code path at a time and the warps finish together;
-// the rings are written back in the original order with coalesced stores.
+// One CTA takes a window of 768 consecutive events.  Their sites are staged
+// in shared memory in window order, by 16 bulk copies (TMA: x, y, z, e of
+// each slot, 3 KB each) on one mbarrier when the window is whole and the
+// arrays are 16-byte aligned, by plain loads otherwise.  The events are
+// grouped by site count (4, 3, 2, other) through an index, and the warps
+// take 32-event chunks from a shared queue, the costly 4-site chunks first,
+// so that a warp runs one code path at a time and the warps finish
+// together; the rings are written back in the original order with coalesced
+// stores.  Slots past an event's site count are staged too and never read.
 __global__ void __launch_bounds__(kRThreads, 3)
 k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
                     const float *__restrict__ ys, const float *__restrict__ zs,
-                    const float *__restrict__ es, int64_t count, int64_t stride,
+                    const float *__restrict__ es, int64_t count, int64_t stride, int bulk_ok,
                     float sig_e, float sig_pos, float deta_min, float deta_max,
                     float *__restrict__ ax, float *__restrict__ ay,
                     float *__restrict__ az, float *__restrict__ eta,
                     float *__restrict__ deta, uint8_t *__restrict__ valid,
                     uint8_t *__restrict__ perm) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     ReconSmem &S = *reinterpret_cast<ReconSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t base = blockIdx.x * (int64_t)kWin;
+    const bool bulk = bulk_ok && base + kWin <= count;
     if (tid < 4) {
         S.cnt[tid] = 0;
         S.fill[tid] = 0;
     }
-    if (tid == 0) S.next = 0;
+    if (tid == 0) {
+        S.next = 0;
+        S.load_failed = 0;
+        if (bulk) {
+            mbar_init(&S.bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                             smem_u32(&S.bar)), "r"((unsigned)(16 * kWin * sizeof(float)))
+                         : "memory");
+            const float *src[4] = {xs, ys, zs, es};
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int sl = 0; sl < 4; sl++)
+                    bulk_copy(S.v[a][sl], src[a] + sl * stride + base,
+                              (unsigned)(kWin * sizeof(float)), &S.bar);
+        }
+    }
     __syncthreads();
 
     constexpr int kPer = kWin / kRThreads;
     int kk[kPer], cls[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; j++) {
-        const int64_t i = base + tid + j * kRThreads;
+        const int w = tid + j * kRThreads;
+        const int64_t i = base + w;
         kk[j] = i < count ? n[i] : 0;
         cls[j] = kk[j] == 4 ? 0 : kk[j] == 3 ? 1 : kk[j] == 2 ? 2 : 3;
+        S.k[w] = (uint8_t)kk[j];
         atomicAdd(&S.cnt[cls[j]], 1);
+        if (!bulk) {
+#pragma unroll
+            for (int sl = 0; sl < 4; sl++) {
+                const bool used = sl < kk[j];     // kk = 0 past the end
+                const int64_t off = sl * stride + i;
+                S.v[0][sl][w] = used ? __ldg(xs + off) : 0.0f;
+                S.v[1][sl][w] = used ? __ldg(ys + off) : 0.0f;
+                S.v[2][sl][w] = used ? __ldg(zs + off) : 0.0f;
+                S.v[3][sl][w] = used ? __ldg(es + off) : 0.0f;
+            }
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -310,38 +348,35 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kPer; j++) {
-        const int w = tid + j * kRThreads;
-        const int64_t i = base + w;
         const int p = S.start[cls[j]] + atomicAdd(&S.fill[cls[j]], 1);
-        S.k[p] = (uint8_t)kk[j];
-        S.win_of[p] = (uint16_t)w;
-#pragma unroll
-        for (int s = 0; s < 4; s++) {
-            const bool used = s < kk[j];     // kk = 0 past the end
-            const int64_t off = s * stride + i;
-            S.v[0][s][p] = used ? __ldg(xs + off) : 0.0f;
-            S.v[1][s][p] = used ? __ldg(ys + off) : 0.0f;
-            S.v[2][s][p] = used ? __ldg(zs + off) : 0.0f;
-            S.v[3][s][p] = used ? __ldg(es + off) : 0.0f;
-        }
+        S.order[p] = (uint16_t)(tid + j * kRThreads);
     }
+    if (bulk && tid == 0 && !mbar_wait(&S.bar, 0)) S.load_failed = 1;
     __syncthreads();
 
-    for (;;) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(&S.next, 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= kChunks) break;
-        const int p = c * 32 + lane;
-        float x[4], y[4], z[4], e[4];
+    if (!S.load_failed) {
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&S.next, 1);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= kChunks) break;
+            const int w = S.order[c * 32 + lane];
+            float x[4], y[4], z[4], e[4];
 #pragma unroll
-        for (int s = 0; s < 4; s++) {
-            x[s] = S.v[0][s][p];
-            y[s] = S.v[1][s][p];
-            z[s] = S.v[2][s][p];
-            e[s] = S.v[3][s][p];
+            for (int sl = 0; sl < 4; sl++) {
+                x[sl] = S.v[0][sl][w];
+                y[sl] = S.v[1][sl][w];
+                z[sl] = S.v[2][sl][w];
+                e[sl] = S.v[3][sl][w];
+            }
+            ring_of_event(S, w, S.k[w], x, y, z, e, sig_e, sig_pos, deta_min, deta_max);
         }
-        ring_of_event(S, S.win_of[p], S.k[p], x, y, z, e, sig_e, sig_pos, deta_min, deta_max);
+    } else {   // a bounded wait gave up: the window's rings are left invalid
+        for (int w = tid; w < kWin; w += kRThreads) {
+            S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
+            S.ov[w] = 0;
+            S.op[w] = 255;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -394,8 +429,10 @@ cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
     if (e != cudaSuccess) return e;
     int64_t blocks = (ev.count + kWin - 1) / kWin;
     TraceScope ts(CC_STAGE_RECON, s);
+    auto a16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    const int bulk_ok = a16(ev.x) && a16(ev.y) && a16(ev.z) && a16(ev.e) && (ev.stride % 4) == 0;
     k_rings_from_events<<<(unsigned)blocks, kRThreads, smem, s>>>(
-        ev.n, ev.x, ev.y, ev.z, ev.e, ev.count, ev.stride, p.sigma_e_frac,
+        ev.n, ev.x, ev.y, ev.z, ev.e, ev.count, ev.stride, bulk_ok, p.sigma_e_frac,
         p.sigma_pos_cm, p.deta_min, p.deta_max, out.ax, out.ay, out.az, out.eta,
         out.deta, out.valid, out.perm);
     return cudaGetLastError();
