@@ -126,16 +126,6 @@ __device__ __forceinline__ float order_chi2_t(const OrderTables<K> &T, const int
     return ok ? chi2 : kInf;
 }
 
-// Two-site validity (no intermediate site): the first-site cone only.
-__device__ __forceinline__ bool two_site_valid(const float (&x)[4], const float (&y)[4],
-                                               const float (&z)[4], const float (&e)[4],
-                                               int p0) {
-    float e0 = set_energy<2>(e, 3u);
-    float e2 = set_energy<2>(e, 3u & ~(1u << p0));
-    float c1 = compton_cos(e2, e0);
-    return (e0 > 0.0f) && (e2 > 0.0f) && in_unit(c1) && (sqdist(x, y, z, 0, 1) > 1e-12f);
-}
-
 // Klein-Nishina angular weight P^2 (P + 1/P - sin^2 eta), binary32 sequence.
 __device__ __forceinline__ float kn_weight(float P, float c) {
     float s2 = __fsub_rn(1.0f, __fmul_rn(c, c));
@@ -157,12 +147,18 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
                                             const float (&z)[4], const float (&e)[4],
                                             int &f0, int &f1) {
     if constexpr (K == 2) {
-        bool ok0 = two_site_valid(x, y, z, e, 0);
-        bool ok1 = two_site_valid(x, y, z, e, 1);
-        float e0 = set_energy<2>(e, 3u);
+        // two-site validity is the first-site cone alone; the binary32
+        // sequence of compton_cos with each shared quantity computed once;
         // set_energy of a single slot is the deposit itself (0 + e = e)
-        float w0 = kn_weight(__fdiv_rn(e[1], e0), compton_cos(e[1], e0));
-        float w1 = kn_weight(__fdiv_rn(e[0], e0), compton_cos(e[0], e0));
+        const float e0 = set_energy<2>(e, 3u);
+        const float ie0 = rcp_exact(e0);
+        const float c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[1]), ie0)));
+        const float c1 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[0]), ie0)));
+        const bool apart = sqdist(x, y, z, 0, 1) > 1e-12f;
+        const bool ok0 = (e0 > 0.0f) && (e[1] > 0.0f) && in_unit(c0) && apart;
+        const bool ok1 = (e0 > 0.0f) && (e[0] > 0.0f) && in_unit(c1) && apart;
+        const float w0 = kn_weight(__fdiv_rn(e[1], e0), c0);
+        const float w1 = kn_weight(__fdiv_rn(e[0], e0), c1);
         if (ok1 && (!ok0 || w1 > w0)) { f0 = 1; f1 = 0; return 1; }
         if (ok0) { f0 = 0; f1 = 1; return 0; }
         return -1;
@@ -205,7 +201,9 @@ struct ReconSmem {
     uint16_t order[kWin];     // sorted position -> window position
     uint8_t k[kWin];          // site count by window position
     uint8_t ov[kWin], op[kWin];
-    int cnt[4], start[4], fill[4], next;
+    int grp[kWin / 32][4];    // events of each class in each 32-event group
+    int off[kWin / 32][4];    // sorted position of each group's first event of a class
+    int next;
     unsigned long long bar;
     int load_failed;
 };
@@ -291,10 +289,6 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t base = blockIdx.x * (int64_t)kWin;
     const bool bulk = bulk_ok && base + kWin <= count;
-    if (tid < 4) {
-        S.cnt[tid] = 0;
-        S.fill[tid] = 0;
-    }
     if (tid == 0) {
         S.next = 0;
         S.load_failed = 0;
@@ -315,8 +309,10 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     }
     __syncthreads();
 
+    // group the window by site count: 32-event groups g = w / 32 count their
+    // classes by ballot, one warp scans the counts into positions
     constexpr int kPer = kWin / kRThreads;
-    int kk[kPer], cls[kPer];
+    int kk[kPer], cls[kPer], rk[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; j++) {
         const int w = tid + j * kRThreads;
@@ -324,7 +320,14 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
         kk[j] = i < count ? n[i] : 0;
         cls[j] = kk[j] == 4 ? 0 : kk[j] == 3 ? 1 : kk[j] == 2 ? 2 : 3;
         S.k[w] = (uint8_t)kk[j];
-        atomicAdd(&S.cnt[cls[j]], 1);
+        unsigned mine = 0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const unsigned m = __ballot_sync(0xffffffffu, cls[j] == c);
+            if (lane == 0) S.grp[w >> 5][c] = __popc(m);
+            mine = cls[j] == c ? m : mine;
+        }
+        rk[j] = __popc(mine & ((1u << lane) - 1u));
         if (!bulk) {
 #pragma unroll
             for (int sl = 0; sl < 4; sl++) {
@@ -338,18 +341,27 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        int b = 0;
+    if (tid < 32) {                       // kWin / 32 = 24 groups: one lane each
+        constexpr int G = kWin / 32;
+        int before = 0;                   // events of earlier classes
+#pragma unroll
         for (int c = 0; c < 4; c++) {
-            S.start[c] = b;
-            b += S.cnt[c];
+            const int v = tid < G ? S.grp[tid][c] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (tid >= o) x += y;
+            }
+            if (tid < G) S.off[tid][c] = before + x - v;
+            before += __shfl_sync(0xffffffffu, x, 31);
         }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kPer; j++) {
-        const int p = S.start[cls[j]] + atomicAdd(&S.fill[cls[j]], 1);
-        S.order[p] = (uint16_t)(tid + j * kRThreads);
+        const int w = tid + j * kRThreads;
+        S.order[S.off[w >> 5][cls[j]] + rk[j]] = (uint16_t)w;
     }
     if (bulk && tid == 0 && !mbar_wait(&S.bar, 0)) S.load_failed = 1;
     __syncthreads();
