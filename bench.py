@@ -577,7 +577,9 @@ def run_serve(args):
     out_arms = {}
     gpu_index = local
     for name, kw in arms.items():
-        srv = serve.Server(grid, p, hbm_budget=8 << 30, max_active=48, **kw)
+        srv = serve.Server(grid, p, hbm_budget=8 << 30, max_active=48, graphs=bool(args.graphs),
+                           **kw)
+        srv.prepare([b.count for b in bursts])                         # capture the graphs
         srv.run(bursts[:args.warmup * 4], realtime=False)              # warm-up
         torch.cuda.synchronize()
         cc.trace_read(reset=True)
@@ -629,6 +631,7 @@ def run_serve(args):
                       "background": "uniform 1-50x", "directions": M,
                       "grid": "HEALPix nside 64 RING", "hbm_budget_gb": 8, "max_active": 48,
                       "arrivals": "real time (Poisson)",
+                      "front_end": "CUDA graph per size bucket" if args.graphs else "launched",
                       "filter": {"train_events": args.train_events, "train_s": t_train,
                                  "loss_first_last": [losses[0], losses[-1]], "tau": args.tau}},
            "latency_ms": {"plain": pl["latency_ms"], "learned": le["latency_ms"]},
@@ -866,6 +869,8 @@ def main():
     ap.add_argument("--train-events", type=int, default=1_000_000,
                     help="serve: events simulated to train the ring filter")
     ap.add_argument("--tau", type=float, default=0.0, help="serve: ring filter score threshold")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="serve: 1 = per-burst front end as a CUDA graph per size bucket")
     ap.add_argument("--kcut", type=float, default=0.0,
                     help="burst1m: angular selection |r| <= kcut on a NESTED grid (0: off)")
     ap.add_argument("--quick", action="store_true", help="skip e2e, recon pile and CPU baseline")

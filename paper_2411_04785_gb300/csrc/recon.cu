@@ -34,12 +34,6 @@ __device__ __forceinline__ float set_energy(const float (&e)[4], unsigned mask) 
     return s;
 }
 
-__device__ __forceinline__ float compton_cos(float e_after, float e_before) {
-    float ia = rcp_exact(e_after);
-    float ib = rcp_exact(e_before);
-    return __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(ia, ib)));
-}
-
 __device__ __forceinline__ float sqdist(const float (&x)[4], const float (&y)[4],
                                         const float (&z)[4], int p, int q) {
     float dx = __fsub_rn(x[q], x[p]);
@@ -147,9 +141,10 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
                                             const float (&z)[4], const float (&e)[4],
                                             int &f0, int &f1) {
     if constexpr (K == 2) {
-        // two-site validity is the first-site cone alone; the binary32
-        // sequence of compton_cos with each shared quantity computed once;
-        // set_energy of a single slot is the deposit itself (0 + e = e)
+        // two-site validity is the first-site cone alone; its cosine is
+        // 1 - m_e c^2 (1/E2 - 1/E0) in the binary32 sequence above, each
+        // shared quantity computed once; set_energy of a single slot is the
+        // deposit itself (0 + e = e)
         const float e0 = set_energy<2>(e, 3u);
         const float ie0 = rcp_exact(e0);
         const float c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[1]), ie0)));

@@ -15,6 +15,14 @@ A burst's results do not depend on the batch it was swept in (the batched
 sweep keeps each burst's own plan), which the tests check against the same
 burst served alone.  Host code here only schedules and moves buffers: every
 step of the localisation runs in libcompton.so.
+
+With graphs=True the per-burst front end (reconstruction and, on the learned
+path, features, MLP and filter) is a CUDA graph captured once per size bucket
+(powers of two) with static buffers: a burst copies its events in, marks the
+padding events empty (n = 0, so their rings are invalid and compacted away
+before the sweep) and replays one graph instead of launching a dozen kernels
+from the host.  Every event and every MLP row is computed independently, so
+the results equal the graph-less path's bit for bit.
 """
 from __future__ import annotations
 
@@ -58,6 +66,46 @@ class _Active:
     swept: bool = False
     done: torch.cuda.Event | None = None
     out_host: dict = field(default_factory=dict)
+    front: "_Front | None" = None
+
+
+class _Front:
+    """A captured front end for bursts of up to `cap` events."""
+
+    def __init__(self, srv: "Server", cap: int):
+        dev = srv.dev
+        self.cap = cap
+        self.n = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        self.xyze = {k: torch.zeros((4, cap), dtype=torch.float32, device=dev) for k in "xyze"}
+        self.rings = api.empty_rings(cap, dev)
+        learned = srv.filter is not None
+        if learned:
+            self.feats = torch.empty((cap, api.MLP_FEATURES), dtype=torch.bfloat16, device=dev)
+            self.out = torch.empty((cap, 2), dtype=torch.float32, device=dev)
+            self.mws = torch.empty(api.mlp_workspace_bytes(cap), dtype=torch.uint8, device=dev)
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        x, y, z, e = (self.xyze[k] for k in "xyze")
+
+        def body():
+            api.rings_from_events(self.n, x, y, z, e, srv.params, out=self.rings, stream=s)
+            if learned:
+                api.ring_features(self.n, x, y, z, e, self.rings, srv.params, out=self.feats,
+                                  stream=s)
+                srv.filter.forward(self.feats, out=self.out, stream=s, workspace=self.mws)
+                srv.filter.apply(self.rings, self.out, srv.tau, srv.params.deta_min,
+                                 srv.filter_deta_max, stream=s)
+
+        with torch.cuda.stream(s):
+            body()                                   # once outside capture (lazy setup)
+        s.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=s, capture_error_mode="relaxed"):
+            body()
+        torch.cuda.synchronize(dev)
+
+    def ring_views(self, N: int) -> dict:
+        return {k: v[:N] for k, v in self.rings.items()}
 
 
 def burst_bytes(N: int, M: int, params: api.Params, learned: bool) -> int:
@@ -75,7 +123,7 @@ class Server:
 
     def __init__(self, grid, params: api.Params | None = None, hbm_budget: int = 2 << 30,
                  max_active: int = 48, ring_filter: api.RingFilter | None = None,
-                 tau: float = 0.0, filter_deta_max: float | None = None):
+                 tau: float = 0.0, filter_deta_max: float | None = None, graphs: bool = False):
         self.grid = grid
         self.M = grid[0].numel()
         self.dev = grid[0].device
@@ -88,11 +136,31 @@ class Server:
         self.sweep_streams = [torch.cuda.Stream(self.dev) for _ in range(2)]
         self._ss = 0
         self._gs = api._grid_struct(grid)
+        self.graphs = graphs
+        self._fronts: dict[int, list[_Front]] = {}     # free captured front ends per bucket
+
+    @staticmethod
+    def bucket(N: int) -> int:
+        return max(512, 1 << max(0, (N - 1).bit_length()))
+
+    def _front(self, N: int) -> _Front:
+        cap = self.bucket(N)
+        free = self._fronts.setdefault(cap, [])
+        return free.pop() if free else _Front(self, cap)
+
+    def prepare(self, counts):
+        """Capture front ends ahead of time, one per distinct bucket of `counts`."""
+        if self.graphs:
+            for cap in sorted({self.bucket(c) for c in counts}):
+                if not self._fronts.get(cap):
+                    self._fronts.setdefault(cap, []).append(_Front(self, cap))
 
     # -- per-burst front end ------------------------------------------------
     def _admit(self, b: Burst, now: float) -> _Active:
         s = torch.cuda.Stream(self.dev)
         a = _Active(b, s, burst_bytes(b.count, self.M, self.params, self.filter is not None), now)
+        if self.graphs:
+            return self._admit_graph(a)
         d = a.dev
         N = b.count
         with torch.cuda.stream(s):
@@ -119,6 +187,34 @@ class Server:
                                   self.filter_deta_max, stream=s)
             ws_b = api.lib().cc_localize_batch_workspace_bytes(b.count, self.M,
                                                                C.byref(self.params.c()))
+            d["ws"] = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=self.dev)
+            d["map"] = torch.empty(self.M, dtype=torch.float32, device=self.dev)
+            d["argmax"] = torch.empty(1, dtype=torch.int32, device=self.dev)
+            d["seeds"] = torch.empty(self.params.topk, dtype=torch.int32, device=self.dev)
+            d["status"] = torch.empty(1, dtype=torch.int32, device=self.dev)
+            a.ready = torch.cuda.Event()
+            a.ready.record(s)
+        return a
+
+    def _admit_graph(self, a: _Active) -> _Active:
+        b, s, d = a.burst, a.stream, a.dev
+        N = b.count
+        f = a.front = self._front(N)
+        s.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(s):
+            off = 0
+            for part in b.parts:                 # one copy per contiguous row segment
+                k = part[0].numel()
+                f.n[off:off + k].copy_(part[0], non_blocking=True)
+                for name, h in zip("xyze", part[1:]):
+                    for slot in range(4):
+                        f.xyze[name][slot, off:off + k].copy_(h[slot], non_blocking=True)
+                off += k
+            if N < f.cap:
+                f.n[N:].zero_()                  # padding events: no sites, no ring
+            f.graph.replay()
+            d["rings"] = f.ring_views(N)
+            ws_b = api.lib().cc_localize_batch_workspace_bytes(N, self.M, C.byref(self.params.c()))
             d["ws"] = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=self.dev)
             d["map"] = torch.empty(self.M, dtype=torch.float32, device=self.dev)
             d["argmax"] = torch.empty(1, dtype=torch.int32, device=self.dev)
@@ -212,6 +308,8 @@ class Server:
                                       "rings": b.count}
                     if keep_maps:
                         results[b.bid]["map"] = a.out_host["map"].numpy()
+                    if a.front is not None:      # its buffers are free again
+                        self._fronts[a.front.cap].append(a.front)
                     used -= a.bytes
                     progressed = True
                 else:

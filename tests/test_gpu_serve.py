@@ -141,3 +141,26 @@ def test_server_learned_path_mixed_equals_alone(cc):
         np.testing.assert_array_equal(m["map"], a["map"])
         assert m["argmax"] == a["argmax"]
         np.testing.assert_array_equal(m["dir"], a["dir"])
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_graph_front_ends_equal_the_launched_path(cc, learned):
+    """The per-size-bucket CUDA graphs of the front end give every burst the
+    same map, argmax and direction as launching the kernels one by one."""
+    from paper_2411_04785_gb300 import serve
+    dev = torch.device("cuda:0")
+    grid = cc.grid_healpix_ring(32, dev)
+    p = cc.Params()
+    kw = dict(ring_filter=cc.RingFilter(dev, seed=5), tau=0.2) if learned else {}
+    bursts = serve.make_bursts(10, rate_hz=400.0, seed=9, median=3000, hi=40000, n_dirs=2,
+                               pool_src=20000, pool_bkg=40000)
+    plain, _ = serve.Server(grid, p, max_active=8, **kw).run(bursts, realtime=False,
+                                                             keep_maps=True)
+    srv = serve.Server(grid, p, max_active=8, graphs=True, **kw)
+    srv.prepare([b.count for b in bursts])
+    graphed, stats = srv.run(bursts, realtime=True, keep_maps=True)
+    for b in bursts:
+        a, g = plain[b.bid], graphed[b.bid]
+        np.testing.assert_array_equal(g["map"], a["map"])
+        assert g["argmax"] == a["argmax"]
+        np.testing.assert_array_equal(g["dir"], a["dir"])
