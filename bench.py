@@ -586,7 +586,7 @@ def run_serve(args):
         barrier(pg)
         with ClockSampler(gpu_index) as clk:
             time.sleep(0.5)
-            res_arm, stats = srv.run(bursts, realtime=True)
+            res_arm, stats = srv.run(bursts, realtime=True, breakdown=True)
         launches = sum(v["launches"] for v in cc.trace_read(reset=True).values())
         lat = np.array([res_arm[b.bid]["latency"] for b in bursts]) * 1e3
         err = np.array([math.degrees(math.atan2(np.linalg.norm(np.cross(res_arm[b.bid]["dir"], b.source)),
@@ -602,7 +602,10 @@ def run_serve(args):
             "error_vs_source_deg": {"p50": float(np.percentile(err, 50)),
                                     "p90": float(np.percentile(err, 90)),
                                     "within_0.5": float((err <= 0.5).mean())},
-            "gpu_launches": launches, "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "breakdown_ms": {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+                             for k, v in ((k, [res_arm[b.bid]["breakdown_ms"][k] for b in bursts])
+                                          for k in res_arm[bursts[0].bid]["breakdown_ms"])}}
         if name == "plain":
             plain_res = res_arm
     # oracle parity of the plain path on the smallest bursts (rank 0)

@@ -123,6 +123,19 @@ void cc_params_default(cc_params *p);
  * `ev`, `out` and `p` are host pointers to structs of device pointers;
  * out->count must equal ev->count.  count = 0 is valid (nothing launched).
  */
+/*
+ * Copy `count` events between two event sets (host or device; pinned host
+ * memory keeps the copy asynchronous): dst events [dst_offset, +count) get
+ * src events [src_offset, +count), n and the 4 slot rows of x, y, z, e (one
+ * 2D copy per array, each side with its own stride).  dst's arrays are
+ * written through their (const-qualified) pointers.  Needs
+ * dst_offset + count <= dst->stride, src_offset + count <= src->stride.
+ * Plumbing for callers that stage events (e.g. a server filling a device
+ * buffer from slices of a host pool); no counterpart in the paper.
+ */
+cc_status cc_events_copy(const cc_events *dst, int64_t dst_offset, const cc_events *src,
+                         int64_t src_offset, int64_t count, void *stream);
+
 cc_status cc_rings_from_events(const cc_events *ev, const cc_rings *out,
                                const cc_params *p, void *stream);
 

@@ -144,6 +144,9 @@ def lib() -> C.CDLL:
         L.cc_backproject.argtypes = [C.POINTER(cc_rings), _P, _P, _P, C.POINTER(cc_grid),
                                      C.POINTER(cc_params), _P, _P, _P, _P, C.c_size_t, _P]
         L.cc_backproject.restype = S
+        L.cc_events_copy.argtypes = [C.POINTER(cc_events), C.c_int64, C.POINTER(cc_events),
+                                     C.c_int64, C.c_int64, _P]
+        L.cc_events_copy.restype = S
         L.cc_selftest_exact_ops.argtypes = [_P, _P]
         L.cc_selftest_exact_ops.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
@@ -716,3 +719,20 @@ def selftest_exact_ops(device="cuda", stream=None):
     out = torch.empty(2, dtype=torch.uint64, device=device)
     _check("cc_selftest_exact_ops", lib().cc_selftest_exact_ops(_ptr(out), _stream(stream)))
     return out
+
+
+def events_copy(dst: tuple, dst_offset: int, src: tuple, src_offset: int = 0, count=None,
+                stream=None):
+    """Copy events between event sets given as (n, x, y, z, e) tensors with
+    x, y, z, e of shape [4, S] (views of a wider buffer allowed: each row's
+    stride is its own).  One library call: n plus one 2D copy per array."""
+    def struct(ev):
+        n, x, y, z, e = ev
+        stride = x.stride(0)
+        if any(t.stride(0) != stride or t.stride(1) != 1 for t in (y, z, e)) or x.stride(1) != 1:
+            raise ValueError("x, y, z, e must share one row stride and have unit column stride")
+        return cc_events(_ptr(n), _ptr(x), _ptr(y), _ptr(z), _ptr(e), n.numel(), stride)
+    count = src[0].numel() - src_offset if count is None else count
+    d, s = struct(dst), struct(src)
+    _check("cc_events_copy", lib().cc_events_copy(C.byref(d), dst_offset, C.byref(s), src_offset,
+                                                   count, _stream(stream)))

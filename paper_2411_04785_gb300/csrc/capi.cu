@@ -106,6 +106,31 @@ cc_status cc_rings_from_events(const cc_events *ev, const cc_rings *out, const c
     return CC_OK;
 }
 
+cc_status cc_events_copy(const cc_events *dst, int64_t dst_offset, const cc_events *src,
+                         int64_t src_offset, int64_t count, void *stream) {
+    g_err[0] = 0;
+    if (!dst || !src) return fail(CC_EINVAL, "events NULL");
+    if (count < 0 || dst_offset < 0 || src_offset < 0 || dst_offset + count > dst->stride ||
+        src_offset + count > src->stride)
+        return fail(CC_EINVAL, "bad offsets or count for the strides");
+    if (count == 0) return CC_OK;
+    if (!dst->n || !dst->x || !dst->y || !dst->z || !dst->e || !src->n || !src->x || !src->y ||
+        !src->z || !src->e)
+        return fail(CC_EINVAL, "event arrays must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(const_cast<uint8_t *>(dst->n) + dst_offset, src->n + src_offset,
+                                    (size_t)count, cudaMemcpyDefault, s);
+    const float *sa[4] = {src->x, src->y, src->z, src->e};
+    const float *da[4] = {dst->x, dst->y, dst->z, dst->e};
+    for (int a = 0; a < 4 && e == cudaSuccess; a++)
+        e = cudaMemcpy2DAsync(const_cast<float *>(da[a]) + dst_offset,
+                              (size_t)dst->stride * sizeof(float), sa[a] + src_offset,
+                              (size_t)src->stride * sizeof(float), (size_t)count * sizeof(float),
+                              4, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(e, "events copy");
+    return CC_OK;
+}
+
 size_t cc_localize_workspace_bytes(int64_t rings, int64_t dirs, const cc_params *p) {
     cc_params d;
     if (!p) { cc_params_default(&d); p = &d; }

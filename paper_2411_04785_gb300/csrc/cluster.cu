@@ -23,24 +23,49 @@
 // amplitude sum is the difference of two prefix sums taken at its two edges
 // with no per-event atomics.  All arithmetic is integer: results are exact.
 //
-// Layout inside a tile: the tile's t (32 KB) and adc (16 KB) are staged in
-// shared memory by two bulk copies (TMA) completing on one mbarrier, so no
-// thread holds the tile in registers and four CTAs fit an SM (measured
-// faster than eight 4-warp CTAs of 2048 detections and than two persistent
-// double-buffered ones); warp w then reads its 512 consecutive detections as 16 rows of 32 (lane l of row r
-// holds detection base + 512 w + 32 r + l), conflict-free, and the row-level
-// prefix counts are ballots.
+// Layout inside a tile: the tile's t (32 KB) and adc (16 KB) arrive in
+// shared memory by two TMA tensor copies (t seen as rows of 16 int64, adc as
+// rows of 32 uint32; 128-byte rows in the 128B swizzle) on one mbarrier.
+// Every lane owns 16 consecutive detections: it reads its own row (or half
+// row) chunk by chunk - the swizzle puts the chunks of 8 neighbouring rows
+// in 8 different bank groups, so the reads are conflict-free - builds its
+// 16 step masks, scans its detections serially, and the lanes of a warp
+// combine their aggregates in one warp scan per 16 detections.  Edges and
+// event ids leave as 16-byte stores.
+#include <cuda.h>
+#include <string.h>
+
 #include "cc_internal.cuh"
 #include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda)
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncodeFn encode_fn() {
+    static const TmapEncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<TmapEncodeFn>(p);
+    }();
+    return fn;
+}
+
 constexpr int kCWarps = 8;
 constexpr int kCThreads = kCWarps * 32;
 constexpr int kRows = 16;
 constexpr int kWarpSpan = kRows * 32;            // 512
 constexpr int kTileSpan = kWarpSpan * kCWarps;   // 4096: 48 KB staged, 4 CTAs per SM
+constexpr int kLook = 1;                         // predecessors per lane per look-back round
 
 struct Carry {
     long long starts;              // event starts in the range
@@ -96,163 +121,205 @@ __device__ __forceinline__ Carry shfl_down_carry(const Carry &c, int o) {
                  __shfl_down_sync(0xffffffffu, c.sum_before, o)};
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    return v;
-}
-
-// Shared memory of one CTA: the tile's time stamps and amplitudes (staged
-// by two bulk copies), the neighbours just outside it, and the scan state.
+// Shared memory of one CTA: the tile's time stamps (256 rows of 16) and
+// amplitudes (128 rows of 32), 128-byte rows in the TMA 128B swizzle (the
+// 16-byte chunk c of row r sits at chunk c ^ (r & 7)), so that a lane reading
+// its own row's chunks never conflicts with the lanes beside it.
 struct ClusterSmem {
-    long long ts[kTileSpan];
-    unsigned as[kTileSpan];
+    unsigned char tsw[kTileSpan * 8];     // t, swizzled
+    unsigned char asw[kTileSpan * 4];     // adc, swizzled
     long long t_prev, t_next;
     unsigned long long bar;
     long long tile;
+    Carry warp_agg[kCWarps];
+    Carry warp_excl[kCWarps];
+    Carry tile_agg, tile_excl;
+    int load_failed;
 };
+constexpr size_t kClusterSmemBytes = sizeof(ClusterSmem) + 1024;   // + alignment of the rows
+
+__device__ __forceinline__ int swz(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
+
+// element e of the tile: its byte offset in tsw / asw
+__device__ __forceinline__ int t_off(int e) { return swz(e >> 4, (e & 15) >> 1) + ((e & 1) << 3); }
+__device__ __forceinline__ int a_off(int e) { return swz(e >> 5, (e & 31) >> 2) + ((e & 3) << 2); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
 
 __global__ void __launch_bounds__(kCThreads)
-k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, long long N,
-          long long dt_max, unsigned char *__restrict__ edge, int *__restrict__ event_id,
-          long long *__restrict__ ev_first, int *__restrict__ ev_count,
-          unsigned long long *__restrict__ ev_adc, long long *__restrict__ n_events,
-          TileState *__restrict__ tiles, unsigned long long *__restrict__ ticket,
-          int *__restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(smem_raw);
-    __shared__ Carry warp_agg[kCWarps];
-    __shared__ Carry warp_excl[kCWarps];
-    __shared__ Carry tile_excl;
-    __shared__ int load_failed;
+k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap amap,
+          int use_tma, const long long *__restrict__ t, const unsigned *__restrict__ adc,
+          long long N, long long dt_max, unsigned char *__restrict__ edge,
+          int *__restrict__ event_id, int vec_out, long long *__restrict__ ev_first,
+          int *__restrict__ ev_count, unsigned long long *__restrict__ ev_adc,
+          long long *__restrict__ n_events, TileState *__restrict__ tiles,
+          unsigned long long *__restrict__ ticket, int *__restrict__ status) {
+    extern __shared__ unsigned char smem_raw[];
+    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long ntiles = (N + kTileSpan - 1) / kTileSpan;
     if (threadIdx.x == 0) {
         S.tile = (long long)atomicAdd(ticket, 1ull);
+        S.load_failed = 0;
         mbar_init(&S.bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        load_failed = 0;
     }
     __syncthreads();
     const long long tile = S.tile;
     const long long base = tile * kTileSpan;
-    const long long n_here = N - base < kTileSpan ? N - base : kTileSpan;
-
-    // ---- stage the tile: whole aligned tiles by two bulk copies on one
-    // mbarrier, the ragged last tile by plain loads
-    const bool bulk = n_here == kTileSpan && ((reinterpret_cast<uintptr_t>(t) & 15u) == 0) &&
-                      (adc == nullptr || (reinterpret_cast<uintptr_t>(adc) & 15u) == 0);
+    // whole tiles inside the tensor maps (rows of 32 detections) by TMA
+    const bool bulk = use_tma && base + kTileSpan <= (N / 32) * 32;
     if (bulk) {
         if (threadIdx.x == 0) {
             const unsigned bytes = kTileSpan * 8u + (adc ? kTileSpan * 4u : 0u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                              smem_u32(&S.bar)), "r"(bytes)
                          : "memory");
-            bulk_copy(S.ts, t + base, kTileSpan * 8u, &S.bar);
-            if (adc) bulk_copy(S.as, adc + base, kTileSpan * 4u, &S.bar);
+            tma_load_2d(S.tsw, &tmap, 0, (int)(base / 16), &S.bar);
+            if (adc) tma_load_2d(S.asw, &amap, 0, (int)(base / 32), &S.bar);
         }
         if (adc == nullptr)
-            for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) S.as[i] = 0u;
+            for (int e = threadIdx.x; e < kTileSpan; e += kCThreads)
+                *reinterpret_cast<unsigned *>(S.asw + a_off(e)) = 0u;
     } else {
-        for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) {
-            const long long g = base + i;
-            S.ts[i] = g < N ? __ldcs(t + g) : 0;
-            S.as[i] = (adc != nullptr && g < N) ? __ldcs(adc + g) : 0u;
+        for (int e = threadIdx.x; e < kTileSpan; e += kCThreads) {
+            const long long g = base + e;
+            *reinterpret_cast<long long *>(S.tsw + t_off(e)) = g < N ? __ldcs(t + g) : 0;
+            *reinterpret_cast<unsigned *>(S.asw + a_off(e)) =
+                (adc != nullptr && g < N) ? __ldcs(adc + g) : 0u;
         }
     }
     if (threadIdx.x == 32) {
         S.t_prev = base > 0 ? __ldg(t + base - 1) : 0;
         S.t_next = base + kTileSpan < N ? __ldg(t + base + kTileSpan) : 0;
     }
-    if (bulk && threadIdx.x == 0 && !mbar_wait(&S.bar, 0)) load_failed = 1;
+    if (bulk && threadIdx.x == 0 && !mbar_wait(&S.bar, 0)) S.load_failed = 1;
     __syncthreads();
-    if (load_failed) {              // a bounded wait gave up: report, publish, go on
+    if (S.load_failed) {          // a bounded wait gave up: report, publish, go on
         if (threadIdx.x == 0) atomicExch(status, (int)CC_ETIMEOUT);
-        for (int i = threadIdx.x; i < kTileSpan; i += kCThreads) {
-            S.ts[i] = 0;
-            S.as[i] = 0u;
-        }
+        for (int i = threadIdx.x; i < kTileSpan * 12 / 16; i += kCThreads)
+            reinterpret_cast<int4 *>(S.tsw)[i] = make_int4(0, 0, 0, 0);
         __syncthreads();
     }
 
-    // ---- masks: bit r of m_after = "step from this detection to the next
-    // is below dt_max", bit r of m_before = the same for the step before
-    const int wl = w * kWarpSpan + lane;                // local index of row 0
-    const long long seg = base + (long long)w * kWarpSpan;
-    unsigned m_after = 0, m_before = 0;
+    // ---- each lane owns 16 consecutive detections: tile elements
+    // e0 .. e0 + 15, row r of the time stamps
+    const int e0 = w * kWarpSpan + lane * 16;
+    const long long i0 = base + e0;
+    const int r = e0 >> 4;
+    unsigned ma = 0, mb = 0;        // bit k: step after / before detection i0 + k is masked
+    {
+        long long tv[16];
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const int li = wl + 32 * r;
-        const long long i = base + li;
-        const long long ti = S.ts[li];
-        const long long tn = li + 1 < kTileSpan ? S.ts[li + 1] : S.t_next;
-        const long long tp = li > 0 ? S.ts[li - 1] : S.t_prev;
-        const bool ma = (i + 1 < N) && step_of(ti, tn) < dt_max;
-        const bool mb = (i > 0) && (i < N) && step_of(tp, ti) < dt_max;
-        m_after |= (unsigned)ma << r;
-        m_before |= (unsigned)mb << r;
-    }
-    // ---- pass 1: the warp's aggregate
-    const unsigned starts_bits = m_after & ~m_before;
-    long long cnt = 0, last = -1;
+        for (int c = 0; c < 8; c++) {
+            const longlong2 v = *reinterpret_cast<const longlong2 *>(S.tsw + swz(r, c));
+            tv[2 * c] = v.x;
+            tv[2 * c + 1] = v.y;
+        }
+        long long tn = __shfl_down_sync(0xffffffffu, tv[0], 1);
+        long long tp = __shfl_up_sync(0xffffffffu, tv[15], 1);
+        if (lane == 31) tn = e0 + 16 < kTileSpan ? *reinterpret_cast<const long long *>(S.tsw + t_off(e0 + 16)) : S.t_next;
+        if (lane == 0) tp = e0 > 0 ? *reinterpret_cast<const long long *>(S.tsw + t_off(e0 - 1)) : S.t_prev;
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const unsigned s = __ballot_sync(0xffffffffu, (starts_bits >> r) & 1u);
-        cnt += __popc(s);
-        if (s) last = seg + 32 * r + (31 - __clz((int)s));
+        for (int k = 0; k < 16; k++) {
+            const long long nx = k < 15 ? tv[k + 1 < 16 ? k + 1 : 15] : tn;
+            const bool a_k = (i0 + k + 1 < N) && step_of(tv[k], nx) < dt_max;
+            ma |= (unsigned)a_k << k;
+        }
+        const bool b0 = (i0 > 0) && (i0 < N) && step_of(tp, tv[0]) < dt_max;
+        mb = ((ma << 1) | (unsigned)b0) & 0xFFFFu;
+        if (i0 + 16 > N) {          // detections past the end have no steps
+            const long long room = N - i0;
+            const unsigned keep = room <= 0 ? 0u : ((1u << (unsigned)room) - 1u);
+            mb &= keep;
+        }
     }
-    unsigned long long own = 0, own_before = 0;
+    const unsigned sbits = ma & ~mb, ebits = mb & ~ma;
+
+    // ---- the lane's aggregate and the warp's inclusive scan of them
+    const int arow = e0 >> 5, ach = (lane & 1) * 4;
+    auto adc_at = [&](int k) -> unsigned {
+        return *reinterpret_cast<const unsigned *>(S.asw + swz(arow, ach + (k >> 2)) + ((k & 3) << 2));
+    };
+    Carry mine{__popc(sbits), -1, 0ull, 0ull};
+    const int lastk = sbits ? 31 - __clz((int)sbits) : -1;
+    if (lastk >= 0) mine.last_start = i0 + lastk;
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const long long i = seg + 32 * r + lane;
-        const unsigned a = S.as[wl + 32 * r];
-        own += a;
-        if (i < last) own_before += a;
+    for (int c = 0; c < 4; c++) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(S.asw + swz(arow, ach + c));
+        const unsigned q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            mine.sum += q[j];
+            if (4 * c + j < lastk) mine.sum_before += q[j];
+        }
     }
-    Carry wa{cnt, last, warp_sum_u64(own), warp_sum_u64(own_before)};
-    if (last < 0) wa.sum_before = 0;
-    if (lane == 0) warp_agg[w] = wa;
+    Carry incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Carry y{__shfl_up_sync(0xffffffffu, incl.starts, o),
+                      __shfl_up_sync(0xffffffffu, incl.last_start, o),
+                      __shfl_up_sync(0xffffffffu, incl.sum, o),
+                      __shfl_up_sync(0xffffffffu, incl.sum_before, o)};
+        if (lane >= o) incl = combine(y, incl);
+    }
+    Carry lane_excl{__shfl_up_sync(0xffffffffu, incl.starts, 1),
+                    __shfl_up_sync(0xffffffffu, incl.last_start, 1),
+                    __shfl_up_sync(0xffffffffu, incl.sum, 1),
+                    __shfl_up_sync(0xffffffffu, incl.sum_before, 1)};
+    if (lane == 0) lane_excl = identity();
+    if (lane == 31) S.warp_agg[w] = incl;
     __syncthreads();
 
     // ---- tile aggregate, look-back, tile prefix.  Warp 0 looks back over
     // windows of 32 predecessors at once: it waits until each has published
     // at least its aggregate, combines (in order) back to the nearest one
     // that has published its inclusive prefix, and stops there.
-    __shared__ Carry tile_agg;
     if (threadIdx.x == 0) {
         Carry acc = identity();
         for (int k = 0; k < kCWarps; k++) {
-            warp_excl[k] = acc;
-            acc = combine(acc, warp_agg[k]);
+            S.warp_excl[k] = acc;
+            acc = combine(acc, S.warp_agg[k]);
         }
-        tile_agg = acc;
+        S.tile_agg = acc;
         volatile TileState *me = tiles + tile;
-        if (tile == 0) {
-            put(&me->incl, acc);
-        } else {
-            put(&me->agg, acc);
-        }
+        if (tile == 0) put(&me->incl, acc);
+        else put(&me->agg, acc);
         __threadfence();
         me->status = tile == 0 ? 2 : 1;
     }
     __syncthreads();
     if (w == 0) {
+        // windows of 32 x kLook predecessors: lane l covers tiles
+        // hi - kLook l - j (j = 0 nearest), all loaded in one round trip
         Carry excl = identity();
         bool timed_out = false;
         unsigned long long t0 = 0;
         for (long long hi = tile - 1; hi >= 0;) {
-            const long long p = hi - lane;              // lane 0: the nearest predecessor
-            int st = p >= 0 ? ((volatile TileState *)tiles)[p].status : 2;
-            for (unsigned it = 0; __any_sync(0xffffffffu, st == 0); ++it) {
-                if (st == 0) st = ((volatile TileState *)tiles)[p].status;
+            int st[kLook];
+            int pending = 0;
+#pragma unroll
+            for (int j = 0; j < kLook; j++) {
+                const long long p = hi - kLook * lane - j;
+                st[j] = p >= 0 ? ((volatile TileState *)tiles)[p].status : 2;
+                pending |= st[j] == 0;
+            }
+            for (unsigned it = 0; __any_sync(0xffffffffu, pending); ++it) {
+                pending = 0;
+#pragma unroll
+                for (int j = 0; j < kLook; j++) {
+                    const long long p = hi - kLook * lane - j;
+                    if (st[j] == 0) st[j] = ((volatile TileState *)tiles)[p].status;
+                    pending |= st[j] == 0;
+                }
                 if ((it & 63) == 0) {   // lane 0's clock for all: the exit stays warp-uniform
                     const unsigned long long now = __shfl_sync(0xffffffffu, globaltimer_ns(), 0);
                     if (t0 == 0) t0 = now;
@@ -261,10 +328,20 @@ k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, lon
             }
             if (timed_out) break;
             __threadfence();
+            // the lane's value: its tiles from the farthest in, cut at its
+            // nearest inclusive prefix
             Carry v = identity();
-            if (p >= 0) v = st == 2 ? get(&((volatile TileState *)tiles)[p].incl)
-                                    : get(&((volatile TileState *)tiles)[p].agg);
-            const unsigned incl_mask = __ballot_sync(0xffffffffu, st == 2);
+            bool has_incl = false;
+#pragma unroll
+            for (int j = kLook - 1; j >= 0; j--) {
+                const long long p = hi - kLook * lane - j;
+                Carry x = identity();
+                if (p >= 0) x = st[j] == 2 ? get(&((volatile TileState *)tiles)[p].incl)
+                                           : get(&((volatile TileState *)tiles)[p].agg);
+                if (st[j] == 2) { v = x; has_incl = true; }
+                else v = combine(v, x);
+            }
+            const unsigned incl_mask = __ballot_sync(0xffffffffu, has_incl);
             const int n = incl_mask ? __ffs(incl_mask) : 32;   // lanes [0, n) take part
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {                 // ordered tree reduction
@@ -273,56 +350,65 @@ k_cluster(const long long *__restrict__ t, const unsigned *__restrict__ adc, lon
             }
             excl = combine(v, excl);                           // lane 0's value is the window's
             if (incl_mask) break;
-            hi -= 32;
+            hi -= 32 * kLook;
         }
         if (lane == 0) {
             if (timed_out) atomicExch(status, (int)CC_ETIMEOUT);
             if (tile > 0) {
                 volatile TileState *me = tiles + tile;
-                put(&me->incl, combine(excl, tile_agg));
+                put(&me->incl, combine(excl, S.tile_agg));
                 __threadfence();
                 me->status = 2;
             }
-            tile_excl = excl;
-            if (tile == (N - 1) / kTileSpan && n_events != nullptr)
-                *n_events = combine(excl, tile_agg).starts;
+            S.tile_excl = excl;
+            if (tile == ntiles - 1 && n_events != nullptr)
+                *n_events = combine(excl, S.tile_agg).starts;
         }
     }
     __syncthreads();
 
-    // ---- pass 2: outputs, row by row with the running prefix
-    Carry c = combine(tile_excl, warp_excl[w]);
-    const unsigned lane_le = 0xffffffffu >> (31 - lane);
+    // ---- outputs: the lane walks its 16 detections with the running prefix
+    const Carry c0 = combine(S.tile_excl, combine(S.warp_excl[w], lane_excl));
+    long long rank = c0.starts, last = c0.last_start;
+    unsigned long long sum = c0.sum, before = c0.sum_before;
+    unsigned eb[4] = {0u, 0u, 0u, 0u};
+    int ids[16];
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-        const long long i = seg + 32 * r + lane;
-        const bool ma = (m_after >> r) & 1u, mb = (m_before >> r) & 1u;
-        const bool st = ma && !mb, en = mb && !ma;
-        const unsigned s = __ballot_sync(0xffffffffu, st);
-        const unsigned a = S.as[wl + 32 * r];
-        const unsigned long long incl = warp_incl_scan_u64(a, lane);
-        const unsigned long long excl_here = incl - a;
-        const unsigned s_le = s & lane_le;
-        const int sl = s_le ? 31 - __clz((int)s_le) : 0;
-        const unsigned long long before_sl = __shfl_sync(0xffffffffu, excl_here, sl);
-        const long long id = c.starts + __popc(s_le) - 1;
-        if (i < N) {
-            if (edge) edge[i] = (unsigned char)(ma ^ mb);
-            if (event_id) event_id[i] = (ma || mb) ? (int)id : -1;
-            if (en) {
-                const long long first = s_le ? seg + 32 * r + sl : c.last_start;
-                const unsigned long long sum_before = s_le ? c.sum + before_sl : c.sum_before;
-                if (ev_first) ev_first[id] = first;
-                if (ev_count) ev_count[id] = (int)(i - first + 1);
-                if (ev_adc) ev_adc[id] = c.sum + incl - sum_before;
+    for (int k = 0; k < 16; k++) {
+        const long long i = i0 + k;
+        const bool st = (sbits >> k) & 1u, en = (ebits >> k) & 1u;
+        const bool in = ((ma | mb) >> k) & 1u;
+        if (st) {
+            last = i;
+            before = sum;
+        }
+        sum += adc_at(k);
+        rank += st;
+        ids[k] = in ? (int)(rank - 1) : -1;
+        eb[k >> 2] |= (unsigned)((((ma ^ mb) >> k) & 1u)) << (8 * (k & 3));
+        if (en && i < N) {
+            const long long id = rank - 1;
+            if (ev_first) ev_first[id] = last;
+            if (ev_count) ev_count[id] = (int)(i - last + 1);
+            if (ev_adc) ev_adc[id] = sum - before;
+        }
+    }
+    if (vec_out && i0 + 16 <= N) {                        // 16-byte stores
+        if (edge) *reinterpret_cast<uint4 *>(edge + i0) = make_uint4(eb[0], eb[1], eb[2], eb[3]);
+        if (event_id) {
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                reinterpret_cast<int4 *>(event_id + i0)[q] =
+                    make_int4(ids[4 * q], ids[4 * q + 1], ids[4 * q + 2], ids[4 * q + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            if (i0 + k < N) {
+                if (edge) edge[i0 + k] = (unsigned char)((eb[k >> 2] >> (8 * (k & 3))) & 1u);
+                if (event_id) event_id[i0 + k] = ids[k];
             }
         }
-        // advance the running prefix by this row
-        const unsigned long long row_sum = __shfl_sync(0xffffffffu, incl, 31);
-        const int ls = s ? 31 - __clz((int)s) : 0;
-        const unsigned long long row_before = __shfl_sync(0xffffffffu, excl_here, ls);
-        Carry row{__popc(s), s ? seg + 32 * r + ls : -1, row_sum, s ? row_before : 0ull};
-        c = combine(c, row);
     }
 }
 
@@ -376,17 +462,44 @@ cudaError_t launch_cluster(const int64_t *t, const uint32_t *adc, int64_t n, int
         if (n_events) return cudaMemsetAsync(n_events, 0, sizeof(int64_t), s);
         return cudaSuccess;
     }
+    // tensor maps of t as [N/16][16] int64 and adc as [N/32][32] uint32 rows,
+    // 128B swizzle, boxes of one tile (256 x 16 and 128 x 32)
+    CUtensorMap tmap, amap;
+    memset(&tmap, 0, sizeof(tmap));
+    memset(&amap, 0, sizeof(amap));
+    auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    int use_tma = n >= kTileSpan && al16(t) && (adc == nullptr || al16(adc)) && encode_fn() != nullptr;
+    if (use_tma) {
+        const cuuint64_t gst[1] = {128};
+        const cuuint32_t es[2] = {1, 1};
+        const cuuint64_t gdt[2] = {16, (cuuint64_t)(n / 16)};
+        const cuuint32_t bt[2] = {16, (cuuint32_t)(kTileSpan / 16)};
+        CUresult r = encode_fn()(&tmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, const_cast<int64_t *>(t),
+                                 gdt, gst, bt, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS && adc != nullptr) {
+            const cuuint64_t gda[2] = {32, (cuuint64_t)(n / 32)};
+            const cuuint32_t ba[2] = {32, (cuuint32_t)(kTileSpan / 32)};
+            r = encode_fn()(&amap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(adc),
+                            gda, gst, ba, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (r != CUDA_SUCCESS) use_tma = 0;          // plain loads instead
+    }
+    const int vec_out = (edge == nullptr || al16(edge)) && (event_id == nullptr || al16(event_id));
     // the staged tile needs more than 48 KB of shared memory (set per call:
     // the attribute belongs to the current device)
     e = cudaFuncSetAttribute((const void *)k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(ClusterSmem));
+                             (int)kClusterSmemBytes);
     if (e != cudaSuccess) return e;
     TraceScope ts(CC_STAGE_CLUSTER, s);
-    k_cluster<<<(unsigned)tiles, kCThreads, sizeof(ClusterSmem), s>>>(
-        reinterpret_cast<const long long *>(t), adc, (long long)n, (long long)dt_max, edge,
-        event_id, reinterpret_cast<long long *>(ev_first), ev_count,
-        reinterpret_cast<unsigned long long *>(ev_adc), reinterpret_cast<long long *>(n_events),
-        state, ticket, st);
+    k_cluster<<<(unsigned)tiles, kCThreads, kClusterSmemBytes, s>>>(
+        tmap, amap, use_tma, reinterpret_cast<const long long *>(t), adc, (long long)n,
+        (long long)dt_max, edge, event_id, vec_out, reinterpret_cast<long long *>(ev_first),
+        ev_count, reinterpret_cast<unsigned long long *>(ev_adc),
+        reinterpret_cast<long long *>(n_events), state, ticket, st);
     return cudaGetLastError();
 }
 

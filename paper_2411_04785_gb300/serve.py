@@ -4,12 +4,13 @@ Bursts (event sets of uneven size) arrive over time.  A burst is admitted as
 soon as a slot and its device-memory budget are free; its events are copied
 to the device and reconstructed into rings (and, on the learned path, scored
 and re-widthed by the ring filter) on a stream of its own.  Every pass of the
-loop sweeps ALL admitted bursts whose rings are ready in one batched launch
+loop sweeps ALL bursts admitted since the last sweep in one batched launch
 (cc_localize_batch: one persistent kernel over the work units of every
-burst), on one of two sweep streams, so a new batch overlaps a running one on
-the GPU; each burst's refinement and result read-back then run on its own
-stream again.  The host only polls events; it never waits for the GPU while
-bursts remain.
+burst), on one of two sweep streams that wait for the bursts' front ends on
+the device, so a new batch overlaps a running one on the GPU; each burst's
+refinement and result read-back then run on its own stream again.  The host
+only polls for completed results; it never waits for the GPU while bursts
+remain.
 
 A burst's results do not depend on the batch it was swept in (the batched
 sweep keeps each burst's own plan), which the tests check against the same
@@ -67,6 +68,9 @@ class _Active:
     done: torch.cuda.Event | None = None
     out_host: dict = field(default_factory=dict)
     front: "_Front | None" = None
+    ev0: torch.cuda.Event | None = None       # breakdown: front end starts
+    swept_ev: torch.cuda.Event | None = None  # breakdown: its batch's sweep ended
+    t_sweep: float = 0.0                      # breakdown: host time the sweep was issued
 
 
 class _Front:
@@ -79,9 +83,26 @@ class _Front:
         self.xyze = {k: torch.zeros((4, cap), dtype=torch.float32, device=dev) for k in "xyze"}
         self.rings = api.empty_rings(cap, dev)
         learned = srv.filter is not None
+        # the burst's outputs and scratch, sized for the bucket
+        pc = srv.params.c()
+        tk = srv.params.topk
+        self.out = {
+            "ws": torch.empty(max(api.lib().cc_localize_batch_workspace_bytes(cap, srv.M, C.byref(pc)),
+                                  256), dtype=torch.uint8, device=dev),
+            "map": torch.empty(srv.M, dtype=torch.float32, device=dev),
+            "argmax": torch.empty(1, dtype=torch.int32, device=dev),
+            "seeds": torch.empty(tk, dtype=torch.int32, device=dev),
+            "status": torch.empty(1, dtype=torch.int32, device=dev),
+            "seed_dirs": torch.empty((tk, 3), dtype=torch.float64, device=dev),
+            "ref_ws": torch.empty(max(api.refine_workspace_bytes(cap, tk), 256), dtype=torch.uint8,
+                                  device=dev),
+            "ref": (torch.empty(3, dtype=torch.float64, device=dev),
+                    torch.empty(1, dtype=torch.float64, device=dev),
+                    torch.empty(1, dtype=torch.int32, device=dev),
+                    torch.empty(1, dtype=torch.int32, device=dev))}
         if learned:
             self.feats = torch.empty((cap, api.MLP_FEATURES), dtype=torch.bfloat16, device=dev)
-            self.out = torch.empty((cap, 2), dtype=torch.float32, device=dev)
+            self.mlp_out = torch.empty((cap, 2), dtype=torch.float32, device=dev)
             self.mws = torch.empty(api.mlp_workspace_bytes(cap), dtype=torch.uint8, device=dev)
         s = torch.cuda.Stream(dev)
         s.wait_stream(torch.cuda.current_stream(dev))
@@ -92,8 +113,8 @@ class _Front:
             if learned:
                 api.ring_features(self.n, x, y, z, e, self.rings, srv.params, out=self.feats,
                                   stream=s)
-                srv.filter.forward(self.feats, out=self.out, stream=s, workspace=self.mws)
-                srv.filter.apply(self.rings, self.out, srv.tau, srv.params.deta_min,
+                srv.filter.forward(self.feats, out=self.mlp_out, stream=s, workspace=self.mws)
+                srv.filter.apply(self.rings, self.mlp_out, srv.tau, srv.params.deta_min,
                                  srv.filter_deta_max, stream=s)
 
         with torch.cuda.stream(s):
@@ -137,6 +158,8 @@ class Server:
         self._ss = 0
         self._gs = api._grid_struct(grid)
         self.graphs = graphs
+        self.breakdown = False
+        self.keep_maps = False
         self._fronts: dict[int, list[_Front]] = {}     # free captured front ends per bucket
 
     @staticmethod
@@ -156,9 +179,15 @@ class Server:
                     self._fronts.setdefault(cap, []).append(_Front(self, cap))
 
     # -- per-burst front end ------------------------------------------------
+    def _event(self):
+        return torch.cuda.Event(enable_timing=self.breakdown)
+
     def _admit(self, b: Burst, now: float) -> _Active:
         s = torch.cuda.Stream(self.dev)
         a = _Active(b, s, burst_bytes(b.count, self.M, self.params, self.filter is not None), now)
+        if self.breakdown:
+            a.ev0 = self._event()
+            a.ev0.record(s)
         if self.graphs:
             return self._admit_graph(a)
         d = a.dev
@@ -167,14 +196,11 @@ class Server:
             d["n"] = torch.empty(N, dtype=torch.uint8, device=self.dev)
             for k in "xyze":
                 d[k] = torch.empty((4, N), dtype=torch.float32, device=self.dev)
+            dst = (d["n"], d["x"], d["y"], d["z"], d["e"])
             off = 0
-            for part in b.parts:                 # one copy per contiguous row segment
-                k = part[0].numel()
-                d["n"][off:off + k].copy_(part[0], non_blocking=True)
-                for name, h in zip("xyze", part[1:]):
-                    for slot in range(4):
-                        d[name][slot, off:off + k].copy_(h[slot], non_blocking=True)
-                off += k
+            for part in b.parts:                 # n + one 2D copy per array
+                api.events_copy(dst, off, part, stream=s)
+                off += part[0].numel()
             d["rings"] = api.rings_from_events(d["n"], d["x"], d["y"], d["z"], d["e"],
                                                self.params, stream=s)
             if self.filter is not None:
@@ -192,7 +218,7 @@ class Server:
             d["argmax"] = torch.empty(1, dtype=torch.int32, device=self.dev)
             d["seeds"] = torch.empty(self.params.topk, dtype=torch.int32, device=self.dev)
             d["status"] = torch.empty(1, dtype=torch.int32, device=self.dev)
-            a.ready = torch.cuda.Event()
+            a.ready = self._event()
             a.ready.record(s)
         return a
 
@@ -202,25 +228,17 @@ class Server:
         f = a.front = self._front(N)
         s.wait_stream(torch.cuda.current_stream(self.dev))
         with torch.cuda.stream(s):
+            dst = (f.n, f.xyze["x"], f.xyze["y"], f.xyze["z"], f.xyze["e"])
             off = 0
-            for part in b.parts:                 # one copy per contiguous row segment
-                k = part[0].numel()
-                f.n[off:off + k].copy_(part[0], non_blocking=True)
-                for name, h in zip("xyze", part[1:]):
-                    for slot in range(4):
-                        f.xyze[name][slot, off:off + k].copy_(h[slot], non_blocking=True)
-                off += k
+            for part in b.parts:                 # n + one 2D copy per array
+                api.events_copy(dst, off, part, stream=s)
+                off += part[0].numel()
             if N < f.cap:
                 f.n[N:].zero_()                  # padding events: no sites, no ring
             f.graph.replay()
             d["rings"] = f.ring_views(N)
-            ws_b = api.lib().cc_localize_batch_workspace_bytes(N, self.M, C.byref(self.params.c()))
-            d["ws"] = torch.empty(max(ws_b, 256), dtype=torch.uint8, device=self.dev)
-            d["map"] = torch.empty(self.M, dtype=torch.float32, device=self.dev)
-            d["argmax"] = torch.empty(1, dtype=torch.int32, device=self.dev)
-            d["seeds"] = torch.empty(self.params.topk, dtype=torch.int32, device=self.dev)
-            d["status"] = torch.empty(1, dtype=torch.int32, device=self.dev)
-            a.ready = torch.cuda.Event()
+            d.update(f.out)                       # outputs and scratch of the bucket
+            a.ready = self._event()
             a.ready.record(s)
         return a
 
@@ -243,31 +261,40 @@ class Server:
         api._check("cc_localize_batch", api.lib().cc_localize_batch(
             n, rings, C.byref(self._gs), C.byref(pc), maps, am, sd, st, ws, wsb,
             C.c_void_p(stream.cuda_stream)))
-        swept = torch.cuda.Event()
+        swept = self._event()
         swept.record(stream)
+        t_issue = time.perf_counter()
         for a in batch:                       # refine + read-back on the burst's stream
             s = a.stream
             s.wait_event(swept)
             d = a.dev
             with torch.cuda.stream(s):
-                seeds_dir = api.grid_gather(self.grid, d["seeds"], stream=s)
-                res = api.refine(d["rings"], seeds_dir, self.params, stream=s)
+                seeds_dir = api.grid_gather(self.grid, d["seeds"], out=d.get("seed_dirs"), stream=s)
+                res = api.refine(d["rings"], seeds_dir, self.params, workspace=d.get("ref_ws"),
+                                 out=d.get("ref"), stream=s)
                 a.out_host = {"dir": res[0].to("cpu", non_blocking=True),
                               "obj": res[1].to("cpu", non_blocking=True),
                               "status": torch.cat([d["status"], res[3]]).to("cpu", non_blocking=True),
                               "argmax": d["argmax"].to("cpu", non_blocking=True)}
                 if self.keep_maps:
                     a.out_host["map"] = d["map"].to("cpu", non_blocking=True)
-                a.done = torch.cuda.Event()
+                a.done = self._event()
                 a.done.record(s)
             a.swept = True
+            a.swept_ev = swept
+            a.t_sweep = t_issue
 
     # -- the loop -------------------------------------------------------------
-    def run(self, bursts: list[Burst], realtime: bool = True, keep_maps: bool = False):
+    def run(self, bursts: list[Burst], realtime: bool = True, keep_maps: bool = False,
+            breakdown: bool = False):
         """Serve the bursts; returns per-burst results and latencies (s).
         With realtime, bursts become available at their arrival times;
-        otherwise all are available at once (arrivals then only order them)."""
+        otherwise all are available at once (arrivals then only order them).
+        With breakdown, each result also carries where its latency went:
+        host admission delay, device front end, wait + batched sweep, refine +
+        read-back (CUDA events), and the host's delay in seeing it done."""
         self.keep_maps = keep_maps
+        self.breakdown = breakdown
         pending = deque(sorted(bursts, key=lambda b: b.arrival))
         active: list[_Active] = []
         used = 0
@@ -287,8 +314,10 @@ class Server:
                 active.append(self._admit(b, now))
                 used += active[-1].bytes
                 progressed = True
-            # sweep everything whose rings are ready, in one batched launch
-            ready = [a for a in active if not a.swept and a.ready.query()]
+            # sweep every admitted burst not yet swept, in one batched launch;
+            # the sweep stream waits for their front ends on the device, so
+            # the host never waits for a burst's rings
+            ready = [a for a in active if not a.swept]
             for i in range(0, len(ready), BATCH_MAX):
                 self._sweep(ready[i:i + BATCH_MAX])
                 batches.append(len(ready[i:i + BATCH_MAX]))
@@ -308,6 +337,13 @@ class Server:
                                       "rings": b.count}
                     if keep_maps:
                         results[b.bid]["map"] = a.out_host["map"].numpy()
+                    if breakdown:
+                        results[b.bid]["breakdown_ms"] = {
+                            "admit_delay": 1e3 * (a.t_admit - arrival),
+                            "front": a.ev0.elapsed_time(a.ready),
+                            "to_swept": a.ready.elapsed_time(a.swept_ev),
+                            "back": a.swept_ev.elapsed_time(a.done),
+                            "issue_after_admit": 1e3 * (a.t_sweep - t0 - a.t_admit)}
                     if a.front is not None:      # its buffers are free again
                         self._fronts[a.front.cap].append(a.front)
                     used -= a.bytes

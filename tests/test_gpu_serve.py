@@ -75,7 +75,7 @@ def test_server_mixed_stream_equals_alone(cc):
     dev = torch.device("cuda:0")
     grid = cc.grid_healpix_ring(32, dev)
     p = cc.Params()
-    bursts = serve.make_bursts(16, rate_hz=400.0, seed=7, median=4000, hi=60000, n_dirs=3,
+    bursts = serve.make_bursts(16, rate_hz=4000.0, seed=7, median=4000, hi=60000, n_dirs=3,
                                pool_src=30000, pool_bkg=60000)
     srv = serve.Server(grid, p, hbm_budget=256 << 20, max_active=8)
     mixed, stats = srv.run(bursts, realtime=True, keep_maps=True)
@@ -129,7 +129,7 @@ def test_server_learned_path_mixed_equals_alone(cc):
     grid = cc.grid_healpix_ring(32, dev)
     p = cc.Params()
     f = cc.RingFilter(dev, seed=3)
-    bursts = serve.make_bursts(12, rate_hz=400.0, seed=8, median=4000, hi=60000, n_dirs=2,
+    bursts = serve.make_bursts(12, rate_hz=4000.0, seed=8, median=4000, hi=60000, n_dirs=2,
                                pool_src=30000, pool_bkg=60000)
     kw = dict(ring_filter=f, tau=0.3)
     mixed, stats = serve.Server(grid, p, hbm_budget=256 << 20, max_active=8, **kw).run(
@@ -152,7 +152,7 @@ def test_graph_front_ends_equal_the_launched_path(cc, learned):
     grid = cc.grid_healpix_ring(32, dev)
     p = cc.Params()
     kw = dict(ring_filter=cc.RingFilter(dev, seed=5), tau=0.2) if learned else {}
-    bursts = serve.make_bursts(10, rate_hz=400.0, seed=9, median=3000, hi=40000, n_dirs=2,
+    bursts = serve.make_bursts(10, rate_hz=4000.0, seed=9, median=3000, hi=40000, n_dirs=2,
                                pool_src=20000, pool_bkg=40000)
     plain, _ = serve.Server(grid, p, max_active=8, **kw).run(bursts, realtime=False,
                                                              keep_maps=True)
