@@ -378,6 +378,142 @@ GemmArgs layer_fwd(const bf16 *A, int in, const bf16 *W, const float *b, int out
     return g;
 }
 
+// ---------------------------------------------------------------------------
+// Inference: the whole network in one kernel.  A CTA stages the BF16 weights
+// (rows padded so that ldmatrix reads are conflict-free) and the FP32 biases
+// in shared memory once, then its warps take 16-row slices of the input.  A
+// warp keeps its slice's activations in registers: the FP32 accumulators of
+// a layer (16 n8 tiles of m16n8k16) become, after bias, ReLU and rounding to
+// BF16, the A fragments of the next layer directly - the C fragment pair of
+// columns 16c .. 16c + 15 is exactly the A fragment of k-chunk c - so no
+// activation leaves the SM.  Rounding points are those of forward_rows.
+// ---------------------------------------------------------------------------
+constexpr int kW1S = kF + 8;        // padded row strides (bf16 elements)
+constexpr int kWHS = kH + 8;
+
+struct FusedSmem {
+    bf16 w1[kH][kW1S];
+    bf16 w2[kH][kWHS];
+    bf16 w3[kH][kWHS];
+    bf16 w4[8][kWHS];               // rows 2..7 zero
+    float b[3][kH];
+    float b4[2];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// acc (16 n8 tiles) + bias, ReLU, BF16 -> A fragments of the 8 k-chunks
+__device__ __forceinline__ void to_afrag(const float (&acc)[16][4], const float *bias, int t,
+                                         uint32_t (&A)[8][4]) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int j = 2 * c + h, col = 8 * j + 2 * t;
+            const float b0 = bias[col], b1 = bias[col + 1];
+            A[c][2 * h] = pack_bf16(fmaxf(acc[j][0] + b0, 0.0f), fmaxf(acc[j][1] + b1, 0.0f));
+            A[c][2 * h + 1] = pack_bf16(fmaxf(acc[j][2] + b0, 0.0f), fmaxf(acc[j][3] + b1, 0.0f));
+        }
+    }
+}
+
+// acc[j] = A (16 x 128) W^T for the 16 n8 tiles of a 128-wide layer
+__device__ __forceinline__ void layer128(const uint32_t (&A)[8][4], const bf16 (*W)[kWHS],
+                                         int lane, float (&acc)[16][4]) {
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    const int r = lane & 7, kh = (lane >> 3) & 1;     // ldmatrix row / k half of this lane
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            uint32_t bfr[2];
+            ldmatrix_x2(bfr, &W[8 * j + r][16 * c + 8 * kh]);
+            mma_bf16(acc[j], A[c], bfr);
+        }
+    }
+}
+
+constexpr int kFusedWarps = 8;
+
+__global__ void __launch_bounds__(kFusedWarps * 32)
+k_mlp_forward_fused(const bf16 *__restrict__ wb, const float *__restrict__ pf,
+                    const bf16 *__restrict__ X, int64_t R, float *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kH * kF; i += blockDim.x) S.w1[i / kF][i % kF] = wb[oW1 + i];
+    for (int i = tid; i < kH * kH; i += blockDim.x) {
+        S.w2[i / kH][i % kH] = wb[oW2 + i];
+        S.w3[i / kH][i % kH] = wb[oW3 + i];
+    }
+    for (int i = tid; i < 8 * kH; i += blockDim.x)
+        S.w4[i / kH][i % kH] = i < 2 * kH ? wb[oW4 + i] : __float2bfloat16(0.0f);
+    for (int i = tid; i < kH; i += blockDim.x) {
+        S.b[0][i] = pf[ob1 + i];
+        S.b[1][i] = pf[ob2 + i];
+        S.b[2][i] = pf[ob3 + i];
+    }
+    if (tid < 2) S.b4[tid] = pf[ob4 + tid];
+    __syncthreads();
+
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t nslices = (R + 15) / 16;
+    for (int64_t sl = (int64_t)blockIdx.x * kFusedWarps + warp; sl < nslices;
+         sl += (int64_t)gridDim.x * kFusedWarps) {
+        const int64_t r0 = sl * 16, ra = r0 + g, rb = ra + 8;
+        // layer 1: the A fragment straight from the feature rows (16 features)
+        uint32_t a1[4];
+        const uint32_t *xa = reinterpret_cast<const uint32_t *>(X + ra * kF);
+        const uint32_t *xb = reinterpret_cast<const uint32_t *>(X + rb * kF);
+        a1[0] = ra < R ? xa[t] : 0u;
+        a1[1] = rb < R ? xb[t] : 0u;
+        a1[2] = ra < R ? xa[4 + t] : 0u;
+        a1[3] = rb < R ? xb[4 + t] : 0u;
+        float acc[16][4];
+        {
+            const int r = lane & 7, kh = (lane >> 3) & 1;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+                uint32_t bfr[2];
+                ldmatrix_x2(bfr, &S.w1[8 * j + r][8 * kh]);
+                mma_bf16(acc[j], a1, bfr);
+            }
+        }
+        uint32_t A[8][4];
+        to_afrag(acc, S.b[0], t, A);
+        layer128(A, S.w2, lane, acc);
+        to_afrag(acc, S.b[1], t, A);
+        layer128(A, S.w3, lane, acc);
+        to_afrag(acc, S.b[2], t, A);
+        // layer 4: one n8 tile, columns 0 and 1 real
+        float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        {
+            const int r = lane & 7, kh = (lane >> 3) & 1;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                uint32_t bfr[2];
+                ldmatrix_x2(bfr, &S.w4[r][16 * c + 8 * kh]);
+                mma_bf16(o, A[c], bfr);
+            }
+        }
+        if (t == 0) {                                     // columns 0, 1 of rows g, g + 8
+            if (ra < R) {
+                out[2 * ra] = o[0] + S.b4[0];
+                out[2 * ra + 1] = o[1] + S.b4[1];
+            }
+            if (rb < R) {
+                out[2 * rb] = o[2] + S.b4[0];
+                out[2 * rb + 1] = o[3] + S.b4[1];
+            }
+        }
+    }
+}
+
 cudaError_t forward_rows(const bf16 *wb, const float *pf, const bf16 *X, int rows, Work &w,
                          cudaStream_t s) {
     cudaError_t e;
@@ -475,18 +611,22 @@ cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, 
 
 cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
                         float *out, char *ws, cudaStream_t s) {
-    Work w;
-    work_layout(R < kChunk ? R : kChunk, &w, ws);
+    (void)ws;                                  // the fused forward keeps activations on chip
+    if (R == 0) return cudaSuccess;
+    const size_t smem = sizeof(FusedSmem);     // > 48 KB: opt in (per device, so every call)
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_fused,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_forward_fused, kFusedWarps * 32, smem);
+    if (occ < 1) occ = 1;
+    int64_t ctas = (int64_t)device_sm_count() * occ;
+    const int64_t need = ((R + 15) / 16 + kFusedWarps - 1) / kFusedWarps;
+    if (ctas > need) ctas = need;
     TraceScope ts(CC_STAGE_MLP, s);
-    for (int64_t r0 = 0; r0 < R; r0 += kChunk) {
-        int rows = (int)(R - r0 < kChunk ? R - r0 : kChunk);
-        Work wc = w;
-        wc.out = out + 2 * r0;
-        cudaError_t e = forward_rows(reinterpret_cast<const bf16 *>(wb), params,
-                                     reinterpret_cast<const bf16 *>(F) + r0 * kF, rows, wc, s);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    k_mlp_forward_fused<<<(unsigned)ctas, kFusedWarps * 32, smem, s>>>(
+        reinterpret_cast<const bf16 *>(wb), params, reinterpret_cast<const bf16 *>(F), R, out);
+    return cudaGetLastError();
 }
 
 cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
