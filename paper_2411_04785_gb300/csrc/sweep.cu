@@ -12,8 +12,10 @@
 // relative (not absolute) FP32 accuracy, so small angles keep their precision.
 // For theta <= pi/2, theta = sqrt(h) Q(h); for theta > pi/2 the mirror
 // identity theta = pi - sqrt(2 - h) Q(2 - h) applies, with
-// Q(s) = acos(1 - s) / sqrt(s) a degree-7 polynomial fitted on [0, 1]
-// (fit_acos.py; |error| <= 1.3e-8 rad before FP32 rounding).  Rings with
+// Q(s) = acos(1 - s) / sqrt(s) a degree-6 polynomial fitted on [0, 1]
+// (fit_acos.py 6: |error| <= 8.8e-8 rad with exact coefficients, 2.7e-7 rad
+// evaluated in FP32 against 2.3e-7 for degree 7 - the FP32 evaluation, not
+// the fit, sets the error, so the seventh FMA per pair is not spent).  Rings with
 // eta > pi/2 are mirrored (a -> -a, eta -> pi - eta; the map is unchanged)
 // so that the ill-conditioned end theta -> pi only meets far tails.  The
 // Gaussian is exp2(-t^2) with t = theta k - eta k, k = sqrt(log2(e)/2)/deta,
@@ -197,14 +199,13 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
         h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
         float2 g = __ffma2_rn(h, m1, two2);             // 2 - h
         float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
-        float2 p = pair(1.4414361e-03f);                // acos_q, FP32x2
-        p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
-        p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
-        p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
-        p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
-        p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
-        p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
-        p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+        float2 p = pair(2.61164433e-03f);               // Q(s), degree 6, FP32x2
+        p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
+        p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
+        p = __ffma2_rn(p, sv, pair(5.94551489e-03f));
+        p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
+        p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
+        p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
         float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
         float2 th = __fmul2_rn(rt, p);
         float2 nbs = make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
@@ -347,7 +348,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                     }
                 }
             } else {
-#pragma unroll 2
+#pragma unroll 4
                 for (int r = 0; r < kTile; r++) ring_pairs<DP, KCUT>(T[r], ncx, ncy, ncz, acc, kc2);
             }
         }

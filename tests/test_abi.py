@@ -93,3 +93,16 @@ def test_voxel_universe_counts_without_gpu(libpath):
     assert L.cc_voxel_count(0, 1025) == -1
     assert L.cc_voxel_universe(1, 0, 1.0, 0, 0, 0, None, None, None, None) == -1
     assert L.cc_voxel_universe(1, 8, 0.0, 0, 0, 0, None, None, None, None) == -1
+
+
+def test_events_copy_argument_checks_without_gpu(libpath):
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import api
+    L = cc.lib()
+    fake = C.c_void_p(1 << 20)
+    ev = lambda stride: api.cc_events(fake, fake, fake, fake, fake, stride, stride)
+    assert L.cc_events_copy(None, 0, C.byref(ev(10)), 0, 5, None) == -1
+    assert L.cc_events_copy(C.byref(ev(10)), 6, C.byref(ev(10)), 0, 5, None) == -1   # past dst
+    assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(4)), 0, 5, None) == -1    # past src
+    assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(10)), 0, -1, None) == -1
+    assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(10)), 0, 0, None) == 0     # nothing

@@ -104,3 +104,20 @@ def test_full_size_stream_and_spectrum(cc):
     h = cc.cluster_spectrum(o["adc"], o["n_events"], 3, 20000)   # global-atomic path
     torch.cuda.synchronize()
     np.testing.assert_array_equal(h.cpu().numpy(), oracle.spectrum(want["adc"], 3, 20000))
+
+
+def test_output_subsets_and_no_amplitudes(cc):
+    """Outputs may be asked for one by one, and amplitudes left out."""
+    t, adc, _ = synth.detection_stream(n_events=1500, seed=6)
+    want = oracle.maxstep_events(t, adc, 15_000)
+    td = torch.from_numpy(t).to("cuda:0")
+    o = cc.cluster_maxstep(td, None, 15_000, outputs=("edge", "event_id", "first", "count"))
+    torch.cuda.synchronize()
+    K = int(o["n_events"].item())
+    np.testing.assert_array_equal(o["edge"].cpu().numpy(), want["edge"])
+    np.testing.assert_array_equal(o["event_id"].cpu().numpy(), want["event_id"])
+    np.testing.assert_array_equal(o["first"][:K].cpu().numpy(), want["first"])
+    np.testing.assert_array_equal(o["count"][:K].cpu().numpy(), want["count"])
+    o = cc.cluster_maxstep(td, torch.from_numpy(adc).to("cuda:0"), 15_000, outputs=("adc",))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(o["adc"][:K].cpu().numpy(), want["adc"])

@@ -164,3 +164,33 @@ def test_graph_front_ends_equal_the_launched_path(cc, learned):
         np.testing.assert_array_equal(g["map"], a["map"])
         assert g["argmax"] == a["argmax"]
         np.testing.assert_array_equal(g["dir"], a["dir"])
+
+
+def test_events_copy_of_pool_slices(cc):
+    """cc_events_copy: slices of a wider host pool land at an offset of a
+    device event set, slot rows and counts intact."""
+    from paper_2411_04785_gb300 import api
+    rng = np.random.default_rng(2)
+    P, cap = 5000, 3000
+    pool = {"n": rng.integers(0, 5, P).astype(np.uint8)}
+    for k in "xyze":
+        pool[k] = rng.standard_normal((4, P)).astype(np.float32)
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in pool.items()}
+    dev = {"n": torch.zeros(cap, dtype=torch.uint8, device="cuda:0")}
+    for k in "xyze":
+        dev[k] = torch.zeros((4, cap), dtype=torch.float32, device="cuda:0")
+    dst = tuple(dev[k] for k in ("n", "x", "y", "z", "e"))
+    a, n1, b, n2 = 1234, 700, 4000, 900
+    part1 = (host["n"][a:a + n1],) + tuple(host[k][:, a:a + n1] for k in "xyze")
+    part2 = (host["n"][b:b + n2],) + tuple(host[k][:, b:b + n2] for k in "xyze")
+    api.events_copy(dst, 10, part1)
+    api.events_copy(dst, 10 + n1, part2)
+    torch.cuda.synchronize()
+    got_n = dev["n"].cpu().numpy()
+    np.testing.assert_array_equal(got_n[10:10 + n1], pool["n"][a:a + n1])
+    np.testing.assert_array_equal(got_n[10 + n1:10 + n1 + n2], pool["n"][b:b + n2])
+    assert (got_n[:10] == 0).all() and (got_n[10 + n1 + n2:] == 0).all()
+    for k in "xyze":
+        g = dev[k].cpu().numpy()
+        np.testing.assert_array_equal(g[:, 10:10 + n1], pool[k][:, a:a + n1])
+        np.testing.assert_array_equal(g[:, 10 + n1:10 + n1 + n2], pool[k][:, b:b + n2])
