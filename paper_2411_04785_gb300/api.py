@@ -526,6 +526,9 @@ class RingFilter:
     def forward(self, feats, out=None, stream=None, workspace=None):
         """MLP outputs [R, 2].  Calls that may run concurrently (other streams)
         must each pass their own workspace (mlp_workspace_bytes)."""
+        _need(feats, torch.bfloat16, "feats")
+        if feats.dim() != 2 or feats.shape[1] != MLP_FEATURES:
+            raise ValueError(f"feats must be [R, {MLP_FEATURES}]")
         R = feats.shape[0]
         out = out if out is not None else torch.empty((R, 2), dtype=torch.float32,
                                                       device=self.dev)

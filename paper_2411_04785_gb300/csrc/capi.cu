@@ -306,6 +306,8 @@ cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
     if (rows == 0) return CC_OK;
     if (!params || !params_bf16 || !features || !out)
         return fail(CC_EINVAL, "params/features/out must be non-NULL");
+    if (!aligned(features, 16) || !aligned(params_bf16, 16) || !aligned(out, 8))
+        return fail(CC_EINVAL, "features and params_bf16 must be 16-byte aligned, out 8-byte");
     if (!workspace || !aligned(workspace, 256))
         return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     size_t need = mlp_workspace_bytes(rows);

@@ -1,14 +1,35 @@
 // cc_pipe.cuh - device helpers shared by the sweeps (far-field directions
-// and near-field voxels): the mbarrier + bulk-copy (TMA) ring-tile pipeline
-// with bounded waits, and the argmax reductions (ties: lowest index).
+// and near-field voxels), the clustering and the ring filter: the mbarrier +
+// bulk-copy and tensor-copy (TMA) pipelines with bounded waits, and the argmax
+// reductions (ties: lowest index).
 #pragma once
 
+#include <cuda.h>
 #include <float.h>
 
 #include "cc_internal.cuh"
 
 namespace cc {
 namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda)
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline TmapEncodeFn encode_fn() {
+    static const TmapEncodeFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<TmapEncodeFn>(p);
+    }();
+    return fn;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -40,6 +61,15 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
 

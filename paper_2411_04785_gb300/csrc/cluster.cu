@@ -32,7 +32,6 @@
 // 16 step masks, scans its detections serially, and the lanes of a warp
 // combine their aggregates in one warp scan per 16 detections.  Edges and
 // event ids leave as 16-byte stores.
-#include <cuda.h>
 #include <string.h>
 
 #include "cc_internal.cuh"
@@ -40,25 +39,6 @@
 
 namespace cc {
 namespace {
-
-// cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda)
-typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-TmapEncodeFn encode_fn() {
-    static const TmapEncodeFn fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            p = nullptr;
-        return reinterpret_cast<TmapEncodeFn>(p);
-    }();
-    return fn;
-}
 
 constexpr int kCWarps = 8;
 constexpr int kCThreads = kCWarps * 32;
@@ -143,15 +123,6 @@ __device__ __forceinline__ int swz(int row, int chunk) { return row * 128 + ((ch
 // element e of the tile: its byte offset in tsw / asw
 __device__ __forceinline__ int t_off(int e) { return swz(e >> 4, (e & 15) >> 1) + ((e & 1) << 3); }
 __device__ __forceinline__ int a_off(int e) { return swz(e >> 5, (e & 31) >> 2) + ((e & 3) << 2); }
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 __global__ void __launch_bounds__(kCThreads)
 k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap amap,

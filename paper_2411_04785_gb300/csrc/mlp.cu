@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 
 #include "cc_math.cuh"
+#include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
@@ -379,138 +380,343 @@ GemmArgs layer_fwd(const bf16 *A, int in, const bf16 *W, const float *b, int out
 }
 
 // ---------------------------------------------------------------------------
-// Inference: the whole network in one kernel.  A CTA stages the BF16 weights
-// (rows padded so that ldmatrix reads are conflict-free) and the FP32 biases
-// in shared memory once, then its warps take 16-row slices of the input.  A
-// warp keeps its slice's activations in registers: the FP32 accumulators of
-// a layer (16 n8 tiles of m16n8k16) become, after bias, ReLU and rounding to
-// BF16, the A fragments of the next layer directly - the C fragment pair of
-// columns 16c .. 16c + 15 is exactly the A fragment of k-chunk c - so no
-// activation leaves the SM.  Rounding points are those of forward_rows.
+// Inference on the fifth-generation tensor cores (tcgen05, accumulators in
+// tensor memory).  One persistent CTA per SM takes 128-row tiles of the
+// features; its warps have fixed roles:
+//   warp 0      TMA producer: feature tiles [128][16] into a 4-stage ring
+//               (32-byte swizzle, zero rows past the end); owns the TMEM
+//               allocation (256 columns = two accumulator slots of 128).
+//   warp 1      MMA issuer (one thread): per tile and layer the products
+//               D[128][N] = A[128][K] W^T on the tensor cores, A and W in
+//               shared memory as K-major operands, D in the tile's TMEM slot;
+//               tcgen05.commit signals the epilogue.
+//   warps 2..5  epilogue: each thread owns one row (its warp's TMEM lane
+//               quarter), loads the row's accumulators, adds the bias, applies
+//               ReLU, rounds to BF16 and stores the row as the next layer's A
+//               operand (128-byte swizzle) - or, after the last layer, writes
+//               the two outputs.
+// Two tiles are in flight, issued pairwise by layer (L1 a, L1 b, L2 a, ...),
+// so the epilogue of one tile overlaps the products of the other.  Weights
+// (72 KB, swizzled) and biases are staged once per CTA.  The rounding points
+// are those of forward_rows: FP32 accumulation, bias and ReLU in FP32, BF16
+// activations.  Every wait is bounded; a CTA that gives up writes NaN to the
+// rows it still owes, so a failure cannot pass for a result.
 // ---------------------------------------------------------------------------
-constexpr int kW1S = kF + 8;        // padded row strides (bf16 elements)
-constexpr int kWHS = kH + 8;
+constexpr int kTM = 128;                  // rows per tile = MMA M
+constexpr int kXStages = 4;
+constexpr int kTcWarps = 6;
+constexpr int kTmemCols = 256;
 
-struct FusedSmem {
-    bf16 w1[kH][kW1S];
-    bf16 w2[kH][kWHS];
-    bf16 w3[kH][kWHS];
-    bf16 w4[8][kWHS];               // rows 2..7 zero
+struct TcSmem {                           // every operand block 1024-byte aligned
+    bf16 w2[2][kH * 64];                  // [k block][n][64 k], 128B swizzle
+    bf16 w3[2][kH * 64];
+    bf16 h[2][2][kTM * 64];               // activations [slot][k block][row][64 k]
+    bf16 w4[2][16 * 64];                  // rows 2..15 zero (MMA N = 16)
+    bf16 w1[kH * kF];                     // [n][16 k], 32B swizzle
+    bf16 x[kXStages][kTM * kF];           // feature tiles, 32B swizzle
     float b[3][kH];
     float b4[2];
+    unsigned long long x_full[kXStages], x_empty[kXStages], acc_full[2], h_done[2], fin;
+    unsigned tmem;
+    int err;
 };
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
+// byte offset of 16-byte chunk `c` of row `r` in the two swizzled layouts
+__device__ __forceinline__ int sw128(int r, int c) { return r * 128 + ((c ^ (r & 7)) << 4); }
+__device__ __forceinline__ int sw32(int r, int c) { return r * 32 + ((c ^ ((r >> 2) & 1)) << 4); }
+
+// shared-memory matrix descriptor: start address, leading byte offset 16
+// (unused by the swizzled K-major layouts), stride byte offset between 8-row
+// groups, descriptor version 1, swizzle mode (2 = 128B, 6 = 32B)
+constexpr uint64_t kSw128 = 2, kSw32 = 6;
+__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned sbo, uint64_t mode) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46) | (mode << 61);
 }
 
-// acc (16 n8 tiles) + bias, ReLU, BF16 -> A fragments of the 8 k-chunks
-__device__ __forceinline__ void to_afrag(const float (&acc)[16][4], const float *bias, int t,
-                                         uint32_t (&A)[8][4]) {
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr unsigned idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+           ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(unsigned d, uint64_t a, uint64_t b, unsigned id, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 64 consecutive FP32 accumulator columns of this thread's TMEM lane; the
+// wait is in the same statement, so the registers are valid on return
+__device__ __forceinline__ void tmem_ld64(unsigned addr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,"
+        "%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,"
+        "%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
+          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
+          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
+          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(addr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld2(unsigned addr, uint32_t (&r)[2]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1])
+        : "r"(addr)
+        : "memory");
+}
+
+// BF16x2 of (max(lo, 0), max(hi, 0)), round to nearest even; lo in the low half
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// accumulator columns [c0, c0 + 64) of one row + bias, ReLU, BF16 -> the
+// row's 8 chunks of k block c0 / 64 of the next layer's A operand
+__device__ __forceinline__ void epi64(const uint32_t (&r)[64], const float *bias, char *hblk,
+                                      int row) {
 #pragma unroll
     for (int c = 0; c < 8; c++) {
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int j = 2 * c + h, col = 8 * j + 2 * t;
-            const float b0 = bias[col], b1 = bias[col + 1];
-            A[c][2 * h] = pack_bf16(fmaxf(acc[j][0] + b0, 0.0f), fmaxf(acc[j][1] + b1, 0.0f));
-            A[c][2 * h + 1] = pack_bf16(fmaxf(acc[j][2] + b0, 0.0f), fmaxf(acc[j][3] + b1, 0.0f));
-        }
+        const float4 b0 = *reinterpret_cast<const float4 *>(bias + 8 * c);
+        const float4 b1 = *reinterpret_cast<const float4 *>(bias + 8 * c + 4);
+        const float2 s0 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c]), __uint_as_float(r[8 * c + 1])),
+                                     make_float2(b0.x, b0.y));
+        const float2 s1 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 2]), __uint_as_float(r[8 * c + 3])),
+                                     make_float2(b0.z, b0.w));
+        const float2 s2 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 4]), __uint_as_float(r[8 * c + 5])),
+                                     make_float2(b1.x, b1.y));
+        const float2 s3 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 6]), __uint_as_float(r[8 * c + 7])),
+                                     make_float2(b1.z, b1.w));
+        uint4 v;
+        v.x = relu_bf16x2(s0.x, s0.y);
+        v.y = relu_bf16x2(s1.x, s1.y);
+        v.z = relu_bf16x2(s2.x, s2.y);
+        v.w = relu_bf16x2(s3.x, s3.y);
+        *reinterpret_cast<uint4 *>(hblk + sw128(row, c)) = v;
     }
 }
 
-// acc[j] = A (16 x 128) W^T for the 16 n8 tiles of a 128-wide layer
-__device__ __forceinline__ void layer128(const uint32_t (&A)[8][4], const bf16 (*W)[kWHS],
-                                         int lane, float (&acc)[16][4]) {
-#pragma unroll
-    for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    const int r = lane & 7, kh = (lane >> 3) & 1;     // ldmatrix row / k half of this lane
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            uint32_t bfr[2];
-            ldmatrix_x2(bfr, &W[8 * j + r][16 * c + 8 * kh]);
-            mma_bf16(acc[j], A[c], bfr);
-        }
-    }
-}
-
-constexpr int kFusedWarps = 8;
-
-__global__ void __launch_bounds__(kFusedWarps * 32)
-k_mlp_forward_fused(const bf16 *__restrict__ wb, const float *__restrict__ pf,
-                    const bf16 *__restrict__ X, int64_t R, float *__restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
+__global__ void __launch_bounds__(kTcWarps * 32, 1)
+k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restrict__ wb,
+                 const float *__restrict__ pf, int64_t R, float *__restrict__ out) {
+    extern __shared__ unsigned char smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kH * kF; i += blockDim.x) S.w1[i / kF][i % kF] = wb[oW1 + i];
-    for (int i = tid; i < kH * kH; i += blockDim.x) {
-        S.w2[i / kH][i % kH] = wb[oW2 + i];
-        S.w3[i / kH][i % kH] = wb[oW3 + i];
+    const int64_t T = (R + kTM - 1) / kTM;
+    const int nt = (int)((T - blockIdx.x + gridDim.x - 1) / gridDim.x);   // this CTA's tiles
+    auto tile_of = [&](int k) { return (int64_t)blockIdx.x + (int64_t)k * gridDim.x; };
+
+    // weights (16-byte chunks into their swizzled places) and biases
+    const uint4 *wg = reinterpret_cast<const uint4 *>(wb);
+    for (int i = tid; i < kH * 2; i += blockDim.x)
+        *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.w1) + sw32(i >> 1, i & 1)) =
+            wg[oW1 / 8 + i];
+    for (int i = tid; i < kH * 16; i += blockDim.x) {
+        const int n = i >> 4, kb = (i >> 3) & 1, c = i & 7;
+        *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.w2[kb]) + sw128(n, c)) =
+            wg[oW2 / 8 + i];
+        *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.w3[kb]) + sw128(n, c)) =
+            wg[oW3 / 8 + i];
     }
-    for (int i = tid; i < 8 * kH; i += blockDim.x)
-        S.w4[i / kH][i % kH] = i < 2 * kH ? wb[oW4 + i] : __float2bfloat16(0.0f);
+    for (int i = tid; i < 16 * 16; i += blockDim.x) {
+        const int n = i >> 4, kb = (i >> 3) & 1, c = i & 7;
+        *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.w4[kb]) + sw128(n, c)) =
+            n < 2 ? wg[oW4 / 8 + i] : make_uint4(0u, 0u, 0u, 0u);
+    }
     for (int i = tid; i < kH; i += blockDim.x) {
         S.b[0][i] = pf[ob1 + i];
         S.b[1][i] = pf[ob2 + i];
         S.b[2][i] = pf[ob3 + i];
     }
     if (tid < 2) S.b4[tid] = pf[ob4 + tid];
+    if (tid == 0) {
+        for (int i = 0; i < kXStages; i++) {
+            mbar_init(&S.x_full[i], 1);
+            mbar_init(&S.x_empty[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&S.acc_full[i], 1);
+            mbar_init(&S.h_done[i], 4);
+        }
+        mbar_init(&S.fin, 1);
+        S.err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // weights -> tensor cores
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = S.tmem;
+    volatile int *err = &S.err;
 
-    const int g = lane >> 2, t = lane & 3;
-    const int64_t nslices = (R + 15) / 16;
-    for (int64_t sl = (int64_t)blockIdx.x * kFusedWarps + warp; sl < nslices;
-         sl += (int64_t)gridDim.x * kFusedWarps) {
-        const int64_t r0 = sl * 16, ra = r0 + g, rb = ra + 8;
-        // layer 1: the A fragment straight from the feature rows (16 features)
-        uint32_t a1[4];
-        const uint32_t *xa = reinterpret_cast<const uint32_t *>(X + ra * kF);
-        const uint32_t *xb = reinterpret_cast<const uint32_t *>(X + rb * kF);
-        a1[0] = ra < R ? xa[t] : 0u;
-        a1[1] = rb < R ? xb[t] : 0u;
-        a1[2] = ra < R ? xa[4 + t] : 0u;
-        a1[3] = rb < R ? xb[4 + t] : 0u;
-        float acc[16][4];
-        {
-            const int r = lane & 7, kh = (lane >> 3) & 1;
+    if (warp == 0) {
+        if (lane == 0) {                  // producer
+            int uses[kXStages] = {};
+            for (int k = 0; k < nt && !*err; k++) {
+                const int st = k % kXStages;
+                if (uses[st] > 0 && !mbar_wait(&S.x_empty[st], (uses[st] - 1) & 1)) {
+                    *err = 1;
+                    break;
+                }
+                expect_tx(&S.x_full[st], kTM * kF * 2);
+                tma_load_2d(S.x[st], &xmap, 0, (int)(tile_of(k) * kTM), &S.x_full[st]);
+                uses[st]++;
+            }
+            for (int st = 0; st < kXStages; st++)    // no copy may outlive the CTA
+                if (uses[st] > 0 && !mbar_wait(&S.x_full[st], (uses[st] - 1) & 1)) *err = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                  // MMA issuer
+            int hd[2] = {0, 0};
+            const unsigned w1 = smem_u32(S.w1), w4 = smem_u32(S.w4[0]);
+            for (int p = 0; p < nt && !*err; p += 2) {
+                const int q = nt - p < 2 ? nt - p : 2;
+                for (int l = 0; l < 4 && !*err; l++) {
+                    for (int j = 0; j < q; j++) {
+                        const int k = p + j;
+                        const unsigned d = tmem + (unsigned)(j * 128);
+                        if (l == 0) {
+                            const int st = k % kXStages;
+                            if (!mbar_wait(&S.x_full[st], (k / kXStages) & 1) ||
+                                (k >= 2 && !mbar_wait(&S.h_done[j], hd[j]++ & 1))) {
+                                *err = 1;
+                                break;
+                            }
+                            tc_fence_after();
+                            umma(d, sdesc(smem_u32(S.x[st]), 256, kSw32), sdesc(w1, 256, kSw32),
+                                 idesc(kTM, kH), 0);
+                            umma_commit(&S.acc_full[j]);
+                            umma_commit(&S.x_empty[st]);
+                        } else {
+                            if (!mbar_wait(&S.h_done[j], hd[j]++ & 1)) {
+                                *err = 1;
+                                break;
+                            }
+                            tc_fence_after();
+                            const unsigned a0 = smem_u32(S.h[j][0]);
+                            const unsigned b0 = l == 1 ? smem_u32(S.w2[0])
+                                                : l == 2 ? smem_u32(S.w3[0]) : w4;
+                            const unsigned bblk = l == 3 ? 16 * 128 : kH * 128;
+                            const unsigned id = l == 3 ? idesc(kTM, 16) : idesc(kTM, kH);
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-                uint32_t bfr[2];
-                ldmatrix_x2(bfr, &S.w1[8 * j + r][8 * kh]);
-                mma_bf16(acc[j], a1, bfr);
+                            for (int kk = 0; kk < 8; kk++) {
+                                const unsigned off = (unsigned)(kk & 3) * 32;
+                                umma(d, sdesc(a0 + (kk >> 2) * (kTM * 128) + off, 1024, kSw128),
+                                     sdesc(b0 + (kk >> 2) * bblk + off, 1024, kSw128), id, kk > 0);
+                            }
+                            umma_commit(&S.acc_full[j]);
+                        }
+                    }
+                }
+            }
+            umma_commit(&S.fin);          // every product issued has completed
+            if (!mbar_wait(&S.fin, 0)) *err = 1;
+        }
+    } else {                              // epilogue: one row per thread
+        const int qd = warp & 3, row = 32 * qd + lane;
+        const unsigned lanes = (unsigned)(32 * qd) << 16;
+        int af[2] = {0, 0};
+        int p = 0, l = 0, j = 0;
+        for (p = 0; p < nt; p += 2) {
+            const int q = nt - p < 2 ? nt - p : 2;
+            for (l = 0; l < 4; l++) {
+                for (j = 0; j < q; j++) {
+                    const bool ok = !*err && mbar_wait(&S.acc_full[j], af[j]++ & 1);
+                    if (!__all_sync(0xffffffffu, ok)) {    // warp-uniform: the loads are .aligned
+                        *err = 1;
+                        goto fail;
+                    }
+                    tc_fence_after();
+                    const unsigned t = tmem + lanes + (unsigned)(j * 128);
+                    if (l < 3) {
+                        uint32_t r[64];
+                        tmem_ld64(t, r);
+                        epi64(r, S.b[l], reinterpret_cast<char *>(S.h[j][0]), row);
+                        tmem_ld64(t + 64, r);
+                        epi64(r, S.b[l] + 64, reinterpret_cast<char *>(S.h[j][1]), row);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    } else {
+                        uint32_t r[2];
+                        tmem_ld2(t, r);
+                        const int64_t g = tile_of(p + j) * kTM + row;
+                        if (g < R)
+                            *reinterpret_cast<float2 *>(out + 2 * g) =
+                                make_float2(__uint_as_float(r[0]) + S.b4[0],
+                                            __uint_as_float(r[1]) + S.b4[1]);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.h_done[j]);
+                }
             }
         }
-        uint32_t A[8][4];
-        to_afrag(acc, S.b[0], t, A);
-        layer128(A, S.w2, lane, acc);
-        to_afrag(acc, S.b[1], t, A);
-        layer128(A, S.w3, lane, acc);
-        to_afrag(acc, S.b[2], t, A);
-        // layer 4: one n8 tile, columns 0 and 1 real
-        float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        {
-            const int r = lane & 7, kh = (lane >> 3) & 1;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                uint32_t bfr[2];
-                ldmatrix_x2(bfr, &S.w4[r][16 * c + 8 * kh]);
-                mma_bf16(o, A[c], bfr);
+    fail:
+        if (p < nt) {                     // gave up: NaN for every row still owed
+            const float nan = __int_as_float(0x7fc00000);
+            for (int k = p; k < nt; k++) {
+                const int64_t g = tile_of(k) * kTM + row;
+                if (g < R) *reinterpret_cast<float2 *>(out + 2 * g) = make_float2(nan, nan);
             }
         }
-        if (t == 0) {                                     // columns 0, 1 of rows g, g + 8
-            if (ra < R) {
-                out[2 * ra] = o[0] + S.b4[0];
-                out[2 * ra + 1] = o[1] + S.b4[1];
-            }
-            if (rb < R) {
-                out[2 * rb] = o[2] + S.b4[0];
-                out[2 * rb + 1] = o[3] + S.b4[1];
-            }
-        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
     }
 }
 
@@ -611,22 +817,33 @@ cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, 
 
 cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
                         float *out, char *ws, cudaStream_t s) {
-    (void)ws;                                  // the fused forward keeps activations on chip
+    (void)ws;                                  // activations stay on chip
     if (R == 0) return cudaSuccess;
-    const size_t smem = sizeof(FusedSmem);     // > 48 KB: opt in (per device, so every call)
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_fused,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TmapEncodeFn enc = encode_fn();
+    if (enc == nullptr) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmemBytes);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_forward_fused, kFusedWarps * 32, smem);
-    if (occ < 1) occ = 1;
-    int64_t ctas = (int64_t)device_sm_count() * occ;
-    const int64_t need = ((R + 15) / 16 + kFusedWarps - 1) / kFusedWarps;
-    if (ctas > need) ctas = need;
+    const int64_t sms = device_sm_count();
     TraceScope ts(CC_STAGE_MLP, s);
-    k_mlp_forward_fused<<<(unsigned)ctas, kFusedWarps * 32, smem, s>>>(
-        reinterpret_cast<const bf16 *>(wb), params, reinterpret_cast<const bf16 *>(F), R, out);
-    return cudaGetLastError();
+    constexpr int64_t kRowsPerLaunch = (int64_t)1 << 30;   // TMA row coordinates stay int32
+    for (int64_t r0 = 0; r0 < R; r0 += kRowsPerLaunch) {
+        const int64_t n = R - r0 < kRowsPerLaunch ? R - r0 : kRowsPerLaunch;
+        CUtensorMap xmap;
+        const cuuint64_t dims[2] = {(cuuint64_t)kF, (cuuint64_t)n};
+        const cuuint64_t strides[1] = {(cuuint64_t)kF * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kF, (cuuint32_t)kTM};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(F + r0 * kF),
+                dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        const int64_t tiles = (n + kTM - 1) / kTM;
+        k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kTcWarps * 32, kTcSmemBytes, s>>>(
+            xmap, reinterpret_cast<const bf16 *>(wb), params, n, out + 2 * r0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,

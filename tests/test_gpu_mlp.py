@@ -41,17 +41,35 @@ def random_case(seed, B):
     return p, X, y, res, w
 
 
-def test_forward_matches_oracle(cc, dev):
-    p, X, _, _, _ = random_case(1, 3000)
+# 128-row tiles on at most one CTA per SM: one partial tile, exact tiles, a
+# ragged tail, one tile per CTA (3000), several tile pairs per CTA plus an odd
+# tile (70,001 and 500,000 rows)
+@pytest.mark.parametrize("R", [1, 127, 128, 129, 3000, 70_001, 500_000])
+def test_forward_matches_oracle(cc, dev, R):
+    p, X, _, _, _ = random_case(1, R)
     f = cc.RingFilter(dev, params=p)
     out = f.forward(to_dev(X.astype(np.float32), dev).to(torch.bfloat16).contiguous())
     torch.cuda.synchronize()
     want, _, _ = mlp.forward(p, X, round_points=True)
     got = out.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all()
     # FP32 accumulation vs FP64 over K <= 128 BF16 products, plus rare
     # one-ulp BF16 flips of a hidden activation: norm-wise half a BF16 ulp
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < 2.0 ** -9, err
+    # row by row: a row read from or written to the wrong place would be off
+    # by the outputs' own scale
+    dev_ = np.abs(got - want).max(1)
+    assert dev_.max() < 0.05 * np.abs(want).mean(), (dev_.argmax(), dev_.max())
+
+
+def test_forward_rejects_misaligned_features(cc, dev):
+    p, X, _, _, _ = random_case(1, 64)
+    f = cc.RingFilter(dev, params=p)
+    flat = torch.zeros(64 * 16 + 8, dtype=torch.bfloat16, device=dev)
+    feats = flat[1:1 + 64 * 16].view(64, 16)       # contiguous, 2 bytes off 16
+    with pytest.raises(cc.CCError):
+        f.forward(feats)
 
 
 @pytest.mark.parametrize("B", [1, 777, 65536])
