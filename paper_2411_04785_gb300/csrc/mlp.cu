@@ -380,42 +380,55 @@ GemmArgs layer_fwd(const bf16 *A, int in, const bf16 *W, const float *b, int out
 }
 
 // ---------------------------------------------------------------------------
-// Inference on the fifth-generation tensor cores (tcgen05, accumulators in
-// tensor memory).  One persistent CTA per SM takes 128-row tiles of the
-// features; its warps have fixed roles:
+// Inference on the fifth-generation tensor cores (tcgen05, tensor memory).
+// One persistent CTA per SM takes 128-row tiles of the features; its warps
+// have fixed roles:
 //   warp 0      TMA producer: feature tiles [128][16] into a 4-stage ring
 //               (32-byte swizzle, zero rows past the end); owns the TMEM
-//               allocation (256 columns = two accumulator slots of 128).
-//   warp 1      MMA issuer (one thread): per tile and layer the products
-//               D[128][N] = A[128][K] W^T on the tensor cores, A and W in
-//               shared memory as K-major operands, D in the tile's TMEM slot;
+//               allocation (all 512 columns).
+//   warp 1      MMA issuer (one elected lane of a converged warp, operand
+//               descriptors built once): per tile and layer the product
+//               D[128][N] = A[128][K] W^T, W K-major in shared memory, D in
+//               the tile's TMEM slot.  Layer 1 reads A (the features) from
+//               shared memory; layers 2-4 read A (the activations) from
+//               TMEM, so the tensor cores stream only W from shared memory.
 //               tcgen05.commit signals the epilogue.
-//   warps 2..5  epilogue: each thread owns one row (its warp's TMEM lane
-//               quarter), loads the row's accumulators, adds the bias, applies
-//               ReLU, rounds to BF16 and stores the row as the next layer's A
-//               operand (128-byte swizzle) - or, after the last layer, writes
-//               the two outputs.
-// Two tiles are in flight, issued pairwise by layer (L1 a, L1 b, L2 a, ...),
-// so the epilogue of one tile overlaps the products of the other.  Weights
-// (72 KB, swizzled) and biases are staged once per CTA.  The rounding points
-// are those of forward_rows: FP32 accumulation, bias and ReLU in FP32, BF16
-// activations.  Every wait is bounded; a CTA that gives up writes NaN to the
-// rows it still owes, so a failure cannot pass for a result.
+//   warps 2..17 epilogue: a thread owns one row (its warp's TMEM lane
+//               quarter) and one quarter of the columns; it loads the row's
+//               accumulators, applies ReLU, rounds to BF16 and stores the
+//               packed values back into TMEM as the next layer's A - or,
+//               after the last layer, writes the two outputs.
+// The bias rides on the tensor cores: one more K = 16 product per layer
+// multiplies a constant TMEM block whose row is (1, 1, 1, 0, ...) by a block
+// holding each bias as the sum of three BF16 pieces (hi, mid, lo: 24
+// significant bits, the FP32 bias to within its last bit), so the
+// accumulator already holds x W^T + b and the epilogue does no arithmetic
+// but ReLU and rounding.
+// TMEM columns: accumulators of slot 0 / 1 at 0 / 128, activations (BF16
+// pairs) of slot 0 / 1 at 256 / 320, the constant block at 384.  Two tiles
+// are in flight, issued pairwise by layer (L1 a, L1 b, L2 a, ...), so the
+// epilogue of one tile overlaps the products of the other.  Weights (72 KB,
+// swizzled) are staged once per CTA.  The rounding points are those of
+// forward_rows: FP32 accumulation (bias included), ReLU, BF16 activations.
+// Every wait is bounded; a CTA that gives up writes NaN to the rows it still
+// owes, so a failure cannot pass for a result.
 // ---------------------------------------------------------------------------
 constexpr int kTM = 128;                  // rows per tile = MMA M
 constexpr int kXStages = 4;
-constexpr int kTcWarps = 6;
-constexpr int kTmemCols = 256;
+constexpr int kEpiWarps = 16;
+constexpr int kTcWarps = 2 + kEpiWarps;
+constexpr int kTmemCols = 512;
+constexpr unsigned kActCol = 256;         // activations of slot j at kActCol + 64 j
+constexpr unsigned kOnesCol = 384;        // the constant (1, 1, 1, 0, ...) block: K = 16
 
 struct TcSmem {                           // every operand block 1024-byte aligned
     bf16 w2[2][kH * 64];                  // [k block][n][64 k], 128B swizzle
     bf16 w3[2][kH * 64];
-    bf16 h[2][2][kTM * 64];               // activations [slot][k block][row][64 k]
     bf16 w4[2][16 * 64];                  // rows 2..15 zero (MMA N = 16)
     bf16 w1[kH * kF];                     // [n][16 k], 32B swizzle
     bf16 x[kXStages][kTM * kF];           // feature tiles, 32B swizzle
-    float b[3][kH];
-    float b4[2];
+    bf16 bias[3][kH * 16];                // [n][16 k]: hi, mid, lo, 0...; 32B swizzle
+    bf16 bias4[16 * 16];
     unsigned long long x_full[kXStages], x_empty[kXStages], acc_full[2], h_done[2], fin;
     unsigned tmem;
     int err;
@@ -441,17 +454,32 @@ __host__ __device__ constexpr unsigned idesc(int M, int N) {
            ((unsigned)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma(unsigned d, uint64_t a, uint64_t b, unsigned id, int acc) {
+// The issuing helpers are executed by a whole converged warp with uniform
+// operands; elect.sync picks the one lane that issues.
+
+// D (+)= A B^T with A and B in shared memory
+__device__ __forceinline__ void umma_ss(unsigned d, uint64_t a, uint64_t b, unsigned id, int acc) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(id), "r"(acc)
         : "memory");
 }
 
+// D (+)= A B^T with A in tensor memory (row m in lane m, BF16 pairs per column)
+__device__ __forceinline__ void umma_ts(unsigned d, unsigned a, uint64_t b, unsigned id, int acc) {
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+// arrive on `bar` once every product issued so far by this warp has completed
 __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
             smem_u32(bar))
         : "memory");
 }
@@ -473,26 +501,19 @@ __device__ __forceinline__ void expect_tx(unsigned long long *bar, unsigned byte
                  : "memory");
 }
 
-// 64 consecutive FP32 accumulator columns of this thread's TMEM lane; the
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane; the
 // wait is in the same statement, so the registers are valid on return
-__device__ __forceinline__ void tmem_ld64(unsigned addr, uint32_t (&r)[64]) {
+__device__ __forceinline__ void tmem_ld32(unsigned addr, uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,"
-        "%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,"
-        "%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
           "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
-          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
-          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
-          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+          "=r"(r[31])
         : "r"(addr)
         : "memory");
 }
@@ -506,36 +527,23 @@ __device__ __forceinline__ void tmem_ld2(unsigned addr, uint32_t (&r)[2]) {
         : "memory");
 }
 
+// 16 consecutive columns of this thread's TMEM lane; returns once written
+__device__ __forceinline__ void tmem_st16(unsigned addr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};\n"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(addr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15])
+        : "memory");
+}
+
 // BF16x2 of (max(lo, 0), max(hi, 0)), round to nearest even; lo in the low half
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
-}
-
-// accumulator columns [c0, c0 + 64) of one row + bias, ReLU, BF16 -> the
-// row's 8 chunks of k block c0 / 64 of the next layer's A operand
-__device__ __forceinline__ void epi64(const uint32_t (&r)[64], const float *bias, char *hblk,
-                                      int row) {
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const float4 b0 = *reinterpret_cast<const float4 *>(bias + 8 * c);
-        const float4 b1 = *reinterpret_cast<const float4 *>(bias + 8 * c + 4);
-        const float2 s0 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c]), __uint_as_float(r[8 * c + 1])),
-                                     make_float2(b0.x, b0.y));
-        const float2 s1 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 2]), __uint_as_float(r[8 * c + 3])),
-                                     make_float2(b0.z, b0.w));
-        const float2 s2 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 4]), __uint_as_float(r[8 * c + 5])),
-                                     make_float2(b1.x, b1.y));
-        const float2 s3 = __fadd2_rn(make_float2(__uint_as_float(r[8 * c + 6]), __uint_as_float(r[8 * c + 7])),
-                                     make_float2(b1.z, b1.w));
-        uint4 v;
-        v.x = relu_bf16x2(s0.x, s0.y);
-        v.y = relu_bf16x2(s1.x, s1.y);
-        v.z = relu_bf16x2(s2.x, s2.y);
-        v.w = relu_bf16x2(s3.x, s3.y);
-        *reinterpret_cast<uint4 *>(hblk + sw128(row, c)) = v;
-    }
 }
 
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
@@ -566,12 +574,22 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
         *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.w4[kb]) + sw128(n, c)) =
             n < 2 ? wg[oW4 / 8 + i] : make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int i = tid; i < kH; i += blockDim.x) {
-        S.b[0][i] = pf[ob1 + i];
-        S.b[1][i] = pf[ob2 + i];
-        S.b[2][i] = pf[ob3 + i];
+    for (int i = tid; i < 4 * kH; i += blockDim.x) {   // bias rows: 3 x 128, then 16 (2 real)
+        const int l = i / kH, n = i % kH;
+        if (l == 3 && n >= 16) continue;
+        const float b = l < 3 ? pf[(l == 0 ? ob1 : l == 1 ? ob2 : ob3) + n]
+                              : (n < 2 ? pf[ob4 + n] : 0.0f);
+        const bf16 hi = __float2bfloat16_rn(b);
+        const float r1 = b - __bfloat162float(hi);             // exact
+        const bf16 mid = __float2bfloat16_rn(r1);
+        const bf16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+        __align__(16) bf16 row[8] = {hi, mid, lo, __float2bfloat16_rn(0.0f),
+                                     __float2bfloat16_rn(0.0f), __float2bfloat16_rn(0.0f),
+                                     __float2bfloat16_rn(0.0f), __float2bfloat16_rn(0.0f)};
+        char *blk = reinterpret_cast<char *>(l < 3 ? S.bias[l] : S.bias4);
+        *reinterpret_cast<uint4 *>(blk + sw32(n, 0)) = *reinterpret_cast<const uint4 *>(row);
+        *reinterpret_cast<uint4 *>(blk + sw32(n, 1)) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (tid < 2) S.b4[tid] = pf[ob4 + tid];
     if (tid == 0) {
         for (int i = 0; i < kXStages; i++) {
             mbar_init(&S.x_full[i], 1);
@@ -579,7 +597,7 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
         }
         for (int i = 0; i < 2; i++) {
             mbar_init(&S.acc_full[i], 1);
-            mbar_init(&S.h_done[i], 4);
+            mbar_init(&S.h_done[i], kEpiWarps);
         }
         mbar_init(&S.fin, 1);
         S.err = 0;
@@ -598,6 +616,18 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
     tc_fence_after();
     const unsigned tmem = S.tmem;
     volatile int *err = &S.err;
+    if (warp >= 2 && warp < 6) {          // the constant block, one row per thread
+        const uint32_t one2 = 0x3F803F80u, one1 = 0x00003F80u;   // BF16 pairs (1, 1), (1, 0)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+            "tcgen05.wait::st.sync.aligned;" ::"r"(tmem + ((unsigned)(32 * (warp & 3)) << 16) +
+                                                   kOnesCol),
+            "r"(one2), "r"(one1), "r"(0u), "r"(0u), "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+            : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         if (lane == 0) {                  // producer
@@ -616,61 +646,68 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                 if (uses[st] > 0 && !mbar_wait(&S.x_full[st], (uses[st] - 1) & 1)) *err = 1;
         }
     } else if (warp == 1) {
-        if (lane == 0) {                  // MMA issuer
-            int hd[2] = {0, 0};
-            const unsigned w1 = smem_u32(S.w1), w4 = smem_u32(S.w4[0]);
-            for (int p = 0; p < nt && !*err; p += 2) {
-                const int q = nt - p < 2 ? nt - p : 2;
-                for (int l = 0; l < 4 && !*err; l++) {
-                    for (int j = 0; j < q; j++) {
-                        const int k = p + j;
-                        const unsigned d = tmem + (unsigned)(j * 128);
-                        if (l == 0) {
-                            const int st = k % kXStages;
-                            if (!mbar_wait(&S.x_full[st], (k / kXStages) & 1) ||
-                                (k >= 2 && !mbar_wait(&S.h_done[j], hd[j]++ & 1))) {
-                                *err = 1;
-                                break;
-                            }
-                            tc_fence_after();
-                            umma(d, sdesc(smem_u32(S.x[st]), 256, kSw32), sdesc(w1, 256, kSw32),
-                                 idesc(kTM, kH), 0);
-                            umma_commit(&S.acc_full[j]);
-                            umma_commit(&S.x_empty[st]);
-                        } else {
-                            if (!mbar_wait(&S.h_done[j], hd[j]++ & 1)) {
-                                *err = 1;
-                                break;
-                            }
-                            tc_fence_after();
-                            const unsigned a0 = smem_u32(S.h[j][0]);
-                            const unsigned b0 = l == 1 ? smem_u32(S.w2[0])
-                                                : l == 2 ? smem_u32(S.w3[0]) : w4;
-                            const unsigned bblk = l == 3 ? 16 * 128 : kH * 128;
-                            const unsigned id = l == 3 ? idesc(kTM, 16) : idesc(kTM, kH);
+        // MMA issuer.  The whole warp runs the loop, so descriptors and
+        // addresses are warp-uniform; one elected lane issues each product.
+        // Operand descriptors are built once and advanced by adding to their
+        // address field (16-byte units).
+        const uint64_t dx = sdesc(smem_u32(S.x[0]), 256, kSw32);
+        const uint64_t dw1 = sdesc(smem_u32(S.w1), 256, kSw32);
+        const uint64_t dw2 = sdesc(smem_u32(S.w2[0]), 1024, kSw128);
+        const uint64_t dw3 = sdesc(smem_u32(S.w3[0]), 1024, kSw128);
+        const uint64_t dw4 = sdesc(smem_u32(S.w4[0]), 1024, kSw128);
+        const uint64_t db[4] = {sdesc(smem_u32(S.bias[0]), 256, kSw32),
+                                sdesc(smem_u32(S.bias[1]), 256, kSw32),
+                                sdesc(smem_u32(S.bias[2]), 256, kSw32),
+                                sdesc(smem_u32(S.bias4), 256, kSw32)};
+        int hd[2] = {0, 0};
+        bool ok = true;
+        for (int p = 0; p < nt && ok; p += 2) {
+            const int q = nt - p < 2 ? nt - p : 2;
+            for (int l = 0; l < 4 && ok; l++) {
+                for (int j = 0; j < q; j++) {
+                    const int k = p + j;
+                    const unsigned d = tmem + (unsigned)(j * 128);
+                    if (l == 0) {
+                        const int st = k % kXStages;
+                        ok = !*err && mbar_wait(&S.x_full[st], (k / kXStages) & 1) &&
+                             (k < 2 || mbar_wait(&S.h_done[j], hd[j]++ & 1));
+                        if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                        tc_fence_after();
+                        umma_ss(d, dx + (uint64_t)(st * (kTM * kF * 2 / 16)), dw1, idesc(kTM, kH), 0);
+                        umma_ts(d, tmem + kOnesCol, db[0], idesc(kTM, kH), 1);
+                        umma_commit(&S.acc_full[j]);
+                        umma_commit(&S.x_empty[st]);
+                    } else {
+                        ok = !*err && mbar_wait(&S.h_done[j], hd[j]++ & 1);
+                        if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                        tc_fence_after();
+                        const unsigned a0 = tmem + kActCol + (unsigned)(j * 64);
+                        const uint64_t b0 = l == 1 ? dw2 : l == 2 ? dw3 : dw4;
+                        const uint64_t bblk = l == 3 ? (16 * 128) / 16 : (kH * 128) / 16;
+                        const unsigned id = l == 3 ? idesc(kTM, 16) : idesc(kTM, kH);
 #pragma unroll
-                            for (int kk = 0; kk < 8; kk++) {
-                                const unsigned off = (unsigned)(kk & 3) * 32;
-                                umma(d, sdesc(a0 + (kk >> 2) * (kTM * 128) + off, 1024, kSw128),
-                                     sdesc(b0 + (kk >> 2) * bblk + off, 1024, kSw128), id, kk > 0);
-                            }
-                            umma_commit(&S.acc_full[j]);
-                        }
+                        for (int kk = 0; kk < 8; kk++)        // K = 16: 8 TMEM columns of A
+                            umma_ts(d, a0 + (unsigned)(kk * 8),
+                                    b0 + (uint64_t)(kk >> 2) * bblk + (uint64_t)((kk & 3) * 2), id,
+                                    kk > 0);
+                        umma_ts(d, tmem + kOnesCol, db[l], id, 1);
+                        umma_commit(&S.acc_full[j]);
                     }
                 }
             }
-            umma_commit(&S.fin);          // every product issued has completed
-            if (!mbar_wait(&S.fin, 0)) *err = 1;
         }
-    } else {                              // epilogue: one row per thread
-        const int qd = warp & 3, row = 32 * qd + lane;
+        if (!ok && lane == 0) *err = 1;
+        umma_commit(&S.fin);              // every product issued has completed
+        if (!__all_sync(0xffffffffu, mbar_wait(&S.fin, 0)) && lane == 0) *err = 1;
+    } else {                              // epilogue: one row, one column quarter per thread
+        const int qd = warp & 3, cq = (warp - 2) >> 2, row = 32 * qd + lane;
         const unsigned lanes = (unsigned)(32 * qd) << 16;
         int af[2] = {0, 0};
-        int p = 0, l = 0, j = 0;
+        int p = 0;
         for (p = 0; p < nt; p += 2) {
             const int q = nt - p < 2 ? nt - p : 2;
-            for (l = 0; l < 4; l++) {
-                for (j = 0; j < q; j++) {
+            for (int l = 0; l < 4; l++) {
+                for (int j = 0; j < q; j++) {
                     const bool ok = !*err && mbar_wait(&S.acc_full[j], af[j]++ & 1);
                     if (!__all_sync(0xffffffffu, ok)) {    // warp-uniform: the loads are .aligned
                         *err = 1;
@@ -679,20 +716,20 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                     tc_fence_after();
                     const unsigned t = tmem + lanes + (unsigned)(j * 128);
                     if (l < 3) {
-                        uint32_t r[64];
-                        tmem_ld64(t, r);
-                        epi64(r, S.b[l], reinterpret_cast<char *>(S.h[j][0]), row);
-                        tmem_ld64(t + 64, r);
-                        epi64(r, S.b[l] + 64, reinterpret_cast<char *>(S.h[j][1]), row);
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    } else {
+                        uint32_t r[32], w[16];
+                        tmem_ld32(t + (unsigned)(cq * 32), r);
+#pragma unroll
+                        for (int c = 0; c < 16; c++)
+                            w[c] = relu_bf16x2(__uint_as_float(r[2 * c]),
+                                               __uint_as_float(r[2 * c + 1]));
+                        tmem_st16(tmem + lanes + kActCol + (unsigned)(j * 64 + cq * 16), w);
+                    } else if (cq == 0) {
                         uint32_t r[2];
                         tmem_ld2(t, r);
                         const int64_t g = tile_of(p + j) * kTM + row;
                         if (g < R)
                             *reinterpret_cast<float2 *>(out + 2 * g) =
-                                make_float2(__uint_as_float(r[0]) + S.b4[0],
-                                            __uint_as_float(r[1]) + S.b4[1]);
+                                make_float2(__uint_as_float(r[0]), __uint_as_float(r[1]));
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -701,7 +738,7 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
             }
         }
     fail:
-        if (p < nt) {                     // gave up: NaN for every row still owed
+        if (p < nt && cq == 0) {          // gave up: NaN for every row still owed
             const float nan = __int_as_float(0x7fc00000);
             for (int k = p; k < nt; k++) {
                 const int64_t g = tile_of(k) * kTM + row;
