@@ -24,6 +24,7 @@ constexpr int kMaxSeeds = 64;
 constexpr int kGroup = 4;          // seeds evaluated per pass over the rings
 constexpr int kMaxHalvings = 10;
 constexpr int kSums = 9;           // L, n11, n12, n22, a11, a12, a22, g1, g2
+constexpr int kCache = 8;          // rings per thread kept in registers across passes
 
 // ---------------------------------------------------------------------------
 // double-float arithmetic (pairs hi + lo of FP32 values)
@@ -202,6 +203,24 @@ __device__ __forceinline__ void ring_terms(float a0, float a1, float a2, float e
     acc[8] = fmaf(wj2, r, acc[8]);
 }
 
+// Ring i as the per-pass terms use it: unit axis, eta, 1 / deta.
+__device__ __forceinline__ void load_ring(const float *__restrict__ ax,
+                                          const float *__restrict__ ay,
+                                          const float *__restrict__ az,
+                                          const float *__restrict__ eta,
+                                          const float *__restrict__ deta, int64_t i, float &a0,
+                                          float &a1, float &a2, float &et, float &inv_de) {
+    a0 = ax[i];
+    a1 = ay[i];
+    a2 = az[i];
+    const float inv = rsqrt_approx(fmaf(a0, a0, fmaf(a1, a1, a2 * a2)));
+    a0 *= inv;
+    a1 *= inv;
+    a2 *= inv;
+    et = eta[i];
+    inv_de = __frcp_rn(deta[i]);
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
          const float *__restrict__ az, const float *__restrict__ eta,
@@ -233,6 +252,23 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     }
     __syncthreads();
 
+    // The first kCache rings of this thread (unit axis, eta, 1/deta) stay in
+    // registers for every pass; rings beyond them are re-read per pass.  The
+    // order in which a thread visits its rings is the same either way.
+    const int64_t stride = (int64_t)G * kThreads;
+    const int64_t i0 = blockIdx.x * (int64_t)kThreads + tid;
+    float ca0[kCache], ca1[kCache], ca2[kCache], cet[kCache], cid[kCache];
+    unsigned cok = 0;
+#pragma unroll
+    for (int j = 0; j < kCache; j++) {
+        const int64_t i = i0 + j * stride;
+        ca0[j] = ca1[j] = ca2[j] = cet[j] = cid[j] = 0.0f;
+        if (i < R && (valid == nullptr || valid[i])) {
+            load_ring(ax, ay, az, eta, deta, i, ca0[j], ca1[j], ca2[j], cet[j], cid[j]);
+            cok |= 1u << j;
+        }
+    }
+
     for (int pass = 0;; pass++) {
         if (tid < k) {
             for (int c = 0; c < 3; c++) {
@@ -262,15 +298,19 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
 #pragma unroll
                 for (int q = 0; q < kSums; q++) acc[g][q] = 0.0f;
             }
-            for (int64_t i = blockIdx.x * (int64_t)kThreads + tid; i < R;
-                 i += (int64_t)G * kThreads) {
+#pragma unroll
+            for (int j = 0; j < kCache; j++) {
+                if (!(cok & (1u << j))) continue;
+#pragma unroll
+                for (int g = 0; g < kGroup; g++)
+                    if (act[g])
+                        ring_terms(ca0[j], ca1[j], ca2[j], cet[j], cid[j], cf[g0 + g], k_cut,
+                                   L[g], acc[g]);
+            }
+            for (int64_t i = i0 + kCache * stride; i < R; i += stride) {
                 if (valid != nullptr && !valid[i]) continue;
-                float a0 = ax[i], a1 = ay[i], a2 = az[i];
-                float inv = rsqrt_approx(fmaf(a0, a0, fmaf(a1, a1, a2 * a2)));
-                a0 *= inv;
-                a1 *= inv;
-                a2 *= inv;
-                const float et = eta[i], inv_de = __frcp_rn(deta[i]);
+                float a0, a1, a2, et, inv_de;
+                load_ring(ax, ay, az, eta, deta, i, a0, a1, a2, et, inv_de);
 #pragma unroll
                 for (int g = 0; g < kGroup; g++)
                     if (act[g])
@@ -307,9 +347,11 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             const int T = kThreads / nu;                // threads per sum
             const int u = tid % nu, v = tid / nu;
             float2 a = make_float2(0.0f, 0.0f);
-            if (v < T && S[(u0 + u) / kSums].phase != 2)
+            if (v < T && S[(u0 + u) / kSums].phase != 2) {
+#pragma unroll 4
                 for (unsigned b = v; b < G; b += T)
                     a = df_add(a, __ldcg(slot + (size_t)b * P + u0 + u));
+            }
             part[tid] = a;
             __syncthreads();
             if (tid < nu) {
