@@ -9,8 +9,8 @@
 // on GB300 runs at 1/64 of the FP32 rate.  One bounded grid barrier per pass;
 // then every CTA reduces all CTA partials in the same fixed order and runs the
 // same update (accept / halve / solve / stop), so every CTA holds identical
-// state without a second barrier.  FP64 is used only for the 2x2 solve, the
-// step on the sphere and its normalisation.  No host round trip per
+// state without a second barrier.  FP64 is used only for the accepted point
+// and the candidate (the step is added and renormalised in FP64).  No host round trip per
 // iteration; the step and stopping rules are those of the C header.
 #include <float.h>
 
@@ -43,6 +43,17 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     return make_float2(h, e - (h - s.x));
 }
 
+__device__ __forceinline__ bool df_ge(float2 a, float2 b) {   // a >= b, both normalised
+    return a.x > b.x || (a.x == b.x && a.y >= b.y);
+}
+
+__device__ __forceinline__ float2 df_from_double(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+__device__ __forceinline__ double df_to_double(float2 v) { return (double)v.x + (double)v.y; }
+
 __device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
                        __shfl_xor_sync(0xffffffffu, v.y, o));
@@ -52,17 +63,18 @@ __device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
 // seed state (identical in every CTA)
 // ---------------------------------------------------------------------------
 struct SeedState {
-    double s[3], e1[3], e2[3];     // accepted point and tangent basis
-    double c[3], ce1[3], ce2[3];   // candidate under evaluation
-    double cur[kSums];             // sums at s
-    double d1, d2;
+    float2 s[3], c[3];             // accepted point, candidate (double-float)
+    float e1[3], e2[3];            // tangent basis at s
+    float ce1[3], ce2[3];          // tangent basis at c
+    float2 cur[kSums];             // sums at s (double-float)
+    float d1, d2;                  // the step in the tangent basis of s
     int h, iter, phase, st;        // phase 0: first evaluation, 1: trial, 2: done
 };
 
 // Tangent basis at c (FP32: it only orients the step and the FP32 per-ring
 // Jacobian): e1 = unit(c x z) (c x x when |c_z| > 0.9), e2 = c x e1.
-__device__ __forceinline__ void basis(const double *c, double *e1, double *e2) {
-    float s0 = (float)c[0], s1 = (float)c[1], s2 = (float)c[2];
+__device__ __forceinline__ void basis(const float2 *c, float *e1, float *e2) {
+    float s0 = c[0].x, s1 = c[1].x, s2 = c[2].x;
     float r0 = 0.0f, r1 = 0.0f, r2 = 1.0f;
     if (fabsf(s2) > 0.9f) { r0 = 1.0f; r2 = 0.0f; }
     float a0 = s1 * r2 - s2 * r1, a1 = s2 * r0 - s0 * r2, a2 = s0 * r1 - s1 * r0;
@@ -74,7 +86,12 @@ __device__ __forceinline__ void basis(const double *c, double *e1, double *e2) {
     e2[2] = s0 * a1 - s1 * a0;
 }
 
-// Final normalisation (FP64).
+// FP64 arithmetic is slow on GB300 (1/64 of the FP32 rate; the update below
+// is one dependent chain on one thread, and every FP64 operation or
+// conversion on it costs ~100 clocks), so the update runs in FP32: the
+// accepted point and the candidate are double-float pairs (~48 bits), the
+// step t is a small tangent vector, the 2x2 solve and the slope test are
+// FP32.  FP64 appears only when a seed is read and a result written.
 __device__ __forceinline__ void unit3(double *a) {
     double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     a[0] *= inv;
@@ -82,90 +99,110 @@ __device__ __forceinline__ void unit3(double *a) {
     a[2] *= inv;
 }
 
-// Candidate s + f (d1 e1 + d2 e2), renormalised, with its tangent basis.
-__device__ void set_candidate(SeedState &S, double f) {
-    for (int c = 0; c < 3; c++) S.c[c] = S.s[c] + f * (S.d1 * S.e1[c] + S.d2 * S.e2[c]);
-    unit3(S.c);
+// Candidate (s + t) / |s + t| with t = f (d1 e1 + d2 e2), and its tangent
+// basis.  |s| = 1, so |s + t|^2 = 1 + e with e = 2 s.t + |t|^2, and
+// 1 / sqrt(1 + e) = 1 + delta, delta = -e/2 + 3 e^2 / 8 (truncation below
+// 1e-13 for |e| < 1e-4); larger steps renormalise through FP64.
+__device__ void set_candidate(SeedState &S, float f) {
+    float t[3], st = 0.0f, tt = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        t[c] = f * fmaf(S.d1, S.e1[c], S.d2 * S.e2[c]);
+        st = fmaf(S.s[c].x, t[c], st);
+        tt = fmaf(t[c], t[c], tt);
+        S.c[c] = df_add(S.s[c], make_float2(t[c], 0.0f));
+    }
+    const float e = fmaf(2.0f, st, tt);
+    if (fabsf(e) < 1e-4f) {
+        const float delta = e * fmaf(0.375f, e, -0.5f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) S.c[c] = df_add(S.c[c], make_float2(S.c[c].x * delta, 0.0f));
+    } else {
+        double v[3] = {df_to_double(S.c[0]), df_to_double(S.c[1]), df_to_double(S.c[2])};
+        unit3(v);
+#pragma unroll
+        for (int c = 0; c < 3; c++) S.c[c] = df_from_double(v[c]);
+    }
     basis(S.c, S.ce1, S.ce2);
 }
 
 // Normal equations at the accepted point -> next candidate or stop.  The
 // Gauss-Newton matrix N = sum w (1 - r^2) J J^T is used when positive
 // definite, else the IRLS matrix A = sum w J J^T.
-__device__ void next_step(SeedState &S, int max_iter, double tol) {
+__device__ void next_step(SeedState &S, int max_iter, float tol2) {
     if (S.iter >= max_iter) { S.phase = 2; S.st = CC_ENOCONV; return; }
-    double a11 = S.cur[1], a12 = S.cur[2], a22 = S.cur[3], g1 = S.cur[7], g2 = S.cur[8];
-    double det = a11 * a22 - a12 * a12;
-    if (!(a11 > 0.0) || !(det > 0.0) || !isfinite(det)) {
-        a11 = S.cur[4];
-        a12 = S.cur[5];
-        a22 = S.cur[6];
+    float a11 = S.cur[1].x, a12 = S.cur[2].x, a22 = S.cur[3].x;
+    const float g1 = S.cur[7].x, g2 = S.cur[8].x;
+    float det = a11 * a22 - a12 * a12;
+    if (!(a11 > 0.0f) || !(det > 0.0f) || !isfinite(det)) {
+        a11 = S.cur[4].x;
+        a12 = S.cur[5].x;
+        a22 = S.cur[6].x;
         det = a11 * a22 - a12 * a12;
     }
-    if (!(det > 0.0) || !isfinite(det)) { S.phase = 2; S.st = CC_ENOCONV; return; }
-    double idet = 1.0 / det;
-    double d1 = (-g1 * a22 + g2 * a12) * idet;
-    double d2 = (-g2 * a11 + g1 * a12) * idet;
+    if (!(det > 0.0f) || !isfinite(det)) { S.phase = 2; S.st = CC_ENOCONV; return; }
+    const float idet = 1.0f / det;
+    const float d1 = (-g1 * a22 + g2 * a12) * idet;
+    const float d2 = (-g2 * a11 + g1 * a12) * idet;
     if (!isfinite(d1) || !isfinite(d2)) { S.phase = 2; S.st = CC_ENOCONV; return; }
     S.iter++;
-    if (d1 * d1 + d2 * d2 < tol * tol) { S.phase = 2; S.st = CC_OK; return; }
+    if (d1 * d1 + d2 * d2 < tol2) { S.phase = 2; S.st = CC_OK; return; }
     S.d1 = d1;
     S.d2 = d2;
     S.h = 0;
     S.phase = 1;
-    set_candidate(S, 1.0);
+    set_candidate(S, 1.0f);
 }
 
 // Consume the sums evaluated at the candidate.
-__device__ void update(SeedState &S, const double *sums, int max_iter, double tol) {
+__device__ void update(SeedState &S, const float2 *sums, int max_iter, float tol2) {
     if (S.phase == 0) {
+#pragma unroll
         for (int c = 0; c < 3; c++) { S.s[c] = S.c[c]; S.e1[c] = S.ce1[c]; S.e2[c] = S.ce2[c]; }
+#pragma unroll
         for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
-        next_step(S, max_iter, tol);
+        next_step(S, max_iter, tol2);
     } else if (S.phase == 1) {
         // acceptable: L not lower, or the slope of L along the step is still
         // >= 0 at the trial (before the maximum on the step's great circle)
-        double slope = 0.0;
+        float slope = 0.0f;
+        const float s7 = sums[7].x, s8 = sums[8].x;
+#pragma unroll
         for (int c = 0; c < 3; c++) {
-            double Dc = S.d1 * S.e1[c] + S.d2 * S.e2[c];
-            slope -= Dc * (sums[7] * S.ce1[c] + sums[8] * S.ce2[c]);
+            const float Dc = fmaf(S.d1, S.e1[c], S.d2 * S.e2[c]);
+            slope -= Dc * fmaf(s7, S.ce1[c], s8 * S.ce2[c]);
         }
-        if (sums[0] >= S.cur[0] || slope >= 0.0) {
+        if (df_ge(sums[0], S.cur[0]) || slope >= 0.0f) {
+#pragma unroll
             for (int c = 0; c < 3; c++) { S.s[c] = S.c[c]; S.e1[c] = S.ce1[c]; S.e2[c] = S.ce2[c]; }
+#pragma unroll
             for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
-            next_step(S, max_iter, tol);
+            next_step(S, max_iter, tol2);
         } else if (++S.h > kMaxHalvings) {
             S.phase = 2;                 // no acceptable trial: stationary
             S.st = CC_OK;
         } else {
-            set_candidate(S, ldexp(1.0, -S.h));
+            set_candidate(S, ldexpf(1.0f, -S.h));
         }
     }
 }
 
-// Bounded grid barrier (all CTAs co-resident: cooperative launch).
-__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks) {
+// Bounded grid barrier (all CTAs co-resident: cooperative launch) on one
+// counter that only grows: pass n ends when it reaches (n + 1) G.
+__device__ bool grid_sync(unsigned *count, unsigned target) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned *vgen = gen;
-        unsigned g = *vgen;
         __threadfence();
-        unsigned arrived = atomicAdd(count, 1u) + 1u;
-        if (arrived == nblocks) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            unsigned long long t0 = globaltimer_ns();
-            unsigned it = 0;
-            while (*vgen == g) {
-                __nanosleep(32);
-                if ((++it & 255) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
-                    ok = 0;
-                    break;
-                }
+        atomicAdd(count, 1u);
+        const volatile unsigned *vc = count;
+        unsigned long long t0 = 0;
+        for (unsigned it = 0; *vc < target; ++it) {
+            if ((it & 255) == 255) {
+                const unsigned long long now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > kWaitLimitNs) { ok = 0; break; }
             }
         }
         __threadfence();
@@ -176,19 +213,22 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks) {
 
 // One ring's FP32 terms at a candidate point C = (s, e1, e2): the weight w
 // (into the double-float L) and the normal-equation terms.  The angle comes
-// from the chord as in the sweep; sin(theta) = sqrt(h (2 - h)).
+// from the chord as in the sweep; sin(theta) = sqrt(h (2 - h)).  Branch-free
+// (a ring outside the angular selection, or keep = 0, adds exact zeros; a
+// ring with sin(theta) < 1e-6 adds its weight only), so the rings of a thread
+// overlap in the pipeline.
 __device__ __forceinline__ void ring_terms(float a0, float a1, float a2, float eta, float inv_de,
-                                           const float *C, float kcut, float2 &L, float *acc) {
+                                           const float *C, float kcut, bool keep, float2 &L,
+                                           float *acc) {
     float dx = a0 - C[0], dy = a1 - C[1], dz = a2 - C[2];
     float h = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // 1 - cos(theta)
     float th = angle_from_half_chord2(h);
     float r = (th - eta) * inv_de;
-    if (kcut > 0.0f && fabsf(r) > kcut) return;
-    float w = ex2_approx(-0.72134752f * r * r);              // exp(-r^2 / 2)
+    keep = keep && !(kcut > 0.0f && fabsf(r) > kcut);
+    float w = keep ? ex2_approx(-0.72134752f * r * r) : 0.0f;   // exp(-r^2 / 2)
     L = df_add(L, make_float2(w, 0.0f));
     float st2 = h * (2.0f - h);                              // sin^2(theta)
-    if (st2 < 1e-12f) return;                                // sin(theta) < 1e-6
-    float f = -inv_de * rsqrt_approx(st2);                   // -1 / (sin(theta) deta)
+    float f = st2 < 1e-12f ? 0.0f : -inv_de * rsqrt_approx(st2);   // -1 / (sin(theta) deta)
     float j1 = f * fmaf(a0, C[3], fmaf(a1, C[4], a2 * C[5]));
     float j2 = f * fmaf(a0, C[6], fmaf(a1, C[7], a2 * C[8]));
     float wj1 = w * j1, wj2 = w * j2;
@@ -231,24 +271,25 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     __shared__ SeedState S[kMaxSeeds];
     __shared__ float cf[kMaxSeeds][9];                  // FP32 candidate + basis
     __shared__ float2 red[kThreads / 32][kGroup * kSums];
-    __shared__ float2 part[kThreads];
-    __shared__ double sums[kMaxSeeds * kSums];
+    __shared__ float2 sums[kMaxSeeds * kSums];
     __shared__ int active_any;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned G = gridDim.x;
     const int P = k * kSums;                            // partial sums per CTA
+    const float tol2 = (float)(tol * tol);
     if (tid < k) {
         SeedState &T = S[tid];
-        for (int c = 0; c < 3; c++) T.c[c] = seeds[3 * tid + c];
-        unit3(T.c);
+        double v[3] = {seeds[3 * tid], seeds[3 * tid + 1], seeds[3 * tid + 2]};
+        unit3(v);
+        for (int c = 0; c < 3; c++) T.c[c] = df_from_double(v[c]);
         basis(T.c, T.ce1, T.ce2);
         T.phase = 0;
         T.iter = 0;
         T.h = 0;
         T.st = CC_ENOCONV;
-        T.d1 = T.d2 = 0.0;
-        for (int q = 0; q < kSums; q++) T.cur[q] = 0.0;
+        T.d1 = T.d2 = 0.0f;
+        for (int q = 0; q < kSums; q++) T.cur[q] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
 
@@ -272,9 +313,9 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     for (int pass = 0;; pass++) {
         if (tid < k) {
             for (int c = 0; c < 3; c++) {
-                cf[tid][c] = (float)S[tid].c[c];
-                cf[tid][3 + c] = (float)S[tid].ce1[c];
-                cf[tid][6 + c] = (float)S[tid].ce2[c];
+                cf[tid][c] = S[tid].c[c].x;
+                cf[tid][3 + c] = S[tid].ce1[c];
+                cf[tid][6 + c] = S[tid].ce2[c];
             }
         }
         __syncthreads();
@@ -299,13 +340,12 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
                 for (int q = 0; q < kSums; q++) acc[g][q] = 0.0f;
             }
 #pragma unroll
-            for (int j = 0; j < kCache; j++) {
-                if (!(cok & (1u << j))) continue;
+            for (int g = 0; g < kGroup; g++) {
+                if (!act[g]) continue;              // uniform across the CTA
 #pragma unroll
-                for (int g = 0; g < kGroup; g++)
-                    if (act[g])
-                        ring_terms(ca0[j], ca1[j], ca2[j], cet[j], cid[j], cf[g0 + g], k_cut,
-                                   L[g], acc[g]);
+                for (int j = 0; j < kCache; j++)
+                    ring_terms(ca0[j], ca1[j], ca2[j], cet[j], cid[j], cf[g0 + g], k_cut,
+                               (cok >> j) & 1u, L[g], acc[g]);
             }
             for (int64_t i = i0 + kCache * stride; i < R; i += stride) {
                 if (valid != nullptr && !valid[i]) continue;
@@ -314,19 +354,22 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
 #pragma unroll
                 for (int g = 0; g < kGroup; g++)
                     if (act[g])
-                        ring_terms(a0, a1, a2, et, inv_de, cf[g0 + g], k_cut, L[g], acc[g]);
+                        ring_terms(a0, a1, a2, et, inv_de, cf[g0 + g], k_cut, true, L[g], acc[g]);
             }
             // warp and CTA sums in double-float
 #pragma unroll
             for (int g = 0; g < kGroup; g++) {
                 if (!act[g]) continue;
+                float2 v[kSums];                        // the 9 trees advance level by level
 #pragma unroll
-                for (int q = 0; q < kSums; q++) {
-                    float2 v = q == 0 ? L[g] : make_float2(acc[g][q], 0.0f);
+                for (int q = 0; q < kSums; q++) v[q] = q == 0 ? L[g] : make_float2(acc[g][q], 0.0f);
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-                    if (lane == 0) red[wid][g * kSums + q] = v;
-                }
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int q = 0; q < kSums; q++) v[q] = df_add(v[q], df_shfl_xor(v[q], o));
+                if (lane == 0)
+#pragma unroll
+                    for (int q = 0; q < kSums; q++) red[wid][g * kSums + q] = v[q];
             }
             __syncthreads();
             if (tid < kGroup * kSums && g0 + tid / kSums < k) {
@@ -337,31 +380,27 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             }
             __syncthreads();
         }
-        if (!grid_sync(bar, bar + 1, G)) {
+        if (!grid_sync(bar, (unsigned)(pass + 1) * G)) {
             if (tid == 0) atomicExch(status, (int32_t)CC_ETIMEOUT);
             return;
         }
-        // every CTA reduces all CTA partials, all threads, in one fixed order
-        for (int u0 = 0; u0 < P; u0 += kThreads) {
-            const int nu = (P - u0) < kThreads ? (P - u0) : kThreads;
-            const int T = kThreads / nu;                // threads per sum
-            const int u = tid % nu, v = tid / nu;
+        // every CTA reduces all CTA partials in one fixed order: 16 lanes (a
+        // half warp) per sum, each adding the CTAs b = v, v + 16, ... in turn,
+        // then a fixed shuffle tree over the 16
+        for (int u0 = 0; u0 < P; u0 += kThreads / 16) {
+            const int u = u0 + (tid >> 4), v = tid & 15;
             float2 a = make_float2(0.0f, 0.0f);
-            if (v < T && S[(u0 + u) / kSums].phase != 2) {
+            if (u < P && S[u / kSums].phase != 2) {
 #pragma unroll 4
-                for (unsigned b = v; b < G; b += T)
-                    a = df_add(a, __ldcg(slot + (size_t)b * P + u0 + u));
+                for (unsigned b = v; b < G; b += 16)
+                    a = df_add(a, __ldcg(slot + (size_t)b * P + u));
             }
-            part[tid] = a;
-            __syncthreads();
-            if (tid < nu) {
-                float2 t = make_float2(0.0f, 0.0f);
-                for (int vv = 0; vv < T; vv++) t = df_add(t, part[vv * nu + tid]);
-                sums[u0 + tid] = (double)t.x + (double)t.y;
-            }
-            __syncthreads();
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
+            if (v == 0 && u < P) sums[u] = a;
         }
-        if (tid < k && S[tid].phase != 2) update(S[tid], sums + tid * kSums, max_iter, tol);
+        __syncthreads();
+        if (tid < k && S[tid].phase != 2) update(S[tid], sums + tid * kSums, max_iter, tol2);
         if (tid == 0) active_any = 0;
         __syncthreads();
         if (tid < k && S[tid].phase != 2) active_any = 1;
@@ -372,13 +411,14 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     if (blockIdx.x == 0 && tid == 0) {
         int best = 0;
         for (int t = 1; t < k; t++)
-            if (S[t].cur[0] > S[best].cur[0]) best = t;
-        double d[3] = {S[best].s[0], S[best].s[1], S[best].s[2]};
+            if (!df_ge(S[best].cur[0], S[t].cur[0])) best = t;
+        double d[3] = {df_to_double(S[best].s[0]), df_to_double(S[best].s[1]),
+                       df_to_double(S[best].s[2])};
         unit3(d);
         out_dir[0] = d[0];
         out_dir[1] = d[1];
         out_dir[2] = d[2];
-        *out_obj = S[best].cur[0];
+        *out_obj = df_to_double(S[best].cur[0]);
         *out_iters = S[best].iter;
         *status = S[best].st;
     }
@@ -410,7 +450,7 @@ cudaError_t launch_refine(const cc_rings &rings, const double *seeds, int k,
                           int32_t *out_iters, int32_t *status, char *ws, size_t ws_bytes,
                           cudaStream_t s) {
     (void)ws_bytes;
-    cudaError_t e = cudaMemsetAsync(ws, 0, 256, s);   // barrier counter + generation
+    cudaError_t e = cudaMemsetAsync(ws, 0, 256, s);   // barrier counter
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
