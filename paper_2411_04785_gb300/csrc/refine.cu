@@ -391,7 +391,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             const int u = u0 + (tid >> 4), v = tid & 15;
             float2 a = make_float2(0.0f, 0.0f);
             if (u < P && S[u / kSums].phase != 2) {
-#pragma unroll 4
+#pragma unroll 8
                 for (unsigned b = v; b < G; b += 16)
                     a = df_add(a, __ldcg(slot + (size_t)b * P + u));
             }
