@@ -193,8 +193,8 @@ cc_status cc_localize_static(const cc_rings *rings, const cc_grid *grid,
 
 /*
  * Several bursts in one call (continuous batching of a serving loop): the
- * sweep of all of them runs in one persistent launch whose CTAs take work
- * units of every burst from a shared counter; each burst keeps its own plan,
+ * sweep of all of them runs in one launch, one CTA per work unit, the units
+ * of every burst taken from a shared counter; each burst keeps its own plan,
  * rings, map and outputs, and its results do not depend on the other bursts
  * of the batch (the same burst gives the same map alone or in any batch).
  * rings [n] is a host array of ring structs; maps, argmax, seeds (may be

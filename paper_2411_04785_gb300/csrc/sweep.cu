@@ -408,9 +408,10 @@ k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int6
                         out, bb ? bb + blockIdx.x : nullptr, status);
 }
 
-// Several bursts in one persistent launch: CTAs take work units of all the
-// bursts from a shared counter until none is left.  A unit is computed
-// exactly as in k_sweep, so each burst's map does not depend on the others.
+// Several bursts in one launch: CTAs take work units of all the bursts from
+// a shared counter until none is left (launched with one CTA per unit, so
+// most CTAs take one).  A unit is computed exactly as in k_sweep, so each
+// burst's map does not depend on the others.
 struct BurstDesc {
     const RingRec *rec;
     const int64_t *nkept;
@@ -723,12 +724,12 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
                                          : reinterpret_cast<int32_t *>(ws[b] + pl.off_status);
         a.unit_begin[b + 1] = a.unit_begin[b] + pl.ndb * pl.nsplit;
     }
-    int occ = 0;
+    // one CTA per work unit (a CTA still takes its unit from the counter): CTAs
+    // retire as their units finish, so kernels of higher-priority streams
+    // (the bursts' front ends) get SMs without waiting for the whole batch
     void *fn = kcut ? (void *)k_sweep_multi<kBatchD, true> : (void *)k_sweep_multi<kBatchD, false>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, 0);
-    if (occ < 1) occ = 1;
-    int64_t ctas = (int64_t)device_sm_count() * occ;
-    if (ctas > a.unit_begin[n]) ctas = a.unit_begin[n];
+    int64_t ctas = a.unit_begin[n];
+    if (ctas > (int64_t)INT32_MAX) ctas = INT32_MAX;
     if (ctas < 1) ctas = 1;
     void *args[] = {(void *)&a};
     {

@@ -154,7 +154,10 @@ class Server:
         self.filter = ring_filter
         self.tau = tau
         self.filter_deta_max = filter_deta_max or self.params.deta_max
-        self.sweep_streams = [torch.cuda.Stream(self.dev) for _ in range(2)]
+        # bursts' own streams (front end, refinement, read-back) outrank the
+        # sweep streams, so a burst's short kernels take SMs as soon as sweep
+        # CTAs retire instead of queueing behind a whole batch
+        self.sweep_streams = [torch.cuda.Stream(self.dev, priority=0) for _ in range(2)]
         self._ss = 0
         self._gs = api._grid_struct(grid)
         self.graphs = graphs
@@ -183,7 +186,7 @@ class Server:
         return torch.cuda.Event(enable_timing=self.breakdown)
 
     def _admit(self, b: Burst, now: float) -> _Active:
-        s = torch.cuda.Stream(self.dev)
+        s = torch.cuda.Stream(self.dev, priority=-1)
         a = _Active(b, s, burst_bytes(b.count, self.M, self.params, self.filter is not None), now)
         if self.breakdown:
             a.ev0 = self._event()
