@@ -223,14 +223,14 @@ size_t cc_refine_workspace_bytes(int64_t rings, int32_t k);
  * each of the k seeds (seed_dirs, device, k x 3 doubles, row major): weights
  * w_i = exp(-r_i^2/2), J_i = -[a_i.e1, a_i.e2] / (sin theta_i deta_i), step d
  * from N d = -sum w r J with N = sum w (1 - r^2) J J^T (the Gauss-Newton
- * Hessian of L) when positive definite, else sum w J J^T; the
+ * Hessian of L) when positive definite, else sum w J J^T, solved in FP64; the
  * step is tried at full, half, ..., 1/1024 length and the first acceptable
  * trial is taken (L not lower, or the slope of L along the step still >= 0
  * there); stop when |d| < tol_rad or no trial is acceptable (converged), or
  * after max_iter iterations or on singular normal equations (CC_ENOCONV in
  * status).  Per-ring terms are FP32; the sums, the accepted point and the
- * candidate double-float (FP32 pairs, ~48 bits); the 2x2 solve and the step
- * FP32; the result is normalised in FP64.  Of the refined seeds the
+ * candidate double-float (FP32 pairs, ~48 bits); the 2x2 solve FP64, the
+ * step FP32; the result is normalised in FP64.  Of the refined seeds the
  * one with the largest L wins (ties: lower
  * seed index): out_dir [3] double (unit), out_obj [1] double (its L),
  * out_iters [1] int32, status [1] int32 (device pointers).  1 <= k <= 64.

@@ -9,8 +9,8 @@
 // on GB300 runs at 1/64 of the FP32 rate.  One bounded grid barrier per pass;
 // then every CTA reduces all CTA partials in the same fixed order and runs the
 // same update (accept / halve / solve / stop), so every CTA holds identical
-// state without a second barrier.  FP64 is used only for the accepted point
-// and the candidate (the step is added and renormalised in FP64).  No host round trip per
+// state without a second barrier.  FP64 is used only in the 2x2 normal-
+// equation solve and the final normalisation of the result.  No host round trip per
 // iteration; the step and stopping rules are those of the C header.
 #include <float.h>
 
@@ -88,10 +88,11 @@ __device__ __forceinline__ void basis(const float2 *c, float *e1, float *e2) {
 
 // FP64 arithmetic is slow on GB300 (1/64 of the FP32 rate; the update below
 // is one dependent chain on one thread, and every FP64 operation or
-// conversion on it costs ~100 clocks), so the update runs in FP32: the
-// accepted point and the candidate are double-float pairs (~48 bits), the
-// step t is a small tangent vector, the 2x2 solve and the slope test are
-// FP32.  FP64 appears only when a seed is read and a result written.
+// conversion on it costs ~100 clocks), so FP64 is kept to the places that
+// need it - the 2x2 normal-equation solve and the final normalisation of the
+// result - and the rest of the update runs in FP32: the accepted point and
+// the candidate are double-float pairs (~48 bits), the step t a small FP32
+// tangent vector, the slope test FP32.
 __device__ __forceinline__ void unit3(double *a) {
     double inv = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     a[0] *= inv;
@@ -99,69 +100,80 @@ __device__ __forceinline__ void unit3(double *a) {
     a[2] *= inv;
 }
 
-// Candidate (s + t) / |s + t| with t = f (d1 e1 + d2 e2), and its tangent
-// basis.  |s| = 1, so |s + t|^2 = 1 + e with e = 2 s.t + |t|^2, and
-// 1 / sqrt(1 + e) = 1 + delta, delta = -e/2 + 3 e^2 / 8 (truncation below
-// 1e-13 for |e| < 1e-4); larger steps renormalise through FP64.
-__device__ void set_candidate(SeedState &S, float f) {
-    float t[3], st = 0.0f, tt = 0.0f;
+// x^2 as a double-float pair (FMA gives the product's rounding error exactly)
+__device__ __forceinline__ float2 df_sq(float2 x) {
+    const float p = x.x * x.x;
+    const float e = fmaf(x.x, x.x, -p);
+    return two_sum(p, fmaf(2.0f * x.x, x.y, e));
+}
+
+// c / |c| for a double-float vector near the unit sphere: |c|^2 = 1 + e is
+// summed in double-float, so the norm never drifts; 1 / sqrt(1 + e) =
+// 1 + delta with delta = -e/2 + 3 e^2 / 8 (truncation below 1e-13) for
+// |e| < 1e-4, else the FP32 reciprocal square root with one Newton step (the
+// norm is then within ~1e-7 of 1 and the next renormalisation corrects it).
+__device__ __forceinline__ void df_unit3(float2 *c) {
+    float2 n2 = make_float2(-1.0f, 0.0f);
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-        t[c] = f * fmaf(S.d1, S.e1[c], S.d2 * S.e2[c]);
-        st = fmaf(S.s[c].x, t[c], st);
-        tt = fmaf(t[c], t[c], tt);
-        S.c[c] = df_add(S.s[c], make_float2(t[c], 0.0f));
-    }
-    const float e = fmaf(2.0f, st, tt);
+    for (int k = 0; k < 3; k++) n2 = df_add(n2, df_sq(c[k]));
+    const float e = n2.x;                                   // |c|^2 - 1
+    float delta;
     if (fabsf(e) < 1e-4f) {
-        const float delta = e * fmaf(0.375f, e, -0.5f);
-#pragma unroll
-        for (int c = 0; c < 3; c++) S.c[c] = df_add(S.c[c], make_float2(S.c[c].x * delta, 0.0f));
+        delta = e * fmaf(0.375f, e, -0.5f);
     } else {
-        double v[3] = {df_to_double(S.c[0]), df_to_double(S.c[1]), df_to_double(S.c[2])};
-        unit3(v);
-#pragma unroll
-        for (int c = 0; c < 3; c++) S.c[c] = df_from_double(v[c]);
+        const float x = 1.0f + e, y = rsqrt_approx(x);
+        delta = y * fmaf(-0.5f * x * y, y, 1.5f) - 1.0f;
     }
+#pragma unroll
+    for (int k = 0; k < 3; k++) c[k] = df_add(c[k], make_float2(c[k].x * delta, 0.0f));
+}
+
+// Candidate (s + t) / |s + t| with t = f (d1 e1 + d2 e2), and its tangent basis.
+__device__ void set_candidate(SeedState &S, float f) {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        S.c[c] = df_add(S.s[c], make_float2(f * fmaf(S.d1, S.e1[c], S.d2 * S.e2[c]), 0.0f));
+    df_unit3(S.c);
     basis(S.c, S.ce1, S.ce2);
 }
 
-// Normal equations at the accepted point -> next candidate or stop.  The
-// Gauss-Newton matrix N = sum w (1 - r^2) J J^T is used when positive
-// definite, else the IRLS matrix A = sum w J J^T.
-__device__ void next_step(SeedState &S, int max_iter, float tol2) {
+// Normal equations at the accepted point -> next candidate or stop, solved in
+// FP64.  The Gauss-Newton matrix N = sum w (1 - r^2) J J^T is used when
+// positive definite, else the IRLS matrix A = sum w J J^T.
+__device__ void next_step(SeedState &S, int max_iter, double tol) {
     if (S.iter >= max_iter) { S.phase = 2; S.st = CC_ENOCONV; return; }
-    float a11 = S.cur[1].x, a12 = S.cur[2].x, a22 = S.cur[3].x;
-    const float g1 = S.cur[7].x, g2 = S.cur[8].x;
-    float det = a11 * a22 - a12 * a12;
-    if (!(a11 > 0.0f) || !(det > 0.0f) || !isfinite(det)) {
-        a11 = S.cur[4].x;
-        a12 = S.cur[5].x;
-        a22 = S.cur[6].x;
+    double a11 = df_to_double(S.cur[1]), a12 = df_to_double(S.cur[2]),
+           a22 = df_to_double(S.cur[3]);
+    const double g1 = df_to_double(S.cur[7]), g2 = df_to_double(S.cur[8]);
+    double det = a11 * a22 - a12 * a12;
+    if (!(a11 > 0.0) || !(det > 0.0) || !isfinite(det)) {
+        a11 = df_to_double(S.cur[4]);
+        a12 = df_to_double(S.cur[5]);
+        a22 = df_to_double(S.cur[6]);
         det = a11 * a22 - a12 * a12;
     }
-    if (!(det > 0.0f) || !isfinite(det)) { S.phase = 2; S.st = CC_ENOCONV; return; }
-    const float idet = 1.0f / det;
-    const float d1 = (-g1 * a22 + g2 * a12) * idet;
-    const float d2 = (-g2 * a11 + g1 * a12) * idet;
+    if (!(det > 0.0) || !isfinite(det)) { S.phase = 2; S.st = CC_ENOCONV; return; }
+    const double idet = 1.0 / det;
+    const double d1 = (-g1 * a22 + g2 * a12) * idet;
+    const double d2 = (-g2 * a11 + g1 * a12) * idet;
     if (!isfinite(d1) || !isfinite(d2)) { S.phase = 2; S.st = CC_ENOCONV; return; }
     S.iter++;
-    if (d1 * d1 + d2 * d2 < tol2) { S.phase = 2; S.st = CC_OK; return; }
-    S.d1 = d1;
-    S.d2 = d2;
+    if (d1 * d1 + d2 * d2 < tol * tol) { S.phase = 2; S.st = CC_OK; return; }
+    S.d1 = (float)d1;
+    S.d2 = (float)d2;
     S.h = 0;
     S.phase = 1;
     set_candidate(S, 1.0f);
 }
 
 // Consume the sums evaluated at the candidate.
-__device__ void update(SeedState &S, const float2 *sums, int max_iter, float tol2) {
+__device__ void update(SeedState &S, const float2 *sums, int max_iter, double tol) {
     if (S.phase == 0) {
 #pragma unroll
         for (int c = 0; c < 3; c++) { S.s[c] = S.c[c]; S.e1[c] = S.ce1[c]; S.e2[c] = S.ce2[c]; }
 #pragma unroll
         for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
-        next_step(S, max_iter, tol2);
+        next_step(S, max_iter, tol);
     } else if (S.phase == 1) {
         // acceptable: L not lower, or the slope of L along the step is still
         // >= 0 at the trial (before the maximum on the step's great circle)
@@ -177,7 +189,7 @@ __device__ void update(SeedState &S, const float2 *sums, int max_iter, float tol
             for (int c = 0; c < 3; c++) { S.s[c] = S.c[c]; S.e1[c] = S.ce1[c]; S.e2[c] = S.ce2[c]; }
 #pragma unroll
             for (int q = 0; q < kSums; q++) S.cur[q] = sums[q];
-            next_step(S, max_iter, tol2);
+            next_step(S, max_iter, tol);
         } else if (++S.h > kMaxHalvings) {
             S.phase = 2;                 // no acceptable trial: stationary
             S.st = CC_OK;
@@ -277,12 +289,10 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned G = gridDim.x;
     const int P = k * kSums;                            // partial sums per CTA
-    const float tol2 = (float)(tol * tol);
     if (tid < k) {
         SeedState &T = S[tid];
-        double v[3] = {seeds[3 * tid], seeds[3 * tid + 1], seeds[3 * tid + 2]};
-        unit3(v);
-        for (int c = 0; c < 3; c++) T.c[c] = df_from_double(v[c]);
+        for (int c = 0; c < 3; c++) T.c[c] = df_from_double(seeds[3 * tid + c]);
+        df_unit3(T.c);
         basis(T.c, T.ce1, T.ce2);
         T.phase = 0;
         T.iter = 0;
@@ -391,7 +401,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             const int u = u0 + (tid >> 4), v = tid & 15;
             float2 a = make_float2(0.0f, 0.0f);
             if (u < P && S[u / kSums].phase != 2) {
-#pragma unroll 8
+#pragma unroll 4
                 for (unsigned b = v; b < G; b += 16)
                     a = df_add(a, __ldcg(slot + (size_t)b * P + u));
             }
@@ -400,7 +410,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
             if (v == 0 && u < P) sums[u] = a;
         }
         __syncthreads();
-        if (tid < k && S[tid].phase != 2) update(S[tid], sums + tid * kSums, max_iter, tol2);
+        if (tid < k && S[tid].phase != 2) update(S[tid], sums + tid * kSums, max_iter, tol);
         if (tid == 0) active_any = 0;
         __syncthreads();
         if (tid < k && S[tid].phase != 2) active_any = 1;
