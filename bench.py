@@ -884,13 +884,12 @@ def run_filter(args):
     f = cc.RingFilter(dev, seed=0)
     F = cc.ring_features(tn, tx, ty, tz, te, rings, p)
     out = torch.empty((N, 2), dtype=torch.float32, device=dev)
-    ws = torch.empty(cc.api.mlp_workspace_bytes(N), dtype=torch.uint8, device=dev)
     work = {k: v.clone() for k, v in rings.items()}
     stream = torch.cuda.current_stream()
 
     def step():
         cc.ring_features(tn, tx, ty, tz, te, rings, p, out=F)
-        f.forward(F, out=out, workspace=ws)
+        f.forward(F, out=out)
         f.apply(work, out, 0.0, p.deta_min, p.deta_max)
 
     side = torch.cuda.Stream(device=dev)
@@ -906,7 +905,7 @@ def run_filter(args):
     n_fwd = 20
     with torch.cuda.graph(g_fwd):
         for _ in range(n_fwd):
-            f.forward(F, out=out, workspace=ws)
+            f.forward(F, out=out)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         g_step.replay()

@@ -291,13 +291,14 @@ cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k,
 cc_status cc_ring_features(const cc_events *ev, const cc_rings *rings,
                            const cc_params *p, uint16_t *features, void *stream);
 
-/* Workspace bytes of cc_mlp_forward / cc_mlp_grad for `rows` rows. */
+/* Workspace bytes of cc_mlp_grad for `rows` rows. */
 size_t cc_mlp_workspace_bytes(int64_t rows);
 
 /* out [rows][2] = MLP(features); any number of rows.  features [rows][16]
  * BF16 and params_bf16 16-byte aligned, out 8-byte aligned (else
  * CC_EINVAL).  Runs on the tcgen05 tensor cores (FP32 accumulation, BF16
- * activations); a row whose computation could not finish reads NaN. */
+ * activations); a row whose computation could not finish reads NaN.  The
+ * workspace is not used (may be NULL). */
 cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
                          const uint16_t *features, int64_t rows, float *out,
                          void *workspace, size_t ws_bytes, void *stream);

@@ -524,18 +524,16 @@ class RingFilter:
         return self._ws
 
     def forward(self, feats, out=None, stream=None, workspace=None):
-        """MLP outputs [R, 2].  Calls that may run concurrently (other streams)
-        must each pass their own workspace (mlp_workspace_bytes)."""
+        """MLP outputs [R, 2] (the forward needs no workspace; the argument is
+        accepted and ignored)."""
         _need(feats, torch.bfloat16, "feats")
         if feats.dim() != 2 or feats.shape[1] != MLP_FEATURES:
             raise ValueError(f"feats must be [R, {MLP_FEATURES}]")
         R = feats.shape[0]
         out = out if out is not None else torch.empty((R, 2), dtype=torch.float32,
                                                       device=self.dev)
-        ws = workspace if workspace is not None else self._workspace(R)
         _check("cc_mlp_forward", lib().cc_mlp_forward(
-            _ptr(self.p), _ptr(self.wb), _ptr(feats), R, _ptr(out), _ptr(ws), ws.numel(),
-            _stream(stream)))
+            _ptr(self.p), _ptr(self.wb), _ptr(feats), R, _ptr(out), None, 0, _stream(stream)))
         return out
 
     def grad(self, feats, is_source, residual, weight, stream=None):

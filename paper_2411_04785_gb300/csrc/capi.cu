@@ -308,11 +308,9 @@ cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
         return fail(CC_EINVAL, "params/features/out must be non-NULL");
     if (!aligned(features, 16) || !aligned(params_bf16, 16) || !aligned(out, 8))
         return fail(CC_EINVAL, "features and params_bf16 must be 16-byte aligned, out 8-byte");
-    if (!workspace || !aligned(workspace, 256))
-        return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
-    size_t need = mlp_workspace_bytes(rows);
-    if (ws_bytes < need) return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
-    cudaError_t e = mlp_forward(params, params_bf16, features, rows, out, (char *)workspace,
+    (void)workspace;                       // the forward keeps its activations on chip
+    (void)ws_bytes;
+    cudaError_t e = mlp_forward(params, params_bf16, features, rows, out, nullptr,
                                 (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_forward launch");
     return CC_OK;

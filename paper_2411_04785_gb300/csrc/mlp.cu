@@ -3,14 +3,16 @@
 // of a predicted ring width, its loss and gradients, Adam, and the filter that
 // applies it to rings before the sweep.
 //
-// All matrix products run on the tensor cores through one BF16 GEMM kernel
-// (mma.sync m16n8k16, FP32 accumulation, operands staged through shared memory
-// and loaded with ldmatrix).  Strided operand addressing lets the same kernel
-// do the three products of training: activations x W^T (forward), dP x W
-// (backward through a layer) and dP^T x A (weight gradient, reduced over the
-// batch in fixed-order split-K partials, so results are deterministic).
-// Weights, layer inputs and backward signals are BF16; biases, accumulators,
-// losses, gradients and the Adam state are FP32.
+// Inference (k_mlp_forward_tc, below) runs the whole network in one
+// persistent kernel on the tcgen05 tensor cores.  Training runs its matrix
+// products through one BF16 GEMM kernel on the warp-level tensor-core path
+// (mma.sync m16n8k16, FP32 accumulation, operands staged through shared
+// memory and loaded with ldmatrix): strided operand addressing lets the same
+// kernel do the three products of training, activations x W^T (forward),
+// dP x W (backward through a layer) and dP^T x A (weight gradient, reduced
+// over the batch in fixed-order split-K partials, so results are
+// deterministic).  Weights, layer inputs and backward signals are BF16;
+// biases, accumulators, losses, gradients and the Adam state are FP32.
 #include <cuda_bf16.h>
 
 #include "cc_math.cuh"

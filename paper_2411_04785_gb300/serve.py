@@ -103,7 +103,6 @@ class _Front:
         if learned:
             self.feats = torch.empty((cap, api.MLP_FEATURES), dtype=torch.bfloat16, device=dev)
             self.mlp_out = torch.empty((cap, 2), dtype=torch.float32, device=dev)
-            self.mws = torch.empty(api.mlp_workspace_bytes(cap), dtype=torch.uint8, device=dev)
         s = torch.cuda.Stream(dev)
         s.wait_stream(torch.cuda.current_stream(dev))
         x, y, z, e = (self.xyze[k] for k in "xyze")
@@ -113,7 +112,7 @@ class _Front:
             if learned:
                 api.ring_features(self.n, x, y, z, e, self.rings, srv.params, out=self.feats,
                                   stream=s)
-                srv.filter.forward(self.feats, out=self.mlp_out, stream=s, workspace=self.mws)
+                srv.filter.forward(self.feats, out=self.mlp_out, stream=s)
                 srv.filter.apply(self.rings, self.mlp_out, srv.tau, srv.params.deta_min,
                                  srv.filter_deta_max, stream=s)
 
@@ -135,7 +134,7 @@ def burst_bytes(N: int, M: int, params: api.Params, learned: bool) -> int:
     b += api.lib().cc_localize_batch_workspace_bytes(N, M, C.byref(params.c()))
     b += api.refine_workspace_bytes(N, params.topk) + M * 4 + 1024
     if learned:
-        b += N * (api.MLP_FEATURES * 2 + 8) + api.lib().cc_mlp_workspace_bytes(N)
+        b += N * (api.MLP_FEATURES * 2 + 8)                      # features + outputs
     return int(b)
 
 
@@ -209,9 +208,7 @@ class Server:
             if self.filter is not None:
                 F = api.ring_features(d["n"], d["x"], d["y"], d["z"], d["e"], d["rings"],
                                       self.params, stream=s)
-                mws = torch.empty(api.mlp_workspace_bytes(b.count), dtype=torch.uint8,
-                                  device=self.dev)
-                out = self.filter.forward(F, stream=s, workspace=mws)
+                out = self.filter.forward(F, stream=s)
                 self.filter.apply(d["rings"], out, self.tau, self.params.deta_min,
                                   self.filter_deta_max, stream=s)
             ws_b = api.lib().cc_localize_batch_workspace_bytes(b.count, self.M,
