@@ -454,6 +454,19 @@ cc_status cc_backproject(const cc_rings *rings, const float *px, const float *py
 cc_status cc_selftest_exact_ops(uint64_t *mismatches, void *stream);
 
 /*
+ * Self-check of failure detection (no counterpart in the paper): runs one of
+ * the library's bounded device waits against a signal that never comes and
+ * writes the outcome to status (device int32 [1]): CC_ETIMEOUT once limit_ns
+ * has passed.  which = 0: an mbarrier phase (the wait of the TMA and
+ * tensor-core pipelines); which = 1: a global counter (the refinement's grid
+ * barrier).  counter: device uint32 [1] of scratch.  limit_ns in
+ * [1000, 10^10] (the library's own waits give up after 2 s).  The context
+ * stays usable.  Asynchronous on `stream`; CC_EINVAL on bad arguments.
+ */
+cc_status cc_selftest_wait_timeout(int32_t which, int64_t limit_ns, uint32_t *counter,
+                                   int32_t *status, void *stream);
+
+/*
  * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
  * counted per stage; when tracing is enabled each launch is also bracketed by
  * two CUDA events recorded on the launching stream, and cc_trace_read()

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import struct
 import os
 from dataclasses import dataclass
 
@@ -149,6 +150,8 @@ def lib() -> C.CDLL:
         L.cc_events_copy.restype = S
         L.cc_selftest_exact_ops.argtypes = [_P, _P]
         L.cc_selftest_exact_ops.restype = S
+        L.cc_selftest_wait_timeout.argtypes = [C.c_int32, C.c_int64, _P, _P, _P]
+        L.cc_selftest_wait_timeout.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -490,6 +493,38 @@ def ring_features(n, x, y, z, e, rings: dict, params: Params | None = None, out=
     return out
 
 
+# Checkpoint of the ring filter: a flat little-endian file, a 32-byte header
+# (magic, format version, parameter count, Adam step) followed by the FP32
+# parameters and the two FP32 Adam moments.
+_CKPT_MAGIC = b"CCFILTR\0"
+_CKPT_VERSION = 1
+
+
+def pack_filter_state(params, m, v, step: int) -> bytes:
+    """Bytes of a ring-filter checkpoint (host numpy float32 arrays)."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype="<f4") for a in (params, m, v)]
+    n = arrs[0].size
+    if any(a.size != n for a in arrs):
+        raise ValueError("params and moments differ in length")
+    head = _CKPT_MAGIC + struct.pack("<IIq", _CKPT_VERSION, n, int(step)) + bytes(8)
+    return head + b"".join(a.tobytes() for a in arrs)
+
+
+def unpack_filter_state(buf: bytes):
+    """(params, m, v, step) from checkpoint bytes; ValueError on a bad file."""
+    import numpy as np
+    if len(buf) < 32 or buf[:8] != _CKPT_MAGIC:
+        raise ValueError("not a ring-filter checkpoint")
+    version, n, step = struct.unpack("<IIq", buf[8:24])
+    if version != _CKPT_VERSION:
+        raise ValueError(f"checkpoint format version {version}, expected {_CKPT_VERSION}")
+    if len(buf) != 32 + 12 * n:
+        raise ValueError(f"checkpoint of {len(buf)} bytes, expected {32 + 12 * n}")
+    body = np.frombuffer(buf, dtype="<f4", offset=32)
+    return body[:n].copy(), body[n:2 * n].copy(), body[2 * n:].copy(), int(step)
+
+
 class RingFilter:
     """The MLP of the learned ring filter with its FP32 parameters, BF16 copy
     and Adam state on the device; every product runs in libcompton.so."""
@@ -516,6 +551,26 @@ class RingFilter:
         self._ws = None
         _check("cc_mlp_params_to_bf16", lib().cc_mlp_params_to_bf16(
             _ptr(self.p), _ptr(self.wb), _stream(None)))
+
+    def save(self, path) -> None:
+        """Write parameters and Adam state (see pack_filter_state)."""
+        buf = pack_filter_state(self.p.cpu().numpy(), self.m.cpu().numpy(),
+                                self.v.cpu().numpy(), self.step)
+        with open(path, "wb") as fh:
+            fh.write(buf)
+
+    @classmethod
+    def load(cls, path, device):
+        """A filter restored from save(): same outputs, training resumes."""
+        with open(path, "rb") as fh:
+            p, m, v, step = unpack_filter_state(fh.read())
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"checkpoint has {p.size} parameters, the network {MLP_PARAMS}")
+        f = cls(device, params=p)
+        f.m.copy_(torch.from_numpy(m))
+        f.v.copy_(torch.from_numpy(v))
+        f.step = step
+        return f
 
     def _workspace(self, rows):
         need = max(int(lib().cc_mlp_workspace_bytes(rows)), 256)
@@ -712,6 +767,16 @@ def backproject(rings: dict, apex, voxels, params: Params | None = None, workspa
         _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(workspace), workspace.numel(),
         _stream(stream)))
     return out
+
+
+def selftest_wait_timeout(which: int, limit_ns: int, device="cuda", stream=None):
+    """Run a bounded device wait against a signal that never comes; returns
+    the device status tensor [1] (CC_ETIMEOUT once limit_ns has passed)."""
+    counter = torch.empty(1, dtype=torch.int32, device=device)
+    status = torch.full((1,), 99, dtype=torch.int32, device=device)
+    _check("cc_selftest_wait_timeout", lib().cc_selftest_wait_timeout(
+        int(which), int(limit_ns), _ptr(counter), _ptr(status), _stream(stream)))
+    return status
 
 
 def selftest_exact_ops(device="cuda", stream=None):

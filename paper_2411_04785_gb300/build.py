@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcompton.so")
 SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu", "cluster.cu", "voxel.cu",
-           "noalloc.cu", "mlp.cu"]
+           "noalloc.cu", "mlp.cu", "selftest.cu"]
 HEADERS = ["cc_internal.cuh", "cc_math.cuh", os.path.join("..", "..", "include", "compton.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

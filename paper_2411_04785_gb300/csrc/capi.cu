@@ -418,6 +418,18 @@ cc_status cc_selftest_exact_ops(uint64_t *mismatches, void *stream) {
     return CC_OK;
 }
 
+cc_status cc_selftest_wait_timeout(int32_t which, int64_t limit_ns, uint32_t *counter,
+                                   int32_t *status, void *stream) {
+    g_err[0] = 0;
+    if (which != 0 && which != 1) return fail(CC_EINVAL, "which must be 0 or 1");
+    if (limit_ns < 1000 || limit_ns > 10000000000LL)
+        return fail(CC_EINVAL, "limit_ns must be in [1000, 1e10]");
+    if (!counter || !status) return fail(CC_EINVAL, "counter and status must be non-NULL");
+    cudaError_t e = launch_selftest_wait(which, limit_ns, counter, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest launch");
+    return CC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // near-field back projection (Sec. 3)
 // ---------------------------------------------------------------------------

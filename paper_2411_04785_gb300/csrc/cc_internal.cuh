@@ -135,6 +135,8 @@ cudaError_t mlp_apply_filter(const float *out, const cc_rings &r, float tau, flo
                              float dmax, cudaStream_t s);
 
 cudaError_t launch_selftest_exact(uint64_t *bad, cudaStream_t s);   // recon.cu
+cudaError_t launch_selftest_wait(int which, int64_t limit_ns, uint32_t *counter, int32_t *status,
+                                 cudaStream_t s);                    // selftest.cu
 
 // ---------------------------------------------------------------------------
 // event clustering of detections - cluster.cu

@@ -73,8 +73,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Bounded wait for an mbarrier phase: false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Bounded wait for an mbarrier phase: false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     unsigned b = smem_u32(bar);
     unsigned long long t0 = 0;
     for (unsigned it = 0; it < (1u << 30); ++it) {
@@ -89,10 +90,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
         if ((it & 31) == 0) {
             unsigned long long now = globaltimer_ns();
             if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitLimitNs) return false;
+            else if (now - t0 > limit_ns) return false;
         }
     }
     return false;
+}
+
+// Bounded spin until a counter in global memory reaches target (another CTA
+// raises it): false after limit_ns.  One thread calls it; acquire ordering is
+// the caller's (a fence after it returns).
+__device__ __forceinline__ bool spin_until_ge(const unsigned *count, unsigned target,
+                                              unsigned long long limit_ns = kWaitLimitNs) {
+    const volatile unsigned *vc = count;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0; *vc < target; ++it) {
+        if ((it & 255) == 255) {
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
+    }
+    return true;
 }
 
 __device__ __forceinline__ void better(float &v, int &j, float v2, int j2) {

@@ -15,6 +15,7 @@
 #include <float.h>
 
 #include "cc_math.cuh"
+#include "cc_pipe.cuh"
 
 namespace cc {
 namespace {
@@ -208,15 +209,7 @@ __device__ bool grid_sync(unsigned *count, unsigned target) {
         ok = 1;
         __threadfence();
         atomicAdd(count, 1u);
-        const volatile unsigned *vc = count;
-        unsigned long long t0 = 0;
-        for (unsigned it = 0; *vc < target; ++it) {
-            if ((it & 255) == 255) {
-                const unsigned long long now = globaltimer_ns();
-                if (t0 == 0) t0 = now;
-                else if (now - t0 > kWaitLimitNs) { ok = 0; break; }
-            }
-        }
+        ok = spin_until_ge(count, target);
         __threadfence();
     }
     __syncthreads();

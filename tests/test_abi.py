@@ -106,3 +106,14 @@ def test_events_copy_argument_checks_without_gpu(libpath):
     assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(4)), 0, 5, None) == -1    # past src
     assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(10)), 0, -1, None) == -1
     assert L.cc_events_copy(C.byref(ev(10)), 0, C.byref(ev(10)), 0, 0, None) == 0     # nothing
+
+
+def test_wait_selftest_argument_checks_without_gpu(libpath):
+    import paper_2411_04785_gb300 as cc
+    L = cc.lib()
+    fake = C.c_void_p(1 << 20)                     # never dereferenced: checks come first
+    assert L.cc_selftest_wait_timeout(2, 10**6, fake, fake, None) == -1
+    assert L.cc_selftest_wait_timeout(0, 999, fake, fake, None) == -1
+    assert L.cc_selftest_wait_timeout(1, 10**10 + 1, fake, fake, None) == -1
+    assert L.cc_selftest_wait_timeout(0, 10**6, None, fake, None) == -1
+    assert b"NULL" in L.cc_last_error()

@@ -165,3 +165,22 @@ def test_trained_filter_gains_over_the_plain_method(cc, dev):
     err_learned = localize_error(cc, learned, grid, ev["source"], p)
     print(f"plain {err_plain:.3f} deg, learned {err_learned:.3f} deg, losses {losses}")
     assert err_learned < err_plain
+
+
+def test_checkpoint_resumes_training(cc, dev, tmp_path):
+    p, X, y, res, w = random_case(7, 4096)
+    Xd = to_dev(X.astype(np.float32), dev).to(torch.bfloat16).contiguous()
+    yd, rd, wd = to_dev(y, dev), to_dev(res, dev), to_dev(w, dev)
+    f = cc.RingFilter(dev, params=p)
+    for _ in range(3):
+        f.grad(Xd, yd, rd, wd)
+        f.adam(lr=1e-3)
+    f.save(tmp_path / "filter.bin")
+    g = cc.RingFilter.load(tmp_path / "filter.bin", dev)
+    assert g.step == f.step
+    torch.testing.assert_close(g.forward(Xd), f.forward(Xd), rtol=0, atol=0)
+    for h in (f, g):                     # one more step from each: bit-identical
+        h.grad(Xd, yd, rd, wd)
+        h.adam(lr=1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(f.p, g.p) and torch.equal(f.m, g.m) and torch.equal(f.v, g.v)
