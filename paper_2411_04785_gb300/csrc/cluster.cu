@@ -124,7 +124,7 @@ __device__ __forceinline__ int swz(int row, int chunk) { return row * 128 + ((ch
 __device__ __forceinline__ int t_off(int e) { return swz(e >> 4, (e & 15) >> 1) + ((e & 1) << 3); }
 __device__ __forceinline__ int a_off(int e) { return swz(e >> 5, (e & 31) >> 2) + ((e & 3) << 2); }
 
-__global__ void __launch_bounds__(kCThreads)
+__global__ void __launch_bounds__(kCThreads, 4)   // 4 CTAs per SM: 64 registers
 k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap amap,
           int use_tma, const long long *__restrict__ t, const unsigned *__restrict__ adc,
           long long N, long long dt_max, unsigned char *__restrict__ edge,
@@ -251,9 +251,10 @@ k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
     __syncthreads();
 
     // ---- tile aggregate, look-back, tile prefix.  Warp 0 looks back over
-    // windows of 32 predecessors at once: it waits until each has published
-    // at least its aggregate, combines (in order) back to the nearest one
-    // that has published its inclusive prefix, and stops there.
+    // windows of 32 predecessors at once: it waits until each predecessor up
+    // to the nearest one that has published its inclusive prefix has
+    // published at least its aggregate, combines them in order, and stops
+    // there.
     if (threadIdx.x == 0) {
         Carry acc = identity();
         for (int k = 0; k < kCWarps; k++) {
@@ -276,20 +277,30 @@ k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
         unsigned long long t0 = 0;
         for (long long hi = tile - 1; hi >= 0;) {
             int st[kLook];
-            int pending = 0;
+            int pending = 0, incl = 0;
 #pragma unroll
             for (int j = 0; j < kLook; j++) {
                 const long long p = hi - kLook * lane - j;
                 st[j] = p >= 0 ? ((volatile TileState *)tiles)[p].status : 2;
                 pending |= st[j] == 0;
+                incl |= st[j] == 2;
             }
-            for (unsigned it = 0; __any_sync(0xffffffffu, pending); ++it) {
+            // only the lanes up to the nearest inclusive prefix are needed:
+            // wait for those, not for older tiles beyond it
+            auto waiting = [&]() {
+                const unsigned im = __ballot_sync(0xffffffffu, incl);
+                const int need = im ? __ffs(im) : 32;
+                return __any_sync(0xffffffffu, pending && lane < need);
+            };
+            for (unsigned it = 0; waiting(); ++it) {
                 pending = 0;
+                incl = 0;
 #pragma unroll
                 for (int j = 0; j < kLook; j++) {
                     const long long p = hi - kLook * lane - j;
                     if (st[j] == 0) st[j] = ((volatile TileState *)tiles)[p].status;
                     pending |= st[j] == 0;
+                    incl |= st[j] == 2;
                 }
                 if ((it & 63) == 0) {   // lane 0's clock for all: the exit stays warp-uniform
                     const unsigned long long now = __shfl_sync(0xffffffffu, globaltimer_ns(), 0);
