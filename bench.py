@@ -350,7 +350,9 @@ def run_burst(args):
            "gpu_launches": sum(v["launches"] for v in trace.values()),
            "clocks": clk.summary(),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                        "frac": achieved / peak, "traffic": None, "kernel": "k_sweep",
+                        "frac": achieved / peak,
+                        "traffic": ncu_traffic("sweep_burst1m_dram.md", "sweep.cu"),
+                        "kernel": "k_sweep",
                         **({"note": "effective: pairs the angular selection skipped are counted "
                                     "as evaluated, so frac can exceed 1"} if args.kcut > 0 else {})},
            "stages": {k: {"launches_per_step": v["launches"] / args.steps,
@@ -843,7 +845,9 @@ def run_voxel(args):
                       "source_point_cm": S, "l2": "working set re-read each step (no flush)"},
            "gpu_launches": sum(v["launches"] for v in trace.values()), "clocks": clk.summary(),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                        "frac": achieved / peak, "traffic": None, "kernel": "k_backproject",
+                        "frac": achieved / peak,
+                        "traffic": ncu_traffic("voxel_sphere64_ncu.md", "voxel.cu"),
+                        "kernel": "k_backproject",
                         "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x 128/26 pairs/clk/SM"},
            "universes_ms": dict(others, sphere={"voxels": V, "ms": float(np.mean(ms))}),
            "accuracy": {"argmax_voxel_cm": vj.tolist(),
