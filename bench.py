@@ -925,6 +925,36 @@ def run_filter(args):
     flop = N * 2 * (16 * 128 + 128 * 128 * 2 + 128 * 2)
     achieved = flop / (float(np.mean(fms)) / 1e3)
     peak = float(peaks_file().get("bf16_tflops") or 1900.0) * 1e12
+    # training side: gradient (forward + backward) and Adam on 8,192-row
+    # batches of the same features (labels drawn at random), batches gathered
+    # before the timed loop
+    B = 8192
+    g = torch.Generator(device="cpu").manual_seed(1)
+    ys = (torch.rand(N, generator=g) < 0.3).to(torch.uint8).to(dev)
+    rs = (torch.randn(N, generator=g) * 0.3).to(dev)
+    ws_ = torch.ones(N, dtype=torch.uint8, device=dev)
+    nb = N // B
+    batches = [(F[i * B:(i + 1) * B].contiguous(), ys[i * B:(i + 1) * B].contiguous(),
+                rs[i * B:(i + 1) * B].contiguous(), ws_[i * B:(i + 1) * B].contiguous())
+               for i in range(nb)]
+    tf = cc.RingFilter(dev, seed=0)
+    it = [0]
+
+    def train_step():
+        b = batches[it[0] % nb]
+        it[0] += 1
+        tf.grad(*b)
+        tf.adam(1e-3)
+
+    for _ in range(args.warmup):
+        train_step()
+    tms = timed_loop(train_step, max(10, args.steps // 2), stream)
+    train_flop = 3 * B * 2 * (16 * 128 + 128 * 128 * 2 + 128 * 2)    # forward + 2 backward products
+    out_j_train = {"rows_per_s": B / (float(np.mean(tms)) / 1e3),
+                   "ms_per_step": float(np.mean(tms)), "batch": B,
+                   "tflops": train_flop / (float(np.mean(tms)) / 1e3) / 1e12,
+                   "note": "grad (forward + backward through all layers, loss, bias and weight "
+                           "gradients) + Adam per step; warp-level tensor-core GEMMs"}
     out_j = {"metric": "rings filtered/s (learned ring filter inference)",
              "value": world * N * args.steps / tot_s, "unit": "rings/s", "n_gpus": world,
              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
@@ -939,7 +969,8 @@ def run_filter(args):
                           "unit": "TFLOP/s", "frac": achieved / peak,
                           "traffic": ncu_traffic("mlp_forward_500k_ncu.md", "mlp.cu"),
                           "kernel": "k_mlp_forward_tc", "ms_per_launch": float(np.mean(fms)),
-                          "flop_basis": f"{N} rows x 2 FLOP x 35,072 multiply-adds"}}
+                          "flop_basis": f"{N} rows x 2 FLOP x 35,072 multiply-adds"},
+             "training": out_j_train}
     if rank == 0:
         print(json.dumps(out_j))
     if pg is not None:
