@@ -305,7 +305,10 @@ cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
 
 /* Loss (device [1]) and its gradient (device [CC_MLP_PARAMS]) for one batch
  * of 1..CC_MLP_MAX_BATCH rows: is_source [rows] u8, residual [rows] f32 (rad),
- * weight [rows] u8 (0 excludes a row).  Deterministic (fixed-order sums). */
+ * weight [rows] u8 (0 excludes a row).  features and params_bf16 16-byte
+ * aligned.  The forward pass runs on the tcgen05 kernel of cc_mlp_forward,
+ * the backward pass on warp-level tensor-core GEMMs.  Deterministic
+ * (fixed-order sums). */
 cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16,
                       const uint16_t *features, const uint8_t *is_source,
                       const float *residual, const uint8_t *weight,

@@ -326,6 +326,8 @@ cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16, const ui
     if (!params || !params_bf16 || !features || !is_source || !residual || !weight || !grad ||
         !loss)
         return fail(CC_EINVAL, "arguments must be non-NULL");
+    if (!aligned(features, 16) || !aligned(params_bf16, 16))
+        return fail(CC_EINVAL, "features and params_bf16 must be 16-byte aligned");
     if (!workspace || !aligned(workspace, 256))
         return fail(CC_EINVAL, "workspace must be non-NULL and 256-byte aligned");
     size_t need = mlp_workspace_bytes(rows);

@@ -3,16 +3,17 @@
 // of a predicted ring width, its loss and gradients, Adam, and the filter that
 // applies it to rings before the sweep.
 //
-// Inference (k_mlp_forward_tc, below) runs the whole network in one
-// persistent kernel on the tcgen05 tensor cores.  Training runs its matrix
+// The forward pass (k_mlp_forward_tc, below) runs the whole network in one
+// persistent kernel on the tcgen05 tensor cores, for inference and for
+// training (which keeps the activations).  The backward pass runs its matrix
 // products through one BF16 GEMM kernel on the warp-level tensor-core path
 // (mma.sync m16n8k16, FP32 accumulation, operands staged through shared
 // memory and loaded with ldmatrix): strided operand addressing lets the same
-// kernel do the three products of training, activations x W^T (forward),
-// dP x W (backward through a layer) and dP^T x A (weight gradient, reduced
-// over the batch in fixed-order split-K partials, so results are
-// deterministic).  Weights, layer inputs and backward signals are BF16;
-// biases, accumulators, losses, gradients and the Adam state are FP32.
+// kernel do both products of the backward pass, dP x W (through a layer) and
+// dP^T x A (weight gradient, reduced over the batch in fixed-order split-K
+// partials, so results are deterministic).  Weights, layer inputs and
+// backward signals are BF16; biases, accumulators, losses, gradients and the
+// Adam state are FP32.
 #include <cuda_bf16.h>
 
 #include "cc_math.cuh"
@@ -341,7 +342,15 @@ struct Work {
     int64_t rows;
 };
 
-constexpr int kWgSplitRows = 512;                         // rows per weight-gradient split
+// Rows per weight-gradient split: about 64 splits (a 128 x 128 gradient is
+// only 4 CTA tiles, so the batch dimension supplies the parallelism), at
+// least 128 rows and a multiple of the GEMM's K step.
+constexpr int kWgSplits = 64;
+__host__ __device__ inline int64_t wg_split_rows(int64_t rows) {
+    const int64_t r = (rows + kWgSplits - 1) / kWgSplits;
+    const int64_t r32 = (r + BK - 1) / BK * BK;
+    return r32 < 128 ? 128 : r32;
+}
 
 size_t work_layout(int64_t rows, Work *w, char *base) {
     size_t off = 0;
@@ -354,31 +363,11 @@ size_t work_layout(int64_t rows, Work *w, char *base) {
     w->out = (float *)take(rows * 2 * sizeof(float));
     w->dout = (bf16 *)take(rows * 2 * sizeof(bf16));
     for (int l = 0; l < 2; l++) w->dP[l] = (bf16 *)take(rows * kH * sizeof(bf16));
-    int64_t S = (rows + kWgSplitRows - 1) / kWgSplitRows;
+    const int64_t S = (rows + wg_split_rows(rows) - 1) / wg_split_rows(rows);
     w->part = (float *)take((size_t)S * kH * kH * sizeof(float));
     w->loss_part = (float *)take(((rows + 255) / 256) * sizeof(float));
     w->rows = rows;
     return off;
-}
-
-GemmArgs layer_fwd(const bf16 *A, int in, const bf16 *W, const float *b, int out, int rows,
-                   void *C, bool relu, bool c_bf16) {
-    GemmArgs g{};
-    g.M = rows;
-    g.N = out;
-    g.K = in;
-    g.A = A;
-    g.lda_m = in;
-    g.lda_k = 1;
-    g.B = W;             // B(k = input, n = output) = W[n][k]
-    g.ldb_k = 1;
-    g.ldb_n = in;
-    g.bias = b;
-    g.relu = relu;
-    g.C = C;
-    g.ldc = out;
-    g.c_bf16 = c_bf16;
-    return g;
 }
 
 // ---------------------------------------------------------------------------
@@ -410,8 +399,9 @@ GemmArgs layer_fwd(const bf16 *A, int in, const bf16 *W, const float *b, int out
 // pairs) of slot 0 / 1 at 256 / 320, the constant block at 384.  Two tiles
 // are in flight, issued pairwise by layer (L1 a, L1 b, L2 a, ...), so the
 // epilogue of one tile overlaps the products of the other.  Weights (72 KB,
-// swizzled) are staged once per CTA.  The rounding points are those of
-// forward_rows: FP32 accumulation (bias included), ReLU, BF16 activations.
+// swizzled) are staged once per CTA.  Rounding points: FP32 accumulation
+// (bias included), ReLU, BF16 activations.  For training the same kernel
+// also writes the three hidden layers' activations out.
 // Every wait is bounded; a CTA that gives up writes NaN to the rows it still
 // owes, so a failure cannot pass for a result.
 // ---------------------------------------------------------------------------
@@ -550,7 +540,8 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
 
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
 k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restrict__ wb,
-                 const float *__restrict__ pf, int64_t R, float *__restrict__ out) {
+                 const float *__restrict__ pf, int64_t R, float *__restrict__ out,
+                 bf16 *__restrict__ h1, bf16 *__restrict__ h2, bf16 *__restrict__ h3) {
     extern __shared__ unsigned char smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -725,6 +716,14 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                             w[c] = relu_bf16x2(__uint_as_float(r[2 * c]),
                                                __uint_as_float(r[2 * c + 1]));
                         tmem_st16(tmem + lanes + kActCol + (unsigned)(j * 64 + cq * 16), w);
+                        bf16 *hl = l == 0 ? h1 : l == 1 ? h2 : h3;   // training keeps them
+                        const int64_t g = tile_of(p + j) * kTM + row;
+                        if (hl != nullptr && g < R) {
+                            uint4 *dst = reinterpret_cast<uint4 *>(hl + g * kH + cq * 32);
+#pragma unroll
+                            for (int c = 0; c < 4; c++)
+                                dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+                        }
                     } else if (cq == 0) {
                         uint32_t r[2];
                         tmem_ld2(t, r);
@@ -759,17 +758,6 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
     }
 }
 
-cudaError_t forward_rows(const bf16 *wb, const float *pf, const bf16 *X, int rows, Work &w,
-                         cudaStream_t s) {
-    cudaError_t e;
-    if ((e = gemm(layer_fwd(X, kF, wb + oW1, pf + ob1, kH, rows, w.H[0], true, true), s))) return e;
-    if ((e = gemm(layer_fwd(w.H[0], kH, wb + oW2, pf + ob2, kH, rows, w.H[1], true, true), s)))
-        return e;
-    if ((e = gemm(layer_fwd(w.H[1], kH, wb + oW3, pf + ob3, kH, rows, w.H[2], true, true), s)))
-        return e;
-    return gemm(layer_fwd(w.H[2], kH, wb + oW4, pf + ob4, 2, rows, w.out, false, false), s);
-}
-
 // dW[out, in] = dP^T A over the rows (split-K, fixed order); db = column sums of dP
 cudaError_t weight_grad(const bf16 *dP, int out, const bf16 *A, int in, int rows, float *gW,
                         float *gb, Work &w, cudaStream_t s) {
@@ -786,7 +774,7 @@ cudaError_t weight_grad(const bf16 *dP, int out, const bf16 *A, int in, int rows
     g.C = gW;
     g.ldc = in;
     g.part = w.part;
-    g.ksplit = kWgSplitRows;
+    g.ksplit = (int)wg_split_rows(rows);
     cudaError_t e = gemm(g, s);
     if (e != cudaSuccess) return e;
     k_col_sums<<<out, 256, 0, s>>>(dP, rows, out, gb);
@@ -814,10 +802,45 @@ GemmArgs back_data(const bf16 *dP, int out, const bf16 *W, int in, int rows, con
     return g;
 }
 
+// The network on the tcgen05 kernel for R rows of features; with H (the
+// three hidden layers' [R][128] BF16 outputs, for training) the activations
+// are also written out.
+cudaError_t forward_tc(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
+                       float *out, bf16 *const *H, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    TmapEncodeFn enc = encode_fn();
+    if (enc == nullptr) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int64_t sms = device_sm_count();
+    constexpr int64_t kRowsPerLaunch = (int64_t)1 << 30;   // TMA row coordinates stay int32
+    for (int64_t r0 = 0; r0 < R; r0 += kRowsPerLaunch) {
+        const int64_t n = R - r0 < kRowsPerLaunch ? R - r0 : kRowsPerLaunch;
+        CUtensorMap xmap;
+        const cuuint64_t dims[2] = {(cuuint64_t)kF, (cuuint64_t)n};
+        const cuuint64_t strides[1] = {(cuuint64_t)kF * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kF, (cuuint32_t)kTM};
+        const cuuint32_t es[2] = {1, 1};
+        if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(F + r0 * kF),
+                dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        const int64_t tiles = (n + kTM - 1) / kTM;
+        k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kTcWarps * 32, kTcSmemBytes, s>>>(
+            xmap, reinterpret_cast<const bf16 *>(wb), params, n, out + 2 * r0,
+            H ? H[0] + r0 * kH : nullptr, H ? H[1] + r0 * kH : nullptr,
+            H ? H[2] + r0 * kH : nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint8_t *y,
                       const float *res, const uint8_t *wv, int rows, float inv_total,
                       float *grad, Work &w, cudaStream_t s) {
-    cudaError_t e = forward_rows(wb, pf, X, rows, w, s);
+    cudaError_t e = forward_tc(pf, reinterpret_cast<const uint16_t *>(wb),
+                               reinterpret_cast<const uint16_t *>(X), rows, w.out, w.H, s);
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((rows + 255) / 256);
     k_loss_grad<<<nb, 256, 0, s>>>(w.out, y, res, wv, rows, inv_total, w.dout, w.loss_part);
@@ -857,32 +880,8 @@ cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, 
 cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
                         float *out, char *ws, cudaStream_t s) {
     (void)ws;                                  // activations stay on chip
-    if (R == 0) return cudaSuccess;
-    TmapEncodeFn enc = encode_fn();
-    if (enc == nullptr) return cudaErrorNotSupported;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    const int64_t sms = device_sm_count();
     TraceScope ts(CC_STAGE_MLP, s);
-    constexpr int64_t kRowsPerLaunch = (int64_t)1 << 30;   // TMA row coordinates stay int32
-    for (int64_t r0 = 0; r0 < R; r0 += kRowsPerLaunch) {
-        const int64_t n = R - r0 < kRowsPerLaunch ? R - r0 : kRowsPerLaunch;
-        CUtensorMap xmap;
-        const cuuint64_t dims[2] = {(cuuint64_t)kF, (cuuint64_t)n};
-        const cuuint64_t strides[1] = {(cuuint64_t)kF * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)kF, (cuuint32_t)kTM};
-        const cuuint32_t es[2] = {1, 1};
-        if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(F + r0 * kF),
-                dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-        const int64_t tiles = (n + kTM - 1) / kTM;
-        k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kTcWarps * 32, kTcSmemBytes, s>>>(
-            xmap, reinterpret_cast<const bf16 *>(wb), params, n, out + 2 * r0);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return forward_tc(params, wb, F, R, out, nullptr, s);
 }
 
 cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
