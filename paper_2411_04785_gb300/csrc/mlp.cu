@@ -538,6 +538,9 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     return d;
 }
 
+// kKeep: also write the three hidden activations out (training); inference
+// is compiled without those stores.
+template <bool kKeep>
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
 k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restrict__ wb,
                  const float *__restrict__ pf, int64_t R, float *__restrict__ out,
@@ -716,9 +719,9 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                             w[c] = relu_bf16x2(__uint_as_float(r[2 * c]),
                                                __uint_as_float(r[2 * c + 1]));
                         tmem_st16(tmem + lanes + kActCol + (unsigned)(j * 64 + cq * 16), w);
-                        bf16 *hl = l == 0 ? h1 : l == 1 ? h2 : h3;   // training keeps them
+                        bf16 *hl = l == 0 ? h1 : l == 1 ? h2 : h3;
                         const int64_t g = tile_of(p + j) * kTM + row;
-                        if (hl != nullptr && g < R) {
+                        if (kKeep && g < R) {
                             uint4 *dst = reinterpret_cast<uint4 *>(hl + g * kH + cq * 32);
 #pragma unroll
                             for (int c = 0; c < 4; c++)
@@ -810,7 +813,8 @@ cudaError_t forward_tc(const float *params, const uint16_t *wb, const uint16_t *
     if (R == 0) return cudaSuccess;
     TmapEncodeFn enc = encode_fn();
     if (enc == nullptr) return cudaErrorNotSupported;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kern = H ? k_mlp_forward_tc<true> : k_mlp_forward_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTcSmemBytes);
     if (e != cudaSuccess) return e;
     const int64_t sms = device_sm_count();
@@ -827,7 +831,7 @@ cudaError_t forward_tc(const float *params, const uint16_t *wb, const uint16_t *
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
         const int64_t tiles = (n + kTM - 1) / kTM;
-        k_mlp_forward_tc<<<(unsigned)(tiles < sms ? tiles : sms), kTcWarps * 32, kTcSmemBytes, s>>>(
+        kern<<<(unsigned)(tiles < sms ? tiles : sms), kTcWarps * 32, kTcSmemBytes, s>>>(
             xmap, reinterpret_cast<const bf16 *>(wb), params, n, out + 2 * r0,
             H ? H[0] + r0 * kH : nullptr, H ? H[1] + r0 * kH : nullptr,
             H ? H[2] + r0 * kH : nullptr);
