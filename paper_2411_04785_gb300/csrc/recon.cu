@@ -24,15 +24,7 @@ namespace cc {
 namespace {
 
 constexpr float kInf = __builtin_huge_valf();
-
-template <int K>
-__device__ __forceinline__ float set_energy(const float (&e)[4], unsigned mask) {
-    float s = 0.0f;
-#pragma unroll
-    for (int m = 0; m < K; m++)
-        if (mask & (1u << m)) s = __fadd_rn(s, e[m]);
-    return s;
-}
+constexpr float kPosEps2 = 1e-12f;   // |x1 - x2|^2 below (1e-6 cm)^2: no axis
 
 __device__ __forceinline__ float sqdist(const float (&x)[4], const float (&y)[4],
                                         const float (&z)[4], int p, int q) {
@@ -43,81 +35,143 @@ __device__ __forceinline__ float sqdist(const float (&x)[4], const float (&y)[4]
                      __fmul_rn(dz, dz));
 }
 
-__device__ __forceinline__ bool in_unit(float c) { return c >= -1.0f && c <= 1.0f; }
+// -1 <= c <= 1 (false for NaN)
+__device__ __forceinline__ bool in_unit(float c) { return fabsf(c) <= 1.0f; }
 
-// Per-event tables of the binary32 decision sequence, built once and shared
-// by all k! orders (indices are compile-time constants after unrolling):
-// subset energies E[S] and their reciprocals 1/E[S], squared site distances
-// and inverse lengths, and the geometric cosines cos_G(p -> q -> r) =
-// dot(x_q - x_p, x_r - x_q) * (il(p,q) * il(q,r)), bitwise symmetric in p, r.
-template <int K>
-struct OrderTables {
+template <bool kFast>
+__device__ __forceinline__ float rcp_k(float x) {
+    if constexpr (kFast) return rcp_core(x);
+    else return rcp_exact(x);
+}
+
+template <bool kFast>
+__device__ __forceinline__ float sqrt_k(float x) {
+    if constexpr (kFast) return sqrt_core(x);
+    else return sqrt_exact(x);
+}
+
+__host__ __device__ constexpr int high_slot(unsigned m) { return m >= 8u ? 3 : m >= 4u ? 2 : m >= 2u ? 1 : 0; }
+
+// Rank (in lexicographic order of the K! orders) of the best order of a
+// K-site event, K = 3 or 4, under the binary32 sequence above; -1 if no
+// order is valid.  Every quantity an order uses is a table entry built once
+// per event: subset energies E[S] (each the previous subset plus its highest
+// slot, which is the increasing-slot sum) and their reciprocals, inverse
+// lengths, geometric cosines cg(p -> q -> r) (bitwise symmetric in p, r),
+// the first step's cosine c1[o0][o1] and, for K = 4, the second step's
+// c2[o2][o3].  An order's validity conditions are folded into those entries
+// as NaN (unphysical first cone or energy cosine, a non-positive energy, a
+// coincident pair), so an invalid order's chi2 is NaN and loses every strict
+// comparison, exactly as the +inf of an invalid order does in the rule (a
+// chi2 that is NaN for a valid order, from an overflow, loses in both).
+// kFast: every deposit is in [2^-100, 2^98] and every squared distance is 0
+// or in [2^-100, 2^100].  Then every subset energy is positive and in
+// [2^-100, 2^100], every reciprocal and root argument is in the range of the
+// one-FMA corrections, and a zero distance's NaN root is never read (both of
+// its geometric cosines are NaN already).
+template <int K, bool kFast>
+__device__ __forceinline__ int order_rank(const float (&x)[4], const float (&y)[4],
+                                          const float (&z)[4], const float (&e)[4],
+                                          const float (&nsq)[4][4]) {
+    constexpr unsigned all = (1u << K) - 1u;
+    const float nan = __int_as_float(0x7fc00000);
     float E[1 << K], inv[1 << K];
-    float nsq[K][K];
-    float cg[K][K][K];
-    bool cgok[K][K][K];   // |x_q - x_p|^2 > 0 and |x_r - x_q|^2 > 0
-
-    __device__ __forceinline__ OrderTables(const float (&x)[4], const float (&y)[4],
-                                           const float (&z)[4], const float (&e)[4]) {
+    E[0] = 0.0f;
 #pragma unroll
-        for (unsigned m = 1; m < (1u << K); m++) {
-            E[m] = set_energy<K>(e, m);
-            inv[m] = rcp_exact(E[m]);
-        }
-        float il[K][K];
+    for (unsigned m = 1; m <= all; m++) {
+        const int h = high_slot(m);
+        E[m] = (kFast && m == (1u << h)) ? e[h] : __fadd_rn(E[m & ~(1u << h)], e[h]);
+        inv[m] = rcp_k<kFast>(E[m]);
+    }
+    auto pos = [&](unsigned m) { return kFast || E[m] > 0.0f; };
+    auto ccos = [&](unsigned after, unsigned before) {
+        return __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(inv[after], inv[before])));
+    };
+    float il[4][4];
+#pragma unroll
+    for (int p = 0; p < K; p++)
+#pragma unroll
+        for (int q = p + 1; q < K; q++) il[p][q] = il[q][p] = rcp_k<kFast>(sqrt_k<kFast>(nsq[p][q]));
+    float cg[4][4][4];
+#pragma unroll
+    for (int q = 0; q < K; q++)
 #pragma unroll
         for (int p = 0; p < K; p++)
 #pragma unroll
-            for (int q = p + 1; q < K; q++) {
-                nsq[p][q] = nsq[q][p] = sqdist(x, y, z, p, q);
-                il[p][q] = il[q][p] = rcp_exact(sqrt_exact(nsq[p][q]));
+            for (int r = p + 1; r < K; r++) {
+                if (p == q || r == q) continue;
+                const float ux = __fsub_rn(x[q], x[p]), uy = __fsub_rn(y[q], y[p]),
+                            uz = __fsub_rn(z[q], z[p]);
+                const float vx = __fsub_rn(x[r], x[q]), vy = __fsub_rn(y[r], y[q]),
+                            vz = __fsub_rn(z[r], z[q]);
+                const float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
+                                            __fmul_rn(uz, vz));
+                const float c = __fmul_rn(dot, __fmul_rn(il[p][q], il[q][r]));
+                cg[p][q][r] = cg[r][q][p] = (nsq[p][q] > 0.0f && nsq[q][r] > 0.0f) ? c : nan;
+            }
+    // o0 -> o1: the first cone (o0 first) and the cosine at o1
+    float c1[4][4];
+#pragma unroll
+    for (int o0 = 0; o0 < K; o0++) {
+        const unsigned m0 = all & ~(1u << o0);
+        const bool first = pos(all) && pos(m0) && in_unit(ccos(m0, all));
+#pragma unroll
+        for (int o1 = 0; o1 < K; o1++) {
+            if (o1 == o0) continue;
+            const unsigned after = m0 & ~(1u << o1);
+            const float ce = ccos(after, m0);
+            c1[o0][o1] = (first && nsq[o0][o1] > kPosEps2 && pos(after) && in_unit(ce)) ? ce : nan;
+        }
+    }
+    float best = kInf;
+    int best_rank = -1, rank = 0;
+    if constexpr (K == 3) {
+#pragma unroll
+        for (int p0 = 0; p0 < 3; p0++)
+#pragma unroll
+            for (int p1 = 0; p1 < 3; p1++) {
+                if (p1 == p0) continue;
+                const float d = __fsub_rn(c1[p0][p1], cg[p0][p1][3 - p0 - p1]);
+                const float c = __fmul_rn(d, d);           // 0 + d^2 = d^2 (d^2 is +0 or more)
+                if (c < best) { best = c; best_rank = rank; }
+                rank++;
+            }
+    } else {
+        // o2 -> o3: the cosine at o2 with o3 last
+        float c2[4][4];
+#pragma unroll
+        for (int o2 = 0; o2 < 4; o2++)
+#pragma unroll
+            for (int o3 = 0; o3 < 4; o3++) {
+                if (o3 == o2) continue;
+                const float ce = ccos(1u << o3, (1u << o2) | (1u << o3));
+                c2[o2][o3] = (pos(1u << o3) && in_unit(ce)) ? ce : nan;
             }
 #pragma unroll
-        for (int q = 0; q < K; q++)
+        for (int p0 = 0; p0 < 4; p0++)
 #pragma unroll
-            for (int p = 0; p < K; p++)
+            for (int p1 = 0; p1 < 4; p1++) {
+                if (p1 == p0) continue;
 #pragma unroll
-                for (int r = p + 1; r < K; r++) {
-                    if (p == q || r == q) continue;
-                    float ux = __fsub_rn(x[q], x[p]), uy = __fsub_rn(y[q], y[p]),
-                          uz = __fsub_rn(z[q], z[p]);
-                    float vx = __fsub_rn(x[r], x[q]), vy = __fsub_rn(y[r], y[q]),
-                          vz = __fsub_rn(z[r], z[q]);
-                    float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
-                                          __fmul_rn(uz, vz));
-                    float c = __fmul_rn(dot, __fmul_rn(il[p][q], il[q][r]));
-                    cg[p][q][r] = cg[r][q][p] = c;
-                    cgok[p][q][r] = cgok[r][q][p] = nsq[p][q] > 0.0f && nsq[q][r] > 0.0f;
+                for (int p2 = 0; p2 < 4; p2++) {
+                    if (p2 == p0 || p2 == p1) continue;
+                    const int p3 = 6 - p0 - p1 - p2;
+                    const float d1 = __fsub_rn(c1[p0][p1], cg[p0][p1][p2]);
+                    const float d2 = __fsub_rn(c2[p2][p3], cg[p1][p2][p3]);
+                    const float c = __fadd_rn(__fmul_rn(d1, d1), __fmul_rn(d2, d2));
+                    if (c < best) { best = c; best_rank = rank; }
+                    rank++;
                 }
+            }
     }
+    return best_rank;
+}
 
-    // 1 - m_e c^2 (1/E[after] - 1/E[before])
-    __device__ __forceinline__ float ccos(unsigned after, unsigned before) const {
-        return __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(inv[after], inv[before])));
-    }
-};
-
-// Compton chi2 of the order o[0..K) from the tables; +inf when invalid.
 template <int K>
-__device__ __forceinline__ float order_chi2_t(const OrderTables<K> &T, const int (&o)[K]) {
-    constexpr unsigned all = (1u << K) - 1u;
-    const unsigned m0 = all & ~(1u << o[0]);
-    float c1 = T.ccos(m0, all);
-    bool ok = (T.E[all] > 0.0f) && (T.E[m0] > 0.0f) && in_unit(c1) &&
-              (T.nsq[o[0]][o[1]] > 1e-12f);
-    float chi2 = 0.0f;
-#pragma unroll
-    for (int j = 1; j + 1 < K; j++) {
-        unsigned before = 0;
-#pragma unroll
-        for (int m = j; m < K; m++) before |= 1u << o[m];
-        const unsigned after = before & ~(1u << o[j]);
-        float ce = T.ccos(after, before);
-        float d = __fsub_rn(ce, T.cg[o[j - 1]][o[j]][o[j + 1]]);
-        chi2 = __fadd_rn(chi2, __fmul_rn(d, d));
-        ok = ok && (T.E[after] > 0.0f) && in_unit(ce) && T.cgok[o[j - 1]][o[j]][o[j + 1]];
-    }
-    return ok ? chi2 : kInf;
+static __device__ __noinline__ int order_rank_slow(const float (&x)[4], const float (&y)[4],
+                                                   const float (&z)[4], const float (&e)[4],
+                                                   const float (&nsq)[4][4]) {
+    return order_rank<K, false>(x, y, z, e, nsq);
 }
 
 // Klein-Nishina angular weight P^2 (P + 1/P - sin^2 eta), binary32 sequence.
@@ -127,11 +181,11 @@ __device__ __forceinline__ float kn_weight(float P, float c) {
     return __fmul_rn(__fmul_rn(P, P), t);
 }
 
+template <int K>
 __device__ __forceinline__ float pick(const float (&v)[4], int i) {
     float r = v[0];
-    r = (i == 1) ? v[1] : r;
-    r = (i == 2) ? v[2] : r;
-    r = (i == 3) ? v[3] : r;
+#pragma unroll
+    for (int s = 1; s < K; s++) r = (i == s) ? v[s] : r;
     return r;
 }
 
@@ -143,13 +197,14 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
     if constexpr (K == 2) {
         // two-site validity is the first-site cone alone; its cosine is
         // 1 - m_e c^2 (1/E2 - 1/E0) in the binary32 sequence above, each
-        // shared quantity computed once; set_energy of a single slot is the
-        // deposit itself (0 + e = e)
-        const float e0 = set_energy<2>(e, 3u);
+        // shared quantity computed once.  A single slot's energy 0 + e is
+        // used as e: they differ only for e = -0, which fails e > 0 on
+        // both sides
+        const float e0 = __fadd_rn(__fadd_rn(0.0f, e[0]), e[1]);
         const float ie0 = rcp_exact(e0);
         const float c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[1]), ie0)));
         const float c1 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[0]), ie0)));
-        const bool apart = sqdist(x, y, z, 0, 1) > 1e-12f;
+        const bool apart = sqdist(x, y, z, 0, 1) > kPosEps2;
         const bool ok0 = (e0 > 0.0f) && (e[1] > 0.0f) && in_unit(c0) && apart;
         const bool ok1 = (e0 > 0.0f) && (e[0] > 0.0f) && in_unit(c1) && apart;
         const float w0 = kn_weight(__fdiv_rn(e[1], e0), c0);
@@ -158,31 +213,26 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
         if (ok0) { f0 = 0; f1 = 1; return 0; }
         return -1;
     } else {
-        const OrderTables<K> T(x, y, z, e);
-        float best = kInf;
-        int best_rank = -1, rank = 0;
+        float nsq[4][4];
+        bool fast = true;
 #pragma unroll
-        for (int p0 = 0; p0 < K; p0++)
+        for (int s = 0; s < K; s++) fast = fast && e[s] >= 0x1p-100f && e[s] <= 0x1p98f;
 #pragma unroll
-            for (int p1 = 0; p1 < K; p1++) {
-                if (p1 == p0) continue;
-                if constexpr (K == 3) {
-                    const int o[3] = {p0, p1, 3 - p0 - p1};
-                    float c = order_chi2_t<3>(T, o);
-                    if (c < best) { best = c; best_rank = rank; f0 = p0; f1 = p1; }
-                    rank++;
-                } else {
+        for (int p = 0; p < K; p++)
 #pragma unroll
-                    for (int p2 = 0; p2 < 4; p2++) {
-                        if (p2 == p0 || p2 == p1) continue;
-                        const int o[4] = {p0, p1, p2, 6 - p0 - p1 - p2};
-                        float c = order_chi2_t<4>(T, o);
-                        if (c < best) { best = c; best_rank = rank; f0 = p0; f1 = p1; }
-                        rank++;
-                    }
-                }
+            for (int q = p + 1; q < K; q++) {
+                const float v = sqdist(x, y, z, p, q);
+                nsq[p][q] = nsq[q][p] = v;
+                fast = fast && v <= 0x1p100f && (v >= 0x1p-100f || v == 0.0f);
             }
-        return best_rank;
+        const int rk = fast ? order_rank<K, true>(x, y, z, e, nsq)
+                            : order_rank_slow<K>(x, y, z, e, nsq);
+        // the rank's first two slots (lexicographic: (K-1)! orders per first slot)
+        constexpr int per0 = K == 4 ? 6 : 2;
+        const int p0 = rk / per0, i1 = (rk % per0) / (per0 / (K - 1));
+        f0 = p0;
+        f1 = i1 + (i1 >= p0 ? 1 : 0);
+        return rk;
     }
 }
 
@@ -192,10 +242,11 @@ constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
 struct ReconSmem {
     float v[4][4][kWin];      // [x|y|z|e][slot][window position]
-    float o[5][kWin];         // ax, ay, az, eta, deta by window position
+    alignas(16) float o[5][kWin];   // ax, ay, az, eta, deta by window position
     uint16_t order[kWin];     // sorted position -> window position
     uint8_t k[kWin];          // site count by window position
-    uint8_t ov[kWin], op[kWin];
+    alignas(16) uint8_t ov[kWin];
+    alignas(16) uint8_t op[kWin];
     int grp[kWin / 32][4];    // events of each class in each 32-event group
     int off[kWin / 32][4];    // sorted position of each group's first event of a class
     int next;
@@ -203,27 +254,36 @@ struct ReconSmem {
     int load_failed;
 };
 
-// Ring of one event (FP32) from its chosen order; writes window position w.
-__device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const float (&x)[4],
-                                              const float (&y)[4], const float (&z)[4],
-                                              const float (&e)[4], float sig_e, float sig_pos,
+__device__ __forceinline__ void no_ring(ReconSmem &S, int w) {
+    S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
+    S.ov[w] = 0;
+    S.op[w] = 255;
+}
+
+// Ring of the K-site event at window position w (FP32) from its chosen order.
+template <int K>
+__device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, float sig_e, float sig_pos,
                                               float deta_min, float deta_max) {
-    int f0 = 0, f1 = 1, rk = -1;
-    if (kk == 2) rk = choose_order<2>(x, y, z, e, f0, f1);
-    else if (kk == 3) rk = choose_order<3>(x, y, z, e, f0, f1);
-    else if (kk == 4) rk = choose_order<4>(x, y, z, e, f0, f1);
+    float x[4] = {}, y[4] = {}, z[4] = {}, e[4] = {};
+#pragma unroll
+    for (int sl = 0; sl < K; sl++) {
+        x[sl] = S.v[0][sl][w];
+        y[sl] = S.v[1][sl][w];
+        z[sl] = S.v[2][sl][w];
+        e[sl] = S.v[3][sl][w];
+    }
+    int f0 = 0, f1 = 1;
+    const int rk = choose_order<K>(x, y, z, e, f0, f1);
     if (rk < 0) {
-        S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
-        S.ov[w] = 0;
-        S.op[w] = 255;
+        no_ring(S, w);
         return;
     }
     // E1 first deposit, E2 the rest, E0 = E1 + E2
-    float e1 = pick(e, f0);
+    float e1 = pick<K>(e, f0);
     float e2 = 0.0f, var2 = 0.0f;
 #pragma unroll
-    for (int s = 0; s < 4; s++)
-        if (s < kk && s != f0) {
+    for (int s = 0; s < K; s++)
+        if (s != f0) {
             e2 += e[s];
             float sd = sig_e * e[s];
             var2 = fmaf(sd, sd, var2);
@@ -237,9 +297,9 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, int kk, const
     float th = angle_from_half_chord2(u);
     float sin_eta = sqrt_approx(fmaxf(u * (2.0f - u), 0.0f));   // sqrt((1-c)(1+c))
 
-    float dx = pick(x, f0) - pick(x, f1);
-    float dy = pick(y, f0) - pick(y, f1);
-    float dz = pick(z, f0) - pick(z, f1);
+    float dx = pick<K>(x, f0) - pick<K>(x, f1);
+    float dy = pick<K>(y, f0) - pick<K>(y, f1);
+    float dz = pick<K>(z, f0) - pick<K>(z, f1);
     float inv_len = rsqrt_approx(dx * dx + dy * dy + dz * dz);
 
     float s1 = sig_e * e1;
@@ -274,6 +334,7 @@ __global__ void __launch_bounds__(kRThreads, 3)
 k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
                     const float *__restrict__ ys, const float *__restrict__ zs,
                     const float *__restrict__ es, int64_t count, int64_t stride, int bulk_ok,
+                    int vec_ok,
                     float sig_e, float sig_pos, float deta_min, float deta_max,
                     float *__restrict__ ax, float *__restrict__ ay,
                     float *__restrict__ az, float *__restrict__ eta,
@@ -368,24 +429,30 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
             c = __shfl_sync(0xffffffffu, c, 0);
             if (c >= kChunks) break;
             const int w = S.order[c * 32 + lane];
-            float x[4], y[4], z[4], e[4];
-#pragma unroll
-            for (int sl = 0; sl < 4; sl++) {
-                x[sl] = S.v[0][sl][w];
-                y[sl] = S.v[1][sl][w];
-                z[sl] = S.v[2][sl][w];
-                e[sl] = S.v[3][sl][w];
-            }
-            ring_of_event(S, w, S.k[w], x, y, z, e, sig_e, sig_pos, deta_min, deta_max);
+            const int kk = S.k[w];
+            if (kk == 4) ring_of_event<4>(S, w, sig_e, sig_pos, deta_min, deta_max);
+            else if (kk == 3) ring_of_event<3>(S, w, sig_e, sig_pos, deta_min, deta_max);
+            else if (kk == 2) ring_of_event<2>(S, w, sig_e, sig_pos, deta_min, deta_max);
+            else no_ring(S, w);
         }
     } else {   // a bounded wait gave up: the window's rings are left invalid
-        for (int w = tid; w < kWin; w += kRThreads) {
-            S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
-            S.ov[w] = 0;
-            S.op[w] = 255;
-        }
+        for (int w = tid; w < kWin; w += kRThreads) no_ring(S, w);
     }
     __syncthreads();
+    if (vec_ok && base + kWin <= count) {     // four events per thread, 16-byte stores
+        static_assert(kWin / 4 <= kRThreads, "one pass of four-event stores");
+        if (tid < kWin / 4) {
+            const int w = 4 * tid;
+            const int64_t i = base + w;
+            float *dst[5] = {ax, ay, az, eta, deta};
+#pragma unroll
+            for (int a = 0; a < 5; a++)
+                *reinterpret_cast<float4 *>(dst[a] + i) = *reinterpret_cast<const float4 *>(&S.o[a][w]);
+            *reinterpret_cast<uint32_t *>(valid + i) = *reinterpret_cast<const uint32_t *>(&S.ov[w]);
+            *reinterpret_cast<uint32_t *>(perm + i) = *reinterpret_cast<const uint32_t *>(&S.op[w]);
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < kPer; j++) {
         const int w = tid + j * kRThreads;
@@ -438,8 +505,11 @@ cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
     TraceScope ts(CC_STAGE_RECON, s);
     auto a16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
     const int bulk_ok = a16(ev.x) && a16(ev.y) && a16(ev.z) && a16(ev.e) && (ev.stride % 4) == 0;
+    auto a4 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 3u) == 0; };
+    const int vec_ok = a16(out.ax) && a16(out.ay) && a16(out.az) && a16(out.eta) &&
+                       a16(out.deta) && a4(out.valid) && a4(out.perm);
     k_rings_from_events<<<(unsigned)blocks, kRThreads, smem, s>>>(
-        ev.n, ev.x, ev.y, ev.z, ev.e, ev.count, ev.stride, bulk_ok, p.sigma_e_frac,
+        ev.n, ev.x, ev.y, ev.z, ev.e, ev.count, ev.stride, bulk_ok, vec_ok, p.sigma_e_frac,
         p.sigma_pos_cm, p.deta_min, p.deta_max, out.ax, out.ay, out.az, out.eta,
         out.deta, out.valid, out.perm);
     return cudaGetLastError();
