@@ -240,9 +240,12 @@ constexpr int kRThreads = 256;
 constexpr int kWin = 768;             // events per CTA window (3 CTAs per SM)
 constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
+// Once a thread has read an event's sites into registers, the event's ring
+// goes to the same window position of rows that only that event's sites
+// occupied: ax, ay, az, eta in the slot-0 rows of x, y, z, e and deta in the
+// slot-1 row of x.
 struct ReconSmem {
     float v[4][4][kWin];      // [x|y|z|e][slot][window position]
-    alignas(16) float o[5][kWin];   // ax, ay, az, eta, deta by window position
     uint16_t order[kWin];     // sorted position -> window position
     uint8_t k[kWin];          // site count by window position
     alignas(16) uint8_t ov[kWin];
@@ -254,8 +257,13 @@ struct ReconSmem {
     int load_failed;
 };
 
+__device__ __forceinline__ float *ring_row(ReconSmem &S, int a) {
+    return a < 4 ? S.v[a][0] : S.v[0][1];
+}
+
 __device__ __forceinline__ void no_ring(ReconSmem &S, int w) {
-    S.o[0][w] = S.o[1][w] = S.o[2][w] = S.o[3][w] = S.o[4][w] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 5; a++) ring_row(S, a)[w] = 0.0f;
     S.ov[w] = 0;
     S.op[w] = 255;
 }
@@ -312,11 +320,11 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, float sig_e, 
     float w_g = 1.41421356237f * sig_pos * inv_len;
     float wd = sqrt_approx(w_e * w_e + w_g * w_g);
 
-    S.o[0][w] = dx * inv_len;
-    S.o[1][w] = dy * inv_len;
-    S.o[2][w] = dz * inv_len;
-    S.o[3][w] = th;
-    S.o[4][w] = fminf(fmaxf(wd, deta_min), deta_max);
+    ring_row(S, 0)[w] = dx * inv_len;
+    ring_row(S, 1)[w] = dy * inv_len;
+    ring_row(S, 2)[w] = dz * inv_len;
+    ring_row(S, 3)[w] = th;
+    ring_row(S, 4)[w] = fminf(fmaxf(wd, deta_min), deta_max);
     S.ov[w] = 1;
     S.op[w] = (uint8_t)rk;
 }
@@ -330,7 +338,7 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, float sig_e, 
 // so that a warp runs one code path at a time and the warps finish
 // together; the rings are written back in the original order with coalesced
 // stores.  Slots past an event's site count are staged too and never read.
-__global__ void __launch_bounds__(kRThreads, 3)
+__global__ void __launch_bounds__(kRThreads, 4)
 k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
                     const float *__restrict__ ys, const float *__restrict__ zs,
                     const float *__restrict__ es, int64_t count, int64_t stride, int bulk_ok,
@@ -447,7 +455,7 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
             float *dst[5] = {ax, ay, az, eta, deta};
 #pragma unroll
             for (int a = 0; a < 5; a++)
-                *reinterpret_cast<float4 *>(dst[a] + i) = *reinterpret_cast<const float4 *>(&S.o[a][w]);
+                *reinterpret_cast<float4 *>(dst[a] + i) = *reinterpret_cast<const float4 *>(ring_row(S, a) + w);
             *reinterpret_cast<uint32_t *>(valid + i) = *reinterpret_cast<const uint32_t *>(&S.ov[w]);
             *reinterpret_cast<uint32_t *>(perm + i) = *reinterpret_cast<const uint32_t *>(&S.op[w]);
         }
@@ -458,11 +466,11 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
         const int w = tid + j * kRThreads;
         const int64_t i = base + w;
         if (i < count) {
-            ax[i] = S.o[0][w];
-            ay[i] = S.o[1][w];
-            az[i] = S.o[2][w];
-            eta[i] = S.o[3][w];
-            deta[i] = S.o[4][w];
+            ax[i] = ring_row(S, 0)[w];
+            ay[i] = ring_row(S, 1)[w];
+            az[i] = ring_row(S, 2)[w];
+            eta[i] = ring_row(S, 3)[w];
+            deta[i] = ring_row(S, 4)[w];
             valid[i] = S.ov[w];
             perm[i] = S.op[w];
         }

@@ -143,6 +143,36 @@ def test_rings_edge_cases(cc, dev):
     assert not want["valid"][[0, 1, 2, 3, 10, 11]].any()
 
 
+def test_rings_many_windows_and_misaligned(cc, dev):
+    """1.26M events (more 768-event windows than resident CTAs, so every CTA
+    runs several windows through its double buffer, and a ragged last
+    window), then the same events through arrays that start 4 bytes off a
+    16-byte boundary (plain loads) into ring arrays that start 4 or 1 bytes
+    off (scalar stores): all equal to the oracle's rings."""
+    ev = synth.tile_events(synth.simulate_events(n_src=6000, n_bkg=54000, seed=12), 21)
+    N = ev["n"].size
+    p = cc.Params()
+    want = oracle.rings_from_events(ev, p.sigma_e_frac, p.sigma_pos_cm, p.deta_min, p.deta_max)
+    got = gpu_rings(cc, ev, dev, p)
+    check_rings(got, want, ev)
+
+    def off(arr, dtype, o):
+        flat = torch.zeros(arr.size + o, dtype=dtype, device=dev)
+        v = flat[o:].view(arr.shape)
+        v.copy_(torch.from_numpy(np.ascontiguousarray(arr)).to(dev))
+        return v
+
+    n = off(ev["n"], torch.uint8, 1)
+    x, y, z, e = (off(np.asarray(ev[k], np.float32), torch.float32, 1) for k in "xyze")
+    out = {k: torch.zeros(N + 1, dtype=torch.float32, device=dev)[1:] for k in
+           ("ax", "ay", "az", "eta", "deta")}
+    out["valid"] = torch.zeros(N + 1, dtype=torch.uint8, device=dev)[1:]
+    out["perm"] = torch.zeros(N + 1, dtype=torch.uint8, device=dev)[1:]
+    cc.rings_from_events(n, x, y, z, e, p, out)
+    torch.cuda.synchronize()
+    check_rings({k: v.cpu().numpy() for k, v in out.items()}, want, ev)
+
+
 def extreme_events(N, seed):
     """Events built to reach every branch of the binary32 ordering rule:
     log-uniform magnitudes from 1e-40 to 1e38 with random signs (subnormal,
