@@ -448,11 +448,13 @@ cc_status cc_backproject(const cc_rings *rings, const float *px, const float *py
                          void *workspace, size_t ws_bytes, void *stream);
 
 /*
- * Self-check of the correctly rounded reciprocal and square root that the
- * ordering decision uses (no counterpart in the paper; it backs the bit-exact
- * ordering): on every float of [1, 4), mismatches[0] counts results that
- * differ from __frcp_rn, mismatches[1] from __fsqrt_rn.  mismatches: device
- * uint64 [2].  Asynchronous on `stream`.
+ * Self-check of the correctly rounded reciprocal, square root and quotient
+ * that the ordering decision uses (no counterpart in the paper; it backs the
+ * bit-exact ordering): on every float of [1, 4), mismatches[0] counts
+ * results that differ from __frcp_rn, mismatches[1] from __fsqrt_rn; on
+ * every float x of [1, 2) and 64 divisors d of [1, 2), mismatches[2] counts
+ * quotients x/d and d/x that differ from __fdiv_rn.  mismatches: device
+ * uint64 [3].  Asynchronous on `stream`.
  */
 cc_status cc_selftest_exact_ops(uint64_t *mismatches, void *stream);
 

@@ -780,9 +780,9 @@ def selftest_wait_timeout(which: int, limit_ns: int, device="cuda", stream=None)
 
 
 def selftest_exact_ops(device="cuda", stream=None):
-    """Mismatches of the decision's correctly rounded reciprocal and square
-    root against the CUDA intrinsics over [1, 4): (rcp, sqrt)."""
-    out = torch.empty(2, dtype=torch.uint64, device=device)
+    """Mismatches of the decision's correctly rounded reciprocal, square root
+    and quotient against the CUDA intrinsics: (rcp, sqrt, div)."""
+    out = torch.empty(3, dtype=torch.uint64, device=device)
     _check("cc_selftest_exact_ops", lib().cc_selftest_exact_ops(_ptr(out), _stream(stream)))
     return out
 

@@ -5,8 +5,9 @@
 // One thread per event, events grouped by site count within each CTA (see
 // k_rings_from_events).  The ORDER is an integer decided by floating point,
 // so it is decided in IEEE binary32 with every operation rounded once
-// (__fadd_rn / __fmul_rn / __fdiv_rn and the correctly rounded rcp_exact /
-// sqrt_exact of cc_math.cuh: no contraction into FMA), in a fixed sequence:
+// (__fadd_rn / __fmul_rn / __fdiv_rn and the correctly rounded reciprocal,
+// root and quotient of cc_math.cuh: no contraction into FMA), in a fixed
+// sequence:
 //   E(S)        = deposits of the slots in set S added in increasing slot order
 //   cos(Ea, Eb) = 1 - m_e c^2 * (1/Ea - 1/Eb)
 //   |x_q - x_p|^2 = ((dx*dx) + (dy*dy)) + (dz*dz), d = x_q - x_p
@@ -201,14 +202,31 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
         // used as e: they differ only for e = -0, which fails e > 0 on
         // both sides
         const float e0 = __fadd_rn(__fadd_rn(0.0f, e[0]), e[1]);
-        const float ie0 = rcp_exact(e0);
-        const float c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[1]), ie0)));
-        const float c1 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[0]), ie0)));
         const bool apart = sqdist(x, y, z, 0, 1) > kPosEps2;
-        const bool ok0 = (e0 > 0.0f) && (e[1] > 0.0f) && in_unit(c0) && apart;
-        const bool ok1 = (e0 > 0.0f) && (e[0] > 0.0f) && in_unit(c1) && apart;
-        const float w0 = kn_weight(__fdiv_rn(e[1], e0), c0);
-        const float w1 = kn_weight(__fdiv_rn(e[0], e0), c1);
+        const bool fast = e[0] >= 0x1p-40f && e[0] <= 0x1p40f && e[1] >= 0x1p-40f &&
+                          e[1] <= 0x1p40f;
+        float c0, c1, w0, w1;
+        bool ok0, ok1;
+        if (fast) {   // every argument and quotient normal: the unchecked corrections
+            const float ie0 = rcp_core(e0);
+            c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_core(e[1]), ie0)));
+            c1 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_core(e[0]), ie0)));
+            ok0 = in_unit(c0) && apart;
+            ok1 = in_unit(c1) && apart;
+            const float P0 = div_core(e[1], e0, ie0), P1 = div_core(e[0], e0, ie0);
+            w0 = __fmul_rn(__fmul_rn(P0, P0), __fsub_rn(__fadd_rn(P0, rcp_core(P0)),
+                                                        __fsub_rn(1.0f, __fmul_rn(c0, c0))));
+            w1 = __fmul_rn(__fmul_rn(P1, P1), __fsub_rn(__fadd_rn(P1, rcp_core(P1)),
+                                                        __fsub_rn(1.0f, __fmul_rn(c1, c1))));
+        } else {
+            const float ie0 = rcp_exact(e0);
+            c0 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[1]), ie0)));
+            c1 = __fsub_rn(1.0f, __fmul_rn(kMeKeV, __fsub_rn(rcp_exact(e[0]), ie0)));
+            ok0 = (e0 > 0.0f) && (e[1] > 0.0f) && in_unit(c0) && apart;
+            ok1 = (e0 > 0.0f) && (e[0] > 0.0f) && in_unit(c1) && apart;
+            w0 = kn_weight(__fdiv_rn(e[1], e0), c0);
+            w1 = kn_weight(__fdiv_rn(e[0], e0), c1);
+        }
         if (ok1 && (!ok0 || w1 > w0)) { f0 = 1; f1 = 0; return 1; }
         if (ok0) { f0 = 0; f1 = 1; return 0; }
         return -1;
@@ -237,7 +255,7 @@ __device__ __forceinline__ int choose_order(const float (&x)[4], const float (&y
 }
 
 constexpr int kRThreads = 256;
-constexpr int kWin = 768;             // events per CTA window (3 CTAs per SM)
+constexpr int kWin = 768;             // events per CTA window (4 CTAs per SM)
 constexpr int kChunks = kWin / 32;    // 32-event chunks, one warp each
 
 // Once a thread has read an event's sites into registers, the event's ring
@@ -336,8 +354,12 @@ __device__ __forceinline__ void ring_of_event(ReconSmem &S, int w, float sig_e, 
 // grouped by site count (4, 3, 2, other) through an index, and the warps
 // take 32-event chunks from a shared queue, the costly 4-site chunks first,
 // so that a warp runs one code path at a time and the warps finish
-// together; the rings are written back in the original order with coalesced
-// stores.  Slots past an event's site count are staged too and never read.
+// together; each event's ring is written over its own staged sites, and the
+// rings go back in the original order with 16-byte stores (coalesced
+// scalar stores for a ragged window or unaligned ring arrays).  Slots past
+// an event's site count are staged too and never read.  Four CTAs share an
+// SM (64 registers, 54 KB of shared memory each), so that while one waits
+// for its window the others compute.
 __global__ void __launch_bounds__(kRThreads, 4)
 k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
                     const float *__restrict__ ys, const float *__restrict__ zs,
@@ -480,22 +502,35 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
 }  // namespace
 
 // Every float of [1, 4) (all mantissas, both exponent parities): the
-// correctly rounded rcp_exact / sqrt_exact against the CUDA intrinsics.
+// correctly rounded rcp_exact / sqrt_exact against the CUDA intrinsics; and
+// div_core on every float of [1, 2) against 64 divisor mantissas, each
+// quotient taken both ways, against __fdiv_rn.
 __global__ void k_selftest_exact(unsigned long long *__restrict__ bad) {
     const uint32_t lo = 0x3F800000u, hi = 0x40800000u;
-    unsigned long long b0 = 0, b1 = 0;
+    unsigned long long b0 = 0, b1 = 0, b2 = 0;
     for (uint32_t u = lo + blockIdx.x * blockDim.x + threadIdx.x; u < hi;
          u += gridDim.x * blockDim.x) {
         const float x = __uint_as_float(u);
         b0 += __float_as_uint(rcp_exact(x)) != __float_as_uint(__frcp_rn(x));
         b1 += __float_as_uint(sqrt_exact(x)) != __float_as_uint(__fsqrt_rn(x));
+        if (u < 0x40000000u) {
+            const float yx = rcp_core(x);
+            uint32_t h = u * 2654435761u;
+            for (int j = 0; j < 64; j++) {
+                h = h * 1664525u + 1013904223u;           // divisor mantissas (LCG)
+                const float d = __uint_as_float(0x3F800000u | (j == 0 ? 0u : h >> 9));
+                b2 += __float_as_uint(div_core(x, d, rcp_core(d))) != __float_as_uint(__fdiv_rn(x, d));
+                b2 += __float_as_uint(div_core(d, x, yx)) != __float_as_uint(__fdiv_rn(d, x));
+            }
+        }
     }
     if (b0) atomicAdd(bad, b0);
     if (b1) atomicAdd(bad + 1, b1);
+    if (b2) atomicAdd(bad + 2, b2);
 }
 
 cudaError_t launch_selftest_exact(uint64_t *bad, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(bad, 0, 2 * sizeof(uint64_t), s);
+    cudaError_t e = cudaMemsetAsync(bad, 0, 3 * sizeof(uint64_t), s);
     if (e != cudaSuccess) return e;
     k_selftest_exact<<<(unsigned)device_sm_count() * 8, 256, 0, s>>>(
         reinterpret_cast<unsigned long long *>(bad));

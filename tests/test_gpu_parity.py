@@ -552,8 +552,10 @@ def test_abi_rejects_bad_arguments(cc, dev):
 def test_exact_reciprocal_and_root_match_the_intrinsics(cc):
     """The ordering decision's correctly rounded reciprocal and square root
     equal __frcp_rn / __fsqrt_rn on every float of [1, 4), hence (the result
-    depending only on mantissa and exponent parity there) on [2^-100, 2^100]."""
+    depending only on mantissa and exponent parity there) on [2^-100, 2^100];
+    its two-correction quotient equals __fdiv_rn on every float of [1, 2)
+    against 64 divisor mantissas, both ways."""
     from paper_2411_04785_gb300 import api
     out = api.selftest_exact_ops("cuda:0")
     torch.cuda.synchronize()
-    assert out.view(torch.int64).cpu().tolist() == [0, 0]
+    assert out.view(torch.int64).cpu().tolist() == [0, 0, 0]
