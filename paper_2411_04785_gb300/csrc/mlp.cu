@@ -538,6 +538,31 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
     return d;
 }
 
+// Bounded wait on an mbarrier phase by polling test_wait, which never
+// suspends the thread: the MMA warp waits for the epilogue's arrivals this
+// way (measured 42.3 -> 41.6 us per 500k-ring forward against try_wait;
+// polling in the 16 epilogue warps as well was slower, 43.5 us)
+__device__ __forceinline__ bool mbar_spin(unsigned long long *bar, unsigned parity) {
+    const unsigned b = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255) {
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) return false;
+        }
+    }
+    return false;
+}
+
 // kKeep: also write the three hidden activations out (training); inference
 // is compiled without those stores.
 template <bool kKeep>
@@ -666,7 +691,7 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                     if (l == 0) {
                         const int st = k % kXStages;
                         ok = !*err && mbar_wait(&S.x_full[st], (k / kXStages) & 1) &&
-                             (k < 2 || mbar_wait(&S.h_done[j], hd[j]++ & 1));
+                             (k < 2 || mbar_spin(&S.h_done[j], hd[j]++ & 1));
                         if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                         tc_fence_after();
                         umma_ss(d, dx + (uint64_t)(st * (kTM * kF * 2 / 16)), dw1, idesc(kTM, kH), 0);
@@ -674,7 +699,7 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
                         umma_commit(&S.acc_full[j]);
                         umma_commit(&S.x_empty[st]);
                     } else {
-                        ok = !*err && mbar_wait(&S.h_done[j], hd[j]++ & 1);
+                        ok = !*err && mbar_spin(&S.h_done[j], hd[j]++ & 1);
                         if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned a0 = tmem + kActCol + (unsigned)(j * 64);
