@@ -68,8 +68,8 @@ __host__ __device__ constexpr int high_slot(unsigned m) { return m >= 8u ? 3 : m
 // kFast: every deposit is in [2^-100, 2^98] and every squared distance is 0
 // or in [2^-100, 2^100].  Then every subset energy is positive and in
 // [2^-100, 2^100], every reciprocal and root argument is in the range of the
-// one-FMA corrections, and a zero distance's NaN root is never read (both of
-// its geometric cosines are NaN already).
+// one-FMA corrections, and a zero distance's root is NaN, which makes both of
+// its geometric cosines NaN, as the rule's validity wants.
 template <int K, bool kFast>
 __device__ __forceinline__ int order_rank(const float (&x)[4], const float (&y)[4],
                                           const float (&z)[4], const float (&e)[4],
@@ -108,7 +108,10 @@ __device__ __forceinline__ int order_rank(const float (&x)[4], const float (&y)[
                 const float dot = __fadd_rn(__fadd_rn(__fmul_rn(ux, vx), __fmul_rn(uy, vy)),
                                             __fmul_rn(uz, vz));
                 const float c = __fmul_rn(dot, __fmul_rn(il[p][q], il[q][r]));
-                cg[p][q][r] = cg[r][q][p] = (nsq[p][q] > 0.0f && nsq[q][r] > 0.0f) ? c : nan;
+                // a zero-length segment makes c NaN by itself on the fast path
+                // (the uncorrected root of 0 is NaN, so is the inverse
+                // length); the checked path selects it
+                cg[p][q][r] = cg[r][q][p] = (kFast || (nsq[p][q] > 0.0f && nsq[q][r] > 0.0f)) ? c : nan;
             }
     // o0 -> o1: the first cone (o0 first) and the cosine at o1
     float c1[4][4];
