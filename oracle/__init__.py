@@ -53,6 +53,16 @@ def _load():
         lib.or_order_chi2.restype = f32
         lib.or_kn_weight_f32.argtypes = [f32, f32]
         lib.or_kn_weight_f32.restype = f32
+        lib.or_order_chi2_f64.argtypes = [i32, P, P, P, P, P]
+        lib.or_order_chi2_f64.restype = f64
+        lib.or_kn_weight_f64.argtypes = [f64, f64]
+        lib.or_kn_weight_f64.restype = f64
+        lib.or_order_event_f64.argtypes = [i32, P, P, P, P]
+        lib.or_order_event_f64.restype = i32
+        lib.or_order_bound.argtypes = [i32, P, P, P, P, P, P, P]
+        lib.or_order_bound.restype = i32
+        lib.or_order_check.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P]
+        lib.or_order_check.restype = None
         lib.or_rings_from_events.argtypes = [i64, i64, P, P, P, P, P, f64, f64,
                                              f64, f64, P, P, P, P, P, P, P]
         lib.or_rings_from_events.restype = None
@@ -139,6 +149,58 @@ def order_chi2(x, y, z, e, order):
 
 def kn_weight_f32(P, cos_eta):
     return _load().or_kn_weight_f32(float(P), float(cos_eta))
+
+
+def order_chi2_f64(x, y, z, e, order):
+    """The definition's chi2 of one order in FP64 (FP32 inputs); +inf when
+    the order is invalid, 0 for a valid 2-site order."""
+    x, y, z, e = (_f32(v) for v in (x, y, z, e))
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    return _load().or_order_chi2_f64(len(x), _p(x), _p(y), _p(z), _p(e), _p(o))
+
+
+def kn_weight_f64(P, cos_eta):
+    return _load().or_kn_weight_f64(float(P), float(cos_eta))
+
+
+def order_event_f64(x, y, z, e):
+    """Rank the ordering rule picks on the FP64 definition (-1: none valid)."""
+    x, y, z, e = (_f32(v) for v in (x, y, z, e))
+    return _load().or_order_event_f64(len(x), _p(x), _p(y), _p(z), _p(e))
+
+
+def order_bound(x, y, z, e, order):
+    """(validity, value, bound) of one order: validity 1/0 as both precisions
+    decide it, -1 within a bound of a threshold, -2 outside the model; value
+    the FP64 chi2 (Klein-Nishina weight for 2 sites) and bound the most the
+    binary32 sequence can differ from it."""
+    x, y, z, e = (_f32(v) for v in (x, y, z, e))
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    val, bnd = C.c_double(0), C.c_double(0)
+    st = _load().or_order_bound(len(x), _p(x), _p(y), _p(z), _p(e), _p(o),
+                                C.addressof(val), C.addressof(bnd))
+    return st, val.value, bnd.value
+
+
+ORDER_DECIDED, ORDER_NEAR_TIE, ORDER_NEAR_THRESHOLD, ORDER_OUTSIDE = 0, 1, 2, 3
+
+
+def order_check(ev):
+    """Binary32 decision vs the FP64 definition for an event set (FP32 inputs).
+
+    Returns dict(rank32, rank64, status, margin); see ``or_order_check``:
+    status 0 = decided (ranks must agree), 1 = near tie within the binary32
+    bound, 2 = a validity threshold within its bound, 3 = outside the model."""
+    n = np.ascontiguousarray(ev["n"], dtype=np.uint8)
+    N = n.shape[0]
+    x, y, z, e = (_f32(ev[k]) for k in ("x", "y", "z", "e"))
+    stride = x.shape[1] if x.ndim == 2 else N
+    out = {"rank32": np.empty(N, np.int32), "rank64": np.empty(N, np.int32),
+           "status": np.empty(N, np.uint8), "margin": np.empty(N)}
+    _load().or_order_check(N, stride, _p(n), _p(x), _p(y), _p(z), _p(e),
+                           _p(out["rank32"]), _p(out["rank64"]), _p(out["status"]),
+                           _p(out["margin"]))
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -36,7 +36,10 @@
  * integer result decided by floating point; it is taken in IEEE binary32 with
  * every operation rounded once (compile with -ffp-contract=off), the same
  * precision the GPU kernel decides in, so the chosen order is comparable bit
- * for bit.
+ * for bit.  That binary32 sequence is fixed; it is pinned to the rule's
+ * definition evaluated plainly in FP64 (or_order_event_f64) by a rigorous
+ * bound on its rounding (or_order_check): wherever the bound decides an
+ * event, the binary32 choice must be the FP64 argmin.
  */
 #include "oracle.h"
 
@@ -247,6 +250,431 @@ int or_order_event(int k, const float *x, const float *y, const float *z,
     if (chi2_out)
         *chi2_out = best;
     return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Site ordering: the definition in FP64, and how far binary32 can stray.   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The decision above is taken in binary32.  What it decides is defined in
+ * real arithmetic on the same (FP32) inputs: the chi2 of each order and, for
+ * two sites, the Klein-Nishina weight.  or_order_chi2_f64 / or_kn_weight_f64
+ * / or_order_event_f64 evaluate that definition plainly in FP64: energies
+ * summed in FP64, cos_E = 1 - m_e c^2 (1/E_after - 1/E_before) with the
+ * CODATA constant, cos_G = d1 . d2 / (|d1| |d2|).  Nothing is shared with the
+ * binary32 sequence.
+ */
+#define ME_KEV_D 510.99895
+#define POS_EPS2_D 1e-12      /* (1e-6 cm)^2 */
+
+static double set_energy_f64(int k, const float *e, unsigned mask)
+{
+    double s = 0.0;
+    for (int m = 0; m < k; m++)
+        if (mask & (1u << m))
+            s += (double)e[m];
+    return s;
+}
+
+static double compton_cos_f64(double e_after, double e_before)
+{
+    return 1.0 - ME_KEV_D * (1.0 / e_after - 1.0 / e_before);
+}
+
+static double sqdist_f64(const float *x, const float *y, const float *z,
+                         int p, int q)
+{
+    double dx = (double)x[q] - (double)x[p];
+    double dy = (double)y[q] - (double)y[p];
+    double dz = (double)z[q] - (double)z[p];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+double or_order_chi2_f64(int k, const float *x, const float *y,
+                         const float *z, const float *e, const int *ord)
+{
+    unsigned all = (1u << k) - 1u;
+    double e0 = set_energy_f64(k, e, all);
+    double e2 = set_energy_f64(k, e, all & ~(1u << ord[0]));
+    if (!(e0 > 0.0) || !(e2 > 0.0))
+        return INFINITY;
+    double c1 = compton_cos_f64(e2, e0);
+    if (!(c1 >= -1.0 && c1 <= 1.0))
+        return INFINITY;
+    if (!(sqdist_f64(x, y, z, ord[0], ord[1]) > POS_EPS2_D))
+        return INFINITY;
+    double chi2 = 0.0;
+    for (int j = 1; j + 1 < k; j++) {
+        unsigned before = 0;
+        for (int m = j; m < k; m++)
+            before |= 1u << ord[m];
+        double eb = set_energy_f64(k, e, before);
+        double ea = set_energy_f64(k, e, before & ~(1u << ord[j]));
+        if (!(ea > 0.0))
+            return INFINITY;
+        double ce = compton_cos_f64(ea, eb);
+        if (!(ce >= -1.0 && ce <= 1.0))
+            return INFINITY;
+        int p = ord[j - 1], q = ord[j], r = ord[j + 1];
+        double d1[3] = {(double)x[q] - x[p], (double)y[q] - y[p], (double)z[q] - z[p]};
+        double d2[3] = {(double)x[r] - x[q], (double)y[r] - y[q], (double)z[r] - z[q]};
+        double n1 = sqrt(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2]);
+        double n2 = sqrt(d2[0] * d2[0] + d2[1] * d2[1] + d2[2] * d2[2]);
+        if (!(n1 > 0.0) || !(n2 > 0.0))
+            return INFINITY;
+        double cg = (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]) / (n1 * n2);
+        chi2 += (ce - cg) * (ce - cg);
+    }
+    return chi2;
+}
+
+double or_kn_weight_f64(double P, double cos_eta)
+{
+    return P * P * (P + 1.0 / P - (1.0 - cos_eta * cos_eta));
+}
+
+/* The ordering rule on the FP64 definition: smallest chi2 (ties: lowest
+ * rank) for k = 3, 4; larger Klein-Nishina weight (ties: input order) for
+ * k = 2.  Returns the rank, or -1 when no order is valid. */
+int or_order_event_f64(int k, const float *x, const float *y, const float *z,
+                       const float *e)
+{
+    if (k < 2 || k > 4)
+        return -1;
+    if (k == 2) {
+        static const int ords[2][2] = {{0, 1}, {1, 0}};
+        double e0 = set_energy_f64(2, e, 3u), w[2];
+        int ok[2];
+        for (int o = 0; o < 2; o++) {
+            ok[o] = or_order_chi2_f64(2, x, y, z, e, ords[o]) == 0.0;
+            double e2 = (double)e[ords[o][1]];
+            w[o] = ok[o] ? or_kn_weight_f64(e2 / e0, compton_cos_f64(e2, e0)) : 0.0;
+        }
+        if (ok[1] && (!ok[0] || w[1] > w[0]))
+            return 1;
+        return ok[0] ? 0 : -1;
+    }
+    int a[4] = {0, 1, 2, 3}, rank = 0, best_rank = -1;
+    double best = INFINITY;
+    do {
+        double c = or_order_chi2_f64(k, x, y, z, e, a);
+        if (c < best) {
+            best = c;
+            best_rank = rank;
+        }
+        rank++;
+    } while (next_permutation(a, k));
+    return best_rank;
+}
+
+/*
+ * How far the binary32 decision can stray from the definition.  Beside each
+ * intermediate value v of the binary32 sequence (in the sequence's own order
+ * of operations, but with v computed in FP64) a bound e on |v32 - v| is
+ * carried, where v32 is the value binary32 computes.  An IEEE binary32
+ * operation returns op(a32, b32)(1 + d) + t with |d| <= 2^-24, and t = 0 for
+ * addition and subtraction (gradual underflow makes them exact below the
+ * normal range) and |t| <= 2^-150 for multiplication, division and square
+ * root; a32 = a + da with |da| <= e_a.  The bound of a result is the worst
+ * case of op over the operand intervals, plus 2^-24 times the largest
+ * magnitude it can take, plus 2^-150 where t applies.  A value that might
+ * overflow, or a divisor or radicand whose interval holds 0, ends the
+ * analysis (BND_OUT): the bound no longer holds.  The FP64 values themselves
+ * err by about 2^-29 of these bounds, covered by a factor 1.001.
+ */
+#define U32 (1.0 / 16777216.0)
+#define TINY32 7.006492321624085e-46      /* 2^-150 */
+#define MAX32 3.4028234663852886e38
+
+typedef struct {
+    double v, e;
+} bv_t;
+
+typedef struct {
+    int out;
+} bctx_t;
+
+static bv_t b_rnd(bctx_t *c, double v, double ep, int tiny)
+{
+    double mag = fabs(v) + ep;
+    if (!(mag * (1.0 + U32) < MAX32))
+        c->out = 1;
+    bv_t r = {v, ep + U32 * mag + (tiny ? TINY32 : 0.0)};
+    return r;
+}
+
+static bv_t b_exact(double v)
+{
+    bv_t r = {v, 0.0};
+    return r;
+}
+
+static bv_t b_add(bctx_t *c, bv_t a, bv_t b)
+{
+    return b_rnd(c, a.v + b.v, a.e + b.e, 0);
+}
+
+static bv_t b_sub(bctx_t *c, bv_t a, bv_t b)
+{
+    return b_rnd(c, a.v - b.v, a.e + b.e, 0);
+}
+
+static bv_t b_mul(bctx_t *c, bv_t a, bv_t b)
+{
+    return b_rnd(c, a.v * b.v, fabs(a.v) * b.e + fabs(b.v) * a.e + a.e * b.e, 1);
+}
+
+/* |1/(a + da) - 1/a| <= e_a / (|a| (|a| - e_a)) while e_a < |a| */
+static bv_t b_rcp(bctx_t *c, bv_t a)
+{
+    if (!(a.e < fabs(a.v))) {
+        c->out = 1;
+        return b_exact(0.0);
+    }
+    return b_rnd(c, 1.0 / a.v, a.e / (fabs(a.v) * (fabs(a.v) - a.e)), 1);
+}
+
+/* |(a + da)/(b + db) - a/b| <= (|a| e_b + |b| e_a) / (|b| (|b| - e_b)) */
+static bv_t b_div(bctx_t *c, bv_t a, bv_t b)
+{
+    if (!(b.e < fabs(b.v))) {
+        c->out = 1;
+        return b_exact(0.0);
+    }
+    double ep = (fabs(a.v) * b.e + fabs(b.v) * a.e) / (fabs(b.v) * (fabs(b.v) - b.e));
+    return b_rnd(c, a.v / b.v, ep, 1);
+}
+
+/* |sqrt(a + da) - sqrt(a)| = |da| / (sqrt(a + da) + sqrt(a)) <= e_a / sqrt(a) */
+static bv_t b_sqrt(bctx_t *c, bv_t a)
+{
+    if (!(a.v > 0.0) || !(a.e < a.v)) {
+        c->out = 1;
+        return b_exact(0.0);
+    }
+    double s = sqrt(a.v);
+    return b_rnd(c, s, a.e / s, 1);
+}
+
+/* The binary32 constant m_e c^2 times a: the constant's own representation
+ * error counts like an operand error. */
+static bv_t b_mul_me(bctx_t *c, bv_t a)
+{
+    bv_t m = {ME_KEV_D, fabs((double)ME_KEV_F - ME_KEV_D)};
+    return b_mul(c, m, a);
+}
+
+/* Does binary32's `v32 > t32` agree with the definition's `v > t`?  Certain
+ * when v lies farther from t than its bound plus the thresholds' gap.
+ * Returns 1 (both true), 0 (both false) or -1 (undecided). */
+static int b_gt(bv_t a, double t, double t32)
+{
+    double slack = a.e + fabs(t - t32);
+    if (a.v - slack > t && a.v - slack > t32)
+        return 1;
+    if (a.v + slack <= t && a.v + slack <= t32)
+        return 0;
+    return -1;
+}
+
+static int b_ge(bv_t a, double t)
+{
+    if (a.v - a.e >= t)
+        return 1;
+    if (a.v + a.e < t)
+        return 0;
+    return -1;
+}
+
+static int b_le(bv_t a, double t)
+{
+    if (a.v + a.e <= t)
+        return 1;
+    if (a.v - a.e > t)
+        return 0;
+    return -1;
+}
+
+static bv_t b_energy(bctx_t *c, int k, const float *e, unsigned mask)
+{
+    bv_t s = b_exact(0.0);
+    for (int m = 0; m < k; m++)
+        if (mask & (1u << m))
+            s = b_add(c, s, b_exact((double)e[m]));
+    return s;
+}
+
+static bv_t b_compton_cos(bctx_t *c, bv_t ea, bv_t eb)
+{
+    bv_t d = b_sub(c, b_rcp(c, ea), b_rcp(c, eb));
+    return b_sub(c, b_exact(1.0), b_mul_me(c, d));
+}
+
+static bv_t b_coord_diff(bctx_t *c, const float *v, int p, int q)
+{
+    return b_sub(c, b_exact((double)v[q]), b_exact((double)v[p]));
+}
+
+static bv_t b_sqdist(bctx_t *c, const float *x, const float *y, const float *z,
+                     int p, int q)
+{
+    bv_t dx = b_coord_diff(c, x, p, q), dy = b_coord_diff(c, y, p, q),
+         dz = b_coord_diff(c, z, p, q);
+    return b_add(c, b_add(c, b_mul(c, dx, dx), b_mul(c, dy, dy)), b_mul(c, dz, dz));
+}
+
+enum { BND_VALID = 1, BND_INVALID = 0, BND_UNDECIDED = -1, BND_OUT = -2 };
+
+/* Validity of one order as both precisions decide it, and for a valid order
+ * the chi2 (k >= 3) or the Klein-Nishina weight (k = 2) with its bound. */
+static int bound_order(int k, const float *x, const float *y, const float *z,
+                       const float *e, const int *ord, bv_t *val)
+{
+    bctx_t c = {0};
+    unsigned all = (1u << k) - 1u;
+    bv_t e0 = b_energy(&c, k, e, all);
+    bv_t e2 = b_energy(&c, k, e, all & ~(1u << ord[0]));
+#define BND_CHECK(cond)                          \
+    do {                                         \
+        int t_ = (cond);                         \
+        if (c.out)                               \
+            return BND_OUT;                      \
+        if (t_ != 1)                             \
+            return t_ == 0 ? BND_INVALID : BND_UNDECIDED; \
+    } while (0)
+    BND_CHECK(b_gt(e0, 0.0, 0.0));
+    BND_CHECK(b_gt(e2, 0.0, 0.0));
+    bv_t c1 = b_compton_cos(&c, e2, e0);
+    BND_CHECK(b_ge(c1, -1.0));
+    BND_CHECK(b_le(c1, 1.0));
+    BND_CHECK(b_gt(b_sqdist(&c, x, y, z, ord[0], ord[1]), POS_EPS2_D, (double)POS_EPS2_F));
+    if (k == 2) {
+        bv_t P = b_div(&c, e2, e0);
+        bv_t s2 = b_sub(&c, b_exact(1.0), b_mul(&c, c1, c1));
+        bv_t t = b_add(&c, P, b_rcp(&c, P));
+        *val = b_mul(&c, b_mul(&c, P, P), b_sub(&c, t, s2));
+        return c.out ? BND_OUT : BND_VALID;
+    }
+    bv_t chi2 = b_exact(0.0);
+    for (int j = 1; j + 1 < k; j++) {
+        unsigned before = 0;
+        for (int m = j; m < k; m++)
+            before |= 1u << ord[m];
+        bv_t eb = b_energy(&c, k, e, before);
+        bv_t ea = b_energy(&c, k, e, before & ~(1u << ord[j]));
+        BND_CHECK(b_gt(ea, 0.0, 0.0));
+        bv_t ce = b_compton_cos(&c, ea, eb);
+        BND_CHECK(b_ge(ce, -1.0));
+        BND_CHECK(b_le(ce, 1.0));
+        int p = ord[j - 1], q = ord[j], r = ord[j + 1];
+        bv_t u[3] = {b_coord_diff(&c, x, p, q), b_coord_diff(&c, y, p, q),
+                     b_coord_diff(&c, z, p, q)};
+        bv_t w[3] = {b_coord_diff(&c, x, q, r), b_coord_diff(&c, y, q, r),
+                     b_coord_diff(&c, z, q, r)};
+        bv_t dot = b_add(&c, b_add(&c, b_mul(&c, u[0], w[0]), b_mul(&c, u[1], w[1])),
+                         b_mul(&c, u[2], w[2]));
+        bv_t npq = b_sqdist(&c, x, y, z, p, q), nqr = b_sqdist(&c, x, y, z, q, r);
+        BND_CHECK(b_gt(npq, 0.0, 0.0));
+        BND_CHECK(b_gt(nqr, 0.0, 0.0));
+        bv_t il = b_mul(&c, b_rcp(&c, b_sqrt(&c, npq)), b_rcp(&c, b_sqrt(&c, nqr)));
+        bv_t d = b_sub(&c, ce, b_mul(&c, dot, il));
+        chi2 = b_add(&c, chi2, b_mul(&c, d, d));
+    }
+#undef BND_CHECK
+    *val = chi2;
+    return c.out ? BND_OUT : BND_VALID;
+}
+
+/* One order: its validity as both precisions decide it (1 valid, 0
+ * invalid, -1 undecided, -2 outside the model) and, when valid, the value
+ * (chi2, or the Klein-Nishina weight for k = 2) with its binary32 bound. */
+int or_order_bound(int k, const float *x, const float *y, const float *z,
+                   const float *e, const int *ord, double *val, double *bnd)
+{
+    bv_t v = {0.0, 0.0};
+    int b = bound_order(k, x, y, z, e, ord, &v);
+    *val = v.v;
+    *bnd = 1.001 * v.e;
+    return b;
+}
+
+/*
+ * Compare the binary32 decision with the FP64 definition on a batch of
+ * events (layout as or_rings_from_events, FP32 inputs).  Per event:
+ * rank32 / rank64 = the rank each chooses (-1: no valid order); status
+ *   0  decided: every order's validity is the same in both precisions and
+ *      the definition's winner beats every other valid order by more than
+ *      the two bounds together, so binary32 must choose the same order;
+ *   1  near tie: the winner's margin over some order is within the bounds;
+ *   2  some order's validity is within its bound of a threshold;
+ *   3  outside the model (non-finite input, or a value that might overflow
+ *      binary32 or make a divisor or radicand vanish);
+ * margin = the smallest (gap / sum of the two bounds) over the orders the
+ * winner is compared with (+inf when it has no rival).
+ */
+void or_order_check(int64_t count, int64_t stride, const uint8_t *n,
+                    const float *x, const float *y, const float *z,
+                    const float *e, int32_t *rank32, int32_t *rank64,
+                    uint8_t *status, double *margin)
+{
+    for (int64_t i = 0; i < count; i++) {
+        int k = n[i];
+        float xf[4], yf[4], zf[4], ef[4];
+        int finite = 1;
+        for (int s = 0; s < k && s < 4; s++) {
+            xf[s] = x[s * stride + i];
+            yf[s] = y[s * stride + i];
+            zf[s] = z[s * stride + i];
+            ef[s] = e[s * stride + i];
+            finite &= isfinite(xf[s]) && isfinite(yf[s]) && isfinite(zf[s]) &&
+                      isfinite(ef[s]);
+        }
+        int ord[4], r32;
+        rank32[i] = or_order_event(k, xf, yf, zf, ef, ord, &r32, NULL) ? r32 : -1;
+        rank64[i] = -1;
+        status[i] = 0;
+        margin[i] = INFINITY;
+        if (k < 2 || k > 4)
+            continue;
+        if (!finite) {
+            status[i] = 3;
+            continue;
+        }
+        rank64[i] = or_order_event_f64(k, xf, yf, zf, ef);
+
+        int a[4] = {0, 1, 2, 3}, rank = 0, nv = 0, st = 0;
+        bv_t vals[24];
+        int ok[24];
+        do {
+            int b = bound_order(k, xf, yf, zf, ef, a, &vals[rank]);
+            if (b == BND_OUT)
+                st = 3;
+            else if (b == BND_UNDECIDED && st < 2)
+                st = 2;
+            ok[rank] = b == BND_VALID;
+            nv += ok[rank];
+            rank++;
+        } while (next_permutation(a, k));
+        if (st == 0 && rank64[i] >= 0) {
+            int w = rank64[i];
+            double m = INFINITY;
+            for (int o = 0; o < rank; o++) {
+                if (o == w || !ok[o])
+                    continue;
+                /* k = 2: the larger weight wins; k >= 3: the smaller chi2 */
+                double gap = k == 2 ? vals[w].v - vals[o].v : vals[o].v - vals[w].v;
+                double bnd = 1.001 * (vals[w].e + vals[o].e);
+                double r = bnd > 0.0 ? gap / bnd : (gap > 0.0 ? INFINITY : 0.0);
+                if (r < m)
+                    m = r;
+            }
+            margin[i] = m;
+            if (!(m > 1.0))
+                st = 1;
+        }
+        status[i] = (uint8_t)st;
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -34,6 +34,33 @@ float or_kn_weight_f32(float P, float cos_eta);
 float or_order_chi2(int k, const float *x, const float *y, const float *z,
                     const float *e, const int *order);
 
+/* The ordering rule's definition evaluated plainly in FP64 on the same FP32
+ * inputs (no shared subexpressions with the binary32 sequence): the chi2 of
+ * one order (+inf when invalid; 0 for a valid 2-site order), the
+ * Klein-Nishina weight, and the chosen rank (-1: no valid order). */
+double or_order_chi2_f64(int k, const float *x, const float *y,
+                         const float *z, const float *e, const int *order);
+double or_kn_weight_f64(double P, double cos_eta);
+int or_order_event_f64(int k, const float *x, const float *y, const float *z,
+                       const float *e);
+
+/* One order's validity in both precisions (1 valid, 0 invalid, -1 within a
+ * bound of a threshold, -2 outside the model) and, when valid, its chi2 (the
+ * Klein-Nishina weight for k = 2) in FP64 with the bound on binary32's
+ * rounding of it. */
+int or_order_bound(int k, const float *x, const float *y, const float *z,
+                   const float *e, const int *order, double *val, double *bnd);
+
+/* Binary32 decision against the FP64 definition on a batch of events (FP32
+ * inputs, layout of or_rings_from_events), with a rigorous bound on the
+ * binary32 rounding of every order's chi2 (see oracle.c).  status: 0 decided
+ * (the two ranks must agree), 1 near tie within the bounds, 2 a validity
+ * threshold within its bound, 3 outside the model (non-finite or overflow). */
+void or_order_check(int64_t count, int64_t stride, const uint8_t *n,
+                    const float *x, const float *y, const float *z,
+                    const float *e, int32_t *rank32, int32_t *rank64,
+                    uint8_t *status, double *margin);
+
 /* Rings from events (ordering, cone axis, opening angle, width). */
 void or_rings_from_events(int64_t count, int64_t stride, const uint8_t *n,
                           const double *x, const double *y, const double *z,

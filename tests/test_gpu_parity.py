@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2411_04785_gb300 import synth
 from tests.helpers import (EPS32, REFINE_TOL_DEG, ang_deg, eta_tol, grid32, grid_to_dev,
-                           map_violations, rings_to_dev, to_dev)
+                           extreme_events, map_violations, rings_to_dev, to_dev)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -171,57 +171,6 @@ def test_rings_many_windows_and_misaligned(cc, dev):
     cc.rings_from_events(n, x, y, z, e, p, out)
     torch.cuda.synchronize()
     check_rings({k: v.cpu().numpy() for k, v in out.items()}, want, ev)
-
-
-def extreme_events(N, seed):
-    """Events built to reach every branch of the binary32 ordering rule:
-    log-uniform magnitudes from 1e-40 to 1e38 with random signs (subnormal,
-    overflowing and negative deposits and distances), zeros, infinities and
-    NaNs, nearly coincident and coincident pairs, and mirror-symmetric 3-site
-    tracks with equal end deposits, whose two directions have bitwise equal
-    chi2 (the lower rank must win)."""
-    rng = np.random.default_rng(seed)
-    n = rng.integers(2, 5, N).astype(np.uint8)
-    kind = rng.integers(0, 6, N)
-    ev = {k: rng.normal(0.0, 10.0, (4, N)).astype(np.float32) for k in "xyz"}
-    ev["e"] = rng.uniform(20.0, 800.0, (4, N)).astype(np.float32)
-    ev["n"] = n
-
-    def logu(lo, hi, shape):
-        return (10.0 ** rng.uniform(lo, hi, shape)) * rng.choice([-1.0, 1.0], shape)
-
-    m = kind == 0                          # wild magnitudes everywhere
-    for k in "xyz":
-        ev[k][:, m] = logu(-40, 38, (4, m.sum())).astype(np.float32)
-    ev["e"][:, m] = np.abs(logu(-40, 38, (4, m.sum()))).astype(np.float32)
-    m = kind == 1                          # wild deposits, some negative or zero
-    ev["e"][:, m] = logu(-42, 38, (4, m.sum())).astype(np.float32)
-    ev["e"][:, m & (rng.random(N) < 0.2)] = 0.0
-    m = np.flatnonzero(kind == 2)          # one pair nearly or exactly coincident
-    d = (10.0 ** rng.uniform(-45, -3, m.size)) * rng.choice([0.0, 1.0, 1.0, 1.0], m.size)
-    for k in "xyz":
-        ev[k][1, m] = (ev[k][0, m] + d).astype(np.float32)
-    m = np.flatnonzero(kind == 3)          # mirror-symmetric 3-site tracks
-    ev["n"][m] = 3
-    c = rng.normal(0.0, 10.0, (3, m.size))
-    u = rng.normal(0.0, 2.0, (3, m.size))
-    pts = np.stack([c - u, c, c + u])      # [site, coord, event], exact in FP32 below
-    pts = np.round(pts * 64.0) / 64.0
-    ends = rng.uniform(50.0, 400.0, m.size).astype(np.float32)
-    mid = rng.uniform(50.0, 400.0, m.size).astype(np.float32)
-    for j, ev_i in enumerate(m):
-        slots = rng.permutation(3)        # which slot holds which site
-        for s_i, site in enumerate(slots):
-            for a, k in enumerate("xyz"):
-                ev[k][s_i, ev_i] = pts[site, a, j]
-            ev["e"][s_i, ev_i] = mid[j] if site == 1 else ends[j]
-    m = kind == 4                          # infinities and NaNs
-    bad = rng.choice(np.array([np.inf, -np.inf, np.nan], np.float32), (4, m.sum()))
-    which = rng.integers(0, 4, m.sum())
-    arr = ev[("x", "y", "z", "e")[int(rng.integers(0, 4))]]
-    arr[which, np.flatnonzero(m)] = bad[which, np.arange(m.sum())]
-    ev["sym"] = np.setdiff1d(np.flatnonzero(kind == 3), np.flatnonzero(m))
-    return ev
 
 
 def test_rings_order_extremes(cc, dev):

@@ -211,6 +211,173 @@ def test_klein_nishina_weight_integrates_to_total_cross_section(kappa):
 
 
 # --------------------------------------------------------------------------
+# Ordering: the binary32 decision against the FP64 definition
+# --------------------------------------------------------------------------
+def _exact_chi2(pos, dep, order):
+    """chi2 of one order from the FP32 inputs in 50-digit arithmetic: sums,
+    differences and products of the inputs are exact rationals, and only the
+    segment lengths are square roots (exact integers on the tracks below,
+    wherever the order follows the track)."""
+    import mpmath as mp
+    from fractions import Fraction as F
+    mp.mp.dps = 50
+    me = F("510.99895")
+    E = [F(float(v)) for v in dep]
+    P = [[F(float(c)) for c in p] for p in pos]
+    chi2 = mp.mpf(0)
+    for j in range(1, len(order) - 1):
+        eb = sum(E[order[m]] for m in range(j, len(order)))
+        ea = eb - E[order[j]]
+        ce = 1 - me * (1 / ea - 1 / eb)
+        p, q, r = (P[order[i]] for i in (j - 1, j, j + 1))
+        d1 = [b - a for a, b in zip(p, q)]
+        d2 = [b - a for a, b in zip(q, r)]
+        dot = sum(a * b for a, b in zip(d1, d2))
+        nn = sum(v * v for v in d1) * sum(v * v for v in d2)
+        n1n2 = mp.sqrt(mp.mpf(nn.numerator) / nn.denominator)
+        cg = mp.mpf(dot.numerator) / dot.denominator / n1n2
+        chi2 += (mp.mpf(ce.numerator) / ce.denominator - cg) ** 2
+    return chi2
+
+
+def test_order_chi2_f64_closed_forms():
+    """The FP64 definition on tracks with integer segment lengths: a right
+    angle whose chi2 is (1 - 510.99895/511)^2 in closed form, a 3-4-5 turn
+    (cos_G = 3/5) and a 4-site track of two Pythagorean turns; every order
+    of each against a 50-digit evaluation, to 1e-14 in sqrt(chi2) (FP64
+    rounding of each residual)."""
+    cases = [
+        ([(0, 0, 0), (3, 0, 0), (3, 4, 0)], [255.5, 255.5, 255.5]),
+        ([(0, 0, 0), (5, 0, 0), (8, 4, 0)], [300.0, 420.0, 180.0]),
+        ([(1, 2, 3), (1, 2, 15), (4, 6, 15), (4, 6, 27)], [100.0, 250.0, 75.0, 320.0]),
+    ]
+    # the right angle along the track: cos_G = 0 exactly, cos_E = 1 - m/511
+    x, y, z = (np.array([p[c] for p in cases[0][0]], np.float32) for c in range(3))
+    got = oracle.order_chi2_f64(x, y, z, np.array(cases[0][1], np.float32), [0, 1, 2])
+    assert math.sqrt(got) == pytest.approx(1.0 - ME / 511.0, abs=1e-15)
+    for pos, dep in cases:
+        k = len(dep)
+        x, y, z = (np.array([p[c] for p in pos], np.float32) for c in range(3))
+        e = np.array(dep, np.float32)
+        for order in PERMS[k]:
+            got = oracle.order_chi2_f64(x, y, z, e, list(order))
+            try:
+                want = float(_exact_chi2(pos, dep, order))
+            except ZeroDivisionError:
+                want = math.inf
+            # the definition's invalid orders (no energy after a site,
+            # |cos_E| > 1) are +inf; the exact value is then irrelevant
+            if not math.isfinite(got):
+                continue
+            # each residual cos_E - cos_G carries FP64 rounding of ~1e-16
+            # absolute; compare the root of the sum of their squares
+            assert abs(math.sqrt(got) - math.sqrt(want)) < 1e-14
+
+
+def test_order_f64_picks_the_simulated_order_on_noise_free_tracks():
+    """On noise-free simulated 3- and 4-site tracks (FP32 inputs) the FP64
+    definition's choice is the simulated order, all but a few degenerate
+    events; the binary32 decision agrees wherever the bound decides."""
+    ev = synth.simulate_events(n_src=3000, n_bkg=0, seed=23, sigma_e_frac=0.0,
+                               sigma_pos_cm=0.0)
+    chk = oracle.order_check(ev)
+    k34 = ev["n"] >= 3
+    truth = np.array([PERMS[k].index(tuple(int(v) for v in ev["order"][i][:k]))
+                      for i, k in enumerate(ev["n"])])
+    assert (chk["rank64"][k34] == truth[k34]).mean() > 0.995
+    dec = chk["status"] == oracle.ORDER_DECIDED
+    np.testing.assert_array_equal(chk["rank32"][dec], chk["rank64"][dec])
+
+
+def test_kn_weight_f64_integrates_to_total_cross_section():
+    c = np.linspace(-1, 1, 200001)
+    for kappa in (0.2, 1.0, 3.0):
+        P = 1.0 / (1.0 + kappa * (1.0 - c))
+        w = np.array([oracle.kn_weight_f64(p, cc) for p, cc in zip(P[::50], c[::50])])
+        integral = 2 * math.pi * np.trapezoid(w, c[::50])
+        k = kappa
+        L = math.log(1 + 2 * k)
+        sigma = 2 * math.pi * ((1 + k) / k ** 2 * (2 * (1 + k) / (1 + 2 * k) - L / k)
+                               + L / (2 * k) - (1 + 3 * k) / (1 + 2 * k) ** 2)
+        assert integral == pytest.approx(2 * sigma, rel=2e-4)
+
+
+def test_binary32_bound_holds_for_every_order():
+    """The bound the oracle derives on binary32's rounding of each order's
+    chi2 (the Klein-Nishina weight for 2 sites) contains the binary32
+    sequence's actual value for every valid order of 6,000 simulated
+    events, and it is tight enough to decide: its median is below 1e-5 of
+    the value wherever the value exceeds 1e-3."""
+    ev = synth.simulate_events(n_src=1000, n_bkg=5000, seed=41)
+    rel = []
+    checked = 0
+    for i in range(ev["n"].size):
+        k = int(ev["n"][i])
+        x, y, z, e = (np.asarray(ev[c][:k, i], np.float32) for c in "xyze")
+        e0 = np.float32(e.sum(dtype=np.float32))
+        for order in PERMS[k]:
+            st, val, bnd = oracle.order_bound(x, y, z, e, list(order))
+            c32 = oracle.order_chi2(x, y, z, e, list(order))
+            assert (st == 1) == np.isfinite(c32) or st < 0
+            if st != 1:
+                continue
+            if k == 2:
+                e2 = np.float32(0.0) + e[order[1]]
+                e0 = (np.float32(0.0) + e[0]) + e[1]
+                ce = np.float32(1.0) - np.float32(oracle.ME_KEV) * (
+                    np.float32(1.0) / e2 - np.float32(1.0) / e0)
+                got = oracle.kn_weight_f32(np.float32(e2 / e0), ce)
+            else:
+                got = c32
+            assert abs(float(got) - val) <= bnd, (i, order, got, val, bnd)
+            checked += 1
+            if abs(val) > 1e-3:
+                rel.append(bnd / abs(val))
+    assert checked > 10000
+    assert np.median(rel) < 1e-5
+
+
+def _order_report(name, chk):
+    st = np.bincount(chk["status"], minlength=4)
+    print(f"\n{name}: {st[0]} decided, {st[1]} near ties, {st[2]} near a validity "
+          f"threshold, {st[3]} outside the model; ranks differ on "
+          f"{int((chk['rank32'] != chk['rank64']).sum())} events in all")
+    return st
+
+
+def test_binary32_decision_is_the_fp64_argmin_event_workload():
+    """The 200,000 events of the event workload: on every event the bound
+    decides (the FP64 winner's chi2 margin over every other valid order
+    exceeds both orders' binary32 bounds, every validity threshold is
+    cleared by more than its bound), the binary32 decision is the FP64
+    definition's argmin; fewer than 0.1 % of the events are left undecided."""
+    ev = synth.simulate_events(n_src=18182, n_bkg=181818, seed=2)
+    chk = oracle.order_check(ev)
+    st = _order_report("event workload", chk)
+    dec = chk["status"] == oracle.ORDER_DECIDED
+    np.testing.assert_array_equal(chk["rank32"][dec], chk["rank64"][dec])
+    assert st[3] == 0
+    assert (~dec).mean() < 1e-3
+
+
+def test_binary32_decision_is_the_fp64_argmin_extremes():
+    """The 60,000 extreme and degenerate events of the GPU ordering test
+    (magnitudes from 1e-40 to 1e38, zeros, negative deposits, infinities,
+    NaNs, coincident pairs, mirror-symmetric tracks): on every event the
+    bound decides, the binary32 decision is the FP64 argmin.  Most of the
+    rest lies outside the binary32 range or on an exact tie, which the
+    lowest-rank rule settles in both precisions alike."""
+    from tests.helpers import extreme_events
+    ev = extreme_events(60000, 91)
+    with np.errstate(all="ignore"):
+        chk = oracle.order_check(ev)
+    st = _order_report("extreme events", chk)
+    dec = chk["status"] == oracle.ORDER_DECIDED
+    np.testing.assert_array_equal(chk["rank32"][dec], chk["rank64"][dec])
+    assert dec.sum() > 15000 and (chk["rank64"][dec] >= 0).sum() > 8000
+
+
+# --------------------------------------------------------------------------
 # Ring width
 # --------------------------------------------------------------------------
 def _ring_stats(sig_e, sig_pos, n_draw=6000, seed=3):
