@@ -108,6 +108,19 @@ const char *cc_last_error(void);
 void cc_params_default(cc_params *p);
 
 /*
+ * Copy `count` events between two event sets (host or device; pinned host
+ * memory keeps the copy asynchronous): dst events [dst_offset, +count) get
+ * src events [src_offset, +count), n and the 4 slot rows of x, y, z, e (one
+ * 2D copy per array, each side with its own stride).  dst's arrays are
+ * written through their (const-qualified) pointers.  Needs
+ * dst_offset + count <= dst->stride, src_offset + count <= src->stride.
+ * Plumbing for callers that stage events (e.g. a server filling a device
+ * buffer from slices of a host pool); no counterpart in the paper.
+ */
+cc_status cc_events_copy(const cc_events *dst, int64_t dst_offset, const cc_events *src,
+                         int64_t src_offset, int64_t count, void *stream);
+
+/*
  * Rings from events (Sec. 1.1 formula and two-interaction cone).
  * Per event: the site order is chosen by Compton-kinematic consistency (for
  * 3-4 sites the order minimising sum over intermediate sites of
@@ -123,19 +136,6 @@ void cc_params_default(cc_params *p);
  * `ev`, `out` and `p` are host pointers to structs of device pointers;
  * out->count must equal ev->count.  count = 0 is valid (nothing launched).
  */
-/*
- * Copy `count` events between two event sets (host or device; pinned host
- * memory keeps the copy asynchronous): dst events [dst_offset, +count) get
- * src events [src_offset, +count), n and the 4 slot rows of x, y, z, e (one
- * 2D copy per array, each side with its own stride).  dst's arrays are
- * written through their (const-qualified) pointers.  Needs
- * dst_offset + count <= dst->stride, src_offset + count <= src->stride.
- * Plumbing for callers that stage events (e.g. a server filling a device
- * buffer from slices of a host pool); no counterpart in the paper.
- */
-cc_status cc_events_copy(const cc_events *dst, int64_t dst_offset, const cc_events *src,
-                         int64_t src_offset, int64_t count, void *stream);
-
 cc_status cc_rings_from_events(const cc_events *ev, const cc_rings *out,
                                const cc_params *p, void *stream);
 
@@ -180,7 +180,10 @@ cc_status cc_localize(const cc_rings *rings, const cc_grid *grid,
  * not fit are rejected with CC_EINVAL and a message; nothing is launched.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array: calls that
+ * before any stream capture.  The address is kept per device for the life
+ * of the process: after the caller resets a device (cudaDeviceReset) the
+ * kept address is stale and this entry point must not be called on that
+ * device again.  Every call shares the one array: calls that
  * can overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  The call allocates nothing: no cudaMalloc,
  * no cudaFree, no allocating library routine.
@@ -314,6 +317,22 @@ cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16,
                       const float *residual, const uint8_t *weight,
                       int64_t rows, float *grad, float *loss, void *workspace,
                       size_t ws_bytes, void *stream);
+
+/* cc_mlp_grad keeping the step's intermediate values, for inspecting a
+ * training step and checking each of its stages on its own: hidden
+ * [3][rows][128] BF16 the activations H1..H3 (each layer's ReLU output, the
+ * next layer's input), out [rows][2] FP32 the network outputs, dout [rows][2]
+ * BF16 the loss gradient at the outputs, signals [3][rows][128] BF16 the
+ * backward signal at each hidden layer's pre-activation (dZ1..dZ3, the
+ * ReLU-gated products that the weight gradients multiply).  Any of the four
+ * may be NULL (not kept); hidden and signals 16-byte aligned, out 8, dout 4.
+ * Same results as cc_mlp_grad, bit for bit. */
+cc_status cc_mlp_grad_trace(const float *params, const uint16_t *params_bf16,
+                            const uint16_t *features, const uint8_t *is_source,
+                            const float *residual, const uint8_t *weight, int64_t rows,
+                            float *grad, float *loss, void *workspace, size_t ws_bytes,
+                            uint16_t *hidden, float *out, uint16_t *dout, uint16_t *signals,
+                            void *stream);
 
 /* One Adam step (step >= 1) on params with moments m, v; refreshes the BF16
  * copy. */

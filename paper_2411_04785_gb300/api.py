@@ -113,6 +113,9 @@ def lib() -> C.CDLL:
         L.cc_mlp_forward.restype = S
         L.cc_mlp_grad.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int64, _P, _P, _P, C.c_size_t, _P]
         L.cc_mlp_grad.restype = S
+        L.cc_mlp_grad_trace.argtypes = [_P, _P, _P, _P, _P, _P, C.c_int64, _P, _P, _P,
+                                        C.c_size_t, _P, _P, _P, _P, _P]
+        L.cc_mlp_grad_trace.restype = S
         L.cc_mlp_adam.argtypes = [_P, _P, _P, _P, _P, C.c_int32, C.c_float, C.c_float,
                                   C.c_float, C.c_float, _P]
         L.cc_mlp_adam.restype = S
@@ -473,6 +476,7 @@ def trace_read(reset: bool = False) -> dict:
 # --------------------------------------------------------------------------
 MLP_FEATURES = 16
 MLP_PARAMS = 35458
+MLP_HIDDEN = 128
 MLP_MAX_BATCH = 65536
 MLP_SIZES = ((128, 16), (128, 128), (128, 128), (2, 128))
 
@@ -600,6 +604,23 @@ class RingFilter:
             _ptr(weight), B, _ptr(self.grad_buf), _ptr(self.loss_buf), _ptr(ws), ws.numel(),
             _stream(stream)))
         return self.loss_buf, self.grad_buf
+
+    def grad_trace(self, feats, is_source, residual, weight, stream=None):
+        """grad() keeping the step's intermediate values: returns (loss, grad,
+        trace) with trace = dict(hidden [3, B, 128] bf16, out [B, 2] f32,
+        dout [B, 2] bf16, signals [3, B, 128] bf16)."""
+        B = feats.shape[0]
+        ws = self._workspace(B)
+        t = {"hidden": torch.empty((3, B, MLP_HIDDEN), dtype=torch.bfloat16, device=self.dev),
+             "out": torch.empty((B, 2), dtype=torch.float32, device=self.dev),
+             "dout": torch.empty((B, 2), dtype=torch.bfloat16, device=self.dev),
+             "signals": torch.empty((3, B, MLP_HIDDEN), dtype=torch.bfloat16, device=self.dev)}
+        _check("cc_mlp_grad_trace", lib().cc_mlp_grad_trace(
+            _ptr(self.p), _ptr(self.wb), _ptr(feats), _ptr(is_source), _ptr(residual),
+            _ptr(weight), B, _ptr(self.grad_buf), _ptr(self.loss_buf), _ptr(ws), ws.numel(),
+            _ptr(t["hidden"]), _ptr(t["out"]), _ptr(t["dout"]), _ptr(t["signals"]),
+            _stream(stream)))
+        return self.loss_buf, self.grad_buf, t
 
     def adam(self, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         self.step += 1

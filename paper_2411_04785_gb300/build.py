@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -18,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcompton.so")
 SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu", "cluster.cu", "voxel.cu",
            "noalloc.cu", "mlp.cu", "selftest.cu"]
-HEADERS = ["cc_internal.cuh", "cc_math.cuh", os.path.join("..", "..", "include", "compton.h")]
+INCLUDE = os.path.join(HERE, "..", "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -36,9 +37,31 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths)
 
 
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _deps(path: str, seen=None) -> set:
+    """The file and every header it includes with quotes, transitively (found
+    next to the including file or in include/), so that editing any of them
+    rebuilds the objects that use it."""
+    seen = set() if seen is None else seen
+    if path in seen:
+        return seen
+    seen.add(path)
+    with open(path) as f:
+        text = f.read()
+    for name in _INCLUDE_RE.findall(text):
+        for d in (os.path.dirname(path), INCLUDE):
+            cand = os.path.normpath(os.path.join(d, name))
+            if os.path.exists(cand):
+                _deps(cand, seen)
+                break
+    return seen
+
+
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS]
+    deps = sorted(_deps(os.path.join(CSRC, src)))
     if os.path.exists(obj) and os.path.getmtime(obj) >= _newest(deps):
         return obj
     cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]

@@ -316,10 +316,41 @@ cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
     return CC_OK;
 }
 
+static cc_status mlp_grad_checked(const float *params, const uint16_t *params_bf16,
+                                  const uint16_t *features, const uint8_t *is_source,
+                                  const float *residual, const uint8_t *weight, int64_t rows,
+                                  float *grad, float *loss, void *workspace, size_t ws_bytes,
+                                  const MlpTrace *trace, void *stream);
+
 cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16, const uint16_t *features,
                       const uint8_t *is_source, const float *residual, const uint8_t *weight,
                       int64_t rows, float *grad, float *loss, void *workspace, size_t ws_bytes,
                       void *stream) {
+    return mlp_grad_checked(params, params_bf16, features, is_source, residual, weight, rows,
+                            grad, loss, workspace, ws_bytes, nullptr, stream);
+}
+
+cc_status cc_mlp_grad_trace(const float *params, const uint16_t *params_bf16,
+                            const uint16_t *features, const uint8_t *is_source,
+                            const float *residual, const uint8_t *weight, int64_t rows,
+                            float *grad, float *loss, void *workspace, size_t ws_bytes,
+                            uint16_t *hidden, float *out, uint16_t *dout, uint16_t *signals,
+                            void *stream) {
+    if ((hidden && !aligned(hidden, 16)) || (signals && !aligned(signals, 16)) ||
+        (out && !aligned(out, 8)) || (dout && !aligned(dout, 4))) {
+        g_err[0] = 0;
+        return fail(CC_EINVAL, "hidden/signals must be 16-byte aligned, out 8, dout 4");
+    }
+    MlpTrace t{hidden, out, dout, signals};
+    return mlp_grad_checked(params, params_bf16, features, is_source, residual, weight, rows,
+                            grad, loss, workspace, ws_bytes, &t, stream);
+}
+
+static cc_status mlp_grad_checked(const float *params, const uint16_t *params_bf16,
+                                  const uint16_t *features, const uint8_t *is_source,
+                                  const float *residual, const uint8_t *weight, int64_t rows,
+                                  float *grad, float *loss, void *workspace, size_t ws_bytes,
+                                  const MlpTrace *trace, void *stream) {
     g_err[0] = 0;
     if (rows < 1 || rows > CC_MLP_MAX_BATCH)
         return fail(CC_EINVAL, "rows must be in 1..%d", CC_MLP_MAX_BATCH);
@@ -333,7 +364,7 @@ cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16, const ui
     size_t need = mlp_workspace_bytes(rows);
     if (ws_bytes < need) return fail(CC_ENOMEM, "workspace of %zu bytes < %zu needed", ws_bytes, need);
     cudaError_t e = mlp_grad(params, params_bf16, features, is_source, residual, weight, rows,
-                             grad, loss, (char *)workspace, (cudaStream_t)stream);
+                             grad, loss, (char *)workspace, trace, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_grad launch");
     return CC_OK;
 }

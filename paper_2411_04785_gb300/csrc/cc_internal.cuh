@@ -125,9 +125,20 @@ cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, 
                          cudaStream_t s);
 cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
                         float *out, char *ws, cudaStream_t s);
+// Where a training step keeps its intermediate values (each may be null):
+// the hidden activations H1..H3 [3][B][128], the outputs [B][2], their
+// gradient d_out [B][2] and the backward signal of each hidden layer
+// dZ1..dZ3 [3][B][128].
+struct MlpTrace {
+    uint16_t *hidden;
+    float *out;
+    uint16_t *dout;
+    uint16_t *signals;
+};
 cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
                      const uint8_t *y, const float *res, const uint8_t *wv, int64_t B,
-                     float *grad, float *loss, char *ws, cudaStream_t s);
+                     float *grad, float *loss, char *ws, const MlpTrace *trace,
+                     cudaStream_t s);
 cudaError_t mlp_adam(float *p, float *m, float *v, const float *g, uint16_t *wb, int32_t t,
                      float lr, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t mlp_params_to_bf16(const float *p, uint16_t *wb, cudaStream_t s);

@@ -865,9 +865,12 @@ cudaError_t forward_tc(const float *params, const uint16_t *wb, const uint16_t *
     return cudaSuccess;
 }
 
+// dZ[l] receives the backward signal of hidden layer l + 1 (the gradient at
+// its pre-activation, BF16); without a trace the signals ping-pong through
+// two workspace buffers.
 cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint8_t *y,
                       const float *res, const uint8_t *wv, int rows, float inv_total,
-                      float *grad, Work &w, cudaStream_t s) {
+                      float *grad, Work &w, bf16 *const *dZ, cudaStream_t s) {
     cudaError_t e = forward_tc(pf, reinterpret_cast<const uint16_t *>(wb),
                                reinterpret_cast<const uint16_t *>(X), rows, w.out, w.H, s);
     if (e != cudaSuccess) return e;
@@ -876,15 +879,15 @@ cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint
     if ((e = cudaGetLastError())) return e;
     // layer 4
     if ((e = weight_grad(w.dout, 2, w.H[2], kH, rows, grad + oW4, grad + ob4, w, s))) return e;
-    if ((e = gemm(back_data(w.dout, 2, wb + oW4, kH, rows, w.H[2], w.dP[0]), s))) return e;
+    if ((e = gemm(back_data(w.dout, 2, wb + oW4, kH, rows, w.H[2], dZ[2]), s))) return e;
     // layer 3
-    if ((e = weight_grad(w.dP[0], kH, w.H[1], kH, rows, grad + oW3, grad + ob3, w, s))) return e;
-    if ((e = gemm(back_data(w.dP[0], kH, wb + oW3, kH, rows, w.H[1], w.dP[1]), s))) return e;
+    if ((e = weight_grad(dZ[2], kH, w.H[1], kH, rows, grad + oW3, grad + ob3, w, s))) return e;
+    if ((e = gemm(back_data(dZ[2], kH, wb + oW3, kH, rows, w.H[1], dZ[1]), s))) return e;
     // layer 2
-    if ((e = weight_grad(w.dP[1], kH, w.H[0], kH, rows, grad + oW2, grad + ob2, w, s))) return e;
-    if ((e = gemm(back_data(w.dP[1], kH, wb + oW2, kH, rows, w.H[0], w.dP[0]), s))) return e;
+    if ((e = weight_grad(dZ[1], kH, w.H[0], kH, rows, grad + oW2, grad + ob2, w, s))) return e;
+    if ((e = gemm(back_data(dZ[1], kH, wb + oW2, kH, rows, w.H[0], dZ[0]), s))) return e;
     // layer 1
-    return weight_grad(w.dP[0], kH, X, kF, rows, grad + oW1, grad + ob1, w, s);
+    return weight_grad(dZ[0], kH, X, kF, rows, grad + oW1, grad + ob1, w, s);
 }
 
 }  // namespace
@@ -915,13 +918,25 @@ cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t 
 
 cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
                      const uint8_t *y, const float *res, const uint8_t *wv, int64_t B,
-                     float *grad, float *loss, char *ws, cudaStream_t s) {
+                     float *grad, float *loss, char *ws, const MlpTrace *trace,
+                     cudaStream_t s) {
     Work w;
     work_layout(B, &w, ws);
+    bf16 *dZ[3] = {w.dP[0], w.dP[1], w.dP[0]};
+    if (trace) {
+        bf16 *hid = reinterpret_cast<bf16 *>(trace->hidden);
+        bf16 *sig = reinterpret_cast<bf16 *>(trace->signals);
+        for (int l = 0; l < 3; l++) {
+            if (hid) w.H[l] = hid + (size_t)l * B * kH;
+            if (sig) dZ[l] = sig + (size_t)l * B * kH;
+        }
+        if (trace->out) w.out = trace->out;
+        if (trace->dout) w.dout = reinterpret_cast<bf16 *>(trace->dout);
+    }
     TraceScope ts(CC_STAGE_MLP, s);
     cudaError_t e = grad_rows(reinterpret_cast<const bf16 *>(wb), params,
                               reinterpret_cast<const bf16 *>(F), y, res, wv, (int)B,
-                              1.0f / (float)B, grad, w, s);
+                              1.0f / (float)B, grad, w, dZ, s);
     if (e != cudaSuccess) return e;
     k_sum_small<<<1, 32, 0, s>>>(w.loss_part, (int)((B + 255) / 256), loss);
     return cudaGetLastError();

@@ -335,9 +335,11 @@ def sample_dirs(M, am, grid, extra=(), n=256, radius_deg=2.0, seed=0):
     return idx.astype(np.int64), near
 
 
-def test_map_event_workload_sampled(cc, dev):
-    """200k simulated events -> oracle rings (FP32) x HEALPix nside 64:
-    sampled directions plus the argmax neighbourhood."""
+def test_map_event_workload_full(cc, dev):
+    """200k simulated events -> oracle rings (FP32) x HEALPix nside 64: every
+    one of the 49,152 directions under the map rule against the oracle's full
+    FP64 map, and the GPU's argmax the oracle's global maximum up to ties
+    (its oracle value within twice the map tolerance of the maximum)."""
     ev = synth.simulate_events(seed=2)
     p = cc.Params()
     r = oracle.rings_from_events(ev, p.sigma_e_frac, p.sigma_pos_cm, p.deta_min, p.deta_max)
@@ -345,14 +347,12 @@ def test_map_event_workload_sampled(cc, dev):
     grid = grid32(oracle.grid_healpix_ring(64))
     got, am, _, st = run_localize(cc, rings, grid, dev)
     assert st == 0
-    idx, near = sample_dirs(grid[0].size, am, grid)
-    want = oracle.likelihood_map(rings, grid, idx=idx)
+    want = oracle.likelihood_map(rings, grid)
     ref_max = want.max()
-    bad = map_violations(got[idx], want, ref_max)
-    assert bad.size == 0, f"{bad.size} of {idx.size} off"
-    wn = dict(zip(idx.tolist(), want))
-    tol = 1e-5 * ref_max
-    assert wn[am] >= max(wn[j] for j in near) - 2 * tol
+    bad = map_violations(got, want, ref_max)
+    assert bad.size == 0, f"{bad.size} of {want.size} off"
+    assert want[am] >= ref_max - 2 * 1e-5 * ref_max
+    assert am == int(np.argmax(got))
     assert ang_deg([grid[0][am], grid[1][am], grid[2][am]], ev["source"]) < 3.0
 
 
@@ -458,8 +458,27 @@ def test_end_to_end_event_workload(cc, dev):
                                   tol_rad=1e-10)
     gd = loc.dir.cpu().numpy()
     assert ang_deg(gd, od) < REFINE_TOL_DEG
-    # the plain method's maximum on this burst lies ~1.5 deg from the source
-    assert ang_deg(gd, ev["source"]) < 3.0
+    # where the likelihood peaks is the method's, not the GPU's: the GPU's
+    # distance to the true source is the oracle's own, to the parity bound
+    err_gpu, err_or = ang_deg(gd, ev["source"]), ang_deg(od, ev["source"])
+    print(f"\nplain method, event workload: {err_gpu:.3f} deg from the source "
+          f"(oracle {err_or:.3f} deg; target 0.5 deg)")
+    assert abs(err_gpu - err_or) < REFINE_TOL_DEG
+
+
+@pytest.mark.xfail(strict=True, reason="the plain method's likelihood peaks ~1.46 deg from "
+                   "the source on the event workload (background 10:1); the 0.5 deg target "
+                   "is not reached by it")
+def test_plain_method_reaches_half_a_degree_on_event_workload(cc, dev):
+    """The accuracy target on the event workload, for the plain method: an
+    explicit, visible gap (strict: it fails loudly once it passes)."""
+    ev = synth.simulate_events(seed=2)
+    gnp = grid32(oracle.grid_healpix_ring(64))
+    loc = cc.Localizer(grid_to_dev(gnp, dev), cc.Params())
+    x, y, z, e = (to_dev(np.asarray(ev[k], np.float32), dev) for k in "xyze")
+    loc.from_events(to_dev(ev["n"], dev), x, y, z, e)
+    torch.cuda.synchronize()
+    assert ang_deg(loc.dir.cpu().numpy(), ev["source"]) <= 0.5
 
 
 # --------------------------------------------------------------------------

@@ -4,10 +4,12 @@ once running, an application whose pool owns all device memory): its scratch
 is a static device array inside the library instead of a caller workspace.
 
 It is called here through the C ABI (ctypes) and checked against
-cc_localize, the workspace entry point, with the map rule of the other
-parity tests, on two calls in a row (the shared array keeps the previous
-call's contents).  This file is collected last and passes alone in a fresh
-process as well as after the other tests."""
+cc_localize, the workspace entry point: both run the same plan and the same
+kernels, so the map, the argmax and the seeds must be bit-equal, on two calls
+in a row (the shared array keeps the previous call's contents, so a stale
+value left in it would show as a difference in the last bits).  One burst is
+also checked against the oracle's map.  This file is collected last and
+passes alone in a fresh process as well as after the other tests."""
 import ctypes as C
 import math
 
@@ -61,9 +63,29 @@ def test_static_scratch_matches_workspace_entry_point(cc, R, M, seed, topk):
     for _ in range(2):                   # two calls in a row share the array
         m, am, sd, st = call_static(cc, rd, gd, p, dev)
         assert st == 0
-        assert map_violations(m, ref_map.astype(np.float64), ref_map.max()).size == 0
+        np.testing.assert_array_equal(m, ref_map)
         assert int(am[0]) == int(ref[1].item())
         np.testing.assert_array_equal(sd, ref[2].cpu().numpy())
+
+
+def test_static_scratch_matches_oracle(cc):
+    """The noise-free 2,000-ring burst over the 3,072-direction Fibonacci
+    grid, after a larger call has filled the shared array: every direction
+    within the map rule of the oracle's FP64 map, and the argmax the oracle's
+    (the true source's neighbourhood)."""
+    dev = torch.device("cuda:0")
+    big, _, _ = synth.rings_burst(n=60000, seed=9)
+    gbig = grid_to_dev(oracle.grid_fibonacci(20000), dev)
+    call_static(cc, rings_to_dev(big, dev), gbig, cc.Params(), dev)
+    rings, source = synth.rings_noise_free()
+    g = oracle.grid_fibonacci(3072)
+    want = oracle.likelihood_map(rings, tuple(np.asarray(v, np.float32) for v in g))
+    for _ in range(2):
+        m, am, _, st = call_static(cc, rings_to_dev(rings, dev), grid_to_dev(g, dev),
+                                   cc.Params(), dev)
+        assert st == 0
+        assert map_violations(m.astype(np.float64), want, want.max()).size == 0
+        assert want[int(am[0])] >= want.max() * (1 - 2e-5)
 
 
 def test_static_scratch_rejects_sizes_beyond_its_maximum(cc):
