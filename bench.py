@@ -142,70 +142,83 @@ def max_over_ranks(pg, v, dev=None):
 # --------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # --------------------------------------------------------------------------
-def oracle_step(ev, rings_needed=True, n_dirs=None, budget_s=10.0, grid=None, threads=None):
-    """Time the oracle on a bounded sample of one step: rings of every event
-    (1 thread), the map of all rings over an evenly spread sample of
-    directions (OpenMP threads, time scaled to all directions), and the
-    refinement from the best sampled direction.  Returns (seconds per full
-    step, details)."""
+ORACLE_PARAMS = dict(sigma_e_frac=0.05, sigma_pos_cm=1.0, deta_min=math.radians(0.5),
+                     deta_max=math.radians(20.0))
+
+
+def event_config(world, n_events, n_valid, M):
+    """The event workload's `config`, the same on both arms."""
+    return {"workload": "events200k_healpix64", "events": n_events, "valid_rings": n_valid,
+            "evals": "valid rings x directions", "directions": M,
+            "grid": "HEALPix nside 64 RING", "sites": "2/3/4 at 0.5/0.3/0.2",
+            "source_to_background": "1:10",
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
+def oracle_path(ev, grid, threads):
+    """The whole path on the oracle (C, FP64) for the events `ev`: rings of
+    every event (1 thread), the map of every valid ring over every direction
+    of `grid` (OpenMP, `threads`), its argmax and the refinement from it.
+    Returns (seconds, valid rings, details)."""
     import oracle
-    threads = threads or os.cpu_count() or 1
-    p = dict(sigma_e_frac=0.05, sigma_pos_cm=1.0, deta_min=math.radians(0.5),
-             deta_max=math.radians(20.0))
     t0 = time.perf_counter()
-    r = oracle.rings_from_events(ev, *p.values())
-    t_recon = time.perf_counter() - t0
-    grid = grid or oracle.grid_healpix_ring(NSIDE)
-    M = grid[0].size
-    if n_dirs is None:   # calibrate: aim the map sample at budget_s
-        t0 = time.perf_counter()
-        oracle.likelihood_map(r, grid, idx=np.arange(16), nthreads=threads)
-        per_dir = max((time.perf_counter() - t0) / 16, 1e-6)
-        n_dirs = int(min(M, max(16, budget_s * 0.8 / per_dir)))
-    idx = np.linspace(0, M - 1, n_dirs).astype(np.int64)
-    t0 = time.perf_counter()
-    sampled = oracle.likelihood_map(r, grid, idx=idx, nthreads=threads)
-    t_map = (time.perf_counter() - t0) * M / n_dirs
-    j = int(idx[oracle.argmax(sampled)])     # seed: best sampled direction
-    t0 = time.perf_counter()
-    d, obj, iters, st = oracle.refine(r, [grid[0][j], grid[1][j], grid[2][j]],
-                                      tol_rad=1e-10)
-    t_ref = time.perf_counter() - t0
-    return t_recon + t_map + t_ref, {
-        "t_recon_s": t_recon, "t_map_s_scaled": t_map, "t_refine_s": t_ref,
-        "n_dirs": n_dirs, "threads": threads, "dir": d, "status": st, "iters": iters,
-        "rings": int(r["valid"].size), "valid": int(r["valid"].sum())}
+    r = oracle.rings_from_events(ev, *ORACLE_PARAMS.values())
+    t1 = time.perf_counter()
+    m = oracle.likelihood_map(r, grid, nthreads=threads)
+    t2 = time.perf_counter()
+    j = oracle.argmax(m)
+    d, obj, iters, st = oracle.refine(r, [grid[0][j], grid[1][j], grid[2][j]], tol_rad=1e-10)
+    t3 = time.perf_counter()
+    return t3 - t0, int(r["valid"].sum()), {
+        "t_recon_s": t1 - t0, "t_map_s": t2 - t1, "t_refine_s": t3 - t2, "argmax": j,
+        "dir": d, "status": st, "iters": iters}
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores.  Each
+    step runs the whole path (rings, map over all 49,152 directions, argmax,
+    refinement) on one slice of 5,000 events of the 200k-event burst, the
+    slices taken in turn; the value is the ring x direction evaluations those
+    steps made divided by the time they took, so the steps, ms_per_step and
+    the timed region are what actually ran."""
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
+    import oracle
     from paper_2411_04785_gb300 import synth
     ev = synth.simulate_events(n_src=N_SRC, n_bkg=N_BKG, seed=2)
-    times, info = [], None
-    n_dirs = None
+    N = ev["n"].size
+    grid = oracle.grid_healpix_ring(NSIDE)
+    M = grid[0].size
+    threads = os.cpu_count() or 1
+    slice_n = 5000
+    n_slices = N // slice_n
+    times, evals = [], 0
     for i in range(args.warmup + args.steps):
-        t, info = oracle_step(ev, n_dirs=n_dirs, budget_s=3.0)
-        n_dirs = info["n_dirs"]
+        a = (i % n_slices) * slice_n
+        part = {"n": ev["n"][a:a + slice_n],
+                **{k: np.ascontiguousarray(ev[k][:, a:a + slice_n]) for k in "xyze"}}
+        t, n_valid, _ = oracle_path(part, grid, threads)
         if i >= args.warmup:
             times.append(t)
-    ms = 1e3 * float(np.mean(times))
-    pairs = info["valid"] * 12 * NSIDE * NSIDE     # valid rings x directions
-    value = pairs / (ms / 1e3)
-    sample = (f"per step: oracle rings of all {N_SRC + N_BKG} events (1 thread) + map of all "
-              f"rings over {n_dirs} of {12 * NSIDE * NSIDE} directions ({info['threads']} "
-              f"threads, time scaled to all directions) + refinement from the best sampled direction")
+            evals += n_valid * M
+    tot = float(np.sum(times))
+    value = evals / tot
+    n_valid_all = int(oracle.rings_from_events(ev, *ORACLE_PARAMS.values())["valid"].sum())
+    sample = (f"each step: the whole path on one 5,000-event slice of the {N}-event burst "
+              f"(slices in turn): oracle rings (1 thread), map of the slice's valid rings over "
+              f"all {M} directions ({threads} threads), argmax, refinement; value = "
+              f"evaluations made / time taken, no extrapolation")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "events200k_healpix64", "events": N_SRC + N_BKG,
-                   "valid_rings": info["valid"], "evals": "valid rings x directions",
-                   "directions": 12 * NSIDE * NSIDE},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"],
-                         "kind": "oracle", "sample": sample},
+        "config": event_config(world, N, n_valid_all, M),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads,
+                         "kind": "oracle", "sample": sample, "timed_s": tot,
+                         "evals": evals, "extrapolated": False},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -286,40 +299,35 @@ def run_recon_pile(args):
                                                    warm=args.warmup, timed=max(args.steps, 1))}))
 
 
-def run_burst(args):
+def burst_record(cc, synth, dev, steps, warmup, kcut=0.0, seed=3, world=1, pg=None,
+                 gpu_index=0):
     """The large-burst configuration: 1,000,000 rings (70 % background, deta
     0.5-10 deg) x 786,432 HEALPix nside-256 directions, sweep + argmax + top-8
-    seeds + refinement per step (no reconstruction: the rings are given)."""
+    seeds + refinement per step (no reconstruction: the rings are given).
+    Returns the record (value, timing, roofline of the sweep, accuracy)."""
     import torch
-
-    import paper_2411_04785_gb300 as cc
-    from paper_2411_04785_gb300 import synth
-
-    world, rank, local, pg = dist_setup(args)
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    rings_np, s, _ = synth.rings_burst(n=1_000_000, seed=3 + rank)
+    rings_np, s, _ = synth.rings_burst(n=1_000_000, seed=seed)
     rings = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in rings_np.items()}
-    # --kcut: the angular selection (Sec. 3) on a NESTED grid, whose compact
+    # kcut: the angular selection (Sec. 3) on a NESTED grid, whose compact
     # blocks let the sweep skip what the cut drops
-    grid = cc.grid_healpix_nest(256, dev) if args.kcut > 0 else cc.grid_healpix_ring(256, dev)
+    grid = cc.grid_healpix_nest(256, dev) if kcut > 0 else cc.grid_healpix_ring(256, dev)
     R, M = rings["ax"].numel(), grid[0].numel()
-    loc = cc.Localizer(grid, cc.Params(topk=8, nms_rad=math.radians(1.0), k_cut=args.kcut),
+    loc = cc.Localizer(grid, cc.Params(topk=8, nms_rad=math.radians(1.0), k_cut=kcut),
                        max_rings=R)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         loc.from_rings(rings)
     torch.cuda.synchronize()
     cc.trace_read(reset=True)
     cc.trace_enable(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     barrier(pg)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(gpu_index) as clk:
         time.sleep(0.5)
-        for i in range(args.steps):
+        for i in range(steps):
             starts[i].record(stream)       # inputs (20 MB of rings) re-read per step
             loc.from_rings(rings)
             ends[i].record(stream)
@@ -335,32 +343,88 @@ def run_burst(args):
     sm_max = float(peaks_file().get("sm_max_mhz") or 2070.0)
     peak = sms * sm_max * 1e6 * alu_pairs_per_clk_sm()
     d = loc.dir.cpu().numpy()
-    out = {"metric": METRIC, "value": world * R * M * args.steps / tot_s, "unit": UNIT,
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "burst1m_healpix256" + (f"_kcut{args.kcut:g}" if args.kcut > 0 else ""),
-                      "rings": R, "directions": M,
-                      "grid": "HEALPix nside 256 " + ("NESTED" if args.kcut > 0 else "RING"),
-                      "topk": 8, "k_cut": args.kcut,
-                      "l2": "working set (20 MB rings + 9.4 MB grid + 60 MB partial maps) "
-                            "re-read each step"},
-           "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                          "p99": float(np.percentile(step_ms, 99))},
-           "gpu_launches": sum(v["launches"] for v in trace.values()),
-           "clocks": clk.summary(),
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                        "frac": achieved / peak,
-                        "traffic": ncu_traffic("sweep_burst1m_dram.md", "sweep.cu"),
-                        "kernel": "k_sweep",
-                        **({"note": "effective: pairs the angular selection skipped are counted "
-                                    "as evaluated, so frac can exceed 1"} if args.kcut > 0 else {})},
-           "stages": {k: {"launches_per_step": v["launches"] / args.steps,
-                          "ms_per_step": v["ms"] / args.steps}
-                      for k, v in trace.items() if v["launches"]},
-           "accuracy": {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s)))),
-                        "refine_iterations": int(loc.iters.item()),
-                        "refine_status": int(loc.ref_status.item())}}
+    return {"metric": METRIC, "value": world * R * M * steps / tot_s, "unit": UNIT,
+            "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * tot_s / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "burst1m_healpix256" + (f"_kcut{kcut:g}" if kcut > 0 else ""),
+                       "rings": R, "directions": M,
+                       "grid": "HEALPix nside 256 " + ("NESTED" if kcut > 0 else "RING"),
+                       "topk": 8, "k_cut": kcut,
+                       "l2": "working set (20 MB rings + 9.4 MB grid + 60 MB partial maps) "
+                             "re-read each step"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "gpu_launches": sum(v["launches"] for v in trace.values()),
+            "clocks": clk.summary(),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
+                         "frac": achieved / peak,
+                         "traffic": ncu_traffic("sweep_burst1m_dram.md", "sweep.cu"),
+                         "kernel": "k_sweep",
+                         **({"note": "effective: pairs the angular selection skipped are "
+                                     "counted as evaluated, so frac can exceed 1"}
+                            if kcut > 0 else {})},
+            "stages": {k: {"launches_per_step": v["launches"] / steps,
+                           "ms_per_step": v["ms"] / steps}
+                       for k, v in trace.items() if v["launches"]},
+            "accuracy": {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s)))),
+                         "refine_iterations": int(loc.iters.item()),
+                         "refine_status": int(loc.ref_status.item())}}
+
+
+def noisefree_record(cc, synth, dev, steps, warmup, flush):
+    """The tiny plain configuration: 2,000 noise-free FP32 rings from one
+    source at (30 deg, 45 deg), deta 1 deg, over the 3,072-direction
+    Fibonacci grid; sweep + argmax + FP64 refinement per step (rings given),
+    L2 flushed before each step.  Launch and latency bound, not throughput
+    bound: the record reports latency beside evals/s."""
+    import torch
+    import oracle
+    rings_np, s = synth.rings_noise_free(n=2000)
+    rings = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in rings_np.items()}
+    grid = cc.grid_fibonacci(3072, dev)
+    R, M = rings["ax"].numel(), grid[0].numel()
+    loc = cc.Localizer(grid, cc.Params(topk=1), max_rings=R)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        loc.from_rings(rings)
+    torch.cuda.synchronize()
+    cc.trace_read(reset=True)
+    cc.trace_enable(True)
+    step_ms = timed_loop(lambda: loc.from_rings(rings), steps, stream, flush)
+    cc.trace_enable(False)
+    trace = cc.trace_read(reset=True)
+    d = loc.dir.cpu().numpy()
+    g32 = tuple(v.astype(np.float32) for v in oracle.grid_fibonacci(M))
+    want = oracle.likelihood_map(rings_np, g32)
+    got = loc.map.cpu().numpy()
+    return {"value": R * M * steps / (step_ms.sum() / 1e3), "unit": UNIT,
+            "steps": steps, "warmup": warmup, "ms_per_step": float(step_ms.mean()),
+            "config": {"workload": "noisefree2k_fib3072", "rings": R, "directions": M,
+                       "grid": "Fibonacci", "l2": "flushed between timed steps (256 MiB write)"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "gpu_launches_per_step": sum(v["launches"] for v in trace.values()) / steps,
+            "stages": {k: {"ms_per_step": v["ms"] / steps} for k, v in trace.items()
+                       if v["launches"]},
+            "accuracy": {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s)))),
+                         "map_max_rel_err_vs_oracle": float(np.max(
+                             np.abs(got - want) / np.maximum(want, 1e-3 * want.max()))),
+                         "argmax_equal_oracle": int(loc.argmax.item()) == oracle.argmax(want)}}
+
+
+def run_burst(args):
+    import torch
+
+    import paper_2411_04785_gb300 as cc
+    from paper_2411_04785_gb300 import synth
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    out = burst_record(cc, synth, dev, args.steps, args.warmup, kcut=args.kcut, seed=3 + rank,
+                       world=world, pg=pg, gpu_index=local)
     if rank == 0:
         print(json.dumps(out))
     if pg is not None:
@@ -459,12 +523,7 @@ def run_gpu(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": "events200k_healpix64", "events": N,
-                      "valid_rings": n_valid, "evals": "valid rings x directions",
-                      "directions": M, "grid": "HEALPix nside 64 RING",
-                      "sites": "2/3/4 at 0.5/0.3/0.2", "source_to_background": "1:10",
-                      "l2": "flushed between timed steps (256 MiB write)",
-                      "parallelism": f"replicas x{world}"},
+           "config": event_config(world, N, n_valid, M),
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                           "p99": float(np.percentile(step_ms, 99))},
            "wall_s": wall, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
@@ -512,25 +571,41 @@ def run_gpu(args):
         # reconstruction on a pile of 16M events (HBM bound, larger than L2)
         out["roofline_recon"] = recon_pile(cc, synth, ev, params, dev)
 
+        # the other configurations, measured in the same run: the largest
+        # single-GPU one (1M rings x 786,432 directions, its own sweep
+        # roofline) and the tiny noise-free one
+        if world == 1:
+            out["configs"] = {
+                "burst1m_healpix256": burst_record(cc, synth, dev, steps=5, warmup=3,
+                                                   gpu_index=gpu_index),
+                "noisefree2k_fib3072": noisefree_record(cc, synth, dev, steps=200, warmup=10,
+                                                        flush=flush)}
+
     # accuracy and the CPU baseline (rank 0, N = 1 only)
     d = loc.dir.cpu().numpy()
     s = ev["source"]
     out["accuracy"] = {"refined_vs_source_deg": math.degrees(math.acos(min(1.0, float(d @ s)))),
                        "refine_iterations": int(loc.iters.item()),
                        "refine_status": int(loc.ref_status.item())}
+    out["accuracy"]["target_deg"] = 0.5
+    out["accuracy"]["target_met"] = out["accuracy"]["refined_vs_source_deg"] <= 0.5
     if rank == 0 and world == 1 and not args.quick:
-        t_cpu, info = oracle_step(ev, budget_s=args.cpu_budget)
-        dd = info.pop("dir")
+        import oracle
+        threads = os.cpu_count() or 1
+        t_cpu, nv_cpu, info = oracle_path(ev, oracle.grid_healpix_ring(NSIDE), threads)
+        dd = info["dir"]
         out["accuracy"]["refined_vs_oracle_deg"] = math.degrees(
             math.atan2(np.linalg.norm(np.cross(d, dd)), float(d @ dd)))
+        out["accuracy"]["oracle_vs_source_deg"] = math.degrees(
+            math.atan2(np.linalg.norm(np.cross(dd, s)), float(dd @ s)))
         out["cpu_baseline"] = {
-            "value": pairs_step / t_cpu, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
-            "sample": (f"oracle (C, FP64) on the same burst: rings of all {N} events on 1 "
-                       f"thread ({info['t_recon_s']:.2f} s), map of all rings over "
-                       f"{info['n_dirs']} of {M} directions on {info['threads']} threads "
-                       f"(scaled to all: {info['t_map_s_scaled']:.1f} s), refinement "
-                       f"({info['t_refine_s']:.2f} s)"),
-            "s_per_step": t_cpu}
+            "value": nv_cpu * M / t_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"one whole step on the oracle (C, FP64), the same burst, no "
+                       f"extrapolation: rings of all {N} events on 1 thread "
+                       f"({info['t_recon_s']:.2f} s), map of all {nv_cpu} valid rings over all "
+                       f"{M} directions on {threads} threads ({info['t_map_s']:.1f} s), argmax, "
+                       f"refinement ({info['t_refine_s']:.2f} s)"),
+            "s_per_step": t_cpu, "extrapolated": False}
     if rank == 0:
         print(json.dumps(out))
     if pg is not None:
@@ -1002,8 +1077,6 @@ def main():
                     help="build and run the FP32 / MUFU rate microbenchmark (csrc/alu_rates.cu)")
     ap.add_argument("--profile-recon", action="store_true",
                     help="only run reconstruction on the 16M-event pile (for ncu)")
-    ap.add_argument("--cpu-budget", type=float, default=12.0,
-                    help="seconds of oracle map work in the CPU baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
