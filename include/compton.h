@@ -491,6 +491,29 @@ cc_status cc_selftest_wait_timeout(int32_t which, int64_t limit_ns, uint32_t *co
                                    int32_t *status, void *stream);
 
 /*
+ * Index bounds checks of the debug build (no counterpart in the paper; a
+ * stand-in for a memory checker).  The library built with
+ * build(debug=True) (libcompton_debug.so) compares the index of each checked
+ * global access - the reconstruction's event and ring arrays and bulk copies,
+ * the ring records, tiles, partial and final maps of the sweeps, the block
+ * bests, the refinement's rings and partial sums, the grids, the
+ * clustering's outputs and the ring filter's GEMM outputs - with the bound of
+ * its buffer.  Out of bounds, the first failure is recorded in one device
+ * word, site << 48 | (index & (2^48 - 1)) with the sites of the CC_SITE_*
+ * list in the library's internal header, and the access is skipped, so the
+ * kernel runs on.
+ * cc_debug_bounds: *word (host uint64) = the recorded word, 0 if no check
+ * failed; reset != 0 clears it.  Synchronous (waits for the device).
+ * cc_debug_selftest_bounds: launches a kernel whose one checked access asks
+ * for element n of a device int32 buffer `buf` of n elements; the check
+ * records (0x7fff, n) and skips the access.  Asynchronous on `stream`.
+ * In the normal build both return CC_EINVAL ("not a debug build") and
+ * launch nothing.
+ */
+cc_status cc_debug_bounds(uint64_t *word, int32_t reset);
+cc_status cc_debug_selftest_bounds(int32_t *buf, int64_t n, void *stream);
+
+/*
  * Stage tracing (CUDA events on the caller's stream).  Every kernel launch is
  * counted per stage; when tracing is enabled each launch is also bracketed by
  * two CUDA events recorded on the launching stream, and cc_trace_read()

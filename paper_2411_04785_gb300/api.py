@@ -15,7 +15,10 @@ from dataclasses import dataclass
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcompton.so")
+# CC_LIBRARY=debug selects the debug build (libcompton_debug.so, index bounds
+# checks; see cc_debug_bounds); the default is the optimised build.
+LIB_PATH = os.path.join(HERE, "libcompton_debug.so" if os.environ.get("CC_LIBRARY") == "debug"
+                        else "libcompton.so")
 
 CC_OK, CC_EINVAL, CC_ECUDA, CC_ENOMEM, CC_ETIMEOUT, CC_ENOCONV = 0, -1, -2, -3, -4, -5
 STATUS_NAMES = {0: "CC_OK", -1: "CC_EINVAL", -2: "CC_ECUDA", -3: "CC_ENOMEM",
@@ -155,6 +158,10 @@ def lib() -> C.CDLL:
         L.cc_selftest_exact_ops.restype = S
         L.cc_selftest_wait_timeout.argtypes = [C.c_int32, C.c_int64, _P, _P, _P]
         L.cc_selftest_wait_timeout.restype = S
+        L.cc_debug_bounds.argtypes = [C.POINTER(C.c_uint64), C.c_int32]
+        L.cc_debug_bounds.restype = S
+        L.cc_debug_selftest_bounds.argtypes = [_P, C.c_int64, _P]
+        L.cc_debug_selftest_bounds.restype = S
         L.cc_trace_enable.argtypes = [C.c_int32]
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
@@ -163,6 +170,14 @@ def lib() -> C.CDLL:
             raise RuntimeError("libcompton.so ABI version mismatch")
         _lib = L
     return _lib
+
+
+def debug_bounds(reset: bool = False) -> int:
+    """The debug build's bounds word: 0 when no checked index was out of
+    bounds, else site << 48 | index (raises CCError in the normal build)."""
+    w = C.c_uint64(0)
+    _check("cc_debug_bounds", lib().cc_debug_bounds(C.byref(w), 1 if reset else 0))
+    return int(w.value)
 
 
 def _check(fn, st):

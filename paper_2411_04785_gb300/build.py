@@ -17,6 +17,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcompton.so")
+# The debug build: every checked index is compared with its buffer's bound and
+# a failure is recorded in one device word instead of being accessed
+# (cc_debug_bounds); relocatable device code lets every translation unit reach
+# that word.
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libcompton_debug.so")
+DEBUG_FLAGS = ["-DCC_DEBUG_BOUNDS", "-rdc=true"]
 SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu", "cluster.cu", "voxel.cu",
            "noalloc.cu", "mlp.cu", "selftest.cu"]
 INCLUDE = os.path.join(HERE, "..", "include")
@@ -59,12 +66,13 @@ def _deps(path: str, seen=None) -> set:
     return seen
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, verbose: bool, debug: bool = False) -> str:
+    obj = os.path.join(BUILD_DEBUG if debug else BUILD, os.path.splitext(src)[0] + ".o")
     deps = sorted(_deps(os.path.join(CSRC, src)))
     if os.path.exists(obj) and os.path.getmtime(obj) >= _newest(deps):
         return obj
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *(DEBUG_FLAGS if debug else []), "-c",
+           os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -75,23 +83,33 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile and link libcompton.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Compile and link libcompton.so (debug=True: libcompton_debug.so, the
+    build with index bounds checks); returns its path."""
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), SOURCES))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < _newest(objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        link_objs = list(objs)
+        if debug:      # device link of the relocatable objects
+            dlink = os.path.join(bdir, "dlink.o")
+            r = subprocess.run([_nvcc(), *ARCH, "-dlink", "-Xcompiler", "-fPIC", *objs,
+                                "-o", dlink], capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"device link failed:\n{r.stdout}\n{r.stderr}")
+            link_objs.append(dlink)
+        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", *link_objs, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, debug="--debug" in sys.argv))

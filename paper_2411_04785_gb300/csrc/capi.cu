@@ -463,6 +463,42 @@ cc_status cc_selftest_wait_timeout(int32_t which, int64_t limit_ns, uint32_t *co
     return CC_OK;
 }
 
+cc_status cc_debug_bounds(uint64_t *word, int32_t reset) {
+    g_err[0] = 0;
+    if (!word) return fail(CC_EINVAL, "word is NULL");
+    *word = 0;
+#ifdef CC_DEBUG_BOUNDS
+    unsigned long long w = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&w, cc::cc_oob_word, sizeof(w));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the bounds word");
+    *word = w;
+    if (reset) {
+        const unsigned long long z = 0;
+        if ((e = cudaMemcpyToSymbol(cc::cc_oob_word, &z, sizeof(z))) != cudaSuccess)
+            return cuda_fail(e, "clearing the bounds word");
+    }
+    return CC_OK;
+#else
+    (void)reset;
+    return fail(CC_EINVAL, "not a debug build");
+#endif
+}
+
+cc_status cc_debug_selftest_bounds(int32_t *buf, int64_t n, void *stream) {
+    g_err[0] = 0;
+#ifdef CC_DEBUG_BOUNDS
+    if (!buf || n < 1) return fail(CC_EINVAL, "need a buffer of n >= 1 elements");
+    cudaError_t e = launch_selftest_bounds(buf, n, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest launch");
+    return CC_OK;
+#else
+    (void)buf;
+    (void)n;
+    (void)stream;
+    return fail(CC_EINVAL, "not a debug build");
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // near-field back projection (Sec. 3)
 // ---------------------------------------------------------------------------

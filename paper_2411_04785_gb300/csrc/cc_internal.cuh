@@ -25,6 +25,38 @@ int device_sm_count();
 // CC_ETIMEOUT instead of hanging.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// ---------------------------------------------------------------------------
+// Index bounds checks of the debug build (build(debug=True): -DCC_DEBUG_BOUNDS,
+// relocatable device code).  A checked access first compares its index with
+// the bound of the buffer it touches; out of bounds, the first such failure is
+// recorded in one device word (site << 48 | low 48 bits of the index) and the
+// access is skipped, so the kernel runs on and the host reads the word
+// (cc_debug_bounds) instead of meeting a fault.  The normal build compiles
+// every check to `true`.
+// ---------------------------------------------------------------------------
+enum : int {
+    CC_SITE_RECON_N = 1, CC_SITE_RECON_SITES, CC_SITE_RECON_BULK, CC_SITE_RECON_RING,
+    CC_SITE_PACK_REC, CC_SITE_SWEEP_TILE, CC_SITE_SWEEP_OUT, CC_SITE_SWEEP_BB,
+    CC_SITE_REDUCE_PART, CC_SITE_SELECT_BB, CC_SITE_SELECT_SEED, CC_SITE_REFINE_RING,
+    CC_SITE_REFINE_SLOT, CC_SITE_GRID_OUT, CC_SITE_CLUSTER_IN, CC_SITE_CLUSTER_OUT,
+    CC_SITE_CLUSTER_EVENT, CC_SITE_VOXEL_TILE, CC_SITE_VOXEL_OUT, CC_SITE_MLP_GEMM_OUT,
+    CC_SITE_MLP_ROWS, CC_SITE_SELFTEST = 0x7fff
+};
+
+#ifdef CC_DEBUG_BOUNDS
+extern __device__ unsigned long long cc_oob_word;
+__device__ __forceinline__ bool in_bounds(int site, int64_t i, int64_t n) {
+    if (i >= 0 && i < n) return true;
+    const unsigned long long w = ((unsigned long long)(site & 0xffff) << 48) |
+                                 ((unsigned long long)i & 0xffffffffffffull);
+    atomicCAS(&cc_oob_word, 0ull, w);
+    return false;
+}
+#define CC_IN_BOUNDS(site, i, n) (::cc::in_bounds((site), (int64_t)(i), (int64_t)(n)))
+#else
+#define CC_IN_BOUNDS(site, i, n) true
+#endif
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -148,6 +180,9 @@ cudaError_t mlp_apply_filter(const float *out, const cc_rings &r, float tau, flo
 cudaError_t launch_selftest_exact(uint64_t *bad, cudaStream_t s);   // recon.cu
 cudaError_t launch_selftest_wait(int which, int64_t limit_ns, uint32_t *counter, int32_t *status,
                                  cudaStream_t s);                    // selftest.cu
+#ifdef CC_DEBUG_BOUNDS
+cudaError_t launch_selftest_bounds(int32_t *buf, int64_t n, cudaStream_t s);   // selftest.cu
+#endif
 
 // ---------------------------------------------------------------------------
 // event clustering of detections - cluster.cu

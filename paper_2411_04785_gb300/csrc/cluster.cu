@@ -381,14 +381,14 @@ k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
         rank += st;
         ids[k] = in ? (int)(rank - 1) : -1;
         eb[k >> 2] |= (unsigned)((((ma ^ mb) >> k) & 1u)) << (8 * (k & 3));
-        if (en && i < N) {
+        if (en && i < N && CC_IN_BOUNDS(CC_SITE_CLUSTER_EVENT, rank - 1, N / 2)) {
             const long long id = rank - 1;
             if (ev_first) ev_first[id] = last;
             if (ev_count) ev_count[id] = (int)(i - last + 1);
             if (ev_adc) ev_adc[id] = sum - before;
         }
     }
-    if (vec_out && i0 + 16 <= N) {                        // 16-byte stores
+    if (vec_out && i0 + 16 <= N && CC_IN_BOUNDS(CC_SITE_CLUSTER_OUT, i0 + 15, N)) {
         if (edge) *reinterpret_cast<uint4 *>(edge + i0) = make_uint4(eb[0], eb[1], eb[2], eb[3]);
         if (event_id) {
 #pragma unroll
@@ -399,7 +399,7 @@ k_cluster(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUte
     } else {
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-            if (i0 + k < N) {
+            if (i0 + k < N && CC_IN_BOUNDS(CC_SITE_CLUSTER_OUT, i0 + k, N)) {
                 if (edge) edge[i0 + k] = (unsigned char)((eb[k >> 2] >> (8 * (k & 3))) & 1u);
                 if (event_id) event_id[i0 + k] = ids[k];
             }

@@ -17,7 +17,7 @@ constexpr unsigned long long kGoldenFrac = 0x61C8864680B583EAull;
 __global__ void k_fibonacci(int64_t n, float *__restrict__ x, float *__restrict__ y,
                             float *__restrict__ z) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || !CC_IN_BOUNDS(CC_SITE_GRID_OUT, i, n)) return;
     // 1 - z = (2i+1)/n and 1 + z = (2n-2i-1)/n: integer numerators, so
     // rho = sqrt((1 - z)(1 + z)) keeps full precision at both poles
     float a = (float)(2 * i + 1), b = (float)(2 * (n - i) - 1), fn = (float)n;
@@ -118,7 +118,10 @@ __device__ __forceinline__ int64_t nest_to_ring(int64_t nside, int64_t p) {
 __global__ void k_healpix_nest(int64_t nside, float *__restrict__ x, float *__restrict__ y,
                                float *__restrict__ z) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < 12 * nside * nside) ring_pixel(nside, nest_to_ring(nside, p), p, x, y, z);
+    if (p < 12 * nside * nside) {
+        const int64_t r = nest_to_ring(nside, p);
+        if (CC_IN_BOUNDS(CC_SITE_GRID_OUT, r, 12 * nside * nside)) ring_pixel(nside, r, p, x, y, z);
+    }
 }
 
 __global__ void k_gather(const float *__restrict__ gx, const float *__restrict__ gy,

@@ -136,7 +136,9 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
             for (int r = 0; r < 4; r++) {
                 const int row = m0 + wm + i * 16 + (lane >> 2) + ((r & 2) ? 8 : 0);
                 const int col = n0 + wn + j * 8 + 2 * (lane & 3) + (r & 1);
-                if (row >= g.M || col >= g.N) continue;
+                if (row >= g.M || col >= g.N ||
+                    !CC_IN_BOUNDS(CC_SITE_MLP_GEMM_OUT, (int64_t)row * g.N + col, (int64_t)g.M * g.N))
+                    continue;
                 float v = acc[i][j][r];
                 if (gridDim.z > 1) {
                     g.part[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;

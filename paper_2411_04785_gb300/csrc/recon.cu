@@ -392,8 +392,9 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
             for (int a = 0; a < 4; a++)
 #pragma unroll
                 for (int sl = 0; sl < 4; sl++)
-                    bulk_copy(S.v[a][sl], src[a] + sl * stride + base,
-                              (unsigned)(kWin * sizeof(float)), &S.bar);
+                    if (CC_IN_BOUNDS(CC_SITE_RECON_BULK, base + kWin - 1, stride))
+                        bulk_copy(S.v[a][sl], src[a] + sl * stride + base,
+                                  (unsigned)(kWin * sizeof(float)), &S.bar);
         }
     }
     __syncthreads();
@@ -406,7 +407,7 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     for (int j = 0; j < kPer; j++) {
         const int w = tid + j * kRThreads;
         const int64_t i = base + w;
-        kk[j] = i < count ? n[i] : 0;
+        kk[j] = (i < count && CC_IN_BOUNDS(CC_SITE_RECON_N, i, count)) ? n[i] : 0;
         cls[j] = kk[j] == 4 ? 0 : kk[j] == 3 ? 1 : kk[j] == 2 ? 2 : 3;
         S.k[w] = (uint8_t)kk[j];
         unsigned mine = 0;
@@ -420,8 +421,9 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
         if (!bulk) {
 #pragma unroll
             for (int sl = 0; sl < 4; sl++) {
-                const bool used = sl < kk[j];     // kk = 0 past the end
                 const int64_t off = sl * stride + i;
+                const bool used = sl < kk[j] &&   // kk = 0 past the end
+                                  CC_IN_BOUNDS(CC_SITE_RECON_SITES, off, 4 * stride);
                 S.v[0][sl][w] = used ? __ldg(xs + off) : 0.0f;
                 S.v[1][sl][w] = used ? __ldg(ys + off) : 0.0f;
                 S.v[2][sl][w] = used ? __ldg(zs + off) : 0.0f;
@@ -474,7 +476,7 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     __syncthreads();
     if (vec_ok && base + kWin <= count) {     // four events per thread, 16-byte stores
         static_assert(kWin / 4 <= kRThreads, "one pass of four-event stores");
-        if (tid < kWin / 4) {
+        if (tid < kWin / 4 && CC_IN_BOUNDS(CC_SITE_RECON_RING, base + 4 * tid + 3, count)) {
             const int w = 4 * tid;
             const int64_t i = base + w;
             float *dst[5] = {ax, ay, az, eta, deta};
@@ -490,7 +492,7 @@ k_rings_from_events(const uint8_t *__restrict__ n, const float *__restrict__ xs,
     for (int j = 0; j < kPer; j++) {
         const int w = tid + j * kRThreads;
         const int64_t i = base + w;
-        if (i < count) {
+        if (i < count && CC_IN_BOUNDS(CC_SITE_RECON_RING, i, count)) {
             ax[i] = ring_row(S, 0)[w];
             ay[i] = ring_row(S, 1)[w];
             az[i] = ring_row(S, 2)[w];

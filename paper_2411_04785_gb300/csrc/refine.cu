@@ -307,7 +307,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
     for (int j = 0; j < kCache; j++) {
         const int64_t i = i0 + j * stride;
         ca0[j] = ca1[j] = ca2[j] = cet[j] = cid[j] = 0.0f;
-        if (i < R && (valid == nullptr || valid[i])) {
+        if (i < R && CC_IN_BOUNDS(CC_SITE_REFINE_RING, i, R) && (valid == nullptr || valid[i])) {
             load_ring(ax, ay, az, eta, deta, i, ca0[j], ca1[j], ca2[j], cet[j], cid[j]);
             cok |= 1u << j;
         }
@@ -351,6 +351,7 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
                                (cok >> j) & 1u, L[g], acc[g]);
             }
             for (int64_t i = i0 + kCache * stride; i < R; i += stride) {
+                if (!CC_IN_BOUNDS(CC_SITE_REFINE_RING, i, R)) break;
                 if (valid != nullptr && !valid[i]) continue;
                 float a0, a1, a2, et, inv_de;
                 load_ring(ax, ay, az, eta, deta, i, a0, a1, a2, et, inv_de);
@@ -379,7 +380,9 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
                 float2 v = make_float2(0.0f, 0.0f);
                 if (act[tid / kSums])
                     for (int ww = 0; ww < kThreads / 32; ww++) v = df_add(v, red[ww][tid]);
-                slot[(size_t)blockIdx.x * P + g0 * kSums + tid] = v;
+                if (CC_IN_BOUNDS(CC_SITE_REFINE_SLOT, (int64_t)blockIdx.x * P + g0 * kSums + tid,
+                                 (int64_t)G * P))
+                    slot[(size_t)blockIdx.x * P + g0 * kSums + tid] = v;
             }
             __syncthreads();
         }

@@ -5,6 +5,12 @@
 #include "cc_pipe.cuh"
 
 namespace cc {
+
+#ifdef CC_DEBUG_BOUNDS
+// The debug build's record of the first failed bounds check (cc_internal.cuh).
+__device__ unsigned long long cc_oob_word = 0;
+#endif
+
 namespace {
 
 // which = 0: an mbarrier phase that never completes (the TMA / tensor-core
@@ -25,7 +31,24 @@ __global__ void k_selftest_wait(int which, unsigned long long limit_ns, unsigned
     *status = ok ? (int32_t)CC_OK : (int32_t)CC_ETIMEOUT;
 }
 
+#ifdef CC_DEBUG_BOUNDS
+// The one checked access asks for element n of an n-element buffer: the
+// check records it and the store is skipped.
+__global__ void k_selftest_bounds(int32_t *buf, int64_t n) {
+    if (threadIdx.x != 0) return;
+    const int64_t i = n;
+    if (CC_IN_BOUNDS(CC_SITE_SELFTEST, i, n)) buf[i] = 1;
+}
+#endif
+
 }  // namespace
+
+#ifdef CC_DEBUG_BOUNDS
+cudaError_t launch_selftest_bounds(int32_t *buf, int64_t n, cudaStream_t s) {
+    k_selftest_bounds<<<1, 32, 0, s>>>(buf, n);
+    return cudaGetLastError();
+}
+#endif
 
 cudaError_t launch_selftest_wait(int which, int64_t limit_ns, uint32_t *counter, int32_t *status,
                                  cudaStream_t s) {

@@ -154,16 +154,17 @@ k_pack_scatter(const float *__restrict__ ax, const float *__restrict__ ay,
             before += k < w ? wcnt[k] : 0;
             total += wcnt[k];
         }
-        if (keep)
-            rec[pos + before + __popc(m & ((1u << l) - 1u))] =
-                make_rec(ax[i], ay[i], az[i], eta[i], deta[i]);
+        const int64_t at = pos + before + __popc(m & ((1u << l) - 1u));
+        if (keep && CC_IN_BOUNDS(CC_SITE_PACK_REC, at, (R + kTile - 1) / kTile * kTile))
+            rec[at] = make_rec(ax[i], ay[i], az[i], eta[i], deta[i]);
         pos += total;
         __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x < kTile) {   // null records up to the tile end
         const int64_t n = *nkept;
         const int64_t end = (n + kTile - 1) / kTile * kTile;
-        if (n + threadIdx.x < end)
+        if (n + threadIdx.x < end &&
+            CC_IN_BOUNDS(CC_SITE_PACK_REC, n + threadIdx.x, (R + kTile - 1) / kTile * kTile))
             rec[n + threadIdx.x] =
                 RingRec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, 0.f, 0.f};
     }
@@ -325,7 +326,9 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < kStages && s < tiles; s++)
-            tma_bulk_load(tile[s], src + (int64_t)s * stride, kTile * sizeof(RingRec), &full[s]);
+            if (CC_IN_BOUNDS(CC_SITE_SWEEP_TILE, split + s * nsplit, ntk))
+                tma_bulk_load(tile[s], src + (int64_t)s * stride, kTile * sizeof(RingRec),
+                              &full[s]);
     }
 
     for (int64_t t = 0; t < tiles; t++) {
@@ -354,7 +357,8 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         }
         __syncthreads();
         if (abort_flag) break;
-        if (tid == 0 && t + kStages < tiles)
+        if (tid == 0 && t + kStages < tiles &&
+            CC_IN_BOUNDS(CC_SITE_SWEEP_TILE, split + (t + kStages) * nsplit, ntk))
             tma_bulk_load(tile[stage], src + (t + kStages) * stride, kTile * sizeof(RingRec),
                           &full[stage]);
 #pragma unroll
@@ -377,11 +381,11 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     for (int q = 0; q < DP; q++) {
         const int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
-        if (ja < M) {
+        if (ja < M && CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + ja, nsplit * M)) {
             out[split * M + ja] = va;
             better(bv, bj, va, (int)ja);
         }
-        if (jb < M) {
+        if (jb < M && CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + jb, nsplit * M)) {
             out[split * M + jb] = vb;
             better(bv, bj, vb, (int)jb);
         }
@@ -462,6 +466,7 @@ k_reduce_splits(const float *__restrict__ part, int64_t nsplit, int64_t M,
     if (j < M) {
         float s = 0.0f, c = 0.0f;
         for (int64_t k = 0; k < nsplit; k++) {
+            if (!CC_IN_BOUNDS(CC_SITE_REDUCE_PART, k * M + j, nsplit * M)) break;
             float y = part[k * M + j] - c;
             float t = s + y;
             c = (t - s) - y;
@@ -487,7 +492,8 @@ k_select(const float *__restrict__ map, const BlockBest *__restrict__ bb, int64_
     __shared__ int nseed;
     float v = -__builtin_huge_valf();
     int j = INT32_MAX;
-    for (int64_t b = threadIdx.x; b < nbb; b += blockDim.x) better(v, j, bb[b].v, bb[b].j);
+    for (int64_t b = threadIdx.x; b < nbb; b += blockDim.x)
+        if (CC_IN_BOUNDS(CC_SITE_SELECT_BB, b, nbb)) better(v, j, bb[b].v, bb[b].j);
     block_best(v, j);
     if (threadIdx.x == 0) {
         if (j < 0 || j >= M) j = 0;   // empty or all-NaN map

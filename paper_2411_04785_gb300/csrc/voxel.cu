@@ -280,8 +280,9 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < kStages && s < tiles; s++)
-            tma_bulk_load(S.tile[s], src + (int64_t)s * stride, kTile * sizeof(NearRec),
-                          &S.full[s]);
+            if (CC_IN_BOUNDS(CC_SITE_VOXEL_TILE, split + s * nsplit, ntk))
+                tma_bulk_load(S.tile[s], src + (int64_t)s * stride, kTile * sizeof(NearRec),
+                              &S.full[s]);
 
     const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
     const float2 nh = pair(-0.5f * kInvSqrt2), th2 = pair(1.5f * kInvSqrt2);
@@ -349,7 +350,8 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
         }
         __syncthreads();
         if (S.abort_flag) break;
-        if (tid == 0 && t + kStages < tiles)
+        if (tid == 0 && t + kStages < tiles &&
+            CC_IN_BOUNDS(CC_SITE_VOXEL_TILE, split + (t + kStages) * nsplit, ntk))
             tma_bulk_load(S.tile[stage], src + (t + kStages) * stride, kTile * sizeof(NearRec),
                           &S.full[stage]);
 #pragma unroll
@@ -371,11 +373,11 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
     for (int q = 0; q < DP; q++) {
         const int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
-        if (ja < V) {
+        if (ja < V && CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + ja, nsplit * V)) {
             out[split * V + ja] = va;
             better(bv, bj, va, (int)ja);
         }
-        if (jb < V) {
+        if (jb < V && CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + jb, nsplit * V)) {
             out[split * V + jb] = vb;
             better(bv, bj, vb, (int)jb);
         }

@@ -82,6 +82,24 @@ def test_cluster_argument_checks_without_gpu(libpath):
     assert L.cc_cluster_spectrum(fake, fake, 4, 0, fake, None) == -1
 
 
+def test_debug_calls_refused_by_the_normal_build(libpath):
+    import paper_2411_04785_gb300 as cc
+    L = cc.lib()
+    w = C.c_uint64(5)
+    assert L.cc_debug_bounds(C.byref(w), 0) == -1 and w.value == 0
+    assert b"debug" in L.cc_last_error()
+    assert L.cc_debug_selftest_bounds(None, 8, None) == -1
+
+
+def test_debug_build_links_and_exports_every_declared_symbol():
+    from paper_2411_04785_gb300 import build
+    path = build.build(debug=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert not [n for n in declared_functions() if n not in exported]
+
+
 def test_voxel_universe_counts_without_gpu(libpath):
     import oracle
     import paper_2411_04785_gb300 as cc
