@@ -1030,7 +1030,7 @@ def run_filter(args):
                    "tflops": train_flop / (float(np.mean(tms)) / 1e3) / 1e12,
                    "note": "grad (forward + backward through all layers, loss, bias and weight "
                            "gradients) + Adam per step; forward on the tcgen05 kernel, backward "
-                           "on warp-level tensor-core GEMMs"}
+                           "on tcgen05 (one launch per hidden layer)"}
     out_j = {"metric": "rings filtered/s (learned ring filter inference)",
              "value": world * N * args.steps / tot_s, "unit": "rings/s", "n_gpus": world,
              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,

@@ -310,7 +310,7 @@ cc_status cc_mlp_forward(const float *params, const uint16_t *params_bf16,
  * of 1..CC_MLP_MAX_BATCH rows: is_source [rows] u8, residual [rows] f32 (rad),
  * weight [rows] u8 (0 excludes a row).  features and params_bf16 16-byte
  * aligned.  The forward pass runs on the tcgen05 kernel of cc_mlp_forward,
- * the backward pass on warp-level tensor-core GEMMs.  Deterministic
+ * the backward pass on tcgen05 kernels as well.  Deterministic
  * (fixed-order sums). */
 cc_status cc_mlp_grad(const float *params, const uint16_t *params_bf16,
                       const uint16_t *features, const uint8_t *is_source,

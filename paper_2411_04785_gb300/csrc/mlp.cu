@@ -5,13 +5,12 @@
 //
 // The forward pass (k_mlp_forward_tc, below) runs the whole network in one
 // persistent kernel on the tcgen05 tensor cores, for inference and for
-// training (which keeps the activations).  The backward pass runs its matrix
-// products through one BF16 GEMM kernel on the warp-level tensor-core path
-// (mma.sync m16n8k16, FP32 accumulation, operands staged through shared
-// memory and loaded with ldmatrix): strided operand addressing lets the same
-// kernel do both products of the backward pass, dP x W (through a layer) and
-// dP^T x A (weight gradient, reduced over the batch in fixed-order split-K
-// partials, so results are deterministic).  Weights, layer inputs and
+// training (which keeps the activations).  The backward pass runs on the
+// tcgen05 tensor cores too (k_mlp_bwd_tc, one launch per hidden layer: the
+// signal through the layer, and the weight and bias gradients read from the
+// same TMA tiles as MN-major operands), with the output layer's K = 2
+// products on CUDA cores (k_bwd_out); per-CTA partial gradients are summed in
+// a fixed order, so results are deterministic.  Weights, layer inputs and
 // backward signals are BF16; biases, accumulators, losses, gradients and the
 // Adam state are FP32.
 #include <cuda_bf16.h>
@@ -33,155 +32,6 @@ constexpr int kChunk = 65536;             // rows per forward/backward pass
 constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
               oW3 = ob2 + kH, ob3 = oW3 + kH * kH, oW4 = ob3 + kH, ob4 = oW4 + 2 * kH;
 static_assert(ob4 + 2 == kP, "parameter layout");
-
-// ---------------------------------------------------------------------------
-// BF16 tensor-core GEMM:  C[M,N] = A[M,K] B[K,N]  (+ bias, ReLU, mask)
-// ---------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-
-struct GemmArgs {
-    int M, N, K;
-    const bf16 *A;
-    int64_t lda_m, lda_k;       // A(m, k) = A[m * lda_m + k * lda_k]
-    const bf16 *B;
-    int64_t ldb_k, ldb_n;       // B(k, n) = B[k * ldb_k + n * ldb_n]
-    const float *bias;          // [N] or null
-    int relu;
-    const bf16 *mask;           // keep C(m, n) only where mask[m * ldmask + n] > 0
-    int64_t ldmask;
-    void *C;                    // output, row stride ldc
-    int64_t ldc;
-    int c_bf16;
-    float *part;                // split-K partials [gridDim.z][M][N] when gridDim.z > 1
-    int ksplit;                 // K per split, multiple of BK
-};
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *p) {
-    unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void ldmatrix_x2(uint32_t (&r)[2], const void *p) {
-    unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r[0]), "=r"(r[1])
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-    __shared__ __align__(16) bf16 As[BM][BK + PAD];   // [m][k]
-    __shared__ __align__(16) bf16 Bs[BN][BK + PAD];   // [n][k]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int kbeg = blockIdx.z * g.ksplit;
-    const int kend = min(g.K, kbeg + g.ksplit);
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const bf16 zero = __float2bfloat16(0.0f);
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) acc[i][j][r] = 0.0f;
-
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        // stage the tiles; consecutive threads walk the unit-stride index
-        for (int e = tid; e < BM * BK; e += 128) {
-            int mm, kk;
-            if (g.lda_m == 1) { mm = e % BM; kk = e / BM; } else { mm = e / BK; kk = e % BK; }
-            const int m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = (m < g.M && k < kend) ? g.A[m * g.lda_m + k * g.lda_k] : zero;
-        }
-        for (int e = tid; e < BN * BK; e += 128) {
-            int nn, kk;
-            if (g.ldb_n == 1) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
-            const int n = n0 + nn, k = k0 + kk;
-            Bs[nn][kk] = (n < g.N && k < kend) ? g.B[k * g.ldb_k + n * g.ldb_n] : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-                ldmatrix_x4(a[i], &As[wm + i * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                ldmatrix_x2(b[j], &Bs[wn + j * 8 + (lane & 7)][kk + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], a[i], b[j]);
-        }
-        __syncthreads();
-    }
-
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int row = m0 + wm + i * 16 + (lane >> 2) + ((r & 2) ? 8 : 0);
-                const int col = n0 + wn + j * 8 + 2 * (lane & 3) + (r & 1);
-                if (row >= g.M || col >= g.N ||
-                    !CC_IN_BOUNDS(CC_SITE_MLP_GEMM_OUT, (int64_t)row * g.N + col, (int64_t)g.M * g.N))
-                    continue;
-                float v = acc[i][j][r];
-                if (gridDim.z > 1) {
-                    g.part[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;
-                    continue;
-                }
-                if (g.bias) v += g.bias[col];
-                if (g.relu) v = fmaxf(v, 0.0f);
-                if (g.mask && !(__bfloat162float(g.mask[row * g.ldmask + col]) > 0.0f)) v = 0.0f;
-                if (g.c_bf16)
-                    static_cast<bf16 *>(g.C)[row * g.ldc + col] = __float2bfloat16(v);
-                else
-                    static_cast<float *>(g.C)[row * g.ldc + col] = v;
-            }
-}
-
-// out[i] = sum over splits of part[s][i], in split order
-__global__ void k_sum_splits(const float *__restrict__ part, int S, int64_t n,
-                             float *__restrict__ out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s = 0.0f;
-    for (int z = 0; z < S; z++) s += part[z * n + i];
-    out[i] = s;
-}
-
-cudaError_t gemm(const GemmArgs &g0, cudaStream_t s) {
-    GemmArgs g = g0;
-    int S = 1;
-    if (g.part) {
-        g.ksplit = ((g.ksplit + BK - 1) / BK) * BK;
-        S = (g.K + g.ksplit - 1) / g.ksplit;
-    } else {
-        g.ksplit = ((g.K + BK - 1) / BK) * BK;
-    }
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, S);
-    k_gemm<<<grid, 128, 0, s>>>(g);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || S == 1) return e;
-    int64_t n = (int64_t)g.M * g.N;
-    k_sum_splits<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.part, S, n,
-                                                             static_cast<float *>(g.C));
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // element-wise kernels
@@ -274,22 +124,6 @@ __global__ void k_loss_grad(const float *__restrict__ out, const uint8_t *__rest
     if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
 }
 
-// Column sums of a BF16 [B, N] matrix (bias gradients), one block per column,
-// fixed order.
-__global__ void k_col_sums(const bf16 *__restrict__ X, int64_t B, int N, float *__restrict__ out) {
-    __shared__ float red[256];
-    const int col = blockIdx.x;
-    float s = 0.0f;
-    for (int64_t r = threadIdx.x; r < B; r += blockDim.x) s += __bfloat162float(X[r * N + col]);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[col] = red[0];
-}
-
 __global__ void k_sum_small(const float *__restrict__ x, int n, float *__restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         float s = 0.0f;
@@ -339,19 +173,30 @@ struct Work {
     float *out;        // [rows, 2]
     bf16 *dout;        // [rows, 2]
     bf16 *dP[2];       // backward signals, [rows, 128], ping-pong
-    float *part;       // split-K partials
+    float *part;       // per-CTA partial gradients of the backward kernels
     float *loss_part;  // per-block loss sums
     int64_t rows;
 };
 
-// Rows per weight-gradient split: about 64 splits (a 128 x 128 gradient is
-// only 4 CTA tiles, so the batch dimension supplies the parallelism), at
-// least 128 rows and a multiple of the GEMM's K step.
-constexpr int kWgSplits = 64;
-__host__ __device__ inline int64_t wg_split_rows(int64_t rows) {
-    const int64_t r = (rows + kWgSplits - 1) / kWgSplits;
-    const int64_t r32 = (r + BK - 1) / BK * BK;
-    return r32 < 128 ? 128 : r32;
+// The CTA plan of the backward kernels for `rows` rows: about four 128-row
+// tiles per CTA (fewer CTAs' partials to sum), every CTA with at least one.
+constexpr int kRowTile = 128, kBwTilesPerCta = 4;
+struct BwPlan {
+    int64_t tiles;
+    int tpc, ncta;
+};
+inline BwPlan bw_plan(int64_t rows) {
+    BwPlan p;
+    p.tiles = (rows + kRowTile - 1) / kRowTile;
+    if (p.tiles < 1) p.tiles = 1;
+    const int64_t n = (p.tiles + kBwTilesPerCta - 1) / kBwTilesPerCta;
+    p.tpc = (int)((p.tiles + n - 1) / n);
+    p.ncta = (int)((p.tiles + p.tpc - 1) / p.tpc);
+    return p;
+}
+// partial gradients of the four layers: [ncta][outputs][inputs + 1]
+inline size_t bw_part_floats(int ncta) {
+    return (size_t)ncta * ((size_t)kH * (kF + 1) + 2 * (size_t)kH * (kH + 1) + 2 * (kH + 1));
 }
 
 size_t work_layout(int64_t rows, Work *w, char *base) {
@@ -365,8 +210,7 @@ size_t work_layout(int64_t rows, Work *w, char *base) {
     w->out = (float *)take(rows * 2 * sizeof(float));
     w->dout = (bf16 *)take(rows * 2 * sizeof(bf16));
     for (int l = 0; l < 2; l++) w->dP[l] = (bf16 *)take(rows * kH * sizeof(bf16));
-    const int64_t S = (rows + wg_split_rows(rows) - 1) / wg_split_rows(rows);
-    w->part = (float *)take((size_t)S * kH * kH * sizeof(float));
+    w->part = (float *)take(bw_part_floats(bw_plan(rows).ncta) * sizeof(float));
     w->loss_part = (float *)take(((rows + 255) / 256) * sizeof(float));
     w->rows = rows;
     return off;
@@ -788,48 +632,395 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
     }
 }
 
-// dW[out, in] = dP^T A over the rows (split-K, fixed order); db = column sums of dP
-cudaError_t weight_grad(const bf16 *dP, int out, const bf16 *A, int in, int rows, float *gW,
-                        float *gb, Work &w, cudaStream_t s) {
-    GemmArgs g{};
-    g.M = out;
-    g.N = in;
-    g.K = rows;
-    g.A = dP;            // A(m = output, k = row) = dP[row][m]
-    g.lda_m = 1;
-    g.lda_k = out;
-    g.B = A;             // B(k = row, n = input) = A[row][n]
-    g.ldb_k = in;
-    g.ldb_n = 1;
-    g.C = gW;
-    g.ldc = in;
-    g.part = w.part;
-    g.ksplit = (int)wg_split_rows(rows);
-    cudaError_t e = gemm(g, s);
-    if (e != cudaSuccess) return e;
-    k_col_sums<<<out, 256, 0, s>>>(dP, rows, out, gb);
-    return cudaGetLastError();
+// ---------------------------------------------------------------------------
+// Backward pass on the fifth-generation tensor cores.  One launch per hidden
+// layer l (3, 2, 1) takes 128-row tiles of the layer's backward signal dZ_l
+// ([rows][128] BF16) and of its input H_(l-1) (the previous layer's
+// activations, or the features for l = 1) by TMA, and computes with
+// tcgen05.mma, FP32 accumulators in TMEM:
+//   D1 = dZ_l W_l               the signal through the layer (l = 3, 2):
+//                               A = the dZ tile (K-major, K = 128 outputs),
+//                               B = W_l^T staged once per CTA (K-major);
+//   D2 += dZ_l^T H_(l-1)        the weight gradient over the CTA's rows:
+//                               both operands are the same tiles read
+//                               MN-major (the row is K), so nothing is
+//                               transposed: the 128B-swizzled [row][64]
+//                               blocks a TMA load leaves are an MN-major
+//                               operand (LBO = block stride, SBO = 8 rows);
+//   D3 += dZ_l^T 1              the bias gradient, against a constant
+//                               block whose first column is 1.
+// The epilogue gates D1 by H_(l-1) > 0 (the ReLU of the layer below), rounds
+// it to BF16 into a swizzled tile and stores it with TMA as dZ_(l-1); after
+// the CTA's last tile it writes D2 and D3 as the CTA's partial gradients,
+// which k_reduce_grad sums over the CTAs in a fixed order (deterministic).
+// Warps: 0 TMA producer (2-stage ring) and TMEM owner, 1 MMA issuer (one
+// elected lane of a converged warp), 2..5 epilogue (one row each).  Every
+// wait is bounded; a CTA that gives up writes NaN partials.
+// ---------------------------------------------------------------------------
+constexpr int kBwStages = 2;
+constexpr int kBwEpiWarps = 4;
+constexpr int kBwWarps = 2 + kBwEpiWarps;
+constexpr unsigned kD1Col = 0, kD2Col = 128, kD3Col = 256;
+static_assert(kTM == kRowTile, "backward tiles are the forward's");
+
+struct BwSmem {                           // every operand block 1024-byte aligned
+    bf16 dz[kBwStages][2][kTM * 64];      // signal tile: 2 blocks [row][64], 128B swizzle
+    bf16 hp[kBwStages][2][kTM * 64];      // layer input tile (features: [row][16], 32B swizzle)
+    bf16 wt[2][kH * 64];                  // W^T: [n = input][64 k = output], 2 k blocks
+    bf16 out[2][kTM * 64];                // the gated signal before its TMA store
+    bf16 ones[kTM * 16];                  // [row][16] = (1, 0, ..., 0), 32B swizzle
+    unsigned long long full[kBwStages], empty[kBwStages], d1_full, d1_free, fin;
+    unsigned tmem;
+    int err;
+};
+constexpr size_t kBwSmemBytes = sizeof(BwSmem) + 1024;
+
+// Shared-memory descriptor of an MN-major operand: `lbo` the byte stride
+// between atoms along M/N, `sbo` between 8-row groups along K.
+__device__ __forceinline__ uint64_t sdesc_mn(unsigned addr, unsigned lbo, unsigned sbo,
+                                             uint64_t mode) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | ((uint64_t)1 << 46) | (mode << 61);
 }
 
-// dP_prev[rows, in] = (dP[rows, out] W[out, in]) where Hprev > 0
-GemmArgs back_data(const bf16 *dP, int out, const bf16 *W, int in, int rows, const bf16 *Hprev,
-                   bf16 *dPprev) {
-    GemmArgs g{};
-    g.M = rows;
-    g.N = in;
-    g.K = out;
-    g.A = dP;
-    g.lda_m = out;
-    g.lda_k = 1;
-    g.B = W;             // B(k = output, n = input) = W[k][n]
-    g.ldb_k = in;
-    g.ldb_n = 1;
-    g.mask = Hprev;
-    g.ldmask = in;
-    g.C = dPprev;
-    g.ldc = in;
-    g.c_bf16 = 1;
-    return g;
+// instruction descriptor with both operands MN-major (transpose bits 15, 16)
+__host__ __device__ constexpr unsigned idesc_mn(int M, int N) {
+    return idesc(M, N) | (1u << 15) | (1u << 16);
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned addr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+        "r"(x), "r"(y), "r"(smem_u32(src))
+        : "memory");
+}
+
+__device__ __forceinline__ void epi_sync() {   // the epilogue warps only
+    asm volatile("bar.sync 1, %0;" ::"r"(kBwEpiWarps * 32) : "memory");
+}
+
+// BF16x2 of (lo, hi), round to nearest even; lo in the low half
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+struct BwArgs {
+    int64_t rows, tiles;
+    int tpc;              // tiles per CTA: CTA c takes tiles [c tpc, (c + 1) tpc)
+    int nin;              // inputs of the layer: 128, or 16 for the first layer
+    const bf16 *w;        // W_l [128 outputs][128 inputs] (signal through the layer)
+    float *part;          // [CTA][128 outputs][nin + 1]: weight then bias partials
+};
+
+template <bool kData>
+__global__ void __launch_bounds__(kBwWarps * 32, 1)
+k_mlp_bwd_tc(const __grid_constant__ CUtensorMap dzmap, const __grid_constant__ CUtensorMap hpmap,
+             const __grid_constant__ CUtensorMap outmap, const BwArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    BwSmem &S = *reinterpret_cast<BwSmem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * a.tpc;
+    const int nt = (int)(a.tiles - t0 < a.tpc ? a.tiles - t0 : a.tpc);
+    const bool wide = a.nin == kH;
+
+    if (kData) {                          // W^T into its K-major swizzled place
+        for (int i = tid; i < kH * kH; i += blockDim.x) {
+            const int o = i / kH, n = i % kH;          // W[o][n] -> B[n][k = o]
+            char *blk = reinterpret_cast<char *>(S.wt[o >> 6]);
+            *reinterpret_cast<bf16 *>(blk + sw128(n, (o & 63) >> 3) + 2 * (o & 7)) = a.w[i];
+        }
+    }
+    for (int r = tid; r < kTM; r += blockDim.x) {     // the constant block
+        char *row = reinterpret_cast<char *>(S.ones);
+        *reinterpret_cast<uint4 *>(row + sw32(r, 0)) = make_uint4(0x3F80u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(row + sw32(r, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kBwStages; i++) {
+            mbar_init(&S.full[i], 1);
+            mbar_init(&S.empty[i], kData ? 1 + kBwEpiWarps : 1);
+        }
+        mbar_init(&S.d1_full, 1);
+        mbar_init(&S.d1_free, kBwEpiWarps);
+        mbar_init(&S.fin, 1);
+        S.err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // staged blocks -> tensor cores
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = S.tmem;
+    volatile int *err = &S.err;
+
+    if (warp == 0) {
+        if (lane == 0) {                  // producer
+            const unsigned bytes = 2 * kTM * 64 * 2 + (wide ? 2 * kTM * 64 * 2 : kTM * kF * 2);
+            int k = 0;
+            for (; k < nt && !*err; k++) {
+                const int st = k % kBwStages;
+                if (k >= kBwStages && !mbar_wait(&S.empty[st], ((k / kBwStages) - 1) & 1)) {
+                    *err = 1;
+                    break;
+                }
+                const int y = (int)((t0 + k) * kTM);
+                expect_tx(&S.full[st], bytes);
+                tma_load_2d(S.dz[st][0], &dzmap, 0, y, &S.full[st]);
+                tma_load_2d(S.dz[st][1], &dzmap, 64, y, &S.full[st]);
+                tma_load_2d(S.hp[st][0], &hpmap, 0, y, &S.full[st]);
+                if (wide) tma_load_2d(S.hp[st][1], &hpmap, 64, y, &S.full[st]);
+            }
+            for (int j = k - kBwStages < 0 ? 0 : k - kBwStages; j < k; j++)   // no copy outlives the CTA
+                if (!mbar_wait(&S.full[j % kBwStages], (j / kBwStages) & 1)) *err = 1;
+        }
+    } else if (warp == 1) {               // MMA issuer (whole warp, one elected lane issues)
+        const uint64_t dw = sdesc(smem_u32(S.wt[0]), 1024, kSw128);
+        const uint64_t d1s = sdesc_mn(smem_u32(S.ones), 4096, 256, kSw32);
+        bool ok = true;
+        for (int k = 0; k < nt && ok; k++) {
+            const int st = k % kBwStages;
+            ok = !*err && mbar_wait(&S.full[st], (k / kBwStages) & 1) &&
+                 (!kData || k == 0 || mbar_spin(&S.d1_free, (k - 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+            tc_fence_after();
+            const unsigned dz0 = smem_u32(S.dz[st][0]), hp0 = smem_u32(S.hp[st][0]);
+            if (kData) {                  // D1 = dZ W: K = 128 outputs in 8 steps of 16
+                const uint64_t da = sdesc(dz0, 1024, kSw128);
+#pragma unroll
+                for (int kk = 0; kk < 8; kk++) {
+                    const uint64_t off = (uint64_t)(kk >> 2) * (kTM * 128 / 16) + (uint64_t)((kk & 3) * 2);
+                    umma_ss(tmem + kD1Col, da + off,
+                            dw + (uint64_t)(kk >> 2) * (kH * 128 / 16) + (uint64_t)((kk & 3) * 2),
+                            idesc(kTM, kH), kk > 0);
+                }
+                umma_commit(&S.d1_full);
+            }
+            // D2 += dZ^T H and D3 += dZ^T 1: K = the tile's 128 rows in 8 steps of 16
+            const uint64_t am = sdesc_mn(dz0, kTM * 128, 1024, kSw128);
+            const uint64_t bm = wide ? sdesc_mn(hp0, kTM * 128, 1024, kSw128)
+                                     : sdesc_mn(hp0, 4096, 256, kSw32);
+#pragma unroll
+            for (int kk = 0; kk < 8; kk++) {
+                const int acc = (k > 0 || kk > 0) ? 1 : 0;
+                umma_ss(tmem + kD2Col, am + (uint64_t)(kk * 2048 / 16),
+                        bm + (uint64_t)(kk * (wide ? 2048 : 512) / 16), idesc_mn(kTM, a.nin), acc);
+                umma_ss(tmem + kD3Col, am + (uint64_t)(kk * 2048 / 16),
+                        d1s + (uint64_t)(kk * 512 / 16), idesc_mn(kTM, 16), acc);
+            }
+            umma_commit(&S.empty[st]);
+        }
+        if (!ok && lane == 0) *err = 1;
+        umma_commit(&S.fin);              // every product issued has completed
+        if (!__all_sync(0xffffffffu, mbar_wait(&S.fin, 0)) && lane == 0) *err = 1;
+    } else {                              // epilogue: one row per thread
+        const int qd = warp & 3, row = 32 * qd + lane;
+        const unsigned lanes = (unsigned)(32 * qd) << 16;
+        const bool leader = warp == 2 && lane == 0;
+        if (kData) {
+            for (int k = 0; k < nt; k++) {
+                const int st = k % kBwStages;
+                const bool ok = !*err && mbar_wait(&S.d1_full, k & 1);
+                if (!__all_sync(0xffffffffu, ok)) {      // warp-uniform: the loads are .aligned
+                    *err = 1;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t r[4][32];
+#pragma unroll
+                for (int q = 0; q < 4; q++) tmem_ld32(tmem + lanes + kD1Col + 32 * q, r[q]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.d1_free);
+                // gate by the layer input > 0, round, into the swizzled out tile
+#pragma unroll
+                for (int c8 = 0; c8 < 16; c8++) {
+                    const char *hb = reinterpret_cast<const char *>(S.hp[st][c8 >> 3]);
+                    const uint4 h = *reinterpret_cast<const uint4 *>(hb + sw128(row, c8 & 7));
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int c = 8 * c8 + 2 * j;
+                        const float v0 = __uint_as_float(r[c >> 5][c & 31]);
+                        const float v1 = __uint_as_float(r[(c + 1) >> 5][(c + 1) & 31]);
+                        const float g0 = __uint_as_float(hw[j] << 16);
+                        const float g1 = __uint_as_float(hw[j] & 0xFFFF0000u);
+                        o[j] = bf16x2(g0 > 0.0f ? v0 : 0.0f, g1 > 0.0f ? v1 : 0.0f);
+                    }
+                    char *ob = reinterpret_cast<char *>(S.out[c8 >> 3]);
+                    *reinterpret_cast<uint4 *>(ob + sw128(row, c8 & 7)) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.empty[st]);   // the mask is read
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                epi_sync();
+                if (leader) {
+                    const int y = (int)((t0 + k) * kTM);
+                    tma_store_2d(&outmap, 0, y, S.out[0]);
+                    tma_store_2d(&outmap, 64, y, S.out[1]);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                }
+                epi_sync();                   // the out tile may be written again
+            }
+            if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
+        // the CTA's partial gradients: row `row` of D2 (weights) and D3 (bias)
+        const bool ok = !*err && mbar_wait(&S.fin, 0);
+        float *dst = a.part + ((int64_t)blockIdx.x * kTM + row) * (a.nin + 1);
+        if (__all_sync(0xffffffffu, ok) && !*err) {
+            tc_fence_after();
+            uint32_t b[2];
+            tmem_ld2(tmem + lanes + kD3Col, b);
+            if (wide) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + lanes + kD2Col + 32 * q, r);
+#pragma unroll
+                    for (int c = 0; c < 32; c++) dst[32 * q + c] = __uint_as_float(r[c]);
+                }
+            } else {
+                uint32_t r[16];
+                tmem_ld16(tmem + lanes + kD2Col, r);
+#pragma unroll
+                for (int c = 0; c < 16; c++) dst[c] = __uint_as_float(r[c]);
+            }
+            dst[a.nin] = __uint_as_float(b[0]);
+        } else {                          // gave up: a failure cannot pass for a gradient
+            for (int c = 0; c <= a.nin; c++) dst[c] = __int_as_float(0x7fc00000);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// Layer 4 on CUDA cores (its products have K = 2 or M = 2, below one
+// tensor-core tile): dZ3 = bf16((dout W4) gated by H3 > 0), and the CTA's
+// partial gradients of layer 4 over its rows, part[cta][o][n] =
+// sum_r dout[r][o] H3[r][n] and part[cta][o][128] = sum_r dout[r][o].  One
+// thread per column n, the rows in order.
+__global__ void __launch_bounds__(kH) k_bwd_out(const bf16 *__restrict__ dout,
+                                                const bf16 *__restrict__ h3,
+                                                const bf16 *__restrict__ w4, int64_t rows, int tpc,
+                                                bf16 *__restrict__ dz3, float *__restrict__ part) {
+    const int n = threadIdx.x;
+    const float w0 = __bfloat162float(w4[n]), w1 = __bfloat162float(w4[kH + n]);
+    const int64_t r0 = (int64_t)blockIdx.x * tpc * kTM;
+    const int64_t r1 = rows < r0 + (int64_t)tpc * kTM ? rows : r0 + (int64_t)tpc * kTM;
+    float g0 = 0.0f, g1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+    for (int64_t r = r0; r < r1; r++) {
+        const float d0 = __bfloat162float(dout[2 * r]), d1 = __bfloat162float(dout[2 * r + 1]);
+        const float h = __bfloat162float(h3[r * kH + n]);
+        const float v = d0 * w0 + d1 * w1;
+        if (CC_IN_BOUNDS(CC_SITE_MLP_ROWS, r, rows)) dz3[r * kH + n] = __float2bfloat16(h > 0.0f ? v : 0.0f);
+        g0 = fmaf(d0, h, g0);
+        g1 = fmaf(d1, h, g1);
+        b0 += d0;
+        b1 += d1;
+    }
+    float *p = part + (int64_t)blockIdx.x * 2 * (kH + 1);
+    p[n] = g0;
+    p[kH + 1 + n] = g1;
+    if (n == 0) {
+        p[kH] = b0;
+        p[2 * kH + 1] = b1;
+    }
+}
+
+// grad = the sum over the CTAs of each layer's partials, CTA 0 first
+// (deterministic).  Layer l's partials: [ncta][outputs][inputs + 1], the
+// bias last.
+struct GradParts {
+    const float *part[4];
+    int ncta;
+};
+
+__global__ void k_reduce_grad(const GradParts g, float *__restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP) return;
+    int l, o, n, nin, nout;
+    if (i < ob1) { l = 0; o = i / kF; n = i % kF; }
+    else if (i < oW2) { l = 0; o = i - ob1; n = kF; }
+    else if (i < ob2) { l = 1; o = (i - oW2) / kH; n = (i - oW2) % kH; }
+    else if (i < oW3) { l = 1; o = i - ob2; n = kH; }
+    else if (i < ob3) { l = 2; o = (i - oW3) / kH; n = (i - oW3) % kH; }
+    else if (i < oW4) { l = 2; o = i - ob3; n = kH; }
+    else if (i < ob4) { l = 3; o = (i - oW4) / kH; n = (i - oW4) % kH; }
+    else { l = 3; o = i - ob4; n = kH; }
+    nin = l == 0 ? kF : kH;
+    nout = l == 3 ? 2 : kH;
+    const int64_t per = (int64_t)nout * (nin + 1);
+    const float *p = g.part[l] + (int64_t)o * (nin + 1) + n;
+    float s = 0.0f;
+    for (int c = 0; c < g.ncta; c++) s += p[c * per];
+    grad[i] = s;
+}
+
+// [rows][inner] BF16, row-major, as a TMA map with boxes of `box` columns x
+// 128 rows
+bool bf16_map(CUtensorMap *m, const void *p, int inner, int64_t rows, int box,
+              CUtensorMapSwizzle sw) {
+    TmapEncodeFn enc = encode_fn();
+    if (enc == nullptr) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    const cuuint32_t boxd[2] = {(cuuint32_t)box, (cuuint32_t)kTM};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(p), dims, strides, boxd,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// One hidden layer's backward launch: dz [rows][128] the layer's signal, hp
+// its input ([rows][128], or the features [rows][16] when nin = 16), out
+// [rows][128] the gated signal of the layer below (nin = 128 only).
+cudaError_t bwd_layer(const bf16 *dz, const bf16 *hp, int nin, const bf16 *w, bf16 *out,
+                      int64_t rows, const BwPlan &pl, float *part, cudaStream_t s) {
+    CUtensorMap mdz, mhp, mout;
+    if (!bf16_map(&mdz, dz, kH, rows, 64, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !bf16_map(&mhp, hp, nin, rows, nin == kH ? 64 : kF,
+                  nin == kH ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B) ||
+        !bf16_map(&mout, out ? (const void *)out : (const void *)dz, kH, rows, 64,
+                  CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
+    auto kern = out ? k_mlp_bwd_tc<true> : k_mlp_bwd_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBwSmemBytes);
+    if (e != cudaSuccess) return e;
+    BwArgs a{rows, pl.tiles, pl.tpc, nin, w, part};
+    kern<<<(unsigned)pl.ncta, kBwWarps * 32, kBwSmemBytes, s>>>(mdz, mhp, mout, a);
+    return cudaGetLastError();
 }
 
 // The network on the tcgen05 kernel for R rows of features; with H (the
@@ -879,17 +1070,28 @@ cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint
     const unsigned nb = (unsigned)((rows + 255) / 256);
     k_loss_grad<<<nb, 256, 0, s>>>(w.out, y, res, wv, rows, inv_total, w.dout, w.loss_part);
     if ((e = cudaGetLastError())) return e;
-    // layer 4
-    if ((e = weight_grad(w.dout, 2, w.H[2], kH, rows, grad + oW4, grad + ob4, w, s))) return e;
-    if ((e = gemm(back_data(w.dout, 2, wb + oW4, kH, rows, w.H[2], dZ[2]), s))) return e;
-    // layer 3
-    if ((e = weight_grad(dZ[2], kH, w.H[1], kH, rows, grad + oW3, grad + ob3, w, s))) return e;
-    if ((e = gemm(back_data(dZ[2], kH, wb + oW3, kH, rows, w.H[1], dZ[1]), s))) return e;
-    // layer 2
-    if ((e = weight_grad(dZ[1], kH, w.H[0], kH, rows, grad + oW2, grad + ob2, w, s))) return e;
-    if ((e = gemm(back_data(dZ[1], kH, wb + oW2, kH, rows, w.H[0], dZ[0]), s))) return e;
-    // layer 1
-    return weight_grad(dZ[0], kH, X, kF, rows, grad + oW1, grad + ob1, w, s);
+    const BwPlan pl = bw_plan(rows);
+    GradParts gp;
+    gp.ncta = pl.ncta;
+    gp.part[0] = w.part;                                           // layer 1: [.][128][17]
+    gp.part[1] = gp.part[0] + (size_t)pl.ncta * kH * (kF + 1);      // layers 2, 3: [.][128][129]
+    gp.part[2] = gp.part[1] + (size_t)pl.ncta * kH * (kH + 1);
+    gp.part[3] = gp.part[2] + (size_t)pl.ncta * kH * (kH + 1);      // layer 4: [.][2][129]
+    // layer 4 (CUDA cores), then layers 3, 2, 1 on the tensor cores
+    k_bwd_out<<<(unsigned)pl.ncta, kH, 0, s>>>(w.dout, w.H[2], wb + oW4, rows, pl.tpc, dZ[2],
+                                               const_cast<float *>(gp.part[3]));
+    if ((e = cudaGetLastError())) return e;
+    if ((e = bwd_layer(dZ[2], w.H[1], kH, wb + oW3, dZ[1], rows, pl,
+                       const_cast<float *>(gp.part[2]), s)))
+        return e;
+    if ((e = bwd_layer(dZ[1], w.H[0], kH, wb + oW2, dZ[0], rows, pl,
+                       const_cast<float *>(gp.part[1]), s)))
+        return e;
+    if ((e = bwd_layer(dZ[0], X, kF, nullptr, nullptr, rows, pl,
+                       const_cast<float *>(gp.part[0]), s)))
+        return e;
+    k_reduce_grad<<<(kP + 255) / 256, 256, 0, s>>>(gp, grad);
+    return cudaGetLastError();
 }
 
 }  // namespace

@@ -59,11 +59,15 @@ def forward_bounds(p, X):
     return out, dz, A, dA
 
 
-def split_rows(rows, splits=64, bk=32):
-    """Rows per weight-gradient split of the GPU's backward pass."""
-    r = -(-rows // splits)
-    r = -(-r // bk) * bk
-    return max(r, 128)
+def bw_accumulations(rows):
+    """Additions behind one weight or bias gradient in the GPU's backward
+    pass: each CTA sums its own rows (about four 128-row tiles, every CTA at
+    least one tile), then the CTAs' partials are summed in order."""
+    tiles = max(1, -(-rows // 128))
+    n = -(-tiles // 4)
+    tpc = -(-tiles // n)
+    ncta = -(-tiles // tpc)
+    return tpc * 128 + ncta
 
 
 def grad_bounds(p, X, y, res, w, out_gpu_bound=None):
@@ -72,9 +76,8 @@ def grad_bounds(p, X, y, res, w, out_gpu_bound=None):
       d_out = w (sigmoid(z) - y) / B, w y (1 - r^2 e^{-2v}) / B in FP32
       (sigmoid' <= 1/4; expf within 2 ulp; 10 roundings of the largest
       magnitude involved, generously),
-      dP = bf16(d_out), then per layer dW = dP^T A (split-K over the rows:
-      n = rows per split + splits), db = column sums of dP (256 strided
-      partial sums, then a tree: n = B/256 + 8), and
+      dP = bf16(d_out), then per layer dW = dP^T A and db = column sums of
+      dP (per CTA over its rows, then over the CTAs: bw_accumulations), and
       dP_prev = bf16(relu gate of (dP W)) (n = K).
     """
     B = X.shape[0]
@@ -93,8 +96,7 @@ def grad_bounds(p, X, y, res, w, out_gpu_bound=None):
     dP = mlp.bf16(d_out)
     ddP = bf16_step(d_out, np.stack([dd0, dd1], 1))
     layers = mlp.unpack(np.asarray(p, np.float64))
-    n_w = split_rows(B) + -(-B // split_rows(B))
-    n_b = -(-B // 256) + 8
+    n_w = n_b = bw_accumulations(B)
     gb = [None] * 4
     for li in range(3, -1, -1):
         W, _ = layers[li]
@@ -164,10 +166,10 @@ def check_signal(sig_in, W, gate, got):
 
 
 def check_weight_grad(sig, a_in, gW, gb):
-    """dW = sig^T a_in over the rows (split-K) and db = column sums of sig."""
+    """dW = sig^T a_in over the rows and db = column sums of sig, each summed
+    per CTA then over the CTAs."""
     B = sig.shape[0]
-    n_w = split_rows(B) + -(-B // split_rows(B))
-    n_b = -(-B // 256) + 8
+    n_w = n_b = bw_accumulations(B)
     vW = sig.T @ a_in
     dW = gamma(n_w) * (np.abs(sig).T @ np.abs(a_in))
     vb = sig.sum(0)
