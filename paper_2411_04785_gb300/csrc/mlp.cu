@@ -178,19 +178,21 @@ struct Work {
     int64_t rows;
 };
 
-// The CTA plan of the backward kernels for `rows` rows: about four 128-row
-// tiles per CTA (fewer CTAs' partials to sum), every CTA with at least one.
-constexpr int kRowTile = 128, kBwTilesPerCta = 4;
+// The CTA plan of the backward kernels for `rows` rows on `sms` SMs: the
+// 128-row tiles spread over at most min(sms, 256) CTAs, tpc consecutive
+// tiles each (a batch of at most one tile per SM gets one tile per CTA);
+// every CTA has at least one tile.
+constexpr int kRowTile = 128, kBwMaxCtas = 256;
 struct BwPlan {
     int64_t tiles;
     int tpc, ncta;
 };
-inline BwPlan bw_plan(int64_t rows) {
+inline BwPlan bw_plan(int64_t rows, int sms) {
     BwPlan p;
     p.tiles = (rows + kRowTile - 1) / kRowTile;
     if (p.tiles < 1) p.tiles = 1;
-    const int64_t n = (p.tiles + kBwTilesPerCta - 1) / kBwTilesPerCta;
-    p.tpc = (int)((p.tiles + n - 1) / n);
+    const int64_t cap = sms < 1 ? 1 : (sms < kBwMaxCtas ? sms : kBwMaxCtas);
+    p.tpc = (int)((p.tiles + cap - 1) / cap);
     p.ncta = (int)((p.tiles + p.tpc - 1) / p.tpc);
     return p;
 }
@@ -210,7 +212,10 @@ size_t work_layout(int64_t rows, Work *w, char *base) {
     w->out = (float *)take(rows * 2 * sizeof(float));
     w->dout = (bf16 *)take(rows * 2 * sizeof(bf16));
     for (int l = 0; l < 2; l++) w->dP[l] = (bf16 *)take(rows * kH * sizeof(bf16));
-    w->part = (float *)take(bw_part_floats(bw_plan(rows).ncta) * sizeof(float));
+    const int64_t tiles = (rows + kRowTile - 1) / kRowTile;     // the most CTAs any plan has
+    w->part = (float *)take(bw_part_floats((int)(tiles < kBwMaxCtas ? (tiles < 1 ? 1 : tiles)
+                                                                     : kBwMaxCtas)) *
+                            sizeof(float));
     w->loss_part = (float *)take(((rows + 255) / 256) * sizeof(float));
     w->rows = rows;
     return off;
@@ -640,7 +645,8 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
 // tcgen05.mma, FP32 accumulators in TMEM:
 //   D1 = dZ_l W_l               the signal through the layer (l = 3, 2):
 //                               A = the dZ tile (K-major, K = 128 outputs),
-//                               B = W_l^T staged once per CTA (K-major);
+//                               B = W_l as stored, [output][input], staged
+//                               once per CTA as an MN-major operand;
 //   D2 += dZ_l^T H_(l-1)        the weight gradient over the CTA's rows:
 //                               both operands are the same tiles read
 //                               MN-major (the row is K), so nothing is
@@ -666,7 +672,7 @@ static_assert(kTM == kRowTile, "backward tiles are the forward's");
 struct BwSmem {                           // every operand block 1024-byte aligned
     bf16 dz[kBwStages][2][kTM * 64];      // signal tile: 2 blocks [row][64], 128B swizzle
     bf16 hp[kBwStages][2][kTM * 64];      // layer input tile (features: [row][16], 32B swizzle)
-    bf16 wt[2][kH * 64];                  // W^T: [n = input][64 k = output], 2 k blocks
+    bf16 wt[2][kH * 64];                  // W: [o = output][64 n = input], 2 n blocks
     bf16 out[2][kTM * 64];                // the gated signal before its TMA store
     bf16 ones[kTM * 16];                  // [row][16] = (1, 0, ..., 0), 32B swizzle
     unsigned long long full[kBwStages], empty[kBwStages], d1_full, d1_free, fin;
@@ -738,11 +744,25 @@ k_mlp_bwd_tc(const __grid_constant__ CUtensorMap dzmap, const __grid_constant__ 
     const int nt = (int)(a.tiles - t0 < a.tpc ? a.tiles - t0 : a.tpc);
     const bool wide = a.nin == kH;
 
-    if (kData) {                          // W^T into its K-major swizzled place
-        for (int i = tid; i < kH * kH; i += blockDim.x) {
-            const int o = i / kH, n = i % kH;          // W[o][n] -> B[n][k = o]
-            char *blk = reinterpret_cast<char *>(S.wt[o >> 6]);
-            *reinterpret_cast<bf16 *>(blk + sw128(n, (o & 63) >> 3) + 2 * (o & 7)) = a.w[i];
+    if (kData) {       // W as it is stored, [o][n], is the MN-major B operand of D1
+        const uint4 *wg = reinterpret_cast<const uint4 *>(a.w);
+        constexpr int kChunks = kH * kH / 8;      // 16-byte chunks: row o, columns 8 c..
+        for (int i0 = tid; i0 < kChunks; i0 += 4 * kBwWarps * 32) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * kBwWarps * 32;
+                v[u] = i < kChunks ? wg[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * kBwWarps * 32;
+                if (i < kChunks) {
+                    const int o = i >> 4, c = i & 15;
+                    *reinterpret_cast<uint4 *>(reinterpret_cast<char *>(S.wt[c >> 3]) +
+                                               sw128(o, c & 7)) = v[u];
+                }
+            }
         }
     }
     for (int r = tid; r < kTM; r += blockDim.x) {     // the constant block
@@ -796,7 +816,7 @@ k_mlp_bwd_tc(const __grid_constant__ CUtensorMap dzmap, const __grid_constant__ 
                 if (!mbar_wait(&S.full[j % kBwStages], (j / kBwStages) & 1)) *err = 1;
         }
     } else if (warp == 1) {               // MMA issuer (whole warp, one elected lane issues)
-        const uint64_t dw = sdesc(smem_u32(S.wt[0]), 1024, kSw128);
+        const uint64_t dw = sdesc_mn(smem_u32(S.wt[0]), kH * 128, 1024, kSw128);
         const uint64_t d1s = sdesc_mn(smem_u32(S.ones), 4096, 256, kSw32);
         bool ok = true;
         for (int k = 0; k < nt && ok; k++) {
@@ -811,9 +831,8 @@ k_mlp_bwd_tc(const __grid_constant__ CUtensorMap dzmap, const __grid_constant__ 
 #pragma unroll
                 for (int kk = 0; kk < 8; kk++) {
                     const uint64_t off = (uint64_t)(kk >> 2) * (kTM * 128 / 16) + (uint64_t)((kk & 3) * 2);
-                    umma_ss(tmem + kD1Col, da + off,
-                            dw + (uint64_t)(kk >> 2) * (kH * 128 / 16) + (uint64_t)((kk & 3) * 2),
-                            idesc(kTM, kH), kk > 0);
+                    umma_ss(tmem + kD1Col, da + off, dw + (uint64_t)(kk * 2048 / 16),
+                            idesc(kTM, kH) | (1u << 16), kk > 0);   // B MN-major
                 }
                 umma_commit(&S.d1_full);
             }
@@ -928,33 +947,51 @@ k_mlp_bwd_tc(const __grid_constant__ CUtensorMap dzmap, const __grid_constant__ 
 // Layer 4 on CUDA cores (its products have K = 2 or M = 2, below one
 // tensor-core tile): dZ3 = bf16((dout W4) gated by H3 > 0), and the CTA's
 // partial gradients of layer 4 over its rows, part[cta][o][n] =
-// sum_r dout[r][o] H3[r][n] and part[cta][o][128] = sum_r dout[r][o].  One
-// thread per column n, the rows in order.
-__global__ void __launch_bounds__(kH) k_bwd_out(const bf16 *__restrict__ dout,
-                                                const bf16 *__restrict__ h3,
-                                                const bf16 *__restrict__ w4, int64_t rows, int tpc,
-                                                bf16 *__restrict__ dz3, float *__restrict__ part) {
-    const int n = threadIdx.x;
+// sum_r dout[r][o] H3[r][n] and part[cta][o][128] = sum_r dout[r][o].
+// kOutGroups row groups of 128 threads (one per column n) take every
+// kOutGroups-th row; their sums are added in group order.
+constexpr int kOutGroups = 4;
+__global__ void __launch_bounds__(kOutGroups * kH)
+k_bwd_out(const bf16 *__restrict__ dout, const bf16 *__restrict__ h3,
+          const bf16 *__restrict__ w4, int64_t rows, int tpc, bf16 *__restrict__ dz3,
+          float *__restrict__ part) {
+    __shared__ float red[kOutGroups][4][kH];
+    const int n = threadIdx.x % kH, grp = threadIdx.x / kH;
     const float w0 = __bfloat162float(w4[n]), w1 = __bfloat162float(w4[kH + n]);
     const int64_t r0 = (int64_t)blockIdx.x * tpc * kTM;
     const int64_t r1 = rows < r0 + (int64_t)tpc * kTM ? rows : r0 + (int64_t)tpc * kTM;
     float g0 = 0.0f, g1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-    for (int64_t r = r0; r < r1; r++) {
-        const float d0 = __bfloat162float(dout[2 * r]), d1 = __bfloat162float(dout[2 * r + 1]);
+#pragma unroll 4
+    for (int64_t r = r0 + grp; r < r1; r += kOutGroups) {
+        const __nv_bfloat162 d = reinterpret_cast<const __nv_bfloat162 *>(dout)[r];
+        const float d0 = __low2float(d), d1 = __high2float(d);
         const float h = __bfloat162float(h3[r * kH + n]);
         const float v = d0 * w0 + d1 * w1;
-        if (CC_IN_BOUNDS(CC_SITE_MLP_ROWS, r, rows)) dz3[r * kH + n] = __float2bfloat16(h > 0.0f ? v : 0.0f);
+        if (CC_IN_BOUNDS(CC_SITE_MLP_ROWS, r, rows))
+            dz3[r * kH + n] = __float2bfloat16(h > 0.0f ? v : 0.0f);
         g0 = fmaf(d0, h, g0);
         g1 = fmaf(d1, h, g1);
         b0 += d0;
         b1 += d1;
     }
-    float *p = part + (int64_t)blockIdx.x * 2 * (kH + 1);
-    p[n] = g0;
-    p[kH + 1 + n] = g1;
-    if (n == 0) {
-        p[kH] = b0;
-        p[2 * kH + 1] = b1;
+    red[grp][0][n] = g0;
+    red[grp][1][n] = g1;
+    red[grp][2][n] = b0;
+    red[grp][3][n] = b1;
+    __syncthreads();
+    if (grp == 0) {
+        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int g = 0; g < kOutGroups; g++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) s[q] += red[g][q][n];
+        float *p = part + (int64_t)blockIdx.x * 2 * (kH + 1);
+        p[n] = s[0];
+        p[kH + 1 + n] = s[1];
+        if (n == 0) {
+            p[kH] = s[2];
+            p[2 * kH + 1] = s[3];
+        }
     }
 }
 
@@ -1070,7 +1107,7 @@ cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint
     const unsigned nb = (unsigned)((rows + 255) / 256);
     k_loss_grad<<<nb, 256, 0, s>>>(w.out, y, res, wv, rows, inv_total, w.dout, w.loss_part);
     if ((e = cudaGetLastError())) return e;
-    const BwPlan pl = bw_plan(rows);
+    const BwPlan pl = bw_plan(rows, device_sm_count());
     GradParts gp;
     gp.ncta = pl.ncta;
     gp.part[0] = w.part;                                           // layer 1: [.][128][17]
@@ -1078,8 +1115,9 @@ cudaError_t grad_rows(const bf16 *wb, const float *pf, const bf16 *X, const uint
     gp.part[2] = gp.part[1] + (size_t)pl.ncta * kH * (kH + 1);
     gp.part[3] = gp.part[2] + (size_t)pl.ncta * kH * (kH + 1);      // layer 4: [.][2][129]
     // layer 4 (CUDA cores), then layers 3, 2, 1 on the tensor cores
-    k_bwd_out<<<(unsigned)pl.ncta, kH, 0, s>>>(w.dout, w.H[2], wb + oW4, rows, pl.tpc, dZ[2],
-                                               const_cast<float *>(gp.part[3]));
+    k_bwd_out<<<(unsigned)pl.ncta, kOutGroups * kH, 0, s>>>(w.dout, w.H[2], wb + oW4, rows,
+                                                            pl.tpc, dZ[2],
+                                                            const_cast<float *>(gp.part[3]));
     if ((e = cudaGetLastError())) return e;
     if ((e = bwd_layer(dZ[2], w.H[1], kH, wb + oW3, dZ[1], rows, pl,
                        const_cast<float *>(gp.part[2]), s)))

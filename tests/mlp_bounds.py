@@ -59,18 +59,19 @@ def forward_bounds(p, X):
     return out, dz, A, dA
 
 
-def bw_accumulations(rows):
+def bw_accumulations(rows, sms):
     """Additions behind one weight or bias gradient in the GPU's backward
-    pass: each CTA sums its own rows (about four 128-row tiles, every CTA at
-    least one tile), then the CTAs' partials are summed in order."""
+    pass on `sms` SMs: each CTA sums its own rows (tpc 128-row tiles, the
+    tiles spread over at most min(sms, 256) CTAs), then the CTAs' partials
+    are summed in order.  With sms = 1 it bounds a plain sequential sum."""
     tiles = max(1, -(-rows // 128))
-    n = -(-tiles // 4)
-    tpc = -(-tiles // n)
+    cap = max(1, min(sms, 256))
+    tpc = -(-tiles // cap)
     ncta = -(-tiles // tpc)
     return tpc * 128 + ncta
 
 
-def grad_bounds(p, X, y, res, w, out_gpu_bound=None):
+def grad_bounds(p, X, y, res, w, sms=1):
     """(want_grad, bound) for the flat gradient: the GPU's backward pass from
     its own forward outputs (bounded by forward_bounds), through
       d_out = w (sigmoid(z) - y) / B, w y (1 - r^2 e^{-2v}) / B in FP32
@@ -96,7 +97,7 @@ def grad_bounds(p, X, y, res, w, out_gpu_bound=None):
     dP = mlp.bf16(d_out)
     ddP = bf16_step(d_out, np.stack([dd0, dd1], 1))
     layers = mlp.unpack(np.asarray(p, np.float64))
-    n_w = n_b = bw_accumulations(B)
+    n_w = n_b = bw_accumulations(B, sms)
     gb = [None] * 4
     for li in range(3, -1, -1):
         W, _ = layers[li]
@@ -165,11 +166,11 @@ def check_signal(sig_in, W, gate, got):
     return in_bf16_interval(got, v, d)
 
 
-def check_weight_grad(sig, a_in, gW, gb):
+def check_weight_grad(sig, a_in, gW, gb, sms=1):
     """dW = sig^T a_in over the rows and db = column sums of sig, each summed
     per CTA then over the CTAs."""
     B = sig.shape[0]
-    n_w = n_b = bw_accumulations(B)
+    n_w = n_b = bw_accumulations(B, sms)
     vW = sig.T @ a_in
     dW = gamma(n_w) * (np.abs(sig).T @ np.abs(a_in))
     vb = sig.sum(0)

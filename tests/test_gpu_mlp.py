@@ -41,6 +41,10 @@ def random_case(seed, B):
     return p, X, y, res, w
 
 
+def SMS():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
 def f64(t):
     return t.float().cpu().numpy().astype(np.float64)
 
@@ -121,7 +125,7 @@ def test_training_step_stage_by_stage(cc, dev, B):
     gl = mlp.unpack(grad)
     sigs = [S[1], S[2], S[3], dout]
     for li in range(4):
-        okW, okb = mb.check_weight_grad(sigs[li], H[li], gl[li][0], gl[li][1])
+        okW, okb = mb.check_weight_grad(sigs[li], H[li], gl[li][0], gl[li][1], sms=SMS())
         assert okW.all() and okb.all(), ("grad", li + 1, np.argwhere(~okW)[:3])
     want_loss, _ = mlp.loss_and_grad(p, X, yf, rf, wf, round_points=True)
     assert l_tr == pytest.approx(want_loss, rel=1e-4, abs=1e-7)
@@ -138,7 +142,8 @@ def test_gradient_matches_oracle(cc, dev, B):
     Xd = to_dev(X.astype(np.float32), dev).to(torch.bfloat16).contiguous()
     _, g = f.grad(Xd, to_dev(y, dev), to_dev(res, dev), to_dev(w, dev))
     torch.cuda.synchronize()
-    want, bound = grad_bounds(p, X, y.astype(float), res.astype(np.float64), w.astype(float))
+    want, bound = grad_bounds(p, X, y.astype(float), res.astype(np.float64), w.astype(float),
+                              sms=SMS())
     got = g.cpu().numpy().astype(np.float64)
     bad = np.nonzero(np.abs(got - want) > bound)[0]
     assert bad.size == 0, (bad[:5], got[bad[:5]], want[bad[:5]], bound[bad[:5]])
