@@ -73,6 +73,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Tensor store of a shared-memory tile (bulk group; the caller commits the
+// group and waits for it before the tile is reused or the CTA exits).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+        "r"(x), "r"(y), "r"(smem_u32(src))
+        : "memory");
+}
+
 // Bounded wait for an mbarrier phase: false after limit_ns.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           unsigned long long limit_ns = kWaitLimitNs) {

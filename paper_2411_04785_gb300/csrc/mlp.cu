@@ -706,13 +706,6 @@ __device__ __forceinline__ void tmem_ld16(unsigned addr, uint32_t (&r)[16]) {
         : "memory");
 }
 
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
-        "r"(x), "r"(y), "r"(smem_u32(src))
-        : "memory");
-}
-
 __device__ __forceinline__ void epi_sync() {   // the epilogue warps only
     asm volatile("bar.sync 1, %0;" ::"r"(kBwEpiWarps * 32) : "memory");
 }
