@@ -82,7 +82,7 @@ def main(path):
     img, _, _ = cc.backproject(rings, apex, vox, p)
     res["image"] = img.cpu().numpy()
 
-    # one training step of the ring filter (tensor-core forward, GEMM backward)
+    # one training step of the ring filter (forward and backward on the tensor cores)
     from oracle import mlp
     rng = np.random.default_rng(2)
     X = torch.from_numpy(mlp.bf16(rng.standard_normal((777, 16))).astype(np.float32))
