@@ -108,7 +108,7 @@ struct SweepPlan {
 // occupancy the plan sizes the grid for (NULL: the far-field sweep).
 typedef void *(*SweepPick)(int d, bool kcut);
 bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d = 0,
-                SweepPick pick = nullptr, size_t rec_bytes = 48);
+                SweepPick pick = nullptr, size_t rec_bytes = sizeof(RingRec));
 // Ring compaction shared by the sweeps: blocks of kPackChunk rings are
 // counted, the counts are scanned into block offsets (in place) and the total
 // is written to *nkept; the plan's split reduction, argmax and seeds follow a
