@@ -15,24 +15,30 @@
 // in three launches that never wait on one another's CTAs:
 //   k_cluster_masks   per tile of 4096 detections: the step masks from t,
 //                     the edges, the masks themselves (2 bits per detection,
-//                     for the third launch) and the tile's aggregate;
+//                     for the third launch) and the tile's aggregate, whose
+//                     amplitude part needs only the detections from the
+//                     tile's last event start on;
 //   k_cluster_scan    the exclusive prefix of the tile aggregates within
 //                     groups of 1024 tiles, and each group's total;
 //   k_cluster_events  per tile: the masks and amplitudes again, the local scan
 //                     from the tile's prefix, event ids and per-event outputs.
 // The scan state of a range of detections is (starts in it, index of its last
-// start, its amplitude sum, its amplitude sum before its last start), which
-// composes associatively, so an event's amplitude sum is the difference of
-// two prefix sums taken at its two edges with no per-event atomics.  All
+// start, its tail: the amplitude sum from its last start to its end, or over
+// all of it when it holds no start), which composes associatively (a
+// segmented sum that restarts at every start), so an event's amplitude sum
+// is the tail carried into its lane plus the lane's own prefix sum, with no
+// per-event atomics.  All
 // arithmetic is integer: results are exact.  A tile's time stamps and
 // amplitudes arrive in shared memory by TMA tensor copies (128-byte rows in
 // the 128B swizzle, so that a lane reading its own row never conflicts with
 // its neighbours), and its event ids leave the same way; every lane owns 16
 // consecutive detections and scans them serially, and the lanes of a warp
 // combine their aggregates in one warp scan per 16 detections.
-// Traffic per detection: t and adc read, edges and masks written, then masks
-// and adc read again and event ids written: 12 + 1.25 + 4.25 + 4 bytes plus
-// the per-event outputs, against 17 + 20 per event for the outputs alone.
+// Traffic per detection: t read, edges and masks written, then masks and adc
+// read and event ids written: 8 + 1.25 + 4.25 + 4 bytes, plus the per-event
+// outputs and each tile's tail amplitudes (a few dozen detections, all 4096
+// for a tile inside one event), against 17 + 20 per event for the inputs and
+// outputs alone.
 #include <string.h>
 
 #include "cc_internal.cuh"
@@ -49,23 +55,21 @@ constexpr int kTileSpan = kWarpSpan * kCWarps;   // 4096 per CTA
 struct Carry {
     long long starts;              // event starts in the range
     long long last_start;          // index of the range's last start, -1 if none
-    unsigned long long sum;        // amplitude sum over the range
-    unsigned long long sum_before; // amplitude sum of the range before its last start
+    unsigned long long tail;       // amplitude sum from the last start on (all: no start)
 };
 
-__device__ __forceinline__ Carry identity() { return Carry{0, -1, 0ull, 0ull}; }
+__device__ __forceinline__ Carry identity() { return Carry{0, -1, 0ull}; }
 
 // a covers the detections just before those of b
 __device__ __forceinline__ Carry combine(const Carry &a, const Carry &b) {
     Carry c;
     c.starts = a.starts + b.starts;
-    c.sum = a.sum + b.sum;
     if (b.last_start >= 0) {
         c.last_start = b.last_start;
-        c.sum_before = a.sum + b.sum_before;
+        c.tail = b.tail;
     } else {
         c.last_start = a.last_start;
-        c.sum_before = a.sum_before;
+        c.tail = a.tail + b.tail;
     }
     return c;
 }
@@ -73,8 +77,7 @@ __device__ __forceinline__ Carry combine(const Carry &a, const Carry &b) {
 __device__ __forceinline__ Carry shfl_up_carry(const Carry &c, int o) {
     return Carry{__shfl_up_sync(0xffffffffu, c.starts, o),
                  __shfl_up_sync(0xffffffffu, c.last_start, o),
-                 __shfl_up_sync(0xffffffffu, c.sum, o),
-                 __shfl_up_sync(0xffffffffu, c.sum_before, o)};
+                 __shfl_up_sync(0xffffffffu, c.tail, o)};
 }
 
 // step from a to b in wrapping 64-bit arithmetic (meaningful for |step| < 2^63)
@@ -92,36 +95,39 @@ __device__ __forceinline__ int a_off(int e) { return swz(e >> 5, (e & 31) >> 2) 
 
 // Stage a tile of 4096 detections starting at `base`: by tensor copies when
 // the tile is whole inside the maps (tma), else by plain loads (0 past the
-// end).  `tsw` may be null (amplitudes only), and the amplitudes are 0
-// without adc.  Thread 0 waits (bounded); returns false on a timeout.
+// end).  `tsw` may be null (amplitudes only), `asw` null (time stamps only),
+// and the amplitudes are 0 without adc.  Thread 0 waits (bounded); returns
+// false on a timeout.
 __device__ __forceinline__ bool stage_tile(unsigned char *tsw, unsigned char *asw,
                                            unsigned long long *bar, const CUtensorMap *tmap,
                                            const CUtensorMap *amap, bool tma,
                                            const long long *__restrict__ t,
                                            const unsigned *__restrict__ adc, long long N,
                                            long long base) {
+    const bool amps = asw != nullptr, load_amps = amps && adc != nullptr;
     if (tma) {
         if (threadIdx.x == 0) {
-            const unsigned bytes = (tsw ? kTileSpan * 8u : 0u) + (adc ? kTileSpan * 4u : 0u);
+            const unsigned bytes = (tsw ? kTileSpan * 8u : 0u) + (load_amps ? kTileSpan * 4u : 0u);
             if (bytes) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                                  smem_u32(bar)), "r"(bytes)
                              : "memory");
                 if (tsw) tma_load_2d(tsw, tmap, 0, (int)(base / 16), bar);
-                if (adc) tma_load_2d(asw, amap, 0, (int)(base / 32), bar);
+                if (load_amps) tma_load_2d(asw, amap, 0, (int)(base / 32), bar);
             } else {
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
             }
         }
-        if (adc == nullptr)
+        if (amps && adc == nullptr)
             for (int e = threadIdx.x; e < kTileSpan; e += kCThreads)
                 *reinterpret_cast<unsigned *>(asw + a_off(e)) = 0u;
     } else {
         for (int e = threadIdx.x; e < kTileSpan; e += kCThreads) {
             const long long g = base + e;
             if (tsw) *reinterpret_cast<long long *>(tsw + t_off(e)) = g < N ? __ldcs(t + g) : 0;
-            *reinterpret_cast<unsigned *>(asw + a_off(e)) =
-                (adc != nullptr && g < N) ? __ldcs(adc + g) : 0u;
+            if (amps)
+                *reinterpret_cast<unsigned *>(asw + a_off(e)) =
+                    (adc != nullptr && g < N) ? __ldcs(adc + g) : 0u;
         }
     }
     return !(tma && threadIdx.x == 0 && !mbar_wait(bar, 0));
@@ -138,19 +144,6 @@ __device__ __forceinline__ void lane_adc(const unsigned char *asw, int e0, unsig
         a[4 * c + 2] = v.z;
         a[4 * c + 3] = v.w;
     }
-}
-
-// The lane's aggregate: starts (sbits), last start, amplitude sums.
-__device__ __forceinline__ Carry lane_carry(unsigned sbits, long long i0, const unsigned (&a)[16]) {
-    Carry mine{__popc(sbits), -1, 0ull, 0ull};
-    const int lastk = sbits ? 31 - __clz((int)sbits) : -1;
-    if (lastk >= 0) mine.last_start = i0 + lastk;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-        mine.sum += a[k];
-        if (k < lastk) mine.sum_before += a[k];
-    }
-    return mine;
 }
 
 // Masks of the lane's detections (tile elements e0 .. e0 + 15, global i0 ..)
@@ -190,33 +183,20 @@ __device__ __forceinline__ void lane_masks(const unsigned char *tsw, long long t
     }
 }
 
-// The tile's aggregate from the lanes' (lane 0 of each warp after the ordered
-// reduction, warps in order): written by thread 0 to *out.
-__device__ __forceinline__ Carry warp_reduce(Carry v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {   // ordered tree: lane l combines l and l + o
-        const Carry y{__shfl_down_sync(0xffffffffu, v.starts, o),
-                      __shfl_down_sync(0xffffffffu, v.last_start, o),
-                      __shfl_down_sync(0xffffffffu, v.sum, o),
-                      __shfl_down_sync(0xffffffffu, v.sum_before, o)};
-        if (lane + o < 32) v = combine(v, y);
-    }
-    return v;
-}
-
 struct MasksSmem {
     unsigned char tsw[kTileSpan * 8];
-    unsigned char asw[kTileSpan * 4];
     long long t_prev, t_next;
     unsigned long long bar;
-    Carry wagg[kCWarps];
+    long long wstarts[kCWarps];
+    long long wlast[kCWarps];
+    unsigned long long wtail[kCWarps];
     int failed;
 };
 
 __global__ void __launch_bounds__(kCThreads, 4)
-k_cluster_masks(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap amap,
-                int use_tma, const long long *__restrict__ t, const unsigned *__restrict__ adc,
-                long long N, long long dt_max, int vec_out, unsigned char *__restrict__ edge,
+k_cluster_masks(const __grid_constant__ CUtensorMap tmap, int use_tma,
+                const long long *__restrict__ t, const unsigned *__restrict__ adc, long long N,
+                long long dt_max, int vec_out, unsigned char *__restrict__ edge,
                 unsigned *__restrict__ masks, Carry *__restrict__ aggs, int *__restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     MasksSmem &S = *reinterpret_cast<MasksSmem *>(
@@ -234,11 +214,15 @@ k_cluster_masks(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
         S.t_prev = base > 0 ? __ldg(t + base - 1) : 0;
         S.t_next = base + kTileSpan < N ? __ldg(t + base + kTileSpan) : 0;
     }
-    if (!stage_tile(S.tsw, S.asw, &S.bar, &tmap, &amap, tma, t, adc, N, base)) S.failed = 1;
+    // the amplitudes of the tile's last 256 detections, loaded while the time
+    // stamps arrive: the tile's tail (below) nearly always lies inside them
+    const long long pref0 = base + kTileSpan - kCThreads, gp = pref0 + threadIdx.x;
+    const unsigned a_pref = (adc != nullptr && gp < N) ? __ldg(adc + gp) : 0u;
+    if (!stage_tile(S.tsw, nullptr, &S.bar, &tmap, nullptr, tma, t, nullptr, N, base)) S.failed = 1;
     __syncthreads();
     if (S.failed) {               // a bounded wait gave up: report, and go on with zeros
         if (threadIdx.x == 0) atomicExch(status, (int)CC_ETIMEOUT);
-        for (int i = threadIdx.x; i < kTileSpan * 12 / 16; i += kCThreads)
+        for (int i = threadIdx.x; i < kTileSpan * 8 / 16; i += kCThreads)
             reinterpret_cast<int4 *>(S.tsw)[i] = make_int4(0, 0, 0, 0);
         __syncthreads();
     }
@@ -264,16 +248,43 @@ k_cluster_masks(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                     edge[i0 + k] = (unsigned char)((eb >> k) & 1u);
         }
     }
-    unsigned a[16];
-    lane_adc(S.asw, e0, a);
-    const Carry v = warp_reduce(lane_carry(ma & ~mb, i0, a), lane);
-    if (lane == 0) S.wagg[w] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Carry acc = identity();
-        for (int k = 0; k < kCWarps; k++) acc = combine(acc, S.wagg[k]);
-        aggs[blockIdx.x] = acc;
+    // the tile's starts and its last start
+    const unsigned sbits = ma & ~mb;
+    long long st = __popc(sbits);
+    long long last = sbits ? i0 + (31 - __clz((int)sbits)) : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+        last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
     }
+    if (lane == 0) {
+        S.wstarts[w] = st;
+        S.wlast[w] = last;
+    }
+    __syncthreads();
+    long long tile_starts = 0, tile_last = -1;
+#pragma unroll
+    for (int k = 0; k < kCWarps; k++) {
+        tile_starts += S.wstarts[k];
+        tile_last = max(tile_last, S.wlast[k]);
+    }
+    // its tail: the amplitudes from the last start to the tile's end (the
+    // whole tile when it holds no start)
+    unsigned long long tail = 0;
+    if (adc != nullptr) {
+        const long long end = base + kTileSpan < N ? base + kTileSpan : N;
+        const long long from = tile_last >= 0 ? tile_last : base;
+        if (gp >= from && gp < end) tail = a_pref;
+        const long long stop = end < pref0 ? end : pref0;   // the rest: a long last event
+        for (long long g = from + threadIdx.x; g < stop; g += kCThreads) tail += __ldg(adc + g);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+        if (lane == 0) S.wtail[w] = tail;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 1; k < kCWarps; k++) tail += S.wtail[k];
+    }
+    if (threadIdx.x == 0) aggs[blockIdx.x] = Carry{tile_starts, tile_last, tail};
 }
 constexpr size_t kMasksSmemBytes = sizeof(MasksSmem) + 1024;
 
@@ -322,8 +333,7 @@ __device__ __forceinline__ Carry groups_before(const Carry *__restrict__ gtot, l
         const Carry s = warp_incl_scan(v, lane);
         const Carry chunk = Carry{__shfl_sync(0xffffffffu, s.starts, 31),
                                   __shfl_sync(0xffffffffu, s.last_start, 31),
-                                  __shfl_sync(0xffffffffu, s.sum, 31),
-                                  __shfl_sync(0xffffffffu, s.sum_before, 31)};
+                                  __shfl_sync(0xffffffffu, s.tail, 31)};
         run = combine(run, chunk);
     }
     return run;
@@ -407,7 +417,7 @@ k_cluster_events(const __grid_constant__ CUtensorMap amap, const __grid_constant
             reinterpret_cast<int4 *>(S.asw)[i] = make_int4(0, 0, 0, 0);
         __syncthreads();
     }
-    Carry mine{__popc(sbits), -1, 0ull, 0ull};
+    Carry mine{__popc(sbits), -1, 0ull};
     {
         unsigned a[16];
         lane_adc(S.asw, e0, a);
@@ -418,10 +428,10 @@ k_cluster_events(const __grid_constant__ CUtensorMap amap, const __grid_constant
             S.psum[k][threadIdx.x] = run;
         }
         const int lastk = sbits ? 31 - __clz((int)sbits) : -1;
-        mine.sum = run;
+        mine.tail = run;
         if (lastk >= 0) {
             mine.last_start = i0 + lastk;
-            mine.sum_before = lastk > 0 ? S.psum[lastk - 1][threadIdx.x] : 0ull;
+            mine.tail = run - (lastk > 0 ? S.psum[lastk - 1][threadIdx.x] : 0ull);
         }
     }
     const Carry incl = warp_incl_scan(mine, lane);
@@ -442,7 +452,8 @@ k_cluster_events(const __grid_constant__ CUtensorMap amap, const __grid_constant
 
     // per-event outputs at the lane's ends: the event's id is the count of
     // starts up to it, its first detection the last start before it (in the
-    // lane, or carried in), its sum a difference of prefix sums
+    // lane, or carried in), its sum a difference of the lane's prefix sums
+    // (start in the lane) or the carried tail plus the lane's prefix sum
     const unsigned valid = i0 + 16 <= N ? 0xFFFFu : (i0 >= N ? 0u : (1u << (unsigned)(N - i0)) - 1u);
     for (unsigned e = ebits & valid; e; e &= e - 1) {
         const int k = __ffs(e) - 1;
@@ -450,13 +461,13 @@ k_cluster_events(const __grid_constant__ CUtensorMap amap, const __grid_constant
         const long long id = c0.starts + __popc(upto) - 1;
         const int lk = upto ? 31 - __clz((int)upto) : -1;
         const long long first = lk >= 0 ? i0 + lk : c0.last_start;
-        const unsigned long long sum = c0.sum + S.psum[k][threadIdx.x];
-        const unsigned long long before =
-            lk >= 0 ? c0.sum + (lk > 0 ? S.psum[lk - 1][threadIdx.x] : 0ull) : c0.sum_before;
+        const unsigned long long upto_k = S.psum[k][threadIdx.x];
+        const unsigned long long sum =
+            lk >= 0 ? upto_k - (lk > 0 ? S.psum[lk - 1][threadIdx.x] : 0ull) : c0.tail + upto_k;
         if (CC_IN_BOUNDS(CC_SITE_CLUSTER_EVENT, id, ev_cap)) {
             if (ev_first) ev_first[id] = first;
             if (ev_count) ev_count[id] = (int)(i0 + k - first + 1);
-            if (ev_adc) ev_adc[id] = sum - before;
+            if (ev_adc) ev_adc[id] = sum;
         }
     }
     // event ids (fewer than 2^31 detections: they fit in 32 bits)
@@ -592,8 +603,7 @@ cudaError_t launch_cluster(const int64_t *t, const uint32_t *adc, int64_t n, int
         return e;
     TraceScope ts(CC_STAGE_CLUSTER, s);
     k_cluster_masks<<<(unsigned)tiles, kCThreads, kMasksSmemBytes, s>>>(
-        tmap, amap, use_tma, tl, adc, (long long)n, (long long)dt_max, vec_out, edge, masks, aggs,
-        st);
+        tmap, use_tma, tl, adc, (long long)n, (long long)dt_max, vec_out, edge, masks, aggs, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cluster_scan<<<(unsigned)groups, kScanThreads, 0, s>>>(aggs, (long long)tiles, excl, gtot);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -69,6 +69,24 @@ def test_one_event_across_every_tile_and_none(cc):
     assert got["count"].size == 0 and not got["edge"].any() and (got["event_id"] == -1).all()
 
 
+def test_long_events_that_cross_tiles(cc):
+    """Events of 1 to 9,000 detections (lengths around 256, the tail a tile
+    reads ahead, and longer than a tile) in random order: a tile's last event
+    starts anywhere in it and runs on into later tiles."""
+    rng = np.random.default_rng(21)
+    lens = rng.choice(np.array([1, 2, 3, 17, 200, 255, 256, 257, 300, 1000, 4095, 4097, 9000]),
+                      size=80)
+    steps = []
+    for L in lens:
+        steps += [1] * (int(L) - 1) + [50]          # joined inside an event, a gap after it
+    t = np.concatenate([[0], np.cumsum(steps[:-1])]).astype(np.int64)
+    adc = rng.integers(0, 1 << 32, t.size, dtype=np.uint64).astype(np.uint32)
+    got, _ = run(cc, t, adc, 2)
+    want = oracle.maxstep_events(t, adc, 2)
+    assert_same(got, want)
+    assert got["count"].size == int((lens > 1).sum())
+
+
 def test_pairs_steps_at_the_limit_and_large_times(cc):
     # alternating pair / gap pattern puts starts and ends on every lane and
     # row boundary; times near 2^62 exercise the 64-bit steps
