@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define CC_ABI_VERSION 1
+#define CC_ABI_VERSION 2
 
 typedef enum {
     CC_OK = 0,
@@ -79,10 +79,15 @@ typedef struct {
     int64_t count;
 } cc_rings;
 
-/* Sky grid: `count` unit direction vectors (x, y, z), structure of arrays. */
+/* Sky grid: `count` unit direction vectors (x, y, z), structure of arrays.
+ * order: NULL, or this grid's direction order from cc_grid_order (device
+ * int32 [count]) for cc_localize and cc_localize_static to reuse instead of
+ * computing it (in their workspace) on every call; it must belong to these
+ * directions. */
 typedef struct {
     const float *x, *y, *z;
     int64_t count;
+    const int32_t *order;
 } cc_grid;
 
 /* Parameters.  cc_params_default() fills the documented defaults. */
@@ -155,7 +160,10 @@ size_t cc_localize_workspace_bytes(int64_t rings, int64_t dirs,
  *              (seeds[0] = argmax; unfilled slots are -1).
  * Only valid rings with finite values and deta > 0 are swept: they are
  * compacted (in index order) before the sweep, so the sweep's time follows
- * the number of such rings, not rings->count.
+ * the number of such rings, not rings->count.  The directions are swept in
+ * the grid's compact order (cc_grid_order; grid->order when given, else
+ * computed in the workspace), which fixes the order of the FP32 sums: the
+ * map is the same bit for bit for the same rings and directions.
  * 0 <= rings->count <= 2^31 - 1 (0 gives an all-zero map), grid->count >= 1.
  * `map` [grid->count] float, `argmax` [1] int32, `seeds` [p->topk] int32
  * (may be NULL), `status` [1] int32 (may be NULL), `workspace` device
@@ -204,7 +212,8 @@ cc_status cc_localize_static(const cc_rings *rings, const cc_grid *grid,
  * NULL), status (may be NULL) and workspaces are host arrays of n device
  * pointers; ws_bytes [n] host.  Workspace i needs
  * cc_localize_batch_workspace_bytes(rings[i].count, grid->count, p) bytes.
- * 1 <= n <= CC_BATCH_MAX.
+ * The directions are swept in grid->order when given, else in grid order
+ * (nothing is computed for the order here).  1 <= n <= CC_BATCH_MAX.
  */
 #define CC_BATCH_MAX 64
 
@@ -260,6 +269,19 @@ cc_status cc_grid_healpix_ring(int32_t nside, float *x, float *y, float *z,
  * by the angular selection (p->k_cut > 0) where no ring reaches them. */
 cc_status cc_grid_healpix_nest(int32_t nside, float *x, float *y, float *z,
                                void *stream);
+
+/* The order in which cc_localize sweeps a grid's directions: the grid sorted
+ * by HEALPix NESTED pixel (Gorski et al. 2005) at the coarsest nside with at
+ * least count pixels, ties in index order, so that each warp's directions
+ * form a compact patch (a ring whose axis is far enough from the patch then
+ * lies wholly on one side of it, and its pairs skip the fold of the angle
+ * formula).  A HEALPix RING grid comes out in its NESTED order.  order
+ * [count] int32 device array (a permutation of 0..count-1); workspace of
+ * cc_grid_order_workspace_bytes(count) bytes (device, 256-byte aligned, else
+ * CC_EINVAL); grid a host pointer to device arrays. */
+size_t cc_grid_order_workspace_bytes(int64_t count);
+cc_status cc_grid_order(const cc_grid *grid, int32_t *order, void *workspace,
+                        size_t ws_bytes, void *stream);
 
 /* Gather k grid directions as FP64 unit vectors (e.g. seeds for
  * cc_refine): out_dirs[3t..3t+2] = grid[idx[t]], renormalised.  Negative

@@ -45,7 +45,7 @@ class cc_rings(C.Structure):
 
 
 class cc_grid(C.Structure):
-    _fields_ = [("x", _P), ("y", _P), ("z", _P), ("count", C.c_int64)]
+    _fields_ = [("x", _P), ("y", _P), ("z", _P), ("count", C.c_int64), ("order", _P)]
 
 
 class cc_detections(C.Structure):
@@ -104,6 +104,10 @@ def lib() -> C.CDLL:
         L.cc_grid_healpix_nest.restype = S
         L.cc_grid_gather.argtypes = [C.POINTER(cc_grid), _P, C.c_int32, _P, _P]
         L.cc_grid_gather.restype = S
+        L.cc_grid_order_workspace_bytes.argtypes = [C.c_int64]
+        L.cc_grid_order_workspace_bytes.restype = C.c_size_t
+        L.cc_grid_order.argtypes = [C.POINTER(cc_grid), _P, _P, C.c_size_t, _P]
+        L.cc_grid_order.restype = S
         L.cc_localize_static.argtypes = [C.POINTER(cc_rings), C.POINTER(cc_grid),
                                          C.POINTER(cc_params), _P, _P, _P, _P, _P]
         L.cc_localize_static.restype = S
@@ -166,7 +170,7 @@ def lib() -> C.CDLL:
         L.cc_trace_enable.restype = S
         L.cc_trace_read.argtypes = [C.POINTER(cc_stage_time), C.c_int32, C.c_int32]
         L.cc_trace_read.restype = S
-        if L.cc_abi_version() != 1:
+        if L.cc_abi_version() != 2:
             raise RuntimeError("libcompton.so ABI version mismatch")
         _lib = L
     return _lib
@@ -293,10 +297,17 @@ def localize_workspace_bytes(R: int, M: int, params: Params | None = None) -> in
 
 
 def _grid_struct(grid) -> cc_grid:
-    gx, gy, gz = grid
+    """(x, y, z) or (x, y, z, order): order from grid_order, reused by the sweep."""
+    gx, gy, gz = grid[:3]
     for t, nm in ((gx, "grid x"), (gy, "grid y"), (gz, "grid z")):
         _need(t, torch.float32, nm)
-    return cc_grid(_ptr(gx), _ptr(gy), _ptr(gz), gx.numel())
+    order = None
+    if len(grid) > 3 and grid[3] is not None:
+        _need(grid[3], torch.int32, "grid order")
+        if grid[3].numel() != gx.numel():
+            raise ValueError("grid order has the wrong length")
+        order = _ptr(grid[3])
+    return cc_grid(_ptr(gx), _ptr(gy), _ptr(gz), gx.numel(), order)
 
 
 def localize(rings: dict, grid, params: Params | None = None, workspace=None, out=None,
@@ -418,6 +429,19 @@ def grid_gather(grid, idx, out=None, stream=None):
     return out
 
 
+def grid_order(grid, stream=None):
+    """The order in which localize sweeps the grid's directions (int32 [M])."""
+    gs = _grid_struct(grid)
+    dev = grid[0].device
+    M = grid[0].numel()
+    out = torch.empty(M, dtype=torch.int32, device=dev)
+    nb = lib().cc_grid_order_workspace_bytes(M)
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=dev)
+    _check("cc_grid_order", lib().cc_grid_order(C.byref(gs), _ptr(out), _ptr(ws), nb,
+                                                _stream(stream)))
+    return out
+
+
 # --------------------------------------------------------------------------
 # the whole path
 # --------------------------------------------------------------------------
@@ -426,7 +450,8 @@ class Localizer:
     workspaces and outputs allocated once and reused across calls."""
 
     def __init__(self, grid, params: Params | None = None, max_rings: int = 0):
-        self.grid = grid
+        # the grid's direction order, computed once and reused by every sweep
+        self.grid = tuple(grid[:3]) + (grid[3] if len(grid) > 3 else grid_order(grid),)
         self.params = params or Params()
         self.M = grid[0].numel()
         self.dev = grid[0].device

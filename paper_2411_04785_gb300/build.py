@@ -25,7 +25,7 @@ BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libcompton_debug.so")
 DEBUG_FLAGS = ["-DCC_DEBUG_BOUNDS", "-rdc=true"]
 SOURCES = ["capi.cu", "recon.cu", "sweep.cu", "refine.cu", "grid.cu", "trace.cu", "cluster.cu", "voxel.cu",
-           "noalloc.cu", "mlp.cu", "selftest.cu"]
+           "noalloc.cu", "mlp.cu", "selftest.cu", "order.cu"]
 INCLUDE = os.path.join(HERE, "..", "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -257,6 +257,24 @@ cc_status cc_grid_healpix_nest(int32_t nside, float *x, float *y, float *z, void
     return CC_OK;
 }
 
+size_t cc_grid_order_workspace_bytes(int64_t count) {
+    return count < 1 ? 0 : direction_order_bytes(count);
+}
+
+cc_status cc_grid_order(const cc_grid *grid, int32_t *order, void *workspace, size_t ws_bytes,
+                        void *stream) {
+    g_err[0] = 0;
+    if (!grid || grid->count < 1 || grid->count > INT32_MAX || !grid->x || !grid->y || !grid->z)
+        return fail(CC_EINVAL, "bad grid");
+    if (!order) return fail(CC_EINVAL, "order must be non-NULL");
+    if (ws_bytes < direction_order_bytes(grid->count) || !workspace ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return fail(CC_EINVAL, "workspace too small or not 256-byte aligned");
+    cudaError_t e = direction_order(*grid, order, static_cast<char *>(workspace), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_order launch");
+    return CC_OK;
+}
+
 cc_status cc_grid_gather(const cc_grid *grid, const int32_t *idx, int32_t k, double *out_dirs,
                          void *stream) {
     g_err[0] = 0;

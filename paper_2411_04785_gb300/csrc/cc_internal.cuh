@@ -40,7 +40,7 @@ enum : int {
     CC_SITE_REDUCE_PART, CC_SITE_SELECT_BB, CC_SITE_SELECT_SEED, CC_SITE_REFINE_RING,
     CC_SITE_REFINE_SLOT, CC_SITE_GRID_OUT, CC_SITE_CLUSTER_IN, CC_SITE_CLUSTER_OUT,
     CC_SITE_CLUSTER_EVENT, CC_SITE_VOXEL_TILE, CC_SITE_VOXEL_OUT, CC_SITE_MLP_GEMM_OUT,
-    CC_SITE_MLP_ROWS, CC_SITE_SELFTEST = 0x7fff
+    CC_SITE_MLP_ROWS, CC_SITE_ORDER, CC_SITE_SELFTEST = 0x7fff
 };
 
 #ifdef CC_DEBUG_BOUNDS
@@ -98,12 +98,15 @@ struct SweepPlan {
     int64_t rpad;      // padded ring count = tiles * nsplit * tile
     int64_t nbb;       // block-best entries
     int64_t npack;     // blocks of the ring compaction
+    bool ordered;      // directions swept in their compact order (order.cu)
     // workspace byte offsets
-    size_t off_rec, off_part, off_bb, off_status, off_counter, off_nkept, off_packcnt, bytes;
+    size_t off_rec, off_part, off_bb, off_status, off_counter, off_nkept, off_packcnt, off_perm,
+        off_order, bytes;
 };
 
-// force_d = 0 lets the planner pick the directions per thread; the batched
-// path fixes it so that bursts share one kernel instantiation.
+// force_d = 0 lets the planner pick the directions per thread and sweeps the
+// directions in their compact order; the batched path fixes it so that
+// bursts share one kernel instantiation, and keeps the grid's own order.
 // `pick` returns the sweep kernel for (directions per thread, k_cut on) whose
 // occupancy the plan sizes the grid for (NULL: the far-field sweep).
 typedef void *(*SweepPick)(int d, bool kcut);
@@ -115,6 +118,10 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
 // sweep through finish_localize (probe coordinates in `grid`).
 constexpr int kPackChunk = 2048;
 cudaError_t launch_pack_scan(int32_t *blockcnt, int64_t nblk, int64_t *nkept, cudaStream_t s);
+// Compact traversal order of a grid's directions (order.cu): perm[k] is the
+// k-th direction swept; scratch of direction_order_bytes(count) bytes.
+size_t direction_order_bytes(int64_t M);
+cudaError_t direction_order(const cc_grid &g, int32_t *perm, char *scratch, cudaStream_t s);
 cudaError_t finish_localize(const cc_grid &grid, const cc_params &p, const SweepPlan &plan,
                             float *map, int32_t *argmax, int32_t *seeds, char *ws,
                             cudaStream_t s);

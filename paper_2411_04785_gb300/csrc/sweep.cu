@@ -176,11 +176,15 @@ k_pack_scatter(const float *__restrict__ ax, const float *__restrict__ ay,
 struct SweepSmem {
     RingRec tile[kStages][kTile];
     unsigned long long full[kStages];
+    unsigned char lst[kThreads / 32][kTile];   // per warp: the tile's rings by side
     int abort_flag;
 };
 
 // The pair term for one ring and DP direction pairs (see the file header).
-template <int DP, bool KCUT>
+// SIDE 1: every pair is known to lie on the ring's near side (h <= 1), SIDE 2:
+// on its far side; the fold and the select then have one outcome, and the
+// result is the same as the general form's (SIDE 0) bit for bit.
+template <int DP, bool KCUT, int SIDE = 0>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
                                            float2 (&acc)[DP], float kc2) {
@@ -198,8 +202,14 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
         float2 h = __fmul2_rn(dx, dx);
         h = __ffma2_rn(dy, dy, h);
         h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
-        float2 g = __ffma2_rn(h, m1, two2);             // 2 - h
-        float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+        float2 sv;
+        if (SIDE == 1) {
+            sv = h;
+        } else {
+            float2 g = __ffma2_rn(h, m1, two2);         // 2 - h
+            sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                           : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+        }
         float2 p = pair(2.61164433e-03f);               // Q(s), degree 6, FP32x2
         p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
         p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
@@ -209,7 +219,9 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
         p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
         float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
         float2 th = __fmul2_rn(rt, p);
-        float2 nbs = make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
+        float2 nbs = SIDE == 1   ? make_float2(P2.x, P2.x)
+                     : SIDE == 2 ? make_float2(P2.y, P2.y)
+                                 : make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
         float2 u = __ffma2_rn(th, k2, nbs);
         float2 u2 = __fmul2_rn(u, u);
         float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
@@ -239,21 +251,40 @@ __device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float c
     return fabsf(u) <= lim;
 }
 
+// The rings of a warp's side list lst[b, e) of tile T, eight at a time.
+template <int DP, int SIDE>
+__device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *lst, int b, int e,
+                                         const float2 (&ncx)[DP], const float2 (&ncy)[DP],
+                                         const float2 (&ncz)[DP], float2 (&acc)[DP]) {
+    int i = b;
+    for (; i + 8 <= e; i += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) ring_pairs<DP, false, SIDE>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
+    }
+    for (; i < e; i++) ring_pairs<DP, false, SIDE>(T[lst[i]], ncx, ncy, ncz, acc, 0.f);
+}
+
 // One work unit of the sweep: the 256 x D directions of direction block db
 // (warp w owns the 32 D consecutive ones from db 256 D + 32 D w; lane l the
-// directions l, l + 32, ...) against the ring tiles split, split + nsplit,
-// split + 2 nsplit, ... of the *nkept packed rings.  With the angular
-// selection on, each warp skips, tile by tile, the rings that cannot reach
-// its directions.  Writes the unit's partial (or full) map row and, when
-// bb_slot is set, its block best.  Returns false when a bounded wait gave up
-// (status set to CC_ETIMEOUT).
+// directions l, l + 32, ...; direction k of the sweep is perm[k] of the grid,
+// or k without perm) against the ring tiles split, split + nsplit,
+// split + 2 nsplit, ... of the *nkept packed rings.  Each warp sorts a
+// tile's rings by side against its cap of directions: a ring whose axis is
+// within pi/2 - rho - 1e-3 of the cap centre has every pair on its near side,
+// beyond pi/2 + rho + 1e-3 on its far side, and those rings skip the fold
+// and the select.  With the angular selection on, each warp skips, tile by
+// tile, the rings that cannot reach its directions instead.  Writes the
+// unit's partial (or full) map row (in grid order) and, when bb_slot is set,
+// its block best.  Returns false when a bounded wait gave up (status set to
+// CC_ETIMEOUT).
 template <int D, bool KCUT>
 __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restrict__ rec,
                                            const int64_t *__restrict__ nkept, int64_t nsplit,
                                            int64_t db, int64_t split,
                                            const float *__restrict__ cx,
                                            const float *__restrict__ cy,
-                                           const float *__restrict__ cz, int64_t M, float kc2,
+                                           const float *__restrict__ cz,
+                                           const int32_t *__restrict__ perm, int64_t M, float kc2,
                                            float *__restrict__ out, BlockBest *bb_slot,
                                            int32_t *__restrict__ status) {
     static_assert(D % 2 == 0, "directions are processed in FP32x2 pairs");
@@ -272,6 +303,10 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         ja = ja < M ? ja : M - 1;
         jb = jb < M ? jb : M - 1;
+        if (perm != nullptr) {
+            ja = __ldg(perm + ja);
+            jb = __ldg(perm + jb);
+        }
         ncx[q] = make_float2(-__ldg(cx + ja) * kInvSqrt2, -__ldg(cx + jb) * kInvSqrt2);
         ncy[q] = make_float2(-__ldg(cy + ja) * kInvSqrt2, -__ldg(cy + jb) * kInvSqrt2);
         ncz[q] = make_float2(-__ldg(cz + ja) * kInvSqrt2, -__ldg(cz + jb) * kInvSqrt2);
@@ -280,7 +315,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
 
     // the warp's cap: centre (scaled by 1/sqrt 2) and angular radius
     float capx = 0.f, capy = 0.f, capz = 0.f, rho = 0.f, kc = 0.f;
-    if (KCUT) {
+    {
         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
         for (int q = 0; q < DP; q++) {
@@ -313,6 +348,10 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         rho = 2.0f * asinf(fminf(sqrtf(0.5f * h), 1.0f)) + 2.0e-5f;
         kc = sqrtf(kc2);
     }
+    // side test: cos(angle(axis, centre)) = 2 a'.cap' against +-sin(rho + 1e-3)
+    // (no side decided when the cap reaches pi/2)
+    const float slim = rho + 1.0e-3f < 1.5707f ? sinf(rho + 1.0e-3f) : 2.0f;
+    const int w = tid >> 5;
 
     const int64_t ntk = (*nkept + kTile - 1) / kTile;
     const int64_t tiles = split < ntk ? (ntk - split + nsplit - 1) / nsplit : 0;
@@ -351,8 +390,38 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                     }
                 }
             } else {
-#pragma unroll 8
-                for (int r = 0; r < kTile; r++) ring_pairs<DP, KCUT>(T[r], ncx, ncy, ncz, acc, kc2);
+                // the tile's rings by side: near from the front of the list,
+                // then far, then the rest, each in tile order
+                unsigned nm[kTile / 32], fm[kTile / 32];
+                int nn = 0, nf = 0;
+#pragma unroll
+                for (int g = 0; g < kTile / 32; g++) {
+                    const RingRec &R = T[32 * g + lane];
+                    const float c2 = 2.0f * fmaf(R.az, capz, fmaf(R.ay, capy, R.ax * capx));
+                    nm[g] = __ballot_sync(0xffffffffu, c2 >= slim);
+                    fm[g] = __ballot_sync(0xffffffffu, c2 <= -slim);
+                    nn += __popc(nm[g]);
+                    nf += __popc(fm[g]);
+                }
+                const unsigned lt = (1u << lane) - 1u;
+                int bn = 0, bf = nn, bm = nn + nf;
+#pragma unroll
+                for (int g = 0; g < kTile / 32; g++) {
+                    const unsigned mm = ~(nm[g] | fm[g]);
+                    const bool isn = (nm[g] >> lane) & 1u, isf = (fm[g] >> lane) & 1u;
+                    const int at = isn ? bn + __popc(nm[g] & lt)
+                                 : isf ? bf + __popc(fm[g] & lt) : bm + __popc(mm & lt);
+                    S.lst[w][at] = (unsigned char)(32 * g + lane);
+                    bn += __popc(nm[g]);
+                    bf += __popc(fm[g]);
+                    bm += __popc(mm);
+                }
+                __syncwarp();
+                const unsigned char *L = S.lst[w];
+                side_run<DP, 1>(T, L, 0, nn, ncx, ncy, ncz, acc);
+                side_run<DP, 2>(T, L, nn, nn + nf, ncx, ncy, ncz, acc);
+                side_run<DP, 0>(T, L, nn + nf, kTile, ncx, ncy, ncz, acc);
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -379,15 +448,21 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     int bj = INT32_MAX;
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        const int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
+        const int64_t ka = j0 + (int64_t)(64 * q), kb = ka + 32;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
-        if (ja < M && CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + ja, nsplit * M)) {
-            out[split * M + ja] = va;
-            better(bv, bj, va, (int)ja);
+        if (ka < M) {
+            const int64_t ja = perm != nullptr ? (int64_t)__ldg(perm + ka) : ka;
+            if (CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + ja, nsplit * M)) {
+                out[split * M + ja] = va;
+                better(bv, bj, va, (int)ja);
+            }
         }
-        if (jb < M && CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + jb, nsplit * M)) {
-            out[split * M + jb] = vb;
-            better(bv, bj, vb, (int)jb);
+        if (kb < M) {
+            const int64_t jb = perm != nullptr ? (int64_t)__ldg(perm + kb) : kb;
+            if (CC_IN_BOUNDS(CC_SITE_SWEEP_OUT, split * M + jb, nsplit * M)) {
+                out[split * M + jb] = vb;
+                better(bv, bj, vb, (int)jb);
+            }
         }
     }
     if (bb_slot != nullptr) {
@@ -404,12 +479,11 @@ __global__ void __launch_bounds__(kThreads)
 k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
         int64_t ndb,
         const float *__restrict__ cx, const float *__restrict__ cy,
-        const float *__restrict__ cz, int64_t M, float kc2, float *__restrict__ out,
-        BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
+        const float *__restrict__ cz, const int32_t *__restrict__ perm, int64_t M, float kc2,
+        float *__restrict__ out, BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
     __shared__ __align__(128) SweepSmem S;
-    sweep_unit<D, KCUT>(S, rec, nkept, nsplit, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, M,
-                        kc2,
-                        out, bb ? bb + blockIdx.x : nullptr, status);
+    sweep_unit<D, KCUT>(S, rec, nkept, nsplit, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, perm,
+                        M, kc2, out, bb ? bb + blockIdx.x : nullptr, status);
 }
 
 // Several bursts in one launch: CTAs take work units of all the bursts from
@@ -430,6 +504,7 @@ struct MultiArgs {
     BurstDesc b[CC_BATCH_MAX];
     int64_t unit_begin[CC_BATCH_MAX + 1];
     const float *cx, *cy, *cz;
+    const int32_t *perm;
     int64_t M;
     float kc2;
     unsigned long long *counter;
@@ -451,7 +526,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant_
         const BurstDesc &d = a.b[b];
         const int64_t lu = u - a.unit_begin[b];
         if (!sweep_unit<D, KCUT>(S, d.rec, d.nkept, d.nsplit, lu % d.ndb, lu / d.ndb, a.cx, a.cy,
-                                 a.cz, a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr, d.status))
+                                 a.cz, a.perm, a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr,
+                                 d.status))
             break;
     }
 }
@@ -631,6 +707,15 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     plan->npack = R > 0 ? (R + kPackChunk - 1) / kPackChunk : 1;
     plan->off_packcnt = off;
     off = align256(off + (size_t)plan->npack * sizeof(int32_t));
+    // the directions' compact order: the single far-field sweep only
+    plan->ordered = force_d == 0 && pick == pick_sweep;
+    plan->off_perm = off;
+    plan->off_order = off;
+    if (plan->ordered) {
+        off = align256(off + (size_t)M * sizeof(int32_t));
+        plan->off_order = off;
+        off = align256(off + direction_order_bytes(M));
+    }
     plan->bytes = off;
     return true;
 }
@@ -699,9 +784,20 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
     void *fn = pick_sweep(plan.d, kcut);
     const int64_t *nkept = reinterpret_cast<const int64_t *>(ws + plan.off_nkept);
-    void *args[] = {(void *)&rec,    (void *)&nkept, (void *)&plan.nsplit, (void *)&plan.ndb,
-                    (void *)&grid.x, (void *)&grid.y, (void *)&grid.z,     (void *)&M,
-                    (void *)&kc2,    (void *)&out,   (void *)&bbk,         (void *)&st};
+    const int32_t *perm = nullptr;
+    if (plan.ordered) {
+        perm = grid.order;
+        if (perm == nullptr) {        // not given with the grid: computed here
+            int32_t *pm = reinterpret_cast<int32_t *>(ws + plan.off_perm);
+            TraceScope ts(CC_STAGE_PACK, s);
+            if ((e = direction_order(grid, pm, ws + plan.off_order, s)) != cudaSuccess) return e;
+            perm = pm;
+        }
+    }
+    void *args[] = {(void *)&rec,    (void *)&nkept,  (void *)&plan.nsplit, (void *)&plan.ndb,
+                    (void *)&grid.x, (void *)&grid.y, (void *)&grid.z,     (void *)&perm,
+                    (void *)&M,      (void *)&kc2,    (void *)&out,         (void *)&bbk,
+                    (void *)&st};
     {
         TraceScope ts(CC_STAGE_SWEEP, s);
         e = cudaLaunchKernel(fn, dim3(grid_ctas), dim3(kThreads), args, 0, s);
@@ -719,6 +815,7 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
     a.cx = grid.x;
     a.cy = grid.y;
     a.cz = grid.z;
+    a.perm = grid.order;     // the grid's order when the caller keeps one
     a.M = grid.count;
     const bool kcut = p.k_cut > 0.0f;
     const float kc = p.k_cut * kGaussK;

@@ -144,6 +144,8 @@ class Server:
     def __init__(self, grid, params: api.Params | None = None, hbm_budget: int = 2 << 30,
                  max_active: int = 48, ring_filter: api.RingFilter | None = None,
                  tau: float = 0.0, filter_deta_max: float | None = None, graphs: bool = False):
+        # the grid's direction order, computed once for every batched sweep
+        grid = tuple(grid[:3]) + (grid[3] if len(grid) > 3 else api.grid_order(grid),)
         self.grid = grid
         self.M = grid[0].numel()
         self.dev = grid[0].device

@@ -46,7 +46,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_host_side_calls_without_gpu(libpath):
     import paper_2411_04785_gb300 as cc
     L = cc.lib()
-    assert L.cc_abi_version() == 1
+    assert L.cc_abi_version() == 2
     p = cc.default_params()
     assert p.topk == 1 and p.max_iter == 50 and abs(p.tol_rad - 1e-7) < 1e-20
     # argument errors are caught before any CUDA call

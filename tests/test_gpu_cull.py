@@ -1,8 +1,10 @@
-"""Angular selection with block skipping: on a NESTED HEALPix grid the
-sweep skips, per warp and tile, rings that cannot reach the warp's compact
-patch.  A skipped ring's terms are all cut to 0 anyway, so the map must be
-bit for bit the map of the same pixels in RING order (where patches are wide
-and little is skipped), and within the oracle's k_cut bracket."""
+"""The sweep's direction order and the angular selection with block
+skipping.  The sweep takes any grid's directions in their NESTED HEALPix
+order (cc_grid_order), so each warp owns a compact patch: per warp and tile
+it skips the rings that cannot reach the patch.  A skipped ring's terms are
+all cut to 0 anyway, so the map must be within the oracle's k_cut bracket,
+and a NESTED grid's map bit for bit the map of the same pixels in RING order
+(swept in the same order)."""
 import math
 
 import numpy as np
@@ -45,6 +47,48 @@ def test_nest_grid_is_the_ring_grid_permuted(cc, nside):
     on = oracle.grid_healpix_nest(nside)
     for a, b in zip(gn, on):
         assert np.abs(a - b).max() < 3e-7
+
+
+@pytest.mark.parametrize("nside", [1, 4, 16, 64])
+def test_ring_grid_is_swept_in_nested_order(cc, nside):
+    perm = nest_to_ring_perm(nside)
+    order = cc.grid_order(cc.grid_healpix_ring(nside, "cuda:0")).cpu().numpy()
+    np.testing.assert_array_equal(order, perm)
+    order = cc.grid_order(cc.grid_healpix_nest(nside, "cuda:0")).cpu().numpy()
+    np.testing.assert_array_equal(order, np.arange(12 * nside * nside))
+
+
+@pytest.mark.parametrize("M", [1, 2, 257, 5003, 100003])
+def test_grid_order_is_a_compact_permutation(cc, M):
+    g = cc.grid_fibonacci(M, "cuda:0")
+    o = cc.grid_order(g).cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o), np.arange(M))
+    if M >= 5003:      # runs of 256 in the order span small patches
+        v = np.stack([t.cpu().numpy() for t in g], 1).astype(np.float64)[o]
+        n = M // 256 * 256
+        c = v[:n].reshape(-1, 256, 3).sum(1)
+        c /= np.linalg.norm(c, axis=1, keepdims=True)
+        spread = np.degrees(np.arccos(np.clip(np.einsum("wkd,wd->wk", v[:n].reshape(-1, 256, 3), c), -1, 1)).max(1))
+        assert np.median(spread) < 2.5 * math.degrees(math.sqrt(4 * math.pi * 256 / M))
+
+
+def test_grid_order_ties_and_bad_directions(cc):
+    """Equal directions keep their index order; zero and NaN directions go last."""
+    dev = "cuda:0"
+    M = 3000
+    x = torch.zeros(M, device=dev)
+    y = torch.zeros(M, device=dev)
+    z = torch.ones(M, device=dev)
+    x[::7] = 1.0
+    z[::7] = 0.0
+    z[5] = 0.0
+    x[11] = float("nan")
+    o = cc.grid_order((x, y, z)).cpu().numpy()
+    np.testing.assert_array_equal(np.sort(o), np.arange(M))
+    assert set(o[-2:].tolist()) == {5, 11}
+    for grp in (np.arange(M)[::7], np.setdiff1d(np.arange(M), np.r_[np.arange(M)[::7], 5, 11])):
+        pos = np.argsort(o)[grp]             # where each index landed
+        assert (np.diff(pos) > 0).all()       # in index order among equals
 
 
 @pytest.mark.parametrize("dmax_deg,kcut", [(2.0, 5.0), (10.0, 3.0), (0.6, 8.0)])
