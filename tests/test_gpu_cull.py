@@ -91,6 +91,28 @@ def test_grid_order_ties_and_bad_directions(cc):
         assert (np.diff(pos) > 0).all()       # in index order among equals
 
 
+def test_kept_order_equals_computed_order(cc):
+    """A grid's order kept with it (cc_grid.order) gives the map computed with
+    the order the call finds itself, bit for bit; any other permutation is a
+    valid traversal too (a different FP32 summation), within the map rule."""
+    r, _, _ = synth.rings_burst(n=20000, seed=5)
+    rd = rings_to_dev(r, "cuda:0")
+    g = cc.grid_healpix_ring(32, "cuda:0")
+    m1, a1, _, st1 = cc.localize(rd, g)
+    m2, a2, _, st2 = cc.localize(rd, tuple(g) + (cc.grid_order(g),))
+    assert int(st1.item()) == 0 and int(st2.item()) == 0
+    assert torch.equal(m1, m2) and torch.equal(a1, a2)
+    ident = torch.arange(g[0].numel(), dtype=torch.int32, device="cuda:0")
+    m3 = cc.localize(rd, tuple(g) + (ident,))[0]
+    want = oracle.likelihood_map({k: np.asarray(r[k], np.float32) for k in ("ax", "ay", "az", "eta", "deta")},
+                                 oracle.grid_healpix_ring(32))
+    for m in (m1, m3):
+        got = m.cpu().numpy()
+        assert (np.abs(got - want) <= 1e-5 * np.maximum(want, 1e-3 * want.max())).all()
+    with pytest.raises(ValueError):
+        cc.localize(rd, tuple(g) + (ident[:-1],))
+
+
 @pytest.mark.parametrize("dmax_deg,kcut", [(2.0, 5.0), (10.0, 3.0), (0.6, 8.0)])
 def test_skipping_is_exact(cc, dmax_deg, kcut):
     nside = 64
