@@ -235,8 +235,10 @@ size_t work_layout(int64_t rows, Work *w, char *base) {
 //               shared memory; layers 2-4 read A (the activations) from
 //               TMEM, so the tensor cores stream only W from shared memory.
 //               tcgen05.commit signals the epilogue.
-//   warps 2..17 epilogue: a thread owns one row (its warp's TMEM lane
-//               quarter) and one quarter of the columns; it loads the row's
+//   warps 2..17 epilogue, in two groups of 8, one per TMEM slot, so that
+//               the two tiles in flight are finished concurrently: a thread
+//               owns one row (its warp's TMEM lane quarter) and one half of
+//               the columns of its group's slot; it loads the row's
 //               accumulators, applies ReLU, rounds to BF16 and stores the
 //               packed values back into TMEM as the next layer's A - or,
 //               after the last layer, writes the two outputs.
@@ -469,7 +471,7 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
         }
         for (int i = 0; i < 2; i++) {
             mbar_init(&S.acc_full[i], 1);
-            mbar_init(&S.h_done[i], kEpiWarps);
+            mbar_init(&S.h_done[i], kEpiWarps / 2);
         }
         mbar_init(&S.fin, 1);
         S.err = 0;
@@ -571,56 +573,61 @@ k_mlp_forward_tc(const __grid_constant__ CUtensorMap xmap, const bf16 *__restric
         if (!ok && lane == 0) *err = 1;
         umma_commit(&S.fin);              // every product issued has completed
         if (!__all_sync(0xffffffffu, mbar_wait(&S.fin, 0)) && lane == 0) *err = 1;
-    } else {                              // epilogue: one row, one column quarter per thread
-        const int qd = warp & 3, cq = (warp - 2) >> 2, row = 32 * qd + lane;
+    } else {                              // epilogue: slot j = grp; one row, one column half
+        const int grp = (warp - 2) >> 3, ch = ((warp - 2) >> 2) & 1, qd = warp & 3,
+                  row = 32 * qd + lane;
         const unsigned lanes = (unsigned)(32 * qd) << 16;
-        int af[2] = {0, 0};
+        int af = 0;
         int p = 0;
         for (p = 0; p < nt; p += 2) {
             const int q = nt - p < 2 ? nt - p : 2;
+            if (grp >= q) continue;       // the last odd tile is slot 0's
+            const int j = grp;
             for (int l = 0; l < 4; l++) {
-                for (int j = 0; j < q; j++) {
-                    const bool ok = !*err && mbar_wait(&S.acc_full[j], af[j]++ & 1);
-                    if (!__all_sync(0xffffffffu, ok)) {    // warp-uniform: the loads are .aligned
-                        *err = 1;
-                        goto fail;
-                    }
-                    tc_fence_after();
-                    const unsigned t = tmem + lanes + (unsigned)(j * 128);
-                    if (l < 3) {
+                const bool ok = !*err && mbar_wait(&S.acc_full[j], af++ & 1);
+                if (!__all_sync(0xffffffffu, ok)) {        // warp-uniform: the loads are .aligned
+                    *err = 1;
+                    goto fail;
+                }
+                tc_fence_after();
+                const unsigned t = tmem + lanes + (unsigned)(j * 128);
+                if (l < 3) {
+                    bf16 *hl = l == 0 ? h1 : l == 1 ? h2 : h3;
+                    const int64_t g = tile_of(p + j) * kTM + row;
+#pragma unroll
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int c0 = ch * 64 + hh * 32;          // accumulator columns
                         uint32_t r[32], w[16];
-                        tmem_ld32(t + (unsigned)(cq * 32), r);
+                        tmem_ld32(t + (unsigned)c0, r);
 #pragma unroll
                         for (int c = 0; c < 16; c++)
                             w[c] = relu_bf16x2(__uint_as_float(r[2 * c]),
                                                __uint_as_float(r[2 * c + 1]));
-                        tmem_st16(tmem + lanes + kActCol + (unsigned)(j * 64 + cq * 16), w);
-                        bf16 *hl = l == 0 ? h1 : l == 1 ? h2 : h3;
-                        const int64_t g = tile_of(p + j) * kTM + row;
+                        tmem_st16(tmem + lanes + kActCol + (unsigned)(j * 64 + c0 / 2), w);
                         if (kKeep && g < R) {
-                            uint4 *dst = reinterpret_cast<uint4 *>(hl + g * kH + cq * 32);
+                            uint4 *dst = reinterpret_cast<uint4 *>(hl + g * kH + c0);
 #pragma unroll
                             for (int c = 0; c < 4; c++)
                                 dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
                         }
-                    } else if (cq == 0) {
-                        uint32_t r[2];
-                        tmem_ld2(t, r);
-                        const int64_t g = tile_of(p + j) * kTM + row;
-                        if (g < R)
-                            *reinterpret_cast<float2 *>(out + 2 * g) =
-                                make_float2(__uint_as_float(r[0]), __uint_as_float(r[1]));
                     }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.h_done[j]);
+                } else if (ch == 0) {
+                    uint32_t r[2];
+                    tmem_ld2(t, r);
+                    const int64_t g = tile_of(p + j) * kTM + row;
+                    if (g < R)
+                        *reinterpret_cast<float2 *>(out + 2 * g) =
+                            make_float2(__uint_as_float(r[0]), __uint_as_float(r[1]));
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.h_done[j]);
             }
         }
     fail:
-        if (p < nt && cq == 0) {          // gave up: NaN for every row still owed
+        if (p < nt && ch == 0) {          // gave up: NaN for every row of this slot still owed
             const float nan = __int_as_float(0x7fc00000);
-            for (int k = p; k < nt; k++) {
+            for (int k = p + grp; k < nt; k += 2) {
                 const int64_t g = tile_of(k) * kTM + row;
                 if (g < R) *reinterpret_cast<float2 *>(out + 2 * g) = make_float2(nan, nan);
             }
