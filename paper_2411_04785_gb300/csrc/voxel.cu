@@ -18,7 +18,10 @@
 //     h = |c|^2 = 1 - cos(theta)  (relative accuracy, also at small angles),
 // and from h on it is the far-field pair: theta from the fitted
 // acos(1 - h)/sqrt(h) polynomial (or its mirror for theta > pi/2), the
-// Gaussian on the MUFU ex2 unit.  Rings with eta > pi/2 are mirrored
+// Gaussian on the MUFU ex2 unit.  As in the far-field sweep, each warp lists
+// a tile's rings by side: a ring whose plane through the apex, normal to the
+// axis, misses the warp's voxels' bounding sphere has every pair on one side
+// (all angles below pi/2, or all above) and skips the fold and the select.  Rings with eta > pi/2 are mirrored
 // (a -> -a, eta -> pi - eta).  The pipeline (TMA bulk tiles through a
 // 4-stage mbarrier ring, ring splits over CTAs with a fixed-order Kahan
 // reduction, block argmax) is the far-field sweep's, with 64-byte records.
@@ -240,11 +243,95 @@ k_near_scatter(NearRings g, const int32_t *__restrict__ offs, const int64_t *__r
 struct NearSmem {
     NearRec tile[kStages][kTile];
     unsigned long long full[kStages];
+    unsigned char lst[kThreads / 32][kTile];   // per warp: the tile's rings by side
     int abort_flag;
 };
 
+// The pair terms of one ring for DP voxel pairs.  SIDE 1: every pair lies on
+// the ring's near side (h <= 1), SIDE 2: on its far side; the fold and the
+// select then have one outcome, and the result is the general form's
+// (SIDE 0) bit for bit.
+template <int DP, bool KCUT, int SIDE>
+__device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2)[DP],
+                                           const float2 (&py2)[DP], const float2 (&pz2)[DP],
+                                           float2 (&acc)[DP], float kc2) {
+    const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
+    const float2 nh = pair(-0.5f * kInvSqrt2), th2 = pair(1.5f * kInvSqrt2);
+    const float4 R0 = *reinterpret_cast<const float4 *>(&Rr.mpx);
+    const float4 R1 = *reinterpret_cast<const float4 *>(&Rr.mpz);
+    const float4 R2 = *reinterpret_cast<const float4 *>(&Rr.msy);
+    const float4 R3 = *reinterpret_cast<const float4 *>(&Rr.k);
+    const float2 mpx = make_float2(R0.x, R0.y), mpy = make_float2(R0.z, R0.w);
+    const float2 mpz = make_float2(R1.x, R1.y), msx = make_float2(R1.z, R1.w);
+    const float2 msy = make_float2(R2.x, R2.y), msz = make_float2(R2.z, R2.w);
+    const float2 k2 = make_float2(R3.x, R3.y);
+#pragma unroll
+    for (int q = 0; q < DP; q++) {
+        const float2 dx = __fadd2_rn(px2[q], mpx);
+        const float2 dy = __fadd2_rn(py2[q], mpy);
+        const float2 dz = __fadd2_rn(pz2[q], mpz);
+        // |d|^2 + 1e-30: a voxel centre on the apex stays finite
+        float2 n2 = __ffma2_rn(dx, dx, pair(1.0e-30f));
+        n2 = __ffma2_rn(dy, dy, n2);
+        n2 = __ffma2_rn(dz, dz, n2);
+        const float2 y0 = make_float2(rsqrt_approx(n2.x), rsqrt_approx(n2.y));
+        float2 tt = __fmul2_rn(n2, y0);
+        tt = __fmul2_rn(tt, y0);
+        const float2 f = __ffma2_rn(tt, nh, th2);
+        const float2 y1 = __fmul2_rn(y0, f);                // rsqrt(|d|^2)/sqrt(2)
+        const float2 cx = __ffma2_rn(dx, y1, msx);
+        const float2 cy = __ffma2_rn(dy, y1, msy);
+        const float2 cz = __ffma2_rn(dz, y1, msz);
+        float2 h = __fmul2_rn(cx, cx);
+        h = __ffma2_rn(cy, cy, h);
+        h = __ffma2_rn(cz, cz, h);                           // 1 - cos(theta)
+        float2 sv;
+        if (SIDE == 1) {
+            sv = h;
+        } else {
+            const float2 g = __ffma2_rn(h, m1, two2);
+            sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                           : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+        }
+        float2 p = pair(1.4414361e-03f);                     // acos_q
+        p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
+        p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
+        p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
+        p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
+        p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
+        p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
+        p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+        const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
+        const float2 th = __fmul2_rn(rt, p);
+        const float2 nbs = SIDE == 1   ? make_float2(R3.z, R3.z)
+                           : SIDE == 2 ? make_float2(R3.w, R3.w)
+                                       : make_float2(h.x <= 1.0f ? R3.z : R3.w,
+                                                     h.y <= 1.0f ? R3.z : R3.w);
+        const float2 u = __ffma2_rn(th, k2, nbs);
+        const float2 u2 = __fmul2_rn(u, u);
+        float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+        if (KCUT) {
+            e.x = u2.x > kc2 ? 0.0f : e.x;
+            e.y = u2.y > kc2 ? 0.0f : e.y;
+        }
+        acc[q] = __fadd2_rn(acc[q], e);
+    }
+}
+
+template <int DP, bool KCUT, int SIDE>
+__device__ __forceinline__ void near_run(const NearRec *T, const unsigned char *lst, int b, int e,
+                                         const float2 (&px2)[DP], const float2 (&py2)[DP],
+                                         const float2 (&pz2)[DP], float2 (&acc)[DP], float kc2) {
+    int i = b;
+    for (; i + 2 <= e; i += 2) {
+        near_pairs<DP, KCUT, SIDE>(T[lst[i]], px2, py2, pz2, acc, kc2);
+        near_pairs<DP, KCUT, SIDE>(T[lst[i + 1]], px2, py2, pz2, acc, kc2);
+    }
+    if (i < e) near_pairs<DP, KCUT, SIDE>(T[lst[i]], px2, py2, pz2, acc, kc2);
+}
+
 template <int D, bool KCUT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
               int64_t ndb, const float *__restrict__ vx, const float *__restrict__ vy,
               const float *__restrict__ vz, int64_t V, float kc2, float *__restrict__ out,
@@ -268,6 +355,40 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
         acc[q] = sum[q] = comp[q] = make_float2(0.0f, 0.0f);
     }
 
+    // the warp's voxels' bounding sphere: centre and radius (plus a margin for
+    // the FP32 side test: 1e-3 of the distance to an apex is added below)
+    const int lane = tid & 31, w = tid >> 5;
+    float bcx = 0.f, bcy = 0.f, bcz = 0.f, brad = 0.f;
+    {
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            bcx += px2[q].x + px2[q].y;
+            bcy += py2[q].x + py2[q].y;
+            bcz += pz2[q].x + pz2[q].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bcx += __shfl_xor_sync(0xffffffffu, bcx, o);
+            bcy += __shfl_xor_sync(0xffffffffu, bcy, o);
+            bcz += __shfl_xor_sync(0xffffffffu, bcz, o);
+        }
+        const float inv = 1.0f / (32.0f * D);
+        bcx *= inv;
+        bcy *= inv;
+        bcz *= inv;
+        float r2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            const float ax_ = px2[q].x - bcx, ay_ = py2[q].x - bcy, az_ = pz2[q].x - bcz;
+            const float bx_ = px2[q].y - bcx, by_ = py2[q].y - bcy, bz_ = pz2[q].y - bcz;
+            r2 = fmaxf(r2, fmaf(az_, az_, fmaf(ay_, ay_, ax_ * ax_)));
+            r2 = fmaxf(r2, fmaf(bz_, bz_, fmaf(by_, by_, bx_ * bx_)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+        brad = sqrtf(r2) * 1.0001f + 1.0e-6f;
+    }
+
     const int64_t ntk = (*nkept + kTile - 1) / kTile;
     const int64_t tiles = split < ntk ? (ntk - split + nsplit - 1) / nsplit : 0;
     const NearRec *src = rec + split * kTile;
@@ -284,8 +405,6 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
                 tma_bulk_load(S.tile[s], src + (int64_t)s * stride, kTile * sizeof(NearRec),
                               &S.full[s]);
 
-    const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
-    const float2 nh = pair(-0.5f * kInvSqrt2), th2 = pair(1.5f * kInvSqrt2);
     for (int64_t t = 0; t < tiles; t++) {
         const int stage = (int)(t % kStages);
         const unsigned parity = (unsigned)((t / kStages) & 1);
@@ -293,60 +412,44 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             S.abort_flag = 1;
         } else {
             const NearRec *T = S.tile[stage];
-#pragma unroll 2
-            for (int r = 0; r < kTile; r++) {
-                const float4 R0 = *reinterpret_cast<const float4 *>(&T[r].mpx);
-                const float4 R1 = *reinterpret_cast<const float4 *>(&T[r].mpz);
-                const float4 R2 = *reinterpret_cast<const float4 *>(&T[r].msy);
-                const float4 R3 = *reinterpret_cast<const float4 *>(&T[r].k);
-                const float2 mpx = make_float2(R0.x, R0.y), mpy = make_float2(R0.z, R0.w);
-                const float2 mpz = make_float2(R1.x, R1.y), msx = make_float2(R1.z, R1.w);
-                const float2 msy = make_float2(R2.x, R2.y), msz = make_float2(R2.z, R2.w);
-                const float2 k2 = make_float2(R3.x, R3.y);
+            // the tile's rings by side against the warp's sphere: the plane
+            // through the apex normal to the axis does not cut the sphere
+            // when |a . (centre - apex)| > radius (+ 1e-3 of the distance)
+            unsigned nm[kTile / 32], fm[kTile / 32];
+            int nn = 0, nf = 0;
 #pragma unroll
-                for (int q = 0; q < DP; q++) {
-                    const float2 dx = __fadd2_rn(px2[q], mpx);
-                    const float2 dy = __fadd2_rn(py2[q], mpy);
-                    const float2 dz = __fadd2_rn(pz2[q], mpz);
-                    // |d|^2 + 1e-30: a voxel centre on the apex stays finite
-                    float2 n2 = __ffma2_rn(dx, dx, pair(1.0e-30f));
-                    n2 = __ffma2_rn(dy, dy, n2);
-                    n2 = __ffma2_rn(dz, dz, n2);
-                    const float2 y0 = make_float2(rsqrt_approx(n2.x), rsqrt_approx(n2.y));
-                    float2 tt = __fmul2_rn(n2, y0);
-                    tt = __fmul2_rn(tt, y0);
-                    const float2 f = __ffma2_rn(tt, nh, th2);
-                    const float2 y1 = __fmul2_rn(y0, f);                // rsqrt(|d|^2)/sqrt(2)
-                    const float2 cx = __ffma2_rn(dx, y1, msx);
-                    const float2 cy = __ffma2_rn(dy, y1, msy);
-                    const float2 cz = __ffma2_rn(dz, y1, msz);
-                    float2 h = __fmul2_rn(cx, cx);
-                    h = __ffma2_rn(cy, cy, h);
-                    h = __ffma2_rn(cz, cz, h);                           // 1 - cos(theta)
-                    const float2 g = __ffma2_rn(h, m1, two2);
-                    const float2 sv = make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
-                    float2 p = pair(1.4414361e-03f);                     // acos_q
-                    p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
-                    p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
-                    p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
-                    p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
-                    p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
-                    p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
-                    p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
-                    const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
-                    const float2 th = __fmul2_rn(rt, p);
-                    const float2 nbs = make_float2(h.x <= 1.0f ? R3.z : R3.w,
-                                                   h.y <= 1.0f ? R3.z : R3.w);
-                    const float2 u = __ffma2_rn(th, k2, nbs);
-                    const float2 u2 = __fmul2_rn(u, u);
-                    float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
-                    if (KCUT) {
-                        e.x = u2.x > kc2 ? 0.0f : e.x;
-                        e.y = u2.y > kc2 ? 0.0f : e.y;
-                    }
-                    acc[q] = __fadd2_rn(acc[q], e);
-                }
+            for (int g = 0; g < kTile / 32; g++) {
+                const NearRec &Rg = T[32 * g + lane];
+                const float ex = bcx + Rg.mpx, ey = bcy + Rg.mpy, ez = bcz + Rg.mpz;   // centre - apex
+                // a = -sqrt(2) ms
+                const float sa = -1.41421356f * fmaf(Rg.msz, ez, fmaf(Rg.msy, ey, Rg.msx * ex));
+                const float dist = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+                const float lim = brad + 1.0e-3f * dist;
+                const bool live = Rg.k != 0.0f;
+                nm[g] = __ballot_sync(0xffffffffu, live && sa > lim);
+                fm[g] = __ballot_sync(0xffffffffu, live && sa < -lim);
+                nn += __popc(nm[g]);
+                nf += __popc(fm[g]);
             }
+            const unsigned lt = (1u << lane) - 1u;
+            int bn = 0, bf = nn, bm = nn + nf;
+#pragma unroll
+            for (int g = 0; g < kTile / 32; g++) {
+                const unsigned mm = ~(nm[g] | fm[g]);
+                const bool isn = (nm[g] >> lane) & 1u, isf = (fm[g] >> lane) & 1u;
+                const int at = isn ? bn + __popc(nm[g] & lt)
+                             : isf ? bf + __popc(fm[g] & lt) : bm + __popc(mm & lt);
+                S.lst[w][at] = (unsigned char)(32 * g + lane);
+                bn += __popc(nm[g]);
+                bf += __popc(fm[g]);
+                bm += __popc(mm);
+            }
+            __syncwarp();
+            const unsigned char *L = S.lst[w];
+            near_run<DP, KCUT, 1>(T, L, 0, nn, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 2>(T, L, nn, nn + nf, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 0>(T, L, nn + nf, kTile, px2, py2, pz2, acc, kc2);
+            __syncwarp();
         }
         __syncthreads();
         if (S.abort_flag) break;
