@@ -129,7 +129,7 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid,
                             const cc_params &p, const SweepPlan &plan,
                             float *map, int32_t *argmax, int32_t *seeds,
                             int32_t *status, char *ws, cudaStream_t s);
-constexpr int kBatchD = 4;   // directions per thread of the batched sweep
+constexpr int kBatchD = 8;   // directions per thread of the batched sweep
 cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &grid,
                                   const cc_params &p, const SweepPlan *plans, float *const *maps,
                                   int32_t *const *argmax, int32_t *const *seeds,
