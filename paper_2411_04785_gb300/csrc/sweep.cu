@@ -25,8 +25,11 @@
 // -b, -b2, duplicated where they meet a direction pair) in the workspace and
 // streamed through shared memory by cp.async.bulk (TMA bulk copy) into a
 // 4-stage mbarrier ring; every CTA owns 256 x D directions held in registers
-// (D per thread, coalesced loads and stores) and a contiguous range of ring
-// tiles.  Directions are processed in pairs with the packed FP32x2 FMA / add
+// (D per thread) and a contiguous range of ring tiles.  The directions are
+// taken in the grid's compact order (order.cu: HEALPix NESTED), so each warp
+// owns a small patch of sky, and per tile each warp lists the rings that lie
+// wholly on one side of its patch (every angle below pi/2, or every one
+// above): those skip the fold and the mirror select, which is most of them.  Directions are processed in pairs with the packed FP32x2 FMA / add
 // / multiply of sm_100+ (one instruction issue per two lanes of FP32 work),
 // which leaves the FP32 pipe, not instruction issue, as the limit.  Per
 // direction the FP32 sum
