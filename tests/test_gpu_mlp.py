@@ -219,6 +219,16 @@ def test_trained_filter_gains_over_the_plain_method(cc, dev):
     err_learned = localize_error(cc, learned, grid, ev["source"], p)
     print(f"plain {err_plain:.3f} deg, learned {err_learned:.3f} deg, losses {losses}")
     assert err_learned < err_plain
+    # the width head learned something per ring: on these held-out events its
+    # width (before the clamp) ranks the source rings' actual residuals
+    src = torch.from_numpy(ev["is_source"]).to(dev) & plain["valid"].bool()
+    res = cc.ring_residuals(plain, to_dev(np.repeat(ev["source"][None, :], ev["n"].size, 0), dev))
+    w = torch.exp(out[:, 1].float())[src].cpu().numpy()
+    r = res.abs()[src].cpu().numpy()
+    rank = lambda a: np.argsort(np.argsort(a)).astype(np.float64)
+    rho = float(np.corrcoef(rank(w), rank(r))[0, 1])
+    print(f"rank correlation of learned width and |residual| on {w.size} source rings: {rho:.3f}")
+    assert rho > 0.3
 
 
 def test_checkpoint_resumes_training(cc, dev, tmp_path):
