@@ -29,7 +29,9 @@
 // taken in the grid's compact order (order.cu: HEALPix NESTED), so each warp
 // owns a small patch of sky, and per tile each warp lists the rings that lie
 // wholly on one side of its patch (every angle below pi/2, or every one
-// above): those skip the fold and the mirror select, which is most of them.  Directions are processed in pairs with the packed FP32x2 FMA / add
+// above): those skip the fold and the mirror select, which is most of them,
+// and the wide ones far enough from both the axis and its opposite take h
+// from the dot product.  Directions are processed in pairs with the packed FP32x2 FMA / add
 // / multiply of sm_100+ (one instruction issue per two lanes of FP32 work),
 // which leaves the FP32 pipe, not instruction issue, as the limit.  Per
 // direction the FP32 sum
@@ -50,6 +52,11 @@ constexpr int kStages = 4;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr float kGaussK = 0.84932180028801907f;   // sqrt(log2(e) / 2)
 constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
+// The dot form of h (below) is used for rings at least this wide (k = kGaussK
+// / deta <= kDotMaxK: deta >= 13.9 deg) whose every pair lies between
+// kDotAngle and pi - kDotAngle from the axis.
+constexpr float kDotAngle = 0.52359878f;          // pi / 6
+constexpr float kDotMaxK = 3.5f;
 
 // Coefficients of acos_q (cc_math.cuh) as FP32x2 pairs.
 __device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
@@ -186,7 +193,13 @@ struct SweepSmem {
 // The pair term for one ring and DP direction pairs (see the file header).
 // SIDE 1: every pair is known to lie on the ring's near side (h <= 1), SIDE 2:
 // on its far side; the fold and the select then have one outcome, and the
-// result is the same as the general form's (SIDE 0) bit for bit.
+// result is the same as the general form's (SIDE 0) bit for bit.  SIDE 3 / 4:
+// near / far side, and every pair between kDotAngle and pi - kDotAngle from
+// the axis: h from the dot product, h = 2 t with t = 1/2 + a'.(-c') (three
+// FMAs instead of the chord's six operations).  Its absolute error (a few
+// 1e-8 in t) is harmless away from theta = 0 and pi: there the angle's
+// error stays below 6e-7 rad (against 3e-7 for the chord), which for rings
+// of k <= kDotMaxK moves a term by at most ~1e-5 of its value.
 template <int DP, bool KCUT, int SIDE = 0>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
@@ -199,19 +212,26 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
     const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        float2 dx = __fadd2_rn(ax2, ncx[q]);
-        float2 dy = __fadd2_rn(ay2, ncy[q]);
-        float2 dz = __fadd2_rn(az2, ncz[q]);
-        float2 h = __fmul2_rn(dx, dx);
-        h = __ffma2_rn(dy, dy, h);
-        h = __ffma2_rn(dz, dz, h);                    // 1 - cos(theta)
-        float2 sv;
-        if (SIDE == 1) {
-            sv = h;
+        float2 h = pair(0.0f), sv;
+        if (SIDE == 3 || SIDE == 4) {             // dot form: t = 1/2 + a'.nc = h / 2
+            float2 t = __ffma2_rn(az2, ncz[q], pair(0.5f));
+            t = __ffma2_rn(ay2, ncy[q], t);
+            t = __ffma2_rn(ax2, ncx[q], t);
+            sv = SIDE == 3 ? __fmul2_rn(t, two2) : __ffma2_rn(t, pair(-2.0f), two2);
         } else {
-            float2 g = __ffma2_rn(h, m1, two2);         // 2 - h
-            sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
-                           : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+            float2 dx = __fadd2_rn(ax2, ncx[q]);
+            float2 dy = __fadd2_rn(ay2, ncy[q]);
+            float2 dz = __fadd2_rn(az2, ncz[q]);
+            h = __fmul2_rn(dx, dx);
+            h = __ffma2_rn(dy, dy, h);
+            h = __ffma2_rn(dz, dz, h);                // 1 - cos(theta)
+            if (SIDE == 1) {
+                sv = h;
+            } else {
+                float2 g = __ffma2_rn(h, m1, two2);     // 2 - h
+                sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                               : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+            }
         }
         float2 p = pair(2.61164433e-03f);               // Q(s), degree 6, FP32x2
         p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
@@ -222,8 +242,8 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
         p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
         float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
         float2 th = __fmul2_rn(rt, p);
-        float2 nbs = SIDE == 1   ? make_float2(P2.x, P2.x)
-                     : SIDE == 2 ? make_float2(P2.y, P2.y)
+        float2 nbs = (SIDE == 1 || SIDE == 3)   ? make_float2(P2.x, P2.x)
+                     : (SIDE == 2 || SIDE == 4) ? make_float2(P2.y, P2.y)
                                  : make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
         float2 u = __ffma2_rn(th, k2, nbs);
         float2 u2 = __fmul2_rn(u, u);
@@ -254,15 +274,16 @@ __device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float c
     return fabsf(u) <= lim;
 }
 
-// The rings of a warp's side list lst[b, e) of tile T, eight at a time.
+// The rings of a warp's side list lst[b, e) of tile T, four at a time (eight
+// made the five list bodies too large for the instruction cache).
 template <int DP, int SIDE>
 __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *lst, int b, int e,
                                          const float2 (&ncx)[DP], const float2 (&ncy)[DP],
                                          const float2 (&ncz)[DP], float2 (&acc)[DP]) {
     int i = b;
-    for (; i + 8 <= e; i += 8) {
+    for (; i + 4 <= e; i += 4) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) ring_pairs<DP, false, SIDE>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
+        for (int k = 0; k < 4; k++) ring_pairs<DP, false, SIDE>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
     }
     for (; i < e; i++) ring_pairs<DP, false, SIDE>(T[lst[i]], ncx, ncy, ncz, acc, 0.f);
 }
@@ -275,7 +296,9 @@ __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *
 // tile's rings by side against its cap of directions: a ring whose axis is
 // within pi/2 - rho - 1e-3 of the cap centre has every pair on its near side,
 // beyond pi/2 + rho + 1e-3 on its far side, and those rings skip the fold
-// and the select.  With the angular selection on, each warp skips, tile by
+// and the select; a wide one whose axis is also more than kDotAngle + rho
+// from the centre and from its opposite takes the dot form (ring_pairs).
+// With the angular selection on, each warp skips, tile by
 // tile, the rings that cannot reach its directions instead.  Writes the
 // unit's partial (or full) map row (in grid order) and, when bb_slot is set,
 // its block best.  Returns false when a bounded wait gave up (status set to
@@ -354,6 +377,8 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
     // side test: cos(angle(axis, centre)) = 2 a'.cap' against +-sin(rho + 1e-3)
     // (no side decided when the cap reaches pi/2)
     const float slim = rho + 1.0e-3f < 1.5707f ? sinf(rho + 1.0e-3f) : 2.0f;
+    // ... and the dot form when cos(angle) also lies within +-cos(kDotAngle + rho)
+    const float cdot = kDotAngle + rho < 1.5707f ? cosf(kDotAngle + rho) : -2.0f;
     const int w = tid >> 5;
 
     const int64_t ntk = (*nkept + kTile - 1) / kTile;
@@ -393,37 +418,53 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                     }
                 }
             } else {
-                // the tile's rings by side: near from the front of the list,
-                // then far, then the rest, each in tile order
-                unsigned nm[kTile / 32], fm[kTile / 32];
-                int nn = 0, nf = 0;
+                // the tile's rings by class: near side (chord form, dot
+                // form), far side (dot, chord), then the rest, each in tile
+                // order
+                unsigned m1s[kTile / 32], m3s[kTile / 32], m4s[kTile / 32], m2s[kTile / 32];
+                int cnt[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int g = 0; g < kTile / 32; g++) {
                     const RingRec &R = T[32 * g + lane];
                     const float c2 = 2.0f * fmaf(R.az, capz, fmaf(R.ay, capy, R.ax * capx));
-                    nm[g] = __ballot_sync(0xffffffffu, c2 >= slim);
-                    fm[g] = __ballot_sync(0xffffffffu, c2 <= -slim);
-                    nn += __popc(nm[g]);
-                    nf += __popc(fm[g]);
+                    const bool wide = R.k <= kDotMaxK;
+                    const bool dn = wide && c2 >= slim && c2 <= cdot;
+                    const bool df = wide && c2 <= -slim && c2 >= -cdot;
+                    m1s[g] = __ballot_sync(0xffffffffu, c2 >= slim && !dn);
+                    m3s[g] = __ballot_sync(0xffffffffu, dn);
+                    m4s[g] = __ballot_sync(0xffffffffu, df);
+                    m2s[g] = __ballot_sync(0xffffffffu, c2 <= -slim && !df);
+                    cnt[0] += __popc(m1s[g]);
+                    cnt[1] += __popc(m3s[g]);
+                    cnt[2] += __popc(m4s[g]);
+                    cnt[3] += __popc(m2s[g]);
                 }
                 const unsigned lt = (1u << lane) - 1u;
-                int bn = 0, bf = nn, bm = nn + nf;
+                int b1 = 0, b3 = cnt[0], b4 = b3 + cnt[1], b2 = b4 + cnt[2], bm = b2 + cnt[3];
+                const int e1 = b3, e3 = b4, e4 = b2, e2 = bm;
 #pragma unroll
                 for (int g = 0; g < kTile / 32; g++) {
-                    const unsigned mm = ~(nm[g] | fm[g]);
-                    const bool isn = (nm[g] >> lane) & 1u, isf = (fm[g] >> lane) & 1u;
-                    const int at = isn ? bn + __popc(nm[g] & lt)
-                                 : isf ? bf + __popc(fm[g] & lt) : bm + __popc(mm & lt);
+                    const unsigned mm = ~(m1s[g] | m3s[g] | m4s[g] | m2s[g]);
+                    const unsigned bit = 1u << lane;
+                    const int at = (m1s[g] & bit) ? b1 + __popc(m1s[g] & lt)
+                                 : (m3s[g] & bit) ? b3 + __popc(m3s[g] & lt)
+                                 : (m4s[g] & bit) ? b4 + __popc(m4s[g] & lt)
+                                 : (m2s[g] & bit) ? b2 + __popc(m2s[g] & lt)
+                                                  : bm + __popc(mm & lt);
                     S.lst[w][at] = (unsigned char)(32 * g + lane);
-                    bn += __popc(nm[g]);
-                    bf += __popc(fm[g]);
+                    b1 += __popc(m1s[g]);
+                    b3 += __popc(m3s[g]);
+                    b4 += __popc(m4s[g]);
+                    b2 += __popc(m2s[g]);
                     bm += __popc(mm);
                 }
                 __syncwarp();
                 const unsigned char *L = S.lst[w];
-                side_run<DP, 1>(T, L, 0, nn, ncx, ncy, ncz, acc);
-                side_run<DP, 2>(T, L, nn, nn + nf, ncx, ncy, ncz, acc);
-                side_run<DP, 0>(T, L, nn + nf, kTile, ncx, ncy, ncz, acc);
+                side_run<DP, 1>(T, L, 0, e1, ncx, ncy, ncz, acc);
+                side_run<DP, 3>(T, L, e1, e3, ncx, ncy, ncz, acc);
+                side_run<DP, 4>(T, L, e3, e4, ncx, ncy, ncz, acc);
+                side_run<DP, 2>(T, L, e4, e2, ncx, ncy, ncz, acc);
+                side_run<DP, 0>(T, L, e2, kTile, ncx, ncy, ncz, acc);
                 __syncwarp();
             }
         }
