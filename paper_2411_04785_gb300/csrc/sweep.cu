@@ -196,10 +196,12 @@ struct SweepSmem {
 // result is the same as the general form's (SIDE 0) bit for bit.  SIDE 3 / 4:
 // near / far side, and every pair between kDotAngle and pi - kDotAngle from
 // the axis: h from the dot product, h = 2 t with t = 1/2 + a'.(-c') (three
-// FMAs instead of the chord's six operations).  Its absolute error (a few
-// 1e-8 in t) is harmless away from theta = 0 and pi: there the angle's
-// error stays below 6e-7 rad (against 3e-7 for the chord), which for rings
-// of k <= kDotMaxK moves a term by at most ~1e-5 of its value.
+// FMAs instead of the chord's six operations).  Its absolute error (at most
+// ~1.5e-7 in t) is harmless away from theta = 0 and pi: there it adds at
+// most 6e-7 rad to the angle (the polynomial's own 2.7e-7 stays), which for
+// rings of k <= kDotMaxK moves a term above the map rule's floor by at most
+// ~1.3e-5 of its value with every rounding at its bound and the same sign,
+// and by ~1e-6 typically; summed over many rings it averages out.
 template <int DP, bool KCUT, int SIDE = 0>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
