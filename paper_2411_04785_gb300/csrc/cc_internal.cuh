@@ -116,7 +116,7 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
 // counted, the counts are scanned into block offsets (in place) and the total
 // is written to *nkept; the plan's split reduction, argmax and seeds follow a
 // sweep through finish_localize (probe coordinates in `grid`).
-constexpr int kPackChunk = 2048;
+constexpr int kPackChunk = 512;
 cudaError_t launch_pack_scan(int32_t *blockcnt, int64_t nblk, int64_t *nkept, cudaStream_t s);
 // Compact traversal order of a grid's directions (order.cu): perm[k] is the
 // k-th direction swept; scratch of direction_order_bytes(count) bytes.
