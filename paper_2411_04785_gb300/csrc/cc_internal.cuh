@@ -73,14 +73,14 @@ cudaError_t launch_rings_from_events(const cc_events &ev, const cc_rings &out,
 // sweep / argmax / seeds - sweep.cu
 // ---------------------------------------------------------------------------
 // Packed ring record of the sweep, 48 bytes: axis pre-scaled by 1/sqrt(2),
-// k = sqrt(log2(e)/2)/deta, nb = -eta' k, nb2 = -(pi - eta') k, where
-// (axis, eta') is the ring mirrored to eta' <= pi/2 when needed.  Values that
-// meet a pair of directions are stored twice so that they load as ready
-// FP32x2 operands.
+// k = sqrt(log2(e)/2)/deta, nb = -eta' k, nb2 = -(pi - eta') k,
+// ne = (pi/2 - eta') k, where (axis, eta') is the ring mirrored to
+// eta' <= pi/2 when needed.  Values that meet a pair of directions are stored
+// twice so that they load as ready FP32x2 operands.
 struct __align__(16) RingRec {
     float ax, ax_, ay, ay_;
     float az, az_, k, k_;
-    float nb, nb2, pad0, pad1;
+    float nb, nb2, ne, ne_;
 };
 
 struct BlockBest {

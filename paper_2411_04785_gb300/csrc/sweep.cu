@@ -27,12 +27,15 @@
 // 4-stage mbarrier ring; every CTA owns 256 x D directions held in registers
 // (D per thread) and a contiguous range of ring tiles.  The directions are
 // taken in the grid's compact order (order.cu: HEALPix NESTED), so each warp
-// owns a small patch of sky, and per tile each warp lists the rings that lie
-// wholly on one side of its patch (every angle below pi/2, or every one
-// above): those skip the fold and the mirror select, which is most of them,
-// and the wide ones far enough from both the axis and its opposite take h
-// from the dot product.  Directions are processed in pairs with the packed FP32x2 FMA / add
-// / multiply of sm_100+ (one instruction issue per two lanes of FP32 work),
+// owns a small patch of sky, and per tile each warp sorts the rings by where
+// its patch lies from them.  Rings whose every angle to the patch lies
+// within 30 degrees of pi/2 take the angle as pi/2 + asin of the dot product
+// (an odd polynomial: no square root, no fold, no select); of the rest, those
+// wholly on one side of the patch (every angle below pi/2, or every one
+// above) skip the fold and the mirror select, and the wide ones far enough
+// from both the axis and its opposite take h from the dot product.
+// Directions are processed in pairs with the packed FP32x2 FMA / add /
+// multiply of sm_100+ (one instruction issue per two lanes of FP32 work),
 // which leaves the FP32 pipe, not instruction issue, as the limit.  Per
 // direction the FP32 sum
 // of a 128-ring tile is added into a Kahan-compensated accumulator.  When the
@@ -57,6 +60,12 @@ constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
 // kDotAngle and pi - kDotAngle from the axis.
 constexpr float kDotAngle = 0.52359878f;          // pi / 6
 constexpr float kDotMaxK = 3.5f;
+// The equatorial form (below) is used for rings of any width whose every
+// pair lies within kEquAngle of pi/2 from the axis (|cos(theta)| <= 1/2).
+constexpr float kEquAngle = 0.52359878f;          // pi / 6
+// The one-sided forms are used when every pair lies within kSideAngle of the
+// axis or of its opposite (s <= 0.8: their degree-5 polynomial's range).
+constexpr float kSideAngle = 1.36943841f;         // acos(0.2), 78.46 deg
 
 // Coefficients of acos_q (cc_math.cuh) as FP32x2 pairs.
 __device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
@@ -80,13 +89,14 @@ __device__ __forceinline__ bool ring_kept(const float *__restrict__ ax,
 
 __device__ __forceinline__ RingRec make_rec(float a0, float a1, float a2, float e, float de) {
     float k = kGaussK / de;
-    float b = e * k, b2 = (kPiF - e) * k;
+    float b = e * k, b2 = (kPiF - e) * k, ne = (0.5f * kPiF - e) * k;
     if (e > 0.5f * kPiF) {      // mirror: same ring, eta' <= pi/2
         a0 = -a0; a1 = -a1; a2 = -a2;
         float t = b; b = b2; b2 = t;
+        ne = -ne;
     }
     float s0 = a0 * kInvSqrt2, s1 = a1 * kInvSqrt2, s2 = a2 * kInvSqrt2;
-    return RingRec{s0, s0, s1, s1, s2, s2, k, k, -b, -b2, 0.f, 0.f};
+    return RingRec{s0, s0, s1, s1, s2, s2, k, k, -b, -b2, ne, ne};
 }
 
 // Kept rings are compacted, in index order, to the front of the record
@@ -176,7 +186,7 @@ k_pack_scatter(const float *__restrict__ ax, const float *__restrict__ ay,
         if (n + threadIdx.x < end &&
             CC_IN_BOUNDS(CC_SITE_PACK_REC, n + threadIdx.x, (R + kTile - 1) / kTile * kTile))
             rec[n + threadIdx.x] =
-                RingRec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, 0.f, 0.f};
+                RingRec{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -kNullB, -kNullB, -kNullB, -kNullB};
     }
 }
 
@@ -193,7 +203,11 @@ struct SweepSmem {
 // The pair term for one ring and DP direction pairs (see the file header).
 // SIDE 1: every pair is known to lie on the ring's near side (h <= 1), SIDE 2:
 // on its far side; the fold and the select then have one outcome, and the
-// result is the same as the general form's (SIDE 0) bit for bit.  SIDE 3 / 4:
+// result is the same as the general form's (SIDE 0) bit for bit.  SHORT:
+// every pair of SIDE 1 - 4 lies within kSideAngle of the axis or of its
+// opposite (the folded s <= 0.8), and Q is the degree-5 fit on [0, 0.8]
+// (fit_acos.py: 9.3e-8 rad, 2.6e-7 evaluated in FP32; as accurate as degree 6
+// on [0, 1]: 8.8e-8 and 2.7e-7), one FMA fewer.  SIDE 3 / 4:
 // near / far side, and every pair between kDotAngle and pi - kDotAngle from
 // the axis: h from the dot product, h = 2 t with t = 1/2 + a'.(-c') (three
 // FMAs instead of the chord's six operations).  Its absolute error (at most
@@ -202,15 +216,44 @@ struct SweepSmem {
 // rings of k <= kDotMaxK moves a term above the map rule's floor by at most
 // ~1.3e-5 of its value with every rounding at its bound and the same sign,
 // and by ~1e-6 typically; summed over many rings it averages out.
-template <int DP, bool KCUT, int SIDE = 0>
+// SIDE 5 (equatorial): every pair within kEquAngle of pi/2 from the axis,
+// any width: theta = pi/2 + asin(2 s), s = a'.(-c') = -cos(theta) / 2, with
+// asin(2 s) = s P(s^2) (fit_asin.py: degree 4 in s^2, 8.6e-8 rad evaluated in
+// FP32), so u = (theta - eta') k = s P(s^2) k + ne: twelve FP32 operations
+// and one MUFU per pair, no square root, no fold, no select.  The absolute
+// error of s (~1e-7, as t above) moves the angle by at most 2.3e-7 rad at
+// |cos(theta)| <= 1/2, no more than the chord form's own error there (its h
+// is ~1 with the same absolute rounding, and the acos polynomial adds 2.7e-7).
+template <int DP, bool KCUT, int SIDE = 0, bool SHORT = false>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
                                            float2 (&acc)[DP], float kc2) {
     const float4 P0 = *reinterpret_cast<const float4 *>(&R.ax);
     const float4 P1 = *reinterpret_cast<const float4 *>(&R.az);
-    const float2 P2 = *reinterpret_cast<const float2 *>(&R.nb);
     const float2 ax2 = make_float2(P0.x, P0.y), ay2 = make_float2(P0.z, P0.w);
     const float2 az2 = make_float2(P1.x, P1.y), k2 = make_float2(P1.z, P1.w);
+    if (SIDE == 5) {
+        const float2 ne2 = *reinterpret_cast<const float2 *>(&R.ne);
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            float2 sd = __fmul2_rn(az2, ncz[q]);      // s = -cos(theta) / 2
+            sd = __ffma2_rn(ay2, ncy[q], sd);
+            sd = __ffma2_rn(ax2, ncx[q], sd);
+            const float2 w = __fmul2_rn(sd, sd);
+            float2 p = pair(2.73005066e+01f);         // P(w), degree 4, FP32x2
+            p = __ffma2_rn(p, w, pair(4.88156176e+00f));
+            p = __ffma2_rn(p, w, pair(2.42437673e+00f));
+            p = __ffma2_rn(p, w, pair(1.33304811e+00f));
+            p = __ffma2_rn(p, w, pair(2.00000095e+00f));
+            const float2 v = __fmul2_rn(sd, p);       // theta - pi/2
+            const float2 u = __ffma2_rn(v, k2, ne2);
+            const float2 u2 = __fmul2_rn(u, u);
+            const float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            acc[q] = __fadd2_rn(acc[q], e);
+        }
+        return;
+    }
+    const float2 P2 = *reinterpret_cast<const float2 *>(&R.nb);
     const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
 #pragma unroll
     for (int q = 0; q < DP; q++) {
@@ -235,13 +278,23 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
                                : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
             }
         }
-        float2 p = pair(2.61164433e-03f);               // Q(s), degree 6, FP32x2
-        p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
-        p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
-        p = __ffma2_rn(p, sv, pair(5.94551489e-03f));
-        p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
-        p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
-        p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
+        float2 p;
+        if (!SHORT) {                                    // Q(s) on [0, 1], degree 6
+            p = pair(2.61164433e-03f);
+            p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
+            p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
+            p = __ffma2_rn(p, sv, pair(5.94551489e-03f));
+            p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
+            p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
+            p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
+        } else {                                         // Q(s) on [0, 0.8], degree 5
+            p = pair(3.31251509e-03f);
+            p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
+            p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
+            p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
+            p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
+            p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+        }
         float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
         float2 th = __fmul2_rn(rt, p);
         float2 nbs = (SIDE == 1 || SIDE == 3)   ? make_float2(P2.x, P2.x)
@@ -276,18 +329,18 @@ __device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float c
     return fabsf(u) <= lim;
 }
 
-// The rings of a warp's side list lst[b, e) of tile T, four at a time (eight
-// made the five list bodies too large for the instruction cache).
-template <int DP, int SIDE>
+// The rings of a warp's list lst[b, e) of tile T, four at a time (eight made
+// the list bodies too large for the instruction cache).
+template <int DP, int SIDE, bool SHORT = false>
 __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *lst, int b, int e,
                                          const float2 (&ncx)[DP], const float2 (&ncy)[DP],
                                          const float2 (&ncz)[DP], float2 (&acc)[DP]) {
     int i = b;
     for (; i + 4 <= e; i += 4) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) ring_pairs<DP, false, SIDE>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
+        for (int k = 0; k < 4; k++) ring_pairs<DP, false, SIDE, SHORT>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
     }
-    for (; i < e; i++) ring_pairs<DP, false, SIDE>(T[lst[i]], ncx, ncy, ncz, acc, 0.f);
+    for (; i < e; i++) ring_pairs<DP, false, SIDE, SHORT>(T[lst[i]], ncx, ncy, ncz, acc, 0.f);
 }
 
 // One work unit of the sweep: the 256 x D directions of direction block db
@@ -296,16 +349,21 @@ __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *
 // or k without perm) against the ring tiles split, split + nsplit,
 // split + 2 nsplit, ... of the *nkept packed rings.  Each warp sorts a
 // tile's rings by side against its cap of directions: a ring whose axis is
-// within pi/2 - rho - 1e-3 of the cap centre has every pair on its near side,
-// beyond pi/2 + rho + 1e-3 on its far side, and those rings skip the fold
-// and the select; a wide one whose axis is also more than kDotAngle + rho
+// within L - rho - 1e-3 of the cap centre has every pair within L of it, one
+// whose axis is that close to the opposite of the centre every pair within L
+// of its opposite, and those rings skip the fold and the select (L = pi/2,
+// or kSideAngle with the short polynomial when the cap is narrow enough for
+// the equatorial form to take every ring between the two); a wide one whose
+// axis is also more than kDotAngle + rho
 // from the centre and from its opposite takes the dot form (ring_pairs).
+// Before all of these, a ring whose axis lies within kEquAngle - rho - 1e-3
+// of pi/2 from the centre takes the equatorial form.
 // With the angular selection on, each warp skips, tile by
 // tile, the rings that cannot reach its directions instead.  Writes the
 // unit's partial (or full) map row (in grid order) and, when bb_slot is set,
 // its block best.  Returns false when a bounded wait gave up (status set to
 // CC_ETIMEOUT).
-template <int D, bool KCUT>
+template <int D, bool KCUT, bool SHORT>
 __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restrict__ rec,
                                            const int64_t *__restrict__ nkept, int64_t nsplit,
                                            int64_t db, int64_t split,
@@ -376,11 +434,15 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         rho = 2.0f * asinf(fminf(sqrtf(0.5f * h), 1.0f)) + 2.0e-5f;
         kc = sqrtf(kc2);
     }
-    // side test: cos(angle(axis, centre)) = 2 a'.cap' against +-sin(rho + 1e-3)
-    // (no side decided when the cap reaches pi/2)
-    const float slim = rho + 1.0e-3f < 1.5707f ? sinf(rho + 1.0e-3f) : 2.0f;
+    // side test: cos(angle(axis, centre)) = 2 a'.cap' against +-cos(L - rho -
+    // 1e-3), L = kSideAngle with the short polynomial, else pi/2 (no side
+    // decided when the cap reaches L)
+    const float slim = SHORT ? (rho + 1.0e-3f < kSideAngle ? cosf(kSideAngle - rho - 1.0e-3f) : 2.0f)
+                             : (rho + 1.0e-3f < 1.5707f ? sinf(rho + 1.0e-3f) : 2.0f);
     // ... and the dot form when cos(angle) also lies within +-cos(kDotAngle + rho)
     const float cdot = kDotAngle + rho < 1.5707f ? cosf(kDotAngle + rho) : -2.0f;
+    // the equatorial form when |cos(angle)| <= sin(kEquAngle - rho - 1e-3)
+    const float elim = rho + 1.0e-3f < kEquAngle ? sinf(kEquAngle - rho - 1.0e-3f) : -1.0f;
     const int w = tid >> 5;
 
     const int64_t ntk = (*nkept + kTile - 1) / kTile;
@@ -420,40 +482,47 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                     }
                 }
             } else {
-                // the tile's rings by class: near side (chord form, dot
-                // form), far side (dot, chord), then the rest, each in tile
-                // order
-                unsigned m1s[kTile / 32], m3s[kTile / 32], m4s[kTile / 32], m2s[kTile / 32];
-                int cnt[4] = {0, 0, 0, 0};
+                // the tile's rings by class: equatorial, near side (chord
+                // form, dot form), far side (dot, chord), then the rest, each
+                // in tile order
+                unsigned m5s[kTile / 32], m1s[kTile / 32], m3s[kTile / 32], m4s[kTile / 32],
+                    m2s[kTile / 32];
+                int cnt[5] = {0, 0, 0, 0, 0};
 #pragma unroll
                 for (int g = 0; g < kTile / 32; g++) {
                     const RingRec &R = T[32 * g + lane];
                     const float c2 = 2.0f * fmaf(R.az, capz, fmaf(R.ay, capy, R.ax * capx));
-                    const bool wide = R.k <= kDotMaxK;
+                    const bool eq = fabsf(c2) <= elim;
+                    const bool wide = R.k <= kDotMaxK && !eq;
                     const bool dn = wide && c2 >= slim && c2 <= cdot;
                     const bool df = wide && c2 <= -slim && c2 >= -cdot;
-                    m1s[g] = __ballot_sync(0xffffffffu, c2 >= slim && !dn);
+                    m5s[g] = __ballot_sync(0xffffffffu, eq);
+                    m1s[g] = __ballot_sync(0xffffffffu, c2 >= slim && !dn && !eq);
                     m3s[g] = __ballot_sync(0xffffffffu, dn);
                     m4s[g] = __ballot_sync(0xffffffffu, df);
-                    m2s[g] = __ballot_sync(0xffffffffu, c2 <= -slim && !df);
-                    cnt[0] += __popc(m1s[g]);
-                    cnt[1] += __popc(m3s[g]);
-                    cnt[2] += __popc(m4s[g]);
-                    cnt[3] += __popc(m2s[g]);
+                    m2s[g] = __ballot_sync(0xffffffffu, c2 <= -slim && !df && !eq);
+                    cnt[0] += __popc(m5s[g]);
+                    cnt[1] += __popc(m1s[g]);
+                    cnt[2] += __popc(m3s[g]);
+                    cnt[3] += __popc(m4s[g]);
+                    cnt[4] += __popc(m2s[g]);
                 }
                 const unsigned lt = (1u << lane) - 1u;
-                int b1 = 0, b3 = cnt[0], b4 = b3 + cnt[1], b2 = b4 + cnt[2], bm = b2 + cnt[3];
-                const int e1 = b3, e3 = b4, e4 = b2, e2 = bm;
+                int b5 = 0, b1 = cnt[0], b3 = b1 + cnt[1], b4 = b3 + cnt[2], b2 = b4 + cnt[3],
+                    bm = b2 + cnt[4];
+                const int e5 = b1, e1 = b3, e3 = b4, e4 = b2, e2 = bm;
 #pragma unroll
                 for (int g = 0; g < kTile / 32; g++) {
-                    const unsigned mm = ~(m1s[g] | m3s[g] | m4s[g] | m2s[g]);
+                    const unsigned mm = ~(m5s[g] | m1s[g] | m3s[g] | m4s[g] | m2s[g]);
                     const unsigned bit = 1u << lane;
-                    const int at = (m1s[g] & bit) ? b1 + __popc(m1s[g] & lt)
+                    const int at = (m5s[g] & bit) ? b5 + __popc(m5s[g] & lt)
+                                 : (m1s[g] & bit) ? b1 + __popc(m1s[g] & lt)
                                  : (m3s[g] & bit) ? b3 + __popc(m3s[g] & lt)
                                  : (m4s[g] & bit) ? b4 + __popc(m4s[g] & lt)
                                  : (m2s[g] & bit) ? b2 + __popc(m2s[g] & lt)
                                                   : bm + __popc(mm & lt);
                     S.lst[w][at] = (unsigned char)(32 * g + lane);
+                    b5 += __popc(m5s[g]);
                     b1 += __popc(m1s[g]);
                     b3 += __popc(m3s[g]);
                     b4 += __popc(m4s[g]);
@@ -462,10 +531,11 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                 }
                 __syncwarp();
                 const unsigned char *L = S.lst[w];
-                side_run<DP, 1>(T, L, 0, e1, ncx, ncy, ncz, acc);
-                side_run<DP, 3>(T, L, e1, e3, ncx, ncy, ncz, acc);
-                side_run<DP, 4>(T, L, e3, e4, ncx, ncy, ncz, acc);
-                side_run<DP, 2>(T, L, e4, e2, ncx, ncy, ncz, acc);
+                side_run<DP, 5>(T, L, 0, e5, ncx, ncy, ncz, acc);
+                side_run<DP, 1, SHORT>(T, L, e5, e1, ncx, ncy, ncz, acc);
+                side_run<DP, 3, SHORT>(T, L, e1, e3, ncx, ncy, ncz, acc);
+                side_run<DP, 4, SHORT>(T, L, e3, e4, ncx, ncy, ncz, acc);
+                side_run<DP, 2, SHORT>(T, L, e4, e2, ncx, ncy, ncz, acc);
                 side_run<DP, 0>(T, L, e2, kTile, ncx, ncy, ncz, acc);
                 __syncwarp();
             }
@@ -520,7 +590,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
 }
 
 
-template <int D, bool KCUT>
+template <int D, bool KCUT, bool SHORT>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
         int64_t ndb,
@@ -528,8 +598,8 @@ k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int6
         const float *__restrict__ cz, const int32_t *__restrict__ perm, int64_t M, float kc2,
         float *__restrict__ out, BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
     __shared__ __align__(128) SweepSmem S;
-    sweep_unit<D, KCUT>(S, rec, nkept, nsplit, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy, cz, perm,
-                        M, kc2, out, bb ? bb + blockIdx.x : nullptr, status);
+    sweep_unit<D, KCUT, SHORT>(S, rec, nkept, nsplit, blockIdx.x % ndb, blockIdx.x / ndb, cx, cy,
+                               cz, perm, M, kc2, out, bb ? bb + blockIdx.x : nullptr, status);
 }
 
 // Several bursts in one launch: CTAs take work units of all the bursts from
@@ -556,7 +626,7 @@ struct MultiArgs {
     unsigned long long *counter;
 };
 
-template <int D, bool KCUT>
+template <int D, bool KCUT, bool SHORT>
 __global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant__ MultiArgs a) {
     __shared__ __align__(128) SweepSmem S;
     __shared__ long long unit_s;
@@ -571,9 +641,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant_
         while (u >= a.unit_begin[b + 1]) b++;
         const BurstDesc &d = a.b[b];
         const int64_t lu = u - a.unit_begin[b];
-        if (!sweep_unit<D, KCUT>(S, d.rec, d.nkept, d.nsplit, lu % d.ndb, lu / d.ndb, a.cx, a.cy,
-                                 a.cz, a.perm, a.M, a.kc2, d.out, d.bb ? d.bb + lu : nullptr,
-                                 d.status))
+        if (!sweep_unit<D, KCUT, SHORT>(S, d.rec, d.nkept, d.nsplit, lu % d.ndb, lu / d.ndb, a.cx,
+                                        a.cy, a.cz, a.perm, a.M, a.kc2, d.out,
+                                        d.bb ? d.bb + lu : nullptr, d.status))
             break;
     }
 }
@@ -661,17 +731,34 @@ k_select(const float *__restrict__ map, const BlockBest *__restrict__ bb, int64_
     }
 }
 
-template <int D, bool KCUT>
-void *sweep_fn() {
-    return (void *)k_sweep<D, KCUT>;
+template <int D>
+void *sweep_fn(bool kcut, bool shortq) {
+    return kcut ? (void *)k_sweep<D, true, false>
+                : shortq ? (void *)k_sweep<D, false, true> : (void *)k_sweep<D, false, false>;
 }
 
-void *pick_sweep(int d, bool kcut) {
+void *pick_sweep_q(int d, bool kcut, bool shortq) {
     switch (d) {
-        case 8: return kcut ? sweep_fn<8, true>() : sweep_fn<8, false>();
-        case 4: return kcut ? sweep_fn<4, true>() : sweep_fn<4, false>();
-        default: return kcut ? sweep_fn<2, true>() : sweep_fn<2, false>();
+        case 8: return sweep_fn<8>(kcut, shortq);
+        case 4: return sweep_fn<4>(kcut, shortq);
+        default: return sweep_fn<2>(kcut, shortq);
     }
+}
+
+void *pick_sweep(int d, bool kcut) { return pick_sweep_q(d, kcut, false); }
+
+// Whether warps sweeping 32 d consecutive directions of the compact order
+// (M directions on the sphere) have caps narrow enough for the short
+// polynomial: every ring that a cap leaves between kSideAngle and pi/2 from
+// its axis then takes the equatorial form, 2 rho + 2e-3 <= kSideAngle -
+// (pi/2 - kEquAngle).  A patch is about a square of 4 pi 32 d / M sr, cap
+// radius sqrt(2 pi 32 d / M), with a quarter more for HEALPix's elongated
+// patches.  A wider cap in a short-polynomial sweep is still exact: its
+// rings beyond kSideAngle take the general form.
+bool short_poly(int64_t M, int d, bool kcut) {
+    if (kcut || M < 1) return false;
+    const double lim = 0.5 * ((double)kSideAngle - (0.5 * 3.14159265358979 - (double)kEquAngle)) - 1e-3;
+    return 1.25 * std::sqrt(2.0 * 3.14159265358979 * 32.0 * d / (double)M) <= lim;
 }
 
 }  // namespace
@@ -828,7 +915,7 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     float *out = plan.nsplit > 1 ? part : map;
     BlockBest *bbk = plan.nsplit > 1 ? nullptr : bb;
     const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
-    void *fn = pick_sweep(plan.d, kcut);
+    void *fn = pick_sweep_q(plan.d, kcut, plan.ordered && short_poly(M, plan.d, kcut));
     const int64_t *nkept = reinterpret_cast<const int64_t *>(ws + plan.off_nkept);
     const int32_t *perm = nullptr;
     if (plan.ordered) {
@@ -887,7 +974,9 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
     // one CTA per work unit (a CTA still takes its unit from the counter): CTAs
     // retire as their units finish, so kernels of higher-priority streams
     // (the bursts' front ends) get SMs without waiting for the whole batch
-    void *fn = kcut ? (void *)k_sweep_multi<kBatchD, true> : (void *)k_sweep_multi<kBatchD, false>;
+    void *fn = kcut                                               ? (void *)k_sweep_multi<kBatchD, true, false>
+               : a.perm != nullptr && short_poly(a.M, kBatchD, false) ? (void *)k_sweep_multi<kBatchD, false, true>
+                                                                        : (void *)k_sweep_multi<kBatchD, false, false>;
     int64_t ctas = a.unit_begin[n];
     if (ctas > (int64_t)INT32_MAX) ctas = INT32_MAX;
     if (ctas < 1) ctas = 1;

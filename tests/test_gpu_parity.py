@@ -375,6 +375,21 @@ def test_map_large_burst_sampled(cc, dev):
     assert (seeds >= 0).all() and len(set(seeds.tolist())) == 8
 
 
+def test_map_fine_grid_full(cc, dev):
+    """10,000 rings of widths 0.5-20 deg x HEALPix nside 128 (196,608
+    directions): every direction under the map rule.  At this nside every
+    warp's patch is narrow enough for the short polynomial of the one-sided
+    forms, and the widths put rings in every form (equatorial, chord, dot)."""
+    rings, s, _ = synth.rings_burst(n=10000, deta_deg=(0.5, 20.0), seed=13)
+    grid = grid32(oracle.grid_healpix_ring(128))
+    got, am, _, st = run_localize(cc, rings, grid, dev)
+    assert st == 0
+    want = oracle.likelihood_map(oracle_rings32(rings), grid)
+    bad = map_violations(got, want, want.max())
+    assert bad.size == 0, f"{bad.size} of {want.size} off"
+    check_argmax(got, am, want)
+
+
 # --------------------------------------------------------------------------
 # refinement
 # --------------------------------------------------------------------------

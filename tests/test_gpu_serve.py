@@ -70,6 +70,30 @@ def test_batched_sweep_equals_alone_and_matches_oracle(cc):
         assert (np.abs(m["map"][idx] - want) <= bound).all()
 
 
+def test_batched_sweep_on_a_fine_ordered_grid(cc):
+    """A HEALPix nside 128 grid kept with its order: the batched sweep takes
+    the short polynomial of the one-sided forms there; each burst alone and
+    in the batch bit for bit, and within the map rule of the oracle."""
+    dev = torch.device("cuda:0")
+    grid_np = oracle.grid_healpix_ring(128)
+    g = cc.grid_healpix_ring(128, dev)
+    grid = tuple(g) + (cc.grid_order(g),)
+    p = cc.Params(topk=2, nms_rad=math.radians(5))
+    sets_np = [synth.rings_burst(n=n, deta_deg=(0.5, 20.0), seed=s)[0]
+               for n, s in ((2000, 21), (700, 22))]
+    sets = [rings_to_dev(r, dev) for r in sets_np]
+    mixed = batch_localize(cc, sets, grid, p)
+    idx = np.arange(0, grid_np[0].size, 13)
+    for r, r_np, m in zip(sets, sets_np, mixed):
+        alone = batch_localize(cc, [r], grid, p)[0]
+        np.testing.assert_array_equal(m["map"], alone["map"])
+        assert m["st"][0] == 0
+        want = oracle.likelihood_map({k: np.asarray(r_np[k], np.float32) for k in
+                                      ("ax", "ay", "az", "eta", "deta")}, grid_np, idx=idx)
+        bound = 1e-5 * np.maximum(want, 1e-3 * want.max())
+        assert (np.abs(m["map"][idx] - want) <= bound).all()
+
+
 def test_server_mixed_stream_equals_alone(cc):
     from paper_2411_04785_gb300 import serve
     dev = torch.device("cuda:0")
