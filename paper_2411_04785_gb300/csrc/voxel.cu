@@ -41,6 +41,9 @@ constexpr int kStages = 4;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr float kGaussK = 0.84932180028801907f;   // sqrt(log2(e) / 2)
 constexpr float kNullB = 1.0e4f;
+constexpr float kEquAngle = 0.52359878f;   // pi / 6: the equatorial form's band
+constexpr float kEquSin = 0.49913372f;     // sin(kEquAngle - 1e-3)
+constexpr float kEquCos = 0.86652497f;     // cos(kEquAngle - 1e-3)
 
 struct NearRec {   // 64 bytes; values met by a voxel pair are duplicated
     float mpx, mpx_, mpy, mpy_, mpz, mpz_;   // -p
@@ -265,6 +268,45 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
     const float2 mpz = make_float2(R1.x, R1.y), msx = make_float2(R1.z, R1.w);
     const float2 msy = make_float2(R2.x, R2.y), msz = make_float2(R2.z, R2.w);
     const float2 k2 = make_float2(R3.x, R3.y);
+    if (SIDE == 5) {
+        // equatorial: every pair within kEquAngle of pi/2 from the axis.
+        // s = (-a/sqrt 2).d / |d| = -cos(theta) / sqrt(2), theta = pi/2 +
+        // asin(sqrt(2) s) = pi/2 + s P(s^2) (fit_asin.py, sigma = sqrt(2):
+        // 8.5e-8 rad evaluated in FP32); no Newton step (the approximate
+        // rsqrt's relative error moves cos(theta) by at most 1e-7 of its
+        // |value| <= 1/2), no square root, no fold, no select
+        const float2 ne2 = __ffma2_rn(k2, pair(0.5f * kPiF), make_float2(R3.z, R3.z));
+#pragma unroll
+        for (int q = 0; q < DP; q++) {
+            const float2 dx = __fadd2_rn(px2[q], mpx);
+            const float2 dy = __fadd2_rn(py2[q], mpy);
+            const float2 dz = __fadd2_rn(pz2[q], mpz);
+            float2 n2 = __ffma2_rn(dx, dx, pair(1.0e-30f));
+            n2 = __ffma2_rn(dy, dy, n2);
+            n2 = __ffma2_rn(dz, dz, n2);
+            const float2 y0 = make_float2(rsqrt_approx(n2.x), rsqrt_approx(n2.y));
+            float2 t = __fmul2_rn(msz, dz);
+            t = __ffma2_rn(msy, dy, t);
+            t = __ffma2_rn(msx, dx, t);
+            const float2 sd = __fmul2_rn(t, y0);
+            const float2 w = __fmul2_rn(sd, sd);
+            float2 p = pair(1.20652330e+00f);
+            p = __ffma2_rn(p, w, pair(4.31473166e-01f));
+            p = __ffma2_rn(p, w, pair(4.28573310e-01f));
+            p = __ffma2_rn(p, w, pair(4.71303672e-01f));
+            p = __ffma2_rn(p, w, pair(1.41421425e+00f));
+            const float2 v = __fmul2_rn(sd, p);                    // theta - pi/2
+            const float2 u = __ffma2_rn(v, k2, ne2);
+            const float2 u2 = __fmul2_rn(u, u);
+            float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            if (KCUT) {
+                e.x = u2.x > kc2 ? 0.0f : e.x;
+                e.y = u2.y > kc2 ? 0.0f : e.y;
+            }
+            acc[q] = __fadd2_rn(acc[q], e);
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < DP; q++) {
         const float2 dx = __fadd2_rn(px2[q], mpx);
@@ -341,12 +383,14 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
     __shared__ __align__(128) NearSmem S;
     const int tid = threadIdx.x;
     const int64_t db = blockIdx.x % ndb, split = blockIdx.x / ndb;
-    const int64_t j0 = db * (int64_t)(kThreads * D) + tid;
+    // warp w owns the 32 D consecutive voxels from db 256 D + 32 D w (lane l
+    // the voxels l, l + 32, ...): a compact block when the list is
+    const int64_t j0 = db * (int64_t)(kThreads * D) + (int64_t)(tid >> 5) * (32 * D) + (tid & 31);
 
     float2 px2[DP], py2[DP], pz2[DP], acc[DP], sum[DP], comp[DP];
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         ja = ja < V ? ja : V - 1;
         jb = jb < V ? jb : V - 1;
         px2[q] = make_float2(__ldg(vx + ja), __ldg(vx + jb));
@@ -414,41 +458,58 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             const NearRec *T = S.tile[stage];
             // the tile's rings by side against the warp's sphere: the plane
             // through the apex normal to the axis does not cut the sphere
-            // when |a . (centre - apex)| > radius (+ 1e-3 of the distance)
-            unsigned nm[kTile / 32], fm[kTile / 32];
-            int nn = 0, nf = 0;
+            // when |a . (centre - apex)| > radius (+ 1e-3 of the distance);
+            // equatorial when every voxel of the sphere lies within
+            // kEquAngle - 1e-3 of pi/2 from the axis: with alpha the angle
+            // of the centre and beta = asin(radius / distance) the sphere's
+            // half angle from the apex, |cos(alpha)| <= sin(kEquAngle - 1e-3
+            // - beta), i.e. |a . (centre - apex)| <= sin(A) sqrt(dist^2 -
+            // radius^2) - cos(A) radius, A = kEquAngle - 1e-3
+            unsigned em[kTile / 32], nm[kTile / 32], fm[kTile / 32];
+            int ne = 0, nn = 0, nf = 0;
 #pragma unroll
             for (int g = 0; g < kTile / 32; g++) {
                 const NearRec &Rg = T[32 * g + lane];
                 const float ex = bcx + Rg.mpx, ey = bcy + Rg.mpy, ez = bcz + Rg.mpz;   // centre - apex
                 // a = -sqrt(2) ms
                 const float sa = -1.41421356f * fmaf(Rg.msz, ez, fmaf(Rg.msy, ey, Rg.msx * ex));
-                const float dist = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+                const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                const float dist = sqrtf(d2);
                 const float lim = brad + 1.0e-3f * dist;
+                const float elim = d2 > brad * brad
+                                       ? fmaf(kEquSin, sqrtf(d2 - brad * brad), -kEquCos * brad)
+                                       : -1.0f;
                 const bool live = Rg.k != 0.0f;
-                nm[g] = __ballot_sync(0xffffffffu, live && sa > lim);
-                fm[g] = __ballot_sync(0xffffffffu, live && sa < -lim);
+                const bool eq = live && fabsf(sa) <= elim;
+                em[g] = __ballot_sync(0xffffffffu, eq);
+                nm[g] = __ballot_sync(0xffffffffu, live && !eq && sa > lim);
+                fm[g] = __ballot_sync(0xffffffffu, live && !eq && sa < -lim);
+                ne += __popc(em[g]);
                 nn += __popc(nm[g]);
                 nf += __popc(fm[g]);
             }
             const unsigned lt = (1u << lane) - 1u;
-            int bn = 0, bf = nn, bm = nn + nf;
+            int be = 0, bn = ne, bf = ne + nn, bm = ne + nn + nf;
 #pragma unroll
             for (int g = 0; g < kTile / 32; g++) {
-                const unsigned mm = ~(nm[g] | fm[g]);
-                const bool isn = (nm[g] >> lane) & 1u, isf = (fm[g] >> lane) & 1u;
-                const int at = isn ? bn + __popc(nm[g] & lt)
+                const unsigned mm = ~(em[g] | nm[g] | fm[g]);
+                const bool ise = (em[g] >> lane) & 1u, isn = (nm[g] >> lane) & 1u,
+                           isf = (fm[g] >> lane) & 1u;
+                const int at = ise ? be + __popc(em[g] & lt)
+                             : isn ? bn + __popc(nm[g] & lt)
                              : isf ? bf + __popc(fm[g] & lt) : bm + __popc(mm & lt);
                 S.lst[w][at] = (unsigned char)(32 * g + lane);
+                be += __popc(em[g]);
                 bn += __popc(nm[g]);
                 bf += __popc(fm[g]);
                 bm += __popc(mm);
             }
             __syncwarp();
             const unsigned char *L = S.lst[w];
-            near_run<DP, KCUT, 1>(T, L, 0, nn, px2, py2, pz2, acc, kc2);
-            near_run<DP, KCUT, 2>(T, L, nn, nn + nf, px2, py2, pz2, acc, kc2);
-            near_run<DP, KCUT, 0>(T, L, nn + nf, kTile, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 5>(T, L, 0, ne, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 1>(T, L, ne, ne + nn, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 2>(T, L, ne + nn, ne + nn + nf, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 0>(T, L, ne + nn + nf, kTile, px2, py2, pz2, acc, kc2);
             __syncwarp();
         }
         __syncthreads();
@@ -474,7 +535,7 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
     int bj = INT32_MAX;
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        const int64_t ja = j0 + (int64_t)(2 * q) * kThreads, jb = ja + kThreads;
+        const int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
         if (ja < V && CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + ja, nsplit * V)) {
             out[split * V + ja] = va;
