@@ -108,10 +108,13 @@ struct SweepPlan {
 // directions in their compact order; the batched path fixes it so that
 // bursts share one kernel instantiation, and keeps the grid's own order.
 // `pick` returns the sweep kernel for (directions per thread, k_cut on) whose
-// occupancy the plan sizes the grid for (NULL: the far-field sweep).
+// occupancy the plan sizes the grid for (NULL: the far-field sweep, which
+// sweeps its directions in their compact order; `ordered` asks the same
+// workspace for another sweep).
 typedef void *(*SweepPick)(int d, bool kcut);
 bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d = 0,
-                SweepPick pick = nullptr, size_t rec_bytes = sizeof(RingRec));
+                SweepPick pick = nullptr, size_t rec_bytes = sizeof(RingRec),
+                bool ordered = false);
 // Ring compaction shared by the sweeps: blocks of kPackChunk rings are
 // counted, the counts are scanned into block offsets (in place) and the total
 // is written to *nkept; the plan's split reduction, argmax and seeds follow a
@@ -119,9 +122,14 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
 constexpr int kPackChunk = 512;
 cudaError_t launch_pack_scan(int32_t *blockcnt, int64_t nblk, int64_t *nkept, cudaStream_t s);
 // Compact traversal order of a grid's directions (order.cu): perm[k] is the
-// k-th direction swept; scratch of direction_order_bytes(count) bytes.
+// k-th direction swept; scratch of direction_order_bytes(count) bytes.  The
+// same for a set of points in space (Morton order: point_order, same scratch).
 size_t direction_order_bytes(int64_t M);
 cudaError_t direction_order(const cc_grid &g, int32_t *perm, char *scratch, cudaStream_t s);
+cudaError_t point_order(const float *x, const float *y, const float *z, int64_t M, int32_t *perm,
+                        char *scratch, cudaStream_t s);
+int direction_order_kernels(int64_t M);   // kernels one call launches
+int point_order_kernels(int64_t M);
 cudaError_t finish_localize(const cc_grid &grid, const cc_params &p, const SweepPlan &plan,
                             float *map, int32_t *argmax, int32_t *seeds, char *ws,
                             cudaStream_t s);
@@ -217,11 +225,12 @@ cudaError_t launch_backproject(const cc_rings &rings, const float *px, const flo
                                int32_t *status, char *ws, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// stage tracing - trace.cu.  Construct before a launch, destroy after it.
+// stage tracing - trace.cu.  Construct before the scope's kernel launches
+// (`kernels` of them), destroy after them.
 // ---------------------------------------------------------------------------
 class TraceScope {
   public:
-    TraceScope(int stage, cudaStream_t s);
+    TraceScope(int stage, cudaStream_t s, int kernels = 1);
     ~TraceScope();
 
   private:

@@ -601,7 +601,7 @@ cudaError_t launch_cluster(const int64_t *t, const uint32_t *adc, int64_t n, int
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kEventsSmemBytes)) != cudaSuccess)
         return e;
-    TraceScope ts(CC_STAGE_CLUSTER, s);
+    TraceScope ts(CC_STAGE_CLUSTER, s, 3);   // masks, scan, events (or the total alone)
     k_cluster_masks<<<(unsigned)tiles, kCThreads, kMasksSmemBytes, s>>>(
         tmap, use_tma, tl, adc, (long long)n, (long long)dt_max, vec_out, edge, masks, aggs, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

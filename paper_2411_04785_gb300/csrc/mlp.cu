@@ -27,6 +27,7 @@ constexpr int kH = 128;                   // hidden width
 constexpr int kF = CC_MLP_FEATURES;       // 16 input features
 constexpr int kP = CC_MLP_PARAMS;         // 35,458 parameters
 constexpr int kChunk = 65536;             // rows per forward/backward pass
+constexpr int64_t kFwdRows = (int64_t)1 << 30;   // rows per forward launch (TMA rows stay int32)
 
 // offsets of the flat parameter vector
 constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
@@ -1073,9 +1074,8 @@ cudaError_t forward_tc(const float *params, const uint16_t *wb, const uint16_t *
                                          (int)kTcSmemBytes);
     if (e != cudaSuccess) return e;
     const int64_t sms = device_sm_count();
-    constexpr int64_t kRowsPerLaunch = (int64_t)1 << 30;   // TMA row coordinates stay int32
-    for (int64_t r0 = 0; r0 < R; r0 += kRowsPerLaunch) {
-        const int64_t n = R - r0 < kRowsPerLaunch ? R - r0 : kRowsPerLaunch;
+    for (int64_t r0 = 0; r0 < R; r0 += kFwdRows) {
+        const int64_t n = R - r0 < kFwdRows ? R - r0 : kFwdRows;
         CUtensorMap xmap;
         const cuuint64_t dims[2] = {(cuuint64_t)kF, (cuuint64_t)n};
         const cuuint64_t strides[1] = {(cuuint64_t)kF * 2};
@@ -1154,7 +1154,7 @@ cudaError_t mlp_features(const cc_events &ev, const cc_rings &r, float sig_pos, 
 cudaError_t mlp_forward(const float *params, const uint16_t *wb, const uint16_t *F, int64_t R,
                         float *out, char *ws, cudaStream_t s) {
     (void)ws;                                  // activations stay on chip
-    TraceScope ts(CC_STAGE_MLP, s);
+    TraceScope ts(CC_STAGE_MLP, s, (int)((R + kFwdRows - 1) / kFwdRows));
     return forward_tc(params, wb, F, R, out, nullptr, s);
 }
 
@@ -1175,7 +1175,8 @@ cudaError_t mlp_grad(const float *params, const uint16_t *wb, const uint16_t *F,
         if (trace->out) w.out = trace->out;
         if (trace->dout) w.dout = reinterpret_cast<bf16 *>(trace->dout);
     }
-    TraceScope ts(CC_STAGE_MLP, s);
+    // forward, loss gradient, four backward layers, reduction, loss sum
+    TraceScope ts(CC_STAGE_MLP, s, (int)((B + kFwdRows - 1) / kFwdRows) + 7);
     cudaError_t e = grad_rows(reinterpret_cast<const bf16 *>(wb), params,
                               reinterpret_cast<const bf16 *>(F), y, res, wv, (int)B,
                               1.0f / (float)B, grad, w, dZ, s);

@@ -14,6 +14,10 @@
 // digits, one scan orders the (digit, block) counts, and one warp per block
 // scatters its directions in index order (ranks among equal digits from
 // __match_any_sync).  Everything is deterministic.
+//
+// The near-field back projection takes its voxels in the same way by their
+// Morton (Z-order) key (point_order): 10 bits per coordinate across the
+// set's bounding box, so each warp's run of voxels is a compact block.
 #include "cc_internal.cuh"
 
 namespace cc {
@@ -145,44 +149,168 @@ int order_level(int64_t M) {   // coarsest L with 12 * 4^L >= M, at most 13
     return L;
 }
 
+// Bounding box of a point set: one CTA, lo[3] then hi[3] into box[6]; points
+// that are not finite are ignored (an empty box stays +inf / -inf).
+__global__ void __launch_bounds__(1024)
+k_bbox(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
+       int64_t M, float *__restrict__ box) {
+    __shared__ float red[6][32];
+    float v[6] = {__builtin_huge_valf(), __builtin_huge_valf(), __builtin_huge_valf(),
+                  -__builtin_huge_valf(), -__builtin_huge_valf(), -__builtin_huge_valf()};
+    for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
+        const float a = x[j], b = y[j], c = z[j];
+        if (!isfinite(a) || !isfinite(b) || !isfinite(c)) continue;
+        v[0] = fminf(v[0], a); v[1] = fminf(v[1], b); v[2] = fminf(v[2], c);
+        v[3] = fmaxf(v[3], a); v[4] = fmaxf(v[4], b); v[5] = fmaxf(v[5], c);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            const float u = __shfl_xor_sync(0xffffffffu, v[q], o);
+            v[q] = q < 3 ? fminf(v[q], u) : fmaxf(v[q], u);
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 6; q++) red[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float a = red[threadIdx.x][0];
+        for (int k = 1; k < nw; k++)
+            a = threadIdx.x < 3 ? fminf(a, red[threadIdx.x][k]) : fmaxf(a, red[threadIdx.x][k]);
+        box[threadIdx.x] = a;
+    }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {   // bit i -> bit 3 i (10 bits)
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Morton (Z-order) key of each point: its coordinates quantised to 10 bits
+// each across the bounding box, bits interleaved (x lowest).  A point that is
+// not finite sorts last.
+__global__ void __launch_bounds__(256)
+k_morton_keys(const float *__restrict__ x, const float *__restrict__ y,
+              const float *__restrict__ z, int64_t M, const float *__restrict__ box,
+              uint32_t *__restrict__ keys, int32_t *__restrict__ idx) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const float p[3] = {x[j], y[j], z[j]};
+    uint32_t key = 0;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        ok = ok && isfinite(p[c]);
+        const float lo = box[c], ext = box[3 + c] - box[c];
+        float t = ext > 0.0f ? (p[c] - lo) * (1024.0f / ext) : 0.0f;
+        t = fminf(fmaxf(t, 0.0f), 1023.0f);
+        key |= spread3((uint32_t)t) << c;
+    }
+    keys[j] = ok ? key : 0xFFFFFFFFu;
+    idx[j] = (int32_t)j;
+}
+
+// Scratch of a sort of M keys: two key buffers, one index buffer, the digit
+// counts, the scan total, and a 6-float bounding box.
+struct SortScratch {
+    uint32_t *k0, *k1;
+    int32_t *tmp, *hist;
+    int64_t *total;
+    float *box;
+};
+
+SortScratch carve(char *scratch, int64_t M) {
+    const int64_t nblk = (M + kOrderTile - 1) / kOrderTile;
+    SortScratch q;
+    char *c = scratch;
+    q.k0 = reinterpret_cast<uint32_t *>(c);
+    c += align256((size_t)M * sizeof(uint32_t));
+    q.k1 = reinterpret_cast<uint32_t *>(c);
+    c += align256((size_t)M * sizeof(uint32_t));
+    q.tmp = reinterpret_cast<int32_t *>(c);
+    c += align256((size_t)M * sizeof(int32_t));
+    q.hist = reinterpret_cast<int32_t *>(c);
+    c += align256((size_t)(256 * nblk) * sizeof(int32_t));
+    q.total = reinterpret_cast<int64_t *>(c);
+    c += align256(sizeof(int64_t));
+    q.box = reinterpret_cast<float *>(c);
+    return q;
+}
+
+// Stable LSD radix sort of the (key, index) pairs in (q.k0, idx0) on the low
+// `bits` bits; the sorted indices end in perm.  idx0 is q.tmp or perm, as the
+// pass count requires (first_index_buffer).
+cudaError_t radix_sort(const SortScratch &q, int32_t *perm, int64_t M, int bits,
+                       cudaStream_t s) {
+    const int64_t nblk = (M + kOrderTile - 1) / kOrderTile;
+    const int passes = (bits + 7) / 8;
+    int32_t *ibuf[2] = {passes % 2 ? q.tmp : perm, passes % 2 ? perm : q.tmp};
+    uint32_t *kbuf[2] = {q.k0, q.k1};
+    cudaError_t e;
+    for (int p = 0; p < passes; p++) {
+        const int a = p & 1, b = a ^ 1;
+        k_radix_hist<<<(unsigned)nblk, 32, 0, s>>>(kbuf[a], M, 8 * p, q.hist, nblk);
+        if ((e = launch_pack_scan(q.hist, 256 * nblk, q.total, s)) != cudaSuccess) return e;
+        k_radix_scatter<<<(unsigned)nblk, 32, 0, s>>>(kbuf[a], ibuf[a], M, 8 * p, q.hist, nblk,
+                                                      kbuf[b], ibuf[b]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The index buffer the keys kernel fills: the last pass must leave the
+// indices in perm.
+int32_t *first_index_buffer(const SortScratch &q, int32_t *perm, int bits) {
+    return ((bits + 7) / 8) % 2 ? q.tmp : perm;
+}
+
 }  // namespace
 
 size_t direction_order_bytes(int64_t M) {
     if (M < 1) return 0;
     const int64_t nblk = (M + kOrderTile - 1) / kOrderTile;
     return 2 * align256((size_t)M * sizeof(uint32_t)) + align256((size_t)M * sizeof(int32_t)) +
-           align256((size_t)(256 * nblk) * sizeof(int32_t)) + align256(sizeof(int64_t));
+           align256((size_t)(256 * nblk) * sizeof(int32_t)) + align256(sizeof(int64_t)) +
+           align256(6 * sizeof(float));
 }
 
 cudaError_t direction_order(const cc_grid &g, int32_t *perm, char *scratch, cudaStream_t s) {
     const int64_t M = g.count;
     if (M < 1) return cudaSuccess;
-    const int64_t nblk = (M + kOrderTile - 1) / kOrderTile;
-    uint32_t *k0 = reinterpret_cast<uint32_t *>(scratch);
-    uint32_t *k1 = reinterpret_cast<uint32_t *>(scratch + align256((size_t)M * sizeof(uint32_t)));
-    int32_t *tmp = reinterpret_cast<int32_t *>(scratch + 2 * align256((size_t)M * sizeof(uint32_t)));
-    int32_t *hist = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(tmp) +
-                                                align256((size_t)M * sizeof(int32_t)));
-    int64_t *total = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(hist) +
-                                                 align256((size_t)(256 * nblk) * sizeof(int32_t)));
+    const SortScratch q = carve(scratch, M);
     const int L = order_level(M);
     const int bits = 2 * L + 4;                       // 12 faces < 16
-    const int passes = (bits + 7) / 8;
-    // the last pass must leave the indices in perm
-    int32_t *ibuf[2] = {passes % 2 ? tmp : perm, passes % 2 ? perm : tmp};
-    uint32_t *kbuf[2] = {k0, k1};
-    k_order_keys<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(g.x, g.y, g.z, M, L, kbuf[0], ibuf[0]);
+    k_order_keys<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(g.x, g.y, g.z, M, L, q.k0,
+                                                             first_index_buffer(q, perm, bits));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int p = 0; p < passes; p++) {
-        const int a = p & 1, b = a ^ 1;
-        k_radix_hist<<<(unsigned)nblk, 32, 0, s>>>(kbuf[a], M, 8 * p, hist, nblk);
-        if ((e = launch_pack_scan(hist, 256 * nblk, total, s)) != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)nblk, 32, 0, s>>>(kbuf[a], ibuf[a], M, 8 * p, hist, nblk,
-                                                      kbuf[b], ibuf[b]);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return radix_sort(q, perm, M, bits, s);
+}
+
+int direction_order_kernels(int64_t M) {   // keys, then per pass: counts, scan, scatter
+    return M < 1 ? 0 : 1 + 3 * ((2 * order_level(M) + 4 + 7) / 8);
+}
+
+int point_order_kernels(int64_t M) {       // box, keys, 4 passes
+    return M < 1 ? 0 : 2 + 3 * 4;
+}
+
+cudaError_t point_order(const float *x, const float *y, const float *z, int64_t M, int32_t *perm,
+                        char *scratch, cudaStream_t s) {
+    if (M < 1) return cudaSuccess;
+    const SortScratch q = carve(scratch, M);
+    const int bits = 30;
+    k_bbox<<<1, 1024, 0, s>>>(x, y, z, M, q.box);
+    k_morton_keys<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(x, y, z, M, q.box, q.k0,
+                                                              first_index_buffer(q, perm, bits));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return radix_sort(q, perm, M, bits, s);
 }
 
 }  // namespace cc

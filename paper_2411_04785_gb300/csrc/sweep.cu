@@ -767,7 +767,7 @@ bool short_poly(int64_t M, int d, bool kcut) {
 // launch planning
 // ---------------------------------------------------------------------------
 bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int force_d,
-                SweepPick pick, size_t rec_bytes) {
+                SweepPick pick, size_t rec_bytes, bool ordered) {
     if (pick == nullptr) pick = pick_sweep;
     if (R < 0 || M < 1 || M > INT32_MAX) return false;
     const int sms = device_sm_count();
@@ -840,8 +840,9 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
     plan->npack = R > 0 ? (R + kPackChunk - 1) / kPackChunk : 1;
     plan->off_packcnt = off;
     off = align256(off + (size_t)plan->npack * sizeof(int32_t));
-    // the directions' compact order: the single far-field sweep only
-    plan->ordered = force_d == 0 && pick == pick_sweep;
+    // the directions' compact order: the single far-field sweep (and the
+    // near-field one, which asks for it)
+    plan->ordered = force_d == 0 && (pick == pick_sweep || ordered);
     plan->off_perm = off;
     plan->off_order = off;
     if (plan->ordered) {
@@ -867,7 +868,7 @@ cudaError_t pack_for_plan(const cc_rings &rings, const SweepPlan &plan, int32_t 
     if (e != cudaSuccess) return e;
     int32_t *cnt = reinterpret_cast<int32_t *>(ws + plan.off_packcnt);
     int64_t *nkept = reinterpret_cast<int64_t *>(ws + plan.off_nkept);
-    TraceScope ts(CC_STAGE_PACK, s);
+    TraceScope ts(CC_STAGE_PACK, s, 3);   // count, scan, scatter
     const unsigned nb = (unsigned)plan.npack;
     k_pack_count<<<nb, 256, 0, s>>>(rings.ax, rings.ay, rings.az, rings.eta, rings.deta,
                                     rings.valid, rings.count, cnt);
@@ -922,7 +923,7 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
         perm = grid.order;
         if (perm == nullptr) {        // not given with the grid: computed here
             int32_t *pm = reinterpret_cast<int32_t *>(ws + plan.off_perm);
-            TraceScope ts(CC_STAGE_PACK, s);
+            TraceScope ts(CC_STAGE_PACK, s, direction_order_kernels(M));
             if ((e = direction_order(grid, pm, ws + plan.off_order, s)) != cudaSuccess) return e;
             perm = pm;
         }

@@ -32,9 +32,9 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
-TraceScope::TraceScope(int stage, cudaStream_t s) : stage_(stage), s_(s) {
+TraceScope::TraceScope(int stage, cudaStream_t s, int kernels) : stage_(stage), s_(s) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_acc[stage].launches++;
+    g_acc[stage].launches += kernels;
     if (!g_on) return;
     a_ = take_event();
     if (a_ && cudaEventRecord(a_, s_) != cudaSuccess) {

@@ -18,13 +18,19 @@
 //     h = |c|^2 = 1 - cos(theta)  (relative accuracy, also at small angles),
 // and from h on it is the far-field pair: theta from the fitted
 // acos(1 - h)/sqrt(h) polynomial (or its mirror for theta > pi/2), the
-// Gaussian on the MUFU ex2 unit.  As in the far-field sweep, each warp lists
-// a tile's rings by side: a ring whose plane through the apex, normal to the
-// axis, misses the warp's voxels' bounding sphere has every pair on one side
-// (all angles below pi/2, or all above) and skips the fold and the select.  Rings with eta > pi/2 are mirrored
-// (a -> -a, eta -> pi - eta).  The pipeline (TMA bulk tiles through a
-// 4-stage mbarrier ring, ring splits over CTAs with a fixed-order Kahan
-// reduction, block argmax) is the far-field sweep's, with 64-byte records.
+// Gaussian on the MUFU ex2 unit.  The voxels are swept in Morton order
+// (order.cu), so each warp's 256 voxels are a compact block, and as in the
+// far-field sweep each warp sorts a tile's rings by where its block's
+// bounding sphere lies from them: every voxel within 30 deg of pi/2 from the
+// axis, the equatorial form (cos(theta) from the dot product and the
+// approximate rsqrt, theta = pi/2 + asin by an odd polynomial: no Newton
+// step, no square root, no fold, no select); every voxel within 78.46 deg of
+// the axis or of its opposite, the one-sided form (no fold, no select, a
+// shorter polynomial); the rest, the general form.  Rings with eta > pi/2
+// are mirrored (a -> -a, eta -> pi - eta).  The pipeline (TMA bulk tiles
+// through a 4-stage mbarrier ring, ring splits over CTAs with a fixed-order
+// Kahan reduction, block argmax) is the far-field sweep's, with 64-byte
+// records.
 //
 // Image universes (Sec. 3, spatial optimisation): the n^3 voxels of a cube,
 // or those whose centres lie in the inscribed cylinder (axis z) or sphere,
@@ -44,6 +50,10 @@ constexpr float kNullB = 1.0e4f;
 constexpr float kEquAngle = 0.52359878f;   // pi / 6: the equatorial form's band
 constexpr float kEquSin = 0.49913372f;     // sin(kEquAngle - 1e-3)
 constexpr float kEquCos = 0.86652497f;     // cos(kEquAngle - 1e-3)
+// one-sided forms: every pair within acos(0.2) = 78.46 deg of the axis or of
+// its opposite (s <= 0.8, the short polynomial's range); T = that - 1e-3
+constexpr float kSideCos = 0.20097970f;    // cos(T)
+constexpr float kSideSin = 0.97959541f;    // sin(T)
 
 struct NearRec {   // 64 bytes; values met by a voxel pair are duplicated
     float mpx, mpx_, mpy, mpy_, mpz, mpz_;   // -p
@@ -250,10 +260,12 @@ struct NearSmem {
     int abort_flag;
 };
 
-// The pair terms of one ring for DP voxel pairs.  SIDE 1: every pair lies on
-// the ring's near side (h <= 1), SIDE 2: on its far side; the fold and the
-// select then have one outcome, and the result is the general form's
-// (SIDE 0) bit for bit.
+// The pair terms of one ring for DP voxel pairs.  SIDE 1: every pair lies
+// within acos(0.2) = 78.46 deg of the axis (h <= 0.8), SIDE 2: of its opposite
+// (2 - h <= 0.8); the fold and the select then have one outcome, and the
+// acos polynomial is the degree-5 fit on [0, 0.8] (fit_acos.py: 2.6e-7 rad
+// evaluated in FP32, as accurate as the general form's degree 7 on [0, 1]:
+// 2.3e-7).  SIDE 5: the equatorial form (below).
 template <int DP, bool KCUT, int SIDE>
 __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2)[DP],
                                            const float2 (&py2)[DP], const float2 (&pz2)[DP],
@@ -335,14 +347,24 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
             sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
                            : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
         }
-        float2 p = pair(1.4414361e-03f);                     // acos_q
-        p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
-        p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
-        p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
-        p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
-        p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
-        p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
-        p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+        float2 p;
+        if (SIDE == 0) {                                     // acos_q on [0, 1], degree 7
+            p = pair(1.4414361e-03f);
+            p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
+            p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
+            p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
+            p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
+            p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
+            p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
+            p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+        } else {                                             // on [0, 0.8], degree 5
+            p = pair(3.31251509e-03f);
+            p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
+            p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
+            p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
+            p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
+            p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+        }
         const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
         const float2 th = __fmul2_rn(rt, p);
         const float2 nbs = SIDE == 1   ? make_float2(R3.z, R3.z)
@@ -376,7 +398,8 @@ template <int D, bool KCUT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
               int64_t ndb, const float *__restrict__ vx, const float *__restrict__ vy,
-              const float *__restrict__ vz, int64_t V, float kc2, float *__restrict__ out,
+              const float *__restrict__ vz, const int32_t *__restrict__ perm, int64_t V,
+              float kc2, float *__restrict__ out,
               BlockBest *__restrict__ bb, int32_t *__restrict__ status) {
     static_assert(D % 2 == 0, "voxels are processed in FP32x2 pairs");
     constexpr int DP = D / 2;
@@ -393,6 +416,10 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
         int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
         ja = ja < V ? ja : V - 1;
         jb = jb < V ? jb : V - 1;
+        if (perm != nullptr) {
+            ja = __ldg(perm + ja);
+            jb = __ldg(perm + jb);
+        }
         px2[q] = make_float2(__ldg(vx + ja), __ldg(vx + jb));
         py2[q] = make_float2(__ldg(vy + ja), __ldg(vy + jb));
         pz2[q] = make_float2(__ldg(vz + ja), __ldg(vz + jb));
@@ -456,15 +483,16 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             S.abort_flag = 1;
         } else {
             const NearRec *T = S.tile[stage];
-            // the tile's rings by side against the warp's sphere: the plane
-            // through the apex normal to the axis does not cut the sphere
-            // when |a . (centre - apex)| > radius (+ 1e-3 of the distance);
-            // equatorial when every voxel of the sphere lies within
-            // kEquAngle - 1e-3 of pi/2 from the axis: with alpha the angle
-            // of the centre and beta = asin(radius / distance) the sphere's
-            // half angle from the apex, |cos(alpha)| <= sin(kEquAngle - 1e-3
-            // - beta), i.e. |a . (centre - apex)| <= sin(A) sqrt(dist^2 -
-            // radius^2) - cos(A) radius, A = kEquAngle - 1e-3
+            // the tile's rings by class against the warp's sphere (centre C,
+            // radius rad): alpha = angle(a, C - apex), beta = asin(rad /
+            // dist) the sphere's half angle from the apex, so every voxel of
+            // the sphere lies between alpha - beta and alpha + beta from the
+            // axis.  Equatorial when |alpha - pi/2| <= A - beta, A =
+            // kEquAngle - 1e-3: |a . (C - apex)| <= sin(A) sqrt(dist^2 -
+            // rad^2) - cos(A) rad.  Near side (far side) when alpha + beta
+            // <= T (pi - alpha + beta <= T), T = acos(0.2) - 1e-3:
+            // +-a . (C - apex) >= cos(T) sqrt(dist^2 - rad^2) + sin(T) rad,
+            // with beta <= T.  The rest take the general form.
             unsigned em[kTile / 32], nm[kTile / 32], fm[kTile / 32];
             int ne = 0, nn = 0, nf = 0;
 #pragma unroll
@@ -474,16 +502,16 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
                 // a = -sqrt(2) ms
                 const float sa = -1.41421356f * fmaf(Rg.msz, ez, fmaf(Rg.msy, ey, Rg.msx * ex));
                 const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                const float dist = sqrtf(d2);
-                const float lim = brad + 1.0e-3f * dist;
-                const float elim = d2 > brad * brad
-                                       ? fmaf(kEquSin, sqrtf(d2 - brad * brad), -kEquCos * brad)
-                                       : -1.0f;
+                const float r2 = brad * brad;
+                const float cb = d2 > r2 ? sqrtf(d2 - r2) : 0.0f;     // dist cos(beta)
+                const float elim = d2 > r2 ? fmaf(kEquSin, cb, -kEquCos * brad) : -1.0f;
+                const float lim = r2 < kSideSin * kSideSin * d2 ? fmaf(kSideCos, cb, kSideSin * brad)
+                                                                : __builtin_huge_valf();
                 const bool live = Rg.k != 0.0f;
                 const bool eq = live && fabsf(sa) <= elim;
                 em[g] = __ballot_sync(0xffffffffu, eq);
-                nm[g] = __ballot_sync(0xffffffffu, live && !eq && sa > lim);
-                fm[g] = __ballot_sync(0xffffffffu, live && !eq && sa < -lim);
+                nm[g] = __ballot_sync(0xffffffffu, live && !eq && sa >= lim);
+                fm[g] = __ballot_sync(0xffffffffu, live && !eq && -sa >= lim);
                 ne += __popc(em[g]);
                 nn += __popc(nm[g]);
                 nf += __popc(fm[g]);
@@ -535,15 +563,21 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
     int bj = INT32_MAX;
 #pragma unroll
     for (int q = 0; q < DP; q++) {
-        const int64_t ja = j0 + (int64_t)(64 * q), jb = ja + 32;
+        const int64_t ka = j0 + (int64_t)(64 * q), kb = ka + 32;
         const float va = sum[q].x - comp[q].x, vb = sum[q].y - comp[q].y;
-        if (ja < V && CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + ja, nsplit * V)) {
-            out[split * V + ja] = va;
-            better(bv, bj, va, (int)ja);
+        if (ka < V) {
+            const int64_t ja = perm != nullptr ? (int64_t)__ldg(perm + ka) : ka;
+            if (CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + ja, nsplit * V)) {
+                out[split * V + ja] = va;
+                better(bv, bj, va, (int)ja);
+            }
         }
-        if (jb < V && CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + jb, nsplit * V)) {
-            out[split * V + jb] = vb;
-            better(bv, bj, vb, (int)jb);
+        if (kb < V) {
+            const int64_t jb = perm != nullptr ? (int64_t)__ldg(perm + kb) : kb;
+            if (CC_IN_BOUNDS(CC_SITE_VOXEL_OUT, split * V + jb, nsplit * V)) {
+                out[split * V + jb] = vb;
+                better(bv, bj, vb, (int)jb);
+            }
         }
     }
     if (bb != nullptr) {
@@ -568,7 +602,7 @@ void *pick_bp(int d, bool kcut) {
 }  // namespace
 
 bool plan_backproject(int64_t R, int64_t V, const cc_params &p, SweepPlan *plan) {
-    return plan_sweep(R, V, p, plan, 0, pick_bp, sizeof(NearRec));
+    return plan_sweep(R, V, p, plan, 0, pick_bp, sizeof(NearRec), true);
 }
 
 int64_t universe_count(int shape, int n) {
@@ -612,7 +646,7 @@ cudaError_t launch_backproject(const cc_rings &rings, const float *px, const flo
     NearRings g{rings.ax, rings.ay, rings.az, rings.eta, rings.deta, px, py, pz, rings.valid,
                 rings.count};
     {
-        TraceScope ts(CC_STAGE_PACK, s);
+        TraceScope ts(CC_STAGE_PACK, s, 3);   // count, scan, scatter
         k_near_count<<<(unsigned)plan.npack, 256, 0, s>>>(g, cnt);
         if ((e = launch_pack_scan(cnt, plan.npack, nkept, s)) != cudaSuccess) return e;
         k_near_scatter<<<(unsigned)plan.npack, 256, 0, s>>>(g, cnt, nkept, rec);
@@ -628,9 +662,18 @@ cudaError_t launch_backproject(const cc_rings &rings, const float *px, const flo
     void *fn = pick_bp(plan.d, kcut);
     const NearRec *crec = rec;
     const int64_t *cnk = nkept;
+    const int32_t *perm = nullptr;
+    if (plan.ordered) {             // the voxels in Morton order (order.cu)
+        int32_t *pm = reinterpret_cast<int32_t *>(ws + plan.off_perm);
+        TraceScope ts(CC_STAGE_PACK, s, point_order_kernels(V));
+        if ((e = point_order(vox.x, vox.y, vox.z, V, pm, ws + plan.off_order, s)) != cudaSuccess)
+            return e;
+        perm = pm;
+    }
     void *args[] = {(void *)&crec,  (void *)&cnk,   (void *)&plan.nsplit, (void *)&plan.ndb,
-                    (void *)&vox.x, (void *)&vox.y, (void *)&vox.z,       (void *)&V,
-                    (void *)&kc2,   (void *)&out,   (void *)&bbk,         (void *)&st};
+                    (void *)&vox.x, (void *)&vox.y, (void *)&vox.z,       (void *)&perm,
+                    (void *)&V,     (void *)&kc2,   (void *)&out,         (void *)&bbk,
+                    (void *)&st};
     {
         TraceScope ts(CC_STAGE_VOXEL, s);
         e = cudaLaunchKernel(fn, dim3(ctas), dim3(kThreads), args, 0, s);

@@ -129,6 +129,31 @@ def test_image_matches_oracle(cc, shape, R, kcut):
     assert img[j] == img.max() and (img[:j] < img[j]).all()
 
 
+def test_voxels_in_any_order_give_the_same_image(cc):
+    """The sweep takes the voxels in their Morton order, found from the
+    coordinates, so a shuffled voxel list (positions all distinct) gives the
+    same image, permuted, bit for bit; and it satisfies the parity rule."""
+    rng = np.random.default_rng(31)
+    S = np.array([1.3, -0.7, 20.2])
+    rings, apex = near_rings(rng, 3000, S, deta_deg=(0.5, 20.0))
+    vnp = tuple(v.astype(np.float32) for v in oracle.universe("sphere", 24, 0.8, (0.0, 0.0, 20.0)))
+    V = vnp[0].size
+    sh = rng.permutation(V)
+    rd = rings_dev(rings)
+    ap = tuple(dev(apex[:, c]) for c in range(3))
+    img, am, st = cc.backproject(rd, ap, tuple(dev(v) for v in vnp))
+    img_s, am_s, st_s = cc.backproject(rd, ap, tuple(dev(v[sh]) for v in vnp))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(st_s.item()) == 0
+    img, img_s = img.cpu().numpy(), img_s.cpu().numpy()
+    np.testing.assert_array_equal(img_s, img[sh])
+    j = int(am_s.item())                    # the first maximum of the shuffled list
+    assert img_s[j] == img_s.max() and (img_s[:j] < img_s[j]).all()
+    idx = np.arange(0, V, 5)
+    want = oracle.backproject(rings, apex, vnp, idx=idx)
+    check_image(img[idx], want, fp32_bound(rings, apex, vnp, idx))
+
+
 def test_planted_source_voxel_and_invalid_rings(cc):
     rng = np.random.default_rng(4)
     n, pitch = 32, 0.5
