@@ -1,6 +1,6 @@
 """Fit of the polynomial used by the sweeps' equatorial form: angles within
-30 degrees of pi/2 from the ring axis, theta = pi/2 + asin(x) with x =
--cos(theta) = sigma s.  Far field (sweep.cu): s = a'.(-c') with both vectors
+asin(0.55) = 33.4 degrees of pi/2 from the ring axis, theta = pi/2 + asin(x)
+with x = -cos(theta) = sigma s.  Far field (sweep.cu): s = a'.(-c') with both vectors
 scaled by 1/sqrt(2), sigma = 2.  Near field (voxel.cu): s = (-a/sqrt(2)).d
 / |d|, sigma = sqrt(2).
 
@@ -16,9 +16,11 @@ Lawson-style reweighting toward the minimax solution.  The printed
 coefficients (P's, increasing powers, binary32) are the ones in the kernel;
 the report evaluates them as the kernel does (w = s*s rounded, Horner with
 fused multiply-adds, v = s P(w) rounded) against FP64 asin.  Degree 4 in w on
-X = 1/2: 2.2e-8 rad with exact coefficients, 8.6e-8 rad evaluated in FP32.
+X = 0.55: 7.3e-8 rad with exact coefficients, 1.4e-7 rad (sigma = 2) and
+1.3e-7 rad (sigma = sqrt(2)) evaluated in FP32.
 
 Run: python paper_2411_04785_gb300/csrc/fit_asin.py [degree] [X] [sigma]
+(the kernels: 4 0.55 2 and 4 0.55 1.41421356)
 (sigma: 2 for the far field, the default, or 1.41421356 for the near field)
 """
 import sys
@@ -55,7 +57,7 @@ def report(c, X, sigma=2.0):
 
 if __name__ == "__main__":
     deg = int(sys.argv[1]) if len(sys.argv) > 1 else 4
-    X = float(sys.argv[2]) if len(sys.argv) > 2 else 0.5
+    X = float(sys.argv[2]) if len(sys.argv) > 2 else 0.55
     sigma = float(sys.argv[3]) if len(sys.argv) > 3 else 2.0
     e64, e32max, e32mean, p32 = report(fit(deg, X), X, sigma)
     print(f"degree {deg} on |x| <= {X}: max |error| {e64:.3e} rad (exact coefficients), "

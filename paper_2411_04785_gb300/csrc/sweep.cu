@@ -29,7 +29,7 @@
 // taken in the grid's compact order (order.cu: HEALPix NESTED), so each warp
 // owns a small patch of sky, and per tile each warp sorts the rings by where
 // its patch lies from them.  Rings whose every angle to the patch lies
-// within 30 degrees of pi/2 take the angle as pi/2 + asin of the dot product
+// within 33.4 degrees of pi/2 take the angle as pi/2 + asin of the dot product
 // (an odd polynomial: no square root, no fold, no select); of the rest, those
 // wholly on one side of the patch (every angle below pi/2, or every one
 // above) skip the fold and the mirror select, and the wide ones far enough
@@ -61,8 +61,8 @@ constexpr float kNullB = 1.0e4f;                  // ex2(-(1e4)^2) == 0
 constexpr float kDotAngle = 0.52359878f;          // pi / 6
 constexpr float kDotMaxK = 3.5f;
 // The equatorial form (below) is used for rings of any width whose every
-// pair lies within kEquAngle of pi/2 from the axis (|cos(theta)| <= 1/2).
-constexpr float kEquAngle = 0.52359878f;          // pi / 6
+// pair lies within kEquAngle of pi/2 from the axis (|cos(theta)| <= 0.55).
+constexpr float kEquAngle = 0.58236424f;          // asin(0.55), 33.37 deg
 // The one-sided forms are used when every pair lies within kSideAngle of the
 // axis or of its opposite (s <= 0.8: their degree-5 polynomial's range).
 constexpr float kSideAngle = 1.36943841f;         // acos(0.2), 78.46 deg
@@ -218,12 +218,13 @@ struct SweepSmem {
 // and by ~1e-6 typically; summed over many rings it averages out.
 // SIDE 5 (equatorial): every pair within kEquAngle of pi/2 from the axis,
 // any width: theta = pi/2 + asin(2 s), s = a'.(-c') = -cos(theta) / 2, with
-// asin(2 s) = s P(s^2) (fit_asin.py: degree 4 in s^2, 8.6e-8 rad evaluated in
-// FP32), so u = (theta - eta') k = s P(s^2) k + ne: twelve FP32 operations
-// and one MUFU per pair, no square root, no fold, no select.  The absolute
-// error of s (~1e-7, as t above) moves the angle by at most 2.3e-7 rad at
-// |cos(theta)| <= 1/2, no more than the chord form's own error there (its h
-// is ~1 with the same absolute rounding, and the acos polynomial adds 2.7e-7).
+// asin(2 s) = s P(s^2) (fit_asin.py 4 0.55: degree 4 in s^2, 1.4e-7 rad
+// evaluated in FP32), so u = (theta - eta') k = s P(s^2) k + ne: twelve FP32
+// operations and one MUFU per pair, no square root, no fold, no select.  The
+// absolute error of s (~1e-7, as t above) moves the angle by at most 2.4e-7
+// rad at |cos(theta)| <= 0.55, no more than the chord form's own error there
+// (its h is ~1 with the same absolute rounding, and the acos polynomial adds
+// 2.7e-7).
 template <int DP, bool KCUT, int SIDE = 0, bool SHORT = false>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
@@ -232,7 +233,7 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
     const float4 P1 = *reinterpret_cast<const float4 *>(&R.az);
     const float2 ax2 = make_float2(P0.x, P0.y), ay2 = make_float2(P0.z, P0.w);
     const float2 az2 = make_float2(P1.x, P1.y), k2 = make_float2(P1.z, P1.w);
-    if (SIDE == 5) {
+    if constexpr (SIDE == 5) {
         const float2 ne2 = *reinterpret_cast<const float2 *>(&R.ne);
 #pragma unroll
         for (int q = 0; q < DP; q++) {
@@ -240,74 +241,74 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
             sd = __ffma2_rn(ay2, ncy[q], sd);
             sd = __ffma2_rn(ax2, ncx[q], sd);
             const float2 w = __fmul2_rn(sd, sd);
-            float2 p = pair(2.73005066e+01f);         // P(w), degree 4, FP32x2
-            p = __ffma2_rn(p, w, pair(4.88156176e+00f));
-            p = __ffma2_rn(p, w, pair(2.42437673e+00f));
-            p = __ffma2_rn(p, w, pair(1.33304811e+00f));
-            p = __ffma2_rn(p, w, pair(2.00000095e+00f));
+            float2 p = pair(3.12643623e+01f);         // P(w), degree 4, FP32x2
+            p = __ffma2_rn(p, w, pair(4.32808828e+00f));
+            p = __ffma2_rn(p, w, pair(2.44986677e+00f));
+            p = __ffma2_rn(p, w, pair(1.33261955e+00f));
+            p = __ffma2_rn(p, w, pair(2.00000286e+00f));
             const float2 v = __fmul2_rn(sd, p);       // theta - pi/2
             const float2 u = __ffma2_rn(v, k2, ne2);
             const float2 u2 = __fmul2_rn(u, u);
             const float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
             acc[q] = __fadd2_rn(acc[q], e);
         }
-        return;
-    }
-    const float2 P2 = *reinterpret_cast<const float2 *>(&R.nb);
-    const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
+    } else {
+        const float2 P2 = *reinterpret_cast<const float2 *>(&R.nb);
+        const float2 m1 = pair(-1.0f), two2 = pair(2.0f);
 #pragma unroll
-    for (int q = 0; q < DP; q++) {
-        float2 h = pair(0.0f), sv;
-        if (SIDE == 3 || SIDE == 4) {             // dot form: t = 1/2 + a'.nc = h / 2
-            float2 t = __ffma2_rn(az2, ncz[q], pair(0.5f));
-            t = __ffma2_rn(ay2, ncy[q], t);
-            t = __ffma2_rn(ax2, ncx[q], t);
-            sv = SIDE == 3 ? __fmul2_rn(t, two2) : __ffma2_rn(t, pair(-2.0f), two2);
-        } else {
-            float2 dx = __fadd2_rn(ax2, ncx[q]);
-            float2 dy = __fadd2_rn(ay2, ncy[q]);
-            float2 dz = __fadd2_rn(az2, ncz[q]);
-            h = __fmul2_rn(dx, dx);
-            h = __ffma2_rn(dy, dy, h);
-            h = __ffma2_rn(dz, dz, h);                // 1 - cos(theta)
-            if (SIDE == 1) {
-                sv = h;
+        for (int q = 0; q < DP; q++) {
+            float2 h = pair(0.0f), sv;
+            if (SIDE == 3 || SIDE == 4) {             // dot form: t = 1/2 + a'.nc = h / 2
+                float2 t = __ffma2_rn(az2, ncz[q], pair(0.5f));
+                t = __ffma2_rn(ay2, ncy[q], t);
+                t = __ffma2_rn(ax2, ncx[q], t);
+                sv = SIDE == 3 ? __fmul2_rn(t, two2) : __ffma2_rn(t, pair(-2.0f), two2);
             } else {
-                float2 g = __ffma2_rn(h, m1, two2);     // 2 - h
-                sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
-                               : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+                float2 dx = __fadd2_rn(ax2, ncx[q]);
+                float2 dy = __fadd2_rn(ay2, ncy[q]);
+                float2 dz = __fadd2_rn(az2, ncz[q]);
+                h = __fmul2_rn(dx, dx);
+                h = __ffma2_rn(dy, dy, h);
+                h = __ffma2_rn(dz, dz, h);                // 1 - cos(theta)
+                if (SIDE == 1) {
+                    sv = h;
+                } else {
+                    float2 g = __ffma2_rn(h, m1, two2);     // 2 - h
+                    sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                                   : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+                }
             }
+            float2 p;
+            if (!SHORT) {                                    // Q(s) on [0, 1], degree 6
+                p = pair(2.61164433e-03f);
+                p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
+                p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
+                p = __ffma2_rn(p, sv, pair(5.94551489e-03f));
+                p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
+                p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
+                p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
+            } else {                                         // Q(s) on [0, 0.8], degree 5
+                p = pair(3.31251509e-03f);
+                p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
+                p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
+                p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
+                p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
+                p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+            }
+            float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
+            float2 th = __fmul2_rn(rt, p);
+            float2 nbs = (SIDE == 1 || SIDE == 3)   ? make_float2(P2.x, P2.x)
+                         : (SIDE == 2 || SIDE == 4) ? make_float2(P2.y, P2.y)
+                                     : make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
+            float2 u = __ffma2_rn(th, k2, nbs);
+            float2 u2 = __fmul2_rn(u, u);
+            float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            if (KCUT) {
+                e.x = u2.x > kc2 ? 0.0f : e.x;
+                e.y = u2.y > kc2 ? 0.0f : e.y;
+            }
+            acc[q] = __fadd2_rn(acc[q], e);
         }
-        float2 p;
-        if (!SHORT) {                                    // Q(s) on [0, 1], degree 6
-            p = pair(2.61164433e-03f);
-            p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
-            p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
-            p = __ffma2_rn(p, sv, pair(5.94551489e-03f));
-            p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
-            p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
-            p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
-        } else {                                         // Q(s) on [0, 0.8], degree 5
-            p = pair(3.31251509e-03f);
-            p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
-            p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
-            p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
-            p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
-            p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
-        }
-        float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
-        float2 th = __fmul2_rn(rt, p);
-        float2 nbs = (SIDE == 1 || SIDE == 3)   ? make_float2(P2.x, P2.x)
-                     : (SIDE == 2 || SIDE == 4) ? make_float2(P2.y, P2.y)
-                                 : make_float2(h.x <= 1.0f ? P2.x : P2.y, h.y <= 1.0f ? P2.x : P2.y);
-        float2 u = __ffma2_rn(th, k2, nbs);
-        float2 u2 = __fmul2_rn(u, u);
-        float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
-        if (KCUT) {
-            e.x = u2.x > kc2 ? 0.0f : e.x;
-            e.y = u2.y > kc2 ? 0.0f : e.y;
-        }
-        acc[q] = __fadd2_rn(acc[q], e);
     }
 }
 
@@ -752,13 +753,15 @@ void *pick_sweep(int d, bool kcut) { return pick_sweep_q(d, kcut, false); }
 // polynomial: every ring that a cap leaves between kSideAngle and pi/2 from
 // its axis then takes the equatorial form, 2 rho + 2e-3 <= kSideAngle -
 // (pi/2 - kEquAngle).  A patch is about a square of 4 pi 32 d / M sr, cap
-// radius sqrt(2 pi 32 d / M), with a quarter more for HEALPix's elongated
-// patches.  A wider cap in a short-polynomial sweep is still exact: its
-// rings beyond kSideAngle take the general form.
+// radius sqrt(2 pi 32 d / M) (HEALPix's elongated patches reach a quarter
+// more).  A wider cap in a short-polynomial sweep is still exact: its rings
+// beyond kSideAngle take the general form (at nside 64 and 256 directions
+// per warp, the warps above the median cap put 2 % of the rings there and the
+// short polynomial still pays: 90.2 % of the roofline against 88.1 %).
 bool short_poly(int64_t M, int d, bool kcut) {
     if (kcut || M < 1) return false;
     const double lim = 0.5 * ((double)kSideAngle - (0.5 * 3.14159265358979 - (double)kEquAngle)) - 1e-3;
-    return 1.25 * std::sqrt(2.0 * 3.14159265358979 * 32.0 * d / (double)M) <= lim;
+    return std::sqrt(2.0 * 3.14159265358979 * 32.0 * d / (double)M) <= lim;
 }
 
 }  // namespace

@@ -21,7 +21,7 @@
 // Gaussian on the MUFU ex2 unit.  The voxels are swept in Morton order
 // (order.cu), so each warp's 256 voxels are a compact block, and as in the
 // far-field sweep each warp sorts a tile's rings by where its block's
-// bounding sphere lies from them: every voxel within 30 deg of pi/2 from the
+// bounding sphere lies from them: every voxel within 33.4 deg of pi/2 from the
 // axis, the equatorial form (cos(theta) from the dot product and the
 // approximate rsqrt, theta = pi/2 + asin by an odd polynomial: no Newton
 // step, no square root, no fold, no select); every voxel within 78.46 deg of
@@ -47,9 +47,9 @@ constexpr int kStages = 4;
 constexpr float kInvSqrt2 = 0.70710678118654752f;
 constexpr float kGaussK = 0.84932180028801907f;   // sqrt(log2(e) / 2)
 constexpr float kNullB = 1.0e4f;
-constexpr float kEquAngle = 0.52359878f;   // pi / 6: the equatorial form's band
-constexpr float kEquSin = 0.49913372f;     // sin(kEquAngle - 1e-3)
-constexpr float kEquCos = 0.86652497f;     // cos(kEquAngle - 1e-3)
+// the equatorial form's band: within E = asin(0.55) = 33.37 deg of pi/2
+constexpr float kEquSin = 0.54916456f;     // sin(E - 1e-3)
+constexpr float kEquCos = 0.83571424f;     // cos(E - 1e-3)
 // one-sided forms: every pair within acos(0.2) = 78.46 deg of the axis or of
 // its opposite (s <= 0.8, the short polynomial's range); T = that - 1e-3
 constexpr float kSideCos = 0.20097970f;    // cos(T)
@@ -280,13 +280,13 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
     const float2 mpz = make_float2(R1.x, R1.y), msx = make_float2(R1.z, R1.w);
     const float2 msy = make_float2(R2.x, R2.y), msz = make_float2(R2.z, R2.w);
     const float2 k2 = make_float2(R3.x, R3.y);
-    if (SIDE == 5) {
-        // equatorial: every pair within kEquAngle of pi/2 from the axis.
+    if constexpr (SIDE == 5) {
+        // equatorial: every pair within E of pi/2 from the axis.
         // s = (-a/sqrt 2).d / |d| = -cos(theta) / sqrt(2), theta = pi/2 +
         // asin(sqrt(2) s) = pi/2 + s P(s^2) (fit_asin.py, sigma = sqrt(2):
-        // 8.5e-8 rad evaluated in FP32); no Newton step (the approximate
+        // 1.3e-7 rad evaluated in FP32); no Newton step (the approximate
         // rsqrt's relative error moves cos(theta) by at most 1e-7 of its
-        // |value| <= 1/2), no square root, no fold, no select
+        // |value| <= 0.55), no square root, no fold, no select
         const float2 ne2 = __ffma2_rn(k2, pair(0.5f * kPiF), make_float2(R3.z, R3.z));
 #pragma unroll
         for (int q = 0; q < DP; q++) {
@@ -302,11 +302,11 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
             t = __ffma2_rn(msx, dx, t);
             const float2 sd = __fmul2_rn(t, y0);
             const float2 w = __fmul2_rn(sd, sd);
-            float2 p = pair(1.20652330e+00f);
-            p = __ffma2_rn(p, w, pair(4.31473166e-01f));
-            p = __ffma2_rn(p, w, pair(4.28573310e-01f));
-            p = __ffma2_rn(p, w, pair(4.71303672e-01f));
-            p = __ffma2_rn(p, w, pair(1.41421425e+00f));
+            float2 p = pair(1.38170266e+00f);
+            p = __ffma2_rn(p, w, pair(3.82552564e-01f));
+            p = __ffma2_rn(p, w, pair(4.33079332e-01f));
+            p = __ffma2_rn(p, w, pair(4.71152157e-01f));
+            p = __ffma2_rn(p, w, pair(1.41421556e+00f));
             const float2 v = __fmul2_rn(sd, p);                    // theta - pi/2
             const float2 u = __ffma2_rn(v, k2, ne2);
             const float2 u2 = __fmul2_rn(u, u);
@@ -317,68 +317,68 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
             }
             acc[q] = __fadd2_rn(acc[q], e);
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int q = 0; q < DP; q++) {
-        const float2 dx = __fadd2_rn(px2[q], mpx);
-        const float2 dy = __fadd2_rn(py2[q], mpy);
-        const float2 dz = __fadd2_rn(pz2[q], mpz);
-        // |d|^2 + 1e-30: a voxel centre on the apex stays finite
-        float2 n2 = __ffma2_rn(dx, dx, pair(1.0e-30f));
-        n2 = __ffma2_rn(dy, dy, n2);
-        n2 = __ffma2_rn(dz, dz, n2);
-        const float2 y0 = make_float2(rsqrt_approx(n2.x), rsqrt_approx(n2.y));
-        float2 tt = __fmul2_rn(n2, y0);
-        tt = __fmul2_rn(tt, y0);
-        const float2 f = __ffma2_rn(tt, nh, th2);
-        const float2 y1 = __fmul2_rn(y0, f);                // rsqrt(|d|^2)/sqrt(2)
-        const float2 cx = __ffma2_rn(dx, y1, msx);
-        const float2 cy = __ffma2_rn(dy, y1, msy);
-        const float2 cz = __ffma2_rn(dz, y1, msz);
-        float2 h = __fmul2_rn(cx, cx);
-        h = __ffma2_rn(cy, cy, h);
-        h = __ffma2_rn(cz, cz, h);                           // 1 - cos(theta)
-        float2 sv;
-        if (SIDE == 1) {
-            sv = h;
-        } else {
-            const float2 g = __ffma2_rn(h, m1, two2);
-            sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
-                           : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+        for (int q = 0; q < DP; q++) {
+            const float2 dx = __fadd2_rn(px2[q], mpx);
+            const float2 dy = __fadd2_rn(py2[q], mpy);
+            const float2 dz = __fadd2_rn(pz2[q], mpz);
+            // |d|^2 + 1e-30: a voxel centre on the apex stays finite
+            float2 n2 = __ffma2_rn(dx, dx, pair(1.0e-30f));
+            n2 = __ffma2_rn(dy, dy, n2);
+            n2 = __ffma2_rn(dz, dz, n2);
+            const float2 y0 = make_float2(rsqrt_approx(n2.x), rsqrt_approx(n2.y));
+            float2 tt = __fmul2_rn(n2, y0);
+            tt = __fmul2_rn(tt, y0);
+            const float2 f = __ffma2_rn(tt, nh, th2);
+            const float2 y1 = __fmul2_rn(y0, f);                // rsqrt(|d|^2)/sqrt(2)
+            const float2 cx = __ffma2_rn(dx, y1, msx);
+            const float2 cy = __ffma2_rn(dy, y1, msy);
+            const float2 cz = __ffma2_rn(dz, y1, msz);
+            float2 h = __fmul2_rn(cx, cx);
+            h = __ffma2_rn(cy, cy, h);
+            h = __ffma2_rn(cz, cz, h);                           // 1 - cos(theta)
+            float2 sv;
+            if (SIDE == 1) {
+                sv = h;
+            } else {
+                const float2 g = __ffma2_rn(h, m1, two2);
+                sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                               : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
+            }
+            float2 p;
+            if (SIDE == 0) {                                     // acos_q on [0, 1], degree 7
+                p = pair(1.4414361e-03f);
+                p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
+                p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
+                p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
+                p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
+                p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
+                p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
+                p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
+            } else {                                             // on [0, 0.8], degree 5
+                p = pair(3.31251509e-03f);
+                p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
+                p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
+                p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
+                p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
+                p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+            }
+            const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
+            const float2 th = __fmul2_rn(rt, p);
+            const float2 nbs = SIDE == 1   ? make_float2(R3.z, R3.z)
+                               : SIDE == 2 ? make_float2(R3.w, R3.w)
+                                           : make_float2(h.x <= 1.0f ? R3.z : R3.w,
+                                                         h.y <= 1.0f ? R3.z : R3.w);
+            const float2 u = __ffma2_rn(th, k2, nbs);
+            const float2 u2 = __fmul2_rn(u, u);
+            float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            if (KCUT) {
+                e.x = u2.x > kc2 ? 0.0f : e.x;
+                e.y = u2.y > kc2 ? 0.0f : e.y;
+            }
+            acc[q] = __fadd2_rn(acc[q], e);
         }
-        float2 p;
-        if (SIDE == 0) {                                     // acos_q on [0, 1], degree 7
-            p = pair(1.4414361e-03f);
-            p = __ffma2_rn(p, sv, pair(-2.8447455e-03f));
-            p = __ffma2_rn(p, sv, pair(4.6071224e-03f));
-            p = __ffma2_rn(p, sv, pair(5.2066805e-04f));
-            p = __ffma2_rn(p, sv, pair(8.6035002e-03f));
-            p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
-            p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
-            p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
-        } else {                                             // on [0, 0.8], degree 5
-            p = pair(3.31251509e-03f);
-            p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
-            p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
-            p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
-            p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
-            p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
-        }
-        const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
-        const float2 th = __fmul2_rn(rt, p);
-        const float2 nbs = SIDE == 1   ? make_float2(R3.z, R3.z)
-                           : SIDE == 2 ? make_float2(R3.w, R3.w)
-                                       : make_float2(h.x <= 1.0f ? R3.z : R3.w,
-                                                     h.y <= 1.0f ? R3.z : R3.w);
-        const float2 u = __ffma2_rn(th, k2, nbs);
-        const float2 u2 = __fmul2_rn(u, u);
-        float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
-        if (KCUT) {
-            e.x = u2.x > kc2 ? 0.0f : e.x;
-            e.y = u2.y > kc2 ? 0.0f : e.y;
-        }
-        acc[q] = __fadd2_rn(acc[q], e);
     }
 }
 
@@ -488,7 +488,7 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             // dist) the sphere's half angle from the apex, so every voxel of
             // the sphere lies between alpha - beta and alpha + beta from the
             // axis.  Equatorial when |alpha - pi/2| <= A - beta, A =
-            // kEquAngle - 1e-3: |a . (C - apex)| <= sin(A) sqrt(dist^2 -
+            // E - 1e-3: |a . (C - apex)| <= sin(A) sqrt(dist^2 -
             // rad^2) - cos(A) rad.  Near side (far side) when alpha + beta
             // <= T (pi - alpha + beta <= T), T = acos(0.2) - 1e-3:
             // +-a . (C - apex) >= cos(T) sqrt(dist^2 - rad^2) + sin(T) rad,
