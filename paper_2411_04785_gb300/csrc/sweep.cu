@@ -63,9 +63,11 @@ constexpr float kDotMaxK = 3.5f;
 // The equatorial form (below) is used for rings of any width whose every
 // pair lies within kEquAngle of pi/2 from the axis (|cos(theta)| <= 0.55).
 constexpr float kEquAngle = 0.58236424f;          // asin(0.55), 33.37 deg
-// The one-sided forms are used when every pair lies within kSideAngle of the
-// axis or of its opposite (s <= 0.8: their degree-5 polynomial's range).
+// With the short polynomials the one-sided forms are used when every pair
+// lies within kSideAngle of the axis or of its opposite (s <= 0.8: the
+// degree-5 polynomial's range), or within kSide2Angle (s <= 0.55, degree 4).
 constexpr float kSideAngle = 1.36943841f;         // acos(0.2), 78.46 deg
+constexpr float kSide2Angle = 1.10403099f;        // acos(0.45), 63.26 deg
 
 // Coefficients of acos_q (cc_math.cuh) as FP32x2 pairs.
 __device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
@@ -203,11 +205,13 @@ struct SweepSmem {
 // The pair term for one ring and DP direction pairs (see the file header).
 // SIDE 1: every pair is known to lie on the ring's near side (h <= 1), SIDE 2:
 // on its far side; the fold and the select then have one outcome, and the
-// result is the same as the general form's (SIDE 0) bit for bit.  SHORT:
+// result is the same as the general form's (SIDE 0) bit for bit.  SHORT = 1:
 // every pair of SIDE 1 - 4 lies within kSideAngle of the axis or of its
 // opposite (the folded s <= 0.8), and Q is the degree-5 fit on [0, 0.8]
 // (fit_acos.py: 9.3e-8 rad, 2.6e-7 evaluated in FP32; as accurate as degree 6
-// on [0, 1]: 8.8e-8 and 2.7e-7), one FMA fewer.  SIDE 3 / 4:
+// on [0, 1]: 8.8e-8 and 2.7e-7), one FMA fewer; SHORT = 2: within
+// kSide2Angle (s <= 0.55), the degree-4 fit on [0, 0.55] (7.9e-8 and 2.4e-7),
+// two FMAs fewer.  SIDE 3 / 4:
 // near / far side, and every pair between kDotAngle and pi - kDotAngle from
 // the axis: h from the dot product, h = 2 t with t = 1/2 + a'.(-c') (three
 // FMAs instead of the chord's six operations).  Its absolute error (at most
@@ -225,7 +229,7 @@ struct SweepSmem {
 // rad at |cos(theta)| <= 0.55, no more than the chord form's own error there
 // (its h is ~1 with the same absolute rounding, and the acos polynomial adds
 // 2.7e-7).
-template <int DP, bool KCUT, int SIDE = 0, bool SHORT = false>
+template <int DP, bool KCUT, int SIDE = 0, int SHORT = 0>
 __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)[DP],
                                            const float2 (&ncy)[DP], const float2 (&ncz)[DP],
                                            float2 (&acc)[DP], float kc2) {
@@ -279,7 +283,7 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
                 }
             }
             float2 p;
-            if (!SHORT) {                                    // Q(s) on [0, 1], degree 6
+            if (SHORT == 0) {                                // Q(s) on [0, 1], degree 6
                 p = pair(2.61164433e-03f);
                 p = __ffma2_rn(p, sv, pair(-3.66667798e-03f));
                 p = __ffma2_rn(p, sv, pair(6.92143012e-03f));
@@ -287,13 +291,19 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
                 p = __ffma2_rn(p, sv, pair(2.69628558e-02f));
                 p = __ffma2_rn(p, sv, pair(1.17806636e-01f));
                 p = __ffma2_rn(p, sv, pair(1.41421485e+00f));
-            } else {                                         // Q(s) on [0, 0.8], degree 5
+            } else if (SHORT == 1) {                         // Q(s) on [0, 0.8], degree 5
                 p = pair(3.31251509e-03f);
                 p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
                 p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
                 p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
                 p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
                 p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+            } else {                                         // Q(s) on [0, 0.55], degree 4
+                p = pair(5.02272556e-03f);
+                p = __ffma2_rn(p, sv, pair(6.41390355e-03f));
+                p = __ffma2_rn(p, sv, pair(2.69000251e-02f));
+                p = __ffma2_rn(p, sv, pair(1.17811434e-01f));
+                p = __ffma2_rn(p, sv, pair(1.41421473e+00f));
             }
             float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
             float2 th = __fmul2_rn(rt, p);
@@ -332,7 +342,7 @@ __device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float c
 
 // The rings of a warp's list lst[b, e) of tile T, four at a time (eight made
 // the list bodies too large for the instruction cache).
-template <int DP, int SIDE, bool SHORT = false>
+template <int DP, int SIDE, int SHORT = 0>
 __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *lst, int b, int e,
                                          const float2 (&ncx)[DP], const float2 (&ncy)[DP],
                                          const float2 (&ncz)[DP], float2 (&acc)[DP]) {
@@ -364,7 +374,7 @@ __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *
 // unit's partial (or full) map row (in grid order) and, when bb_slot is set,
 // its block best.  Returns false when a bounded wait gave up (status set to
 // CC_ETIMEOUT).
-template <int D, bool KCUT, bool SHORT>
+template <int D, bool KCUT, int SHORT>
 __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restrict__ rec,
                                            const int64_t *__restrict__ nkept, int64_t nsplit,
                                            int64_t db, int64_t split,
@@ -436,9 +446,10 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
         kc = sqrtf(kc2);
     }
     // side test: cos(angle(axis, centre)) = 2 a'.cap' against +-cos(L - rho -
-    // 1e-3), L = kSideAngle with the short polynomial, else pi/2 (no side
-    // decided when the cap reaches L)
-    const float slim = SHORT ? (rho + 1.0e-3f < kSideAngle ? cosf(kSideAngle - rho - 1.0e-3f) : 2.0f)
+    // 1e-3), L = kSideAngle / kSide2Angle with the short polynomials, else
+    // pi/2 (no side decided when the cap reaches L)
+    const float lside = SHORT == 2 ? kSide2Angle : kSideAngle;
+    const float slim = SHORT ? (rho + 1.0e-3f < lside ? cosf(lside - rho - 1.0e-3f) : 2.0f)
                              : (rho + 1.0e-3f < 1.5707f ? sinf(rho + 1.0e-3f) : 2.0f);
     // ... and the dot form when cos(angle) also lies within +-cos(kDotAngle + rho)
     const float cdot = kDotAngle + rho < 1.5707f ? cosf(kDotAngle + rho) : -2.0f;
@@ -591,7 +602,7 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
 }
 
 
-template <int D, bool KCUT, bool SHORT>
+template <int D, bool KCUT, int SHORT>
 __global__ void __launch_bounds__(kThreads)
 k_sweep(const RingRec *__restrict__ rec, const int64_t *__restrict__ nkept, int64_t nsplit,
         int64_t ndb,
@@ -627,7 +638,7 @@ struct MultiArgs {
     unsigned long long *counter;
 };
 
-template <int D, bool KCUT, bool SHORT>
+template <int D, bool KCUT, int SHORT>
 __global__ void __launch_bounds__(kThreads) k_sweep_multi(const __grid_constant__ MultiArgs a) {
     __shared__ __align__(128) SweepSmem S;
     __shared__ long long unit_s;
@@ -733,12 +744,14 @@ k_select(const float *__restrict__ map, const BlockBest *__restrict__ bb, int64_
 }
 
 template <int D>
-void *sweep_fn(bool kcut, bool shortq) {
-    return kcut ? (void *)k_sweep<D, true, false>
-                : shortq ? (void *)k_sweep<D, false, true> : (void *)k_sweep<D, false, false>;
+void *sweep_fn(bool kcut, int shortq) {
+    return kcut          ? (void *)k_sweep<D, true, 0>
+           : shortq == 2 ? (void *)k_sweep<D, false, 2>
+           : shortq == 1 ? (void *)k_sweep<D, false, 1>
+                         : (void *)k_sweep<D, false, 0>;
 }
 
-void *pick_sweep_q(int d, bool kcut, bool shortq) {
+void *pick_sweep_q(int d, bool kcut, int shortq) {
     switch (d) {
         case 8: return sweep_fn<8>(kcut, shortq);
         case 4: return sweep_fn<4>(kcut, shortq);
@@ -746,22 +759,25 @@ void *pick_sweep_q(int d, bool kcut, bool shortq) {
     }
 }
 
-void *pick_sweep(int d, bool kcut) { return pick_sweep_q(d, kcut, false); }
+void *pick_sweep(int d, bool kcut) { return pick_sweep_q(d, kcut, 0); }
 
-// Whether warps sweeping 32 d consecutive directions of the compact order
-// (M directions on the sphere) have caps narrow enough for the short
-// polynomial: every ring that a cap leaves between kSideAngle and pi/2 from
-// its axis then takes the equatorial form, 2 rho + 2e-3 <= kSideAngle -
-// (pi/2 - kEquAngle).  A patch is about a square of 4 pi 32 d / M sr, cap
-// radius sqrt(2 pi 32 d / M) (HEALPix's elongated patches reach a quarter
-// more).  A wider cap in a short-polynomial sweep is still exact: its rings
-// beyond kSideAngle take the general form (at nside 64 and 256 directions
-// per warp, the warps above the median cap put 2 % of the rings there and the
-// short polynomial still pays: 90.2 % of the roofline against 88.1 %).
-bool short_poly(int64_t M, int d, bool kcut) {
-    if (kcut || M < 1) return false;
-    const double lim = 0.5 * ((double)kSideAngle - (0.5 * 3.14159265358979 - (double)kEquAngle)) - 1e-3;
-    return std::sqrt(2.0 * 3.14159265358979 * 32.0 * d / (double)M) <= lim;
+// Which short polynomial the caps of warps sweeping 32 d consecutive
+// directions of the compact order (M directions on the sphere) allow: level L
+// when every ring that a cap leaves between the one-sided limit (kSideAngle,
+// kSide2Angle) and pi/2 from its axis takes the equatorial form, 2 rho +
+// 2e-3 <= limit - (pi/2 - kEquAngle).  A patch is about a square of
+// 4 pi 32 d / M sr, cap radius sqrt(2 pi 32 d / M) (HEALPix's elongated
+// patches reach a quarter more).  A wider cap in a short-polynomial sweep is
+// still exact: its rings beyond the limit take the general form (at nside 64
+// and 256 directions per warp, the warps above the median cap put 2 % of the
+// rings there and level 1 still pays: 90.2 % of the roofline against 88.1 %).
+int short_level(int64_t M, int d, bool kcut) {
+    if (kcut || M < 1) return 0;
+    const double pi = 3.14159265358979, band = 0.5 * pi - (double)kEquAngle;
+    const double rho = std::sqrt(2.0 * pi * 32.0 * d / (double)M);
+    if (rho <= 0.5 * ((double)kSide2Angle - band) - 1e-3) return 2;
+    if (rho <= 0.5 * ((double)kSideAngle - band) - 1e-3) return 1;
+    return 0;
 }
 
 }  // namespace
@@ -919,7 +935,7 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     float *out = plan.nsplit > 1 ? part : map;
     BlockBest *bbk = plan.nsplit > 1 ? nullptr : bb;
     const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
-    void *fn = pick_sweep_q(plan.d, kcut, plan.ordered && short_poly(M, plan.d, kcut));
+    void *fn = pick_sweep_q(plan.d, kcut, plan.ordered ? short_level(M, plan.d, kcut) : 0);
     const int64_t *nkept = reinterpret_cast<const int64_t *>(ws + plan.off_nkept);
     const int32_t *perm = nullptr;
     if (plan.ordered) {
@@ -978,9 +994,11 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
     // one CTA per work unit (a CTA still takes its unit from the counter): CTAs
     // retire as their units finish, so kernels of higher-priority streams
     // (the bursts' front ends) get SMs without waiting for the whole batch
-    void *fn = kcut                                               ? (void *)k_sweep_multi<kBatchD, true, false>
-               : a.perm != nullptr && short_poly(a.M, kBatchD, false) ? (void *)k_sweep_multi<kBatchD, false, true>
-                                                                        : (void *)k_sweep_multi<kBatchD, false, false>;
+    const int lvl = a.perm != nullptr ? short_level(a.M, kBatchD, kcut) : 0;
+    void *fn = kcut       ? (void *)k_sweep_multi<kBatchD, true, 0>
+               : lvl == 2 ? (void *)k_sweep_multi<kBatchD, false, 2>
+               : lvl == 1 ? (void *)k_sweep_multi<kBatchD, false, 1>
+                          : (void *)k_sweep_multi<kBatchD, false, 0>;
     int64_t ctas = a.unit_begin[n];
     if (ctas > (int64_t)INT32_MAX) ctas = INT32_MAX;
     if (ctas < 1) ctas = 1;

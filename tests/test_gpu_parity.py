@@ -375,13 +375,16 @@ def test_map_large_burst_sampled(cc, dev):
     assert (seeds >= 0).all() and len(set(seeds.tolist())) == 8
 
 
-def test_map_fine_grid_full(cc, dev):
-    """10,000 rings of widths 0.5-20 deg x HEALPix nside 128 (196,608
-    directions): every direction under the map rule.  At this nside every
-    warp's patch is narrow enough for the short polynomial of the one-sided
-    forms, and the widths put rings in every form (equatorial, chord, dot)."""
-    rings, s, _ = synth.rings_burst(n=10000, deta_deg=(0.5, 20.0), seed=13)
-    grid = grid32(oracle.grid_healpix_ring(128))
+@pytest.mark.parametrize("nside,R", [(128, 10000), (256, 2000)])
+def test_map_fine_grid_full(cc, dev, nside, R):
+    """Rings of widths 0.5-20 deg x HEALPix nside 128 (196,608 directions) and
+    256 (786,432): every direction under the map rule.  At these nsides the
+    warps' patches are narrow enough for the short polynomials of the
+    one-sided forms (degree 5 on s <= 0.8 at nside 128, degree 4 on s <= 0.55
+    at nside 256), and the widths put rings in every form (equatorial, chord,
+    dot)."""
+    rings, s, _ = synth.rings_burst(n=R, deta_deg=(0.5, 20.0), seed=13)
+    grid = grid32(oracle.grid_healpix_ring(nside))
     got, am, _, st = run_localize(cc, rings, grid, dev)
     assert st == 0
     want = oracle.likelihood_map(oracle_rings32(rings), grid)
