@@ -253,7 +253,11 @@ __device__ __forceinline__ void ring_pairs(const RingRec &R, const float2 (&ncx)
             const float2 v = __fmul2_rn(sd, p);       // theta - pi/2
             const float2 u = __ffma2_rn(v, k2, ne2);
             const float2 u2 = __fmul2_rn(u, u);
-            const float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            float2 e = make_float2(ex2_approx(-u2.x), ex2_approx(-u2.y));
+            if (KCUT) {
+                e.x = u2.x > kc2 ? 0.0f : e.x;
+                e.y = u2.y > kc2 ? 0.0f : e.y;
+            }
             acc[q] = __fadd2_rn(acc[q], e);
         }
     } else {
@@ -342,16 +346,17 @@ __device__ __forceinline__ bool ring_reaches(const RingRec &R, float cx, float c
 
 // The rings of a warp's list lst[b, e) of tile T, four at a time (eight made
 // the list bodies too large for the instruction cache).
-template <int DP, int SIDE, int SHORT = 0>
+template <int DP, bool KCUT, int SIDE, int SHORT = 0>
 __device__ __forceinline__ void side_run(const RingRec *T, const unsigned char *lst, int b, int e,
                                          const float2 (&ncx)[DP], const float2 (&ncy)[DP],
-                                         const float2 (&ncz)[DP], float2 (&acc)[DP]) {
+                                         const float2 (&ncz)[DP], float2 (&acc)[DP], float kc2) {
     int i = b;
     for (; i + 4 <= e; i += 4) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) ring_pairs<DP, false, SIDE, SHORT>(T[lst[i + k]], ncx, ncy, ncz, acc, 0.f);
+        for (int k = 0; k < 4; k++)
+            ring_pairs<DP, KCUT, SIDE, SHORT>(T[lst[i + k]], ncx, ncy, ncz, acc, kc2);
     }
-    for (; i < e; i++) ring_pairs<DP, false, SIDE, SHORT>(T[lst[i]], ncx, ncy, ncz, acc, 0.f);
+    for (; i < e; i++) ring_pairs<DP, KCUT, SIDE, SHORT>(T[lst[i]], ncx, ncy, ncz, acc, kc2);
 }
 
 // One work unit of the sweep: the 256 x D directions of direction block db
@@ -481,18 +486,65 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
             abort_flag = 1;
         } else {
             const RingRec *T = tile[stage];
-            if (KCUT) {
+            if constexpr (KCUT) {
+                // with the angular selection: the rings that can reach the
+                // warp's cap, by class as below
+                unsigned m5s[kTile / 32], m1s[kTile / 32], m3s[kTile / 32], m4s[kTile / 32],
+                    m2s[kTile / 32], mms[kTile / 32];
+                int cnt[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
                 for (int g = 0; g < kTile / 32; g++) {
-                    unsigned m = __ballot_sync(0xffffffffu,
-                                               ring_reaches(T[32 * g + lane], capx, capy, capz,
-                                                            rho, kc));
-                    while (m) {                        // warp-uniform: the rings that reach
-                        const int r = 32 * g + __ffs(m) - 1;
-                        m &= m - 1;
-                        ring_pairs<DP, KCUT>(T[r], ncx, ncy, ncz, acc, kc2);
-                    }
+                    const RingRec &R = T[32 * g + lane];
+                    const bool reach = ring_reaches(R, capx, capy, capz, rho, kc);
+                    const float c2 = 2.0f * fmaf(R.az, capz, fmaf(R.ay, capy, R.ax * capx));
+                    const bool eq = reach && fabsf(c2) <= elim;
+                    const bool wide = reach && R.k <= kDotMaxK && !eq;
+                    const bool dn = wide && c2 >= slim && c2 <= cdot;
+                    const bool df = wide && c2 <= -slim && c2 >= -cdot;
+                    const bool n1 = reach && c2 >= slim && !dn && !eq;
+                    const bool n2 = reach && c2 <= -slim && !df && !eq;
+                    m5s[g] = __ballot_sync(0xffffffffu, eq);
+                    m1s[g] = __ballot_sync(0xffffffffu, n1);
+                    m3s[g] = __ballot_sync(0xffffffffu, dn);
+                    m4s[g] = __ballot_sync(0xffffffffu, df);
+                    m2s[g] = __ballot_sync(0xffffffffu, n2);
+                    mms[g] = __ballot_sync(0xffffffffu, reach && !(eq || dn || df || n1 || n2));
+                    cnt[0] += __popc(m5s[g]);
+                    cnt[1] += __popc(m1s[g]);
+                    cnt[2] += __popc(m3s[g]);
+                    cnt[3] += __popc(m4s[g]);
+                    cnt[4] += __popc(m2s[g]);
+                    cnt[5] += __popc(mms[g]);
                 }
+                const unsigned lt = (1u << lane) - 1u;
+                int b5 = 0, b1 = cnt[0], b3 = b1 + cnt[1], b4 = b3 + cnt[2], b2 = b4 + cnt[3],
+                    bm = b2 + cnt[4];
+                const int e5 = b1, e1 = b3, e3 = b4, e4 = b2, e2 = bm, em = bm + cnt[5];
+#pragma unroll
+                for (int g = 0; g < kTile / 32; g++) {
+                    const unsigned bit = 1u << lane;
+                    const int at = (m5s[g] & bit) ? b5 + __popc(m5s[g] & lt)
+                                 : (m1s[g] & bit) ? b1 + __popc(m1s[g] & lt)
+                                 : (m3s[g] & bit) ? b3 + __popc(m3s[g] & lt)
+                                 : (m4s[g] & bit) ? b4 + __popc(m4s[g] & lt)
+                                 : (m2s[g] & bit) ? b2 + __popc(m2s[g] & lt)
+                                 : (mms[g] & bit) ? bm + __popc(mms[g] & lt) : -1;
+                    if (at >= 0) S.lst[w][at] = (unsigned char)(32 * g + lane);
+                    b5 += __popc(m5s[g]);
+                    b1 += __popc(m1s[g]);
+                    b3 += __popc(m3s[g]);
+                    b4 += __popc(m4s[g]);
+                    b2 += __popc(m2s[g]);
+                    bm += __popc(mms[g]);
+                }
+                __syncwarp();
+                const unsigned char *L = S.lst[w];
+                side_run<DP, KCUT, 5>(T, L, 0, e5, ncx, ncy, ncz, acc, kc2);
+                side_run<DP, KCUT, 1, SHORT>(T, L, e5, e1, ncx, ncy, ncz, acc, kc2);
+                side_run<DP, KCUT, 3, SHORT>(T, L, e1, e3, ncx, ncy, ncz, acc, kc2);
+                side_run<DP, KCUT, 4, SHORT>(T, L, e3, e4, ncx, ncy, ncz, acc, kc2);
+                side_run<DP, KCUT, 2, SHORT>(T, L, e4, e2, ncx, ncy, ncz, acc, kc2);
+                side_run<DP, KCUT, 0>(T, L, e2, em, ncx, ncy, ncz, acc, kc2);
             } else {
                 // the tile's rings by class: equatorial, near side (chord
                 // form, dot form), far side (dot, chord), then the rest, each
@@ -543,12 +595,12 @@ __device__ __forceinline__ bool sweep_unit(SweepSmem &S, const RingRec *__restri
                 }
                 __syncwarp();
                 const unsigned char *L = S.lst[w];
-                side_run<DP, 5>(T, L, 0, e5, ncx, ncy, ncz, acc);
-                side_run<DP, 1, SHORT>(T, L, e5, e1, ncx, ncy, ncz, acc);
-                side_run<DP, 3, SHORT>(T, L, e1, e3, ncx, ncy, ncz, acc);
-                side_run<DP, 4, SHORT>(T, L, e3, e4, ncx, ncy, ncz, acc);
-                side_run<DP, 2, SHORT>(T, L, e4, e2, ncx, ncy, ncz, acc);
-                side_run<DP, 0>(T, L, e2, kTile, ncx, ncy, ncz, acc);
+                side_run<DP, false, 5>(T, L, 0, e5, ncx, ncy, ncz, acc, 0.0f);
+                side_run<DP, false, 1, SHORT>(T, L, e5, e1, ncx, ncy, ncz, acc, 0.0f);
+                side_run<DP, false, 3, SHORT>(T, L, e1, e3, ncx, ncy, ncz, acc, 0.0f);
+                side_run<DP, false, 4, SHORT>(T, L, e3, e4, ncx, ncy, ncz, acc, 0.0f);
+                side_run<DP, false, 2, SHORT>(T, L, e4, e2, ncx, ncy, ncz, acc, 0.0f);
+                side_run<DP, false, 0>(T, L, e2, kTile, ncx, ncy, ncz, acc, 0.0f);
                 __syncwarp();
             }
         }
@@ -745,10 +797,11 @@ k_select(const float *__restrict__ map, const BlockBest *__restrict__ bb, int64_
 
 template <int D>
 void *sweep_fn(bool kcut, int shortq) {
-    return kcut          ? (void *)k_sweep<D, true, 0>
-           : shortq == 2 ? (void *)k_sweep<D, false, 2>
-           : shortq == 1 ? (void *)k_sweep<D, false, 1>
-                         : (void *)k_sweep<D, false, 0>;
+    if (kcut)
+        return shortq == 2 ? (void *)k_sweep<D, true, 2>
+               : shortq == 1 ? (void *)k_sweep<D, true, 1> : (void *)k_sweep<D, true, 0>;
+    return shortq == 2 ? (void *)k_sweep<D, false, 2>
+           : shortq == 1 ? (void *)k_sweep<D, false, 1> : (void *)k_sweep<D, false, 0>;
 }
 
 void *pick_sweep_q(int d, bool kcut, int shortq) {
@@ -771,8 +824,8 @@ void *pick_sweep(int d, bool kcut) { return pick_sweep_q(d, kcut, 0); }
 // still exact: its rings beyond the limit take the general form (at nside 64
 // and 256 directions per warp, the warps above the median cap put 2 % of the
 // rings there and level 1 still pays: 90.2 % of the roofline against 88.1 %).
-int short_level(int64_t M, int d, bool kcut) {
-    if (kcut || M < 1) return 0;
+int short_level(int64_t M, int d) {
+    if (M < 1) return 0;
     const double pi = 3.14159265358979, band = 0.5 * pi - (double)kEquAngle;
     const double rho = std::sqrt(2.0 * pi * 32.0 * d / (double)M);
     if (rho <= 0.5 * ((double)kSide2Angle - band) - 1e-3) return 2;
@@ -935,7 +988,7 @@ cudaError_t launch_localize(const cc_rings &rings, const cc_grid &grid, const cc
     float *out = plan.nsplit > 1 ? part : map;
     BlockBest *bbk = plan.nsplit > 1 ? nullptr : bb;
     const unsigned grid_ctas = (unsigned)(plan.ndb * plan.nsplit);
-    void *fn = pick_sweep_q(plan.d, kcut, plan.ordered ? short_level(M, plan.d, kcut) : 0);
+    void *fn = pick_sweep_q(plan.d, kcut, plan.ordered ? short_level(M, plan.d) : 0);
     const int64_t *nkept = reinterpret_cast<const int64_t *>(ws + plan.off_nkept);
     const int32_t *perm = nullptr;
     if (plan.ordered) {
@@ -994,11 +1047,13 @@ cudaError_t launch_localize_batch(int n, const cc_rings *rings, const cc_grid &g
     // one CTA per work unit (a CTA still takes its unit from the counter): CTAs
     // retire as their units finish, so kernels of higher-priority streams
     // (the bursts' front ends) get SMs without waiting for the whole batch
-    const int lvl = a.perm != nullptr ? short_level(a.M, kBatchD, kcut) : 0;
-    void *fn = kcut       ? (void *)k_sweep_multi<kBatchD, true, 0>
-               : lvl == 2 ? (void *)k_sweep_multi<kBatchD, false, 2>
-               : lvl == 1 ? (void *)k_sweep_multi<kBatchD, false, 1>
-                          : (void *)k_sweep_multi<kBatchD, false, 0>;
+    const int lvl = a.perm != nullptr ? short_level(a.M, kBatchD) : 0;
+    void *fn = kcut ? (lvl == 2   ? (void *)k_sweep_multi<kBatchD, true, 2>
+                       : lvl == 1 ? (void *)k_sweep_multi<kBatchD, true, 1>
+                                  : (void *)k_sweep_multi<kBatchD, true, 0>)
+                    : (lvl == 2   ? (void *)k_sweep_multi<kBatchD, false, 2>
+                       : lvl == 1 ? (void *)k_sweep_multi<kBatchD, false, 1>
+                                  : (void *)k_sweep_multi<kBatchD, false, 0>);
     int64_t ctas = a.unit_begin[n];
     if (ctas > (int64_t)INT32_MAX) ctas = INT32_MAX;
     if (ctas < 1) ctas = 1;
