@@ -850,14 +850,15 @@ bool plan_sweep(int64_t R, int64_t M, const cc_params &p, SweepPlan *plan, int f
 
     // D = 8 first: four independent direction pairs per ring record give
     // the FP32 pipe more to overlap than two, which outweighs the lower
-    // occupancy (96 registers, 2 CTAs per SM against 4 at D = 4).  Measured
-    // on GB300: the 200k-event sweep 63.9 -> 66.9 % of its roofline, the 1M-ring
-    // burst 64.8 -> 67.5 %, the near-field image 66.7 -> 68.7 % (D = 6, at
-    // 3 CTAs per SM, was slower than D = 4).  With the angular selection
-    // D = 4 first: a warp's cap of 128 directions lets it skip more rings
-    // than one of 256 (the 1M-ring burst at k_cut = 5: 135 ms against 153).
-    const int order8[3] = {8, 4, 2}, order4[3] = {4, 8, 2};
-    const int *order = kcut ? order4 : order8;
+    // occupancy (2 CTAs per SM against 4 at D = 4).  Measured on GB300: the
+    // 200k-event sweep 63.9 -> 66.9 % of its roofline, the 1M-ring burst
+    // 64.8 -> 67.5 %, the near-field image 66.7 -> 68.7 % (D = 6, at 3 CTAs
+    // per SM, was slower than D = 4).  With the angular selection too, now
+    // that the reaching rings take the class lists (the 1M-ring burst at
+    // k_cut = 5: 108 ms against 126 at D = 4; with the general form for
+    // every reaching ring D = 4 had won, 135 ms against 153, its caps of 128
+    // directions skipping more rings).
+    const int order[3] = {8, 4, 2};
     int d = 2;
     int64_t conc = 0;
     for (int ci = 0; ci < 3; ci++) {
