@@ -54,6 +54,9 @@ constexpr float kEquCos = 0.83571424f;     // cos(E - 1e-3)
 // its opposite (s <= 0.8, the short polynomial's range); T = that - 1e-3
 constexpr float kSideCos = 0.20097970f;    // cos(T)
 constexpr float kSideSin = 0.97959541f;    // sin(T)
+// and within acos(0.45) = 63.26 deg (s <= 0.55, degree 4); T2 = that - 1e-3
+constexpr float kSide2Cos = 0.45089280f;    // cos(T2)
+constexpr float kSide2Sin = 0.89257811f;    // sin(T2)
 
 struct NearRec {   // 64 bytes; values met by a voxel pair are duplicated
     float mpx, mpx_, mpy, mpy_, mpz, mpz_;   // -p
@@ -339,11 +342,11 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
             h = __ffma2_rn(cy, cy, h);
             h = __ffma2_rn(cz, cz, h);                           // 1 - cos(theta)
             float2 sv;
-            if (SIDE == 1) {
+            if (SIDE == 1 || SIDE == 3) {
                 sv = h;
             } else {
                 const float2 g = __ffma2_rn(h, m1, two2);
-                sv = SIDE == 2 ? make_float2(fabsf(g.x), fabsf(g.y))
+                sv = (SIDE == 2 || SIDE == 4) ? make_float2(fabsf(g.x), fabsf(g.y))
                                : make_float2(fminf(h.x, fabsf(g.x)), fminf(h.y, fabsf(g.y)));
             }
             float2 p;
@@ -356,18 +359,24 @@ __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2
                 p = __ffma2_rn(p, sv, pair(2.6394552e-02f));
                 p = __ffma2_rn(p, sv, pair(1.1786042e-01f));
                 p = __ffma2_rn(p, sv, pair(1.4142133e+00f));
-            } else {                                             // on [0, 0.8], degree 5
+            } else if (SIDE == 1 || SIDE == 2) {                 // on [0, 0.8], degree 5
                 p = pair(3.31251509e-03f);
                 p = __ffma2_rn(p, sv, pair(-2.59509514e-04f));
                 p = __ffma2_rn(p, sv, pair(9.49506927e-03f));
                 p = __ffma2_rn(p, sv, pair(2.61093955e-02f));
                 p = __ffma2_rn(p, sv, pair(1.17894620e-01f));
                 p = __ffma2_rn(p, sv, pair(1.41421223e+00f));
+            } else {                                             // on [0, 0.55], degree 4
+                p = pair(5.02272556e-03f);
+                p = __ffma2_rn(p, sv, pair(6.41390355e-03f));
+                p = __ffma2_rn(p, sv, pair(2.69000251e-02f));
+                p = __ffma2_rn(p, sv, pair(1.17811434e-01f));
+                p = __ffma2_rn(p, sv, pair(1.41421473e+00f));
             }
             const float2 rt = make_float2(sqrt_approx(sv.x), sqrt_approx(sv.y));
             const float2 th = __fmul2_rn(rt, p);
-            const float2 nbs = SIDE == 1   ? make_float2(R3.z, R3.z)
-                               : SIDE == 2 ? make_float2(R3.w, R3.w)
+            const float2 nbs = (SIDE == 1 || SIDE == 3)   ? make_float2(R3.z, R3.z)
+                               : (SIDE == 2 || SIDE == 4) ? make_float2(R3.w, R3.w)
                                            : make_float2(h.x <= 1.0f ? R3.z : R3.w,
                                                          h.y <= 1.0f ? R3.z : R3.w);
             const float2 u = __ffma2_rn(th, k2, nbs);
@@ -493,8 +502,9 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             // <= T (pi - alpha + beta <= T), T = acos(0.2) - 1e-3:
             // +-a . (C - apex) >= cos(T) sqrt(dist^2 - rad^2) + sin(T) rad,
             // with beta <= T.  The rest take the general form.
-            unsigned em[kTile / 32], nm[kTile / 32], fm[kTile / 32];
-            int ne = 0, nn = 0, nf = 0;
+            unsigned em[kTile / 32], nm[kTile / 32], fm[kTile / 32], n2m[kTile / 32],
+                f2m[kTile / 32];
+            int ne = 0, nn = 0, nf = 0, nn2 = 0, nf2 = 0;
 #pragma unroll
             for (int g = 0; g < kTile / 32; g++) {
                 const NearRec &Rg = T[32 * g + lane];
@@ -505,39 +515,53 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
                 const float r2 = brad * brad;
                 const float cb = d2 > r2 ? sqrtf(d2 - r2) : 0.0f;     // dist cos(beta)
                 const float elim = d2 > r2 ? fmaf(kEquSin, cb, -kEquCos * brad) : -1.0f;
+                const float lim2 = r2 < kSide2Sin * kSide2Sin * d2 ? fmaf(kSide2Cos, cb, kSide2Sin * brad)
+                                                                   : __builtin_huge_valf();
                 const float lim = r2 < kSideSin * kSideSin * d2 ? fmaf(kSideCos, cb, kSideSin * brad)
                                                                 : __builtin_huge_valf();
                 const bool live = Rg.k != 0.0f;
                 const bool eq = live && fabsf(sa) <= elim;
+                const bool n2 = live && !eq && sa >= lim2, f2 = live && !eq && -sa >= lim2;
                 em[g] = __ballot_sync(0xffffffffu, eq);
-                nm[g] = __ballot_sync(0xffffffffu, live && !eq && sa >= lim);
-                fm[g] = __ballot_sync(0xffffffffu, live && !eq && -sa >= lim);
+                n2m[g] = __ballot_sync(0xffffffffu, n2);
+                f2m[g] = __ballot_sync(0xffffffffu, f2);
+                nm[g] = __ballot_sync(0xffffffffu, live && !eq && !n2 && sa >= lim);
+                fm[g] = __ballot_sync(0xffffffffu, live && !eq && !f2 && -sa >= lim);
+                nn2 += __popc(n2m[g]);
+                nf2 += __popc(f2m[g]);
                 ne += __popc(em[g]);
                 nn += __popc(nm[g]);
                 nf += __popc(fm[g]);
             }
             const unsigned lt = (1u << lane) - 1u;
-            int be = 0, bn = ne, bf = ne + nn, bm = ne + nn + nf;
+            int be = 0, bn2 = ne, bf2 = bn2 + nn2, bn = bf2 + nf2, bf = bn + nn, bm = bf + nf;
+            const int ee = bn2, en2 = bf2, ef2 = bn, en = bf, ef = bm;
 #pragma unroll
             for (int g = 0; g < kTile / 32; g++) {
-                const unsigned mm = ~(em[g] | nm[g] | fm[g]);
-                const bool ise = (em[g] >> lane) & 1u, isn = (nm[g] >> lane) & 1u,
-                           isf = (fm[g] >> lane) & 1u;
-                const int at = ise ? be + __popc(em[g] & lt)
-                             : isn ? bn + __popc(nm[g] & lt)
-                             : isf ? bf + __popc(fm[g] & lt) : bm + __popc(mm & lt);
+                const unsigned mm = ~(em[g] | n2m[g] | f2m[g] | nm[g] | fm[g]);
+                const unsigned bit = 1u << lane;
+                const int at = (em[g] & bit)    ? be + __popc(em[g] & lt)
+                             : (n2m[g] & bit) ? bn2 + __popc(n2m[g] & lt)
+                             : (f2m[g] & bit) ? bf2 + __popc(f2m[g] & lt)
+                             : (nm[g] & bit)  ? bn + __popc(nm[g] & lt)
+                             : (fm[g] & bit)  ? bf + __popc(fm[g] & lt)
+                                              : bm + __popc(mm & lt);
                 S.lst[w][at] = (unsigned char)(32 * g + lane);
                 be += __popc(em[g]);
+                bn2 += __popc(n2m[g]);
+                bf2 += __popc(f2m[g]);
                 bn += __popc(nm[g]);
                 bf += __popc(fm[g]);
                 bm += __popc(mm);
             }
             __syncwarp();
             const unsigned char *L = S.lst[w];
-            near_run<DP, KCUT, 5>(T, L, 0, ne, px2, py2, pz2, acc, kc2);
-            near_run<DP, KCUT, 1>(T, L, ne, ne + nn, px2, py2, pz2, acc, kc2);
-            near_run<DP, KCUT, 2>(T, L, ne + nn, ne + nn + nf, px2, py2, pz2, acc, kc2);
-            near_run<DP, KCUT, 0>(T, L, ne + nn + nf, kTile, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 5>(T, L, 0, ee, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 3>(T, L, ee, en2, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 4>(T, L, en2, ef2, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 1>(T, L, ef2, en, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 2>(T, L, en, ef, px2, py2, pz2, acc, kc2);
+            near_run<DP, KCUT, 0>(T, L, ef, kTile, px2, py2, pz2, acc, kc2);
             __syncwarp();
         }
         __syncthreads();

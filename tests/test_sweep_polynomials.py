@@ -81,6 +81,7 @@ def test_far_field_asin_polynomial(sweep_src):
 @pytest.mark.parametrize("marker,deg,smax,bound", [
     ("// acos_q on [0, 1], degree 7", 7, 1.0, 2.4e-7),
     ("// on [0, 0.8], degree 5", 5, 0.8, 2.6e-7),
+    ("// on [0, 0.55], degree 4", 4, 0.55, 2.4e-7),
 ])
 def test_near_field_acos_polynomials(voxel_src, marker, deg, smax, bound):
     coef = block_coeffs(voxel_src, marker, deg + 1)
@@ -114,6 +115,9 @@ def test_class_limits(sweep_src, voxel_src):
     t = math.acos(0.2) - 1e-3
     assert abs(const(voxel_src, "kSideCos") - math.cos(t)) < eps
     assert abs(const(voxel_src, "kSideSin") - math.sin(t)) < eps
+    t2 = math.acos(0.45) - 1e-3
+    assert abs(const(voxel_src, "kSide2Cos") - math.cos(t2)) < eps
+    assert abs(const(voxel_src, "kSide2Sin") - math.sin(t2)) < eps
 
 
 def test_short_polynomial_ranges_cover_the_one_sided_pairs():
