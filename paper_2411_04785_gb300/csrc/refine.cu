@@ -392,13 +392,24 @@ k_refine(const float *__restrict__ ax, const float *__restrict__ ay,
         }
         // every CTA reduces all CTA partials in one fixed order: 16 lanes (a
         // half warp) per sum, each adding the CTAs b = v, v + 16, ... in turn,
-        // then a fixed shuffle tree over the 16
+        // then a fixed shuffle tree over the 16.  The first kBatch partials
+        // of a lane are loaded before any is added, so that their L2 round
+        // trips overlap (adding the zeros of absent CTAs changes nothing:
+        // (0, 0) is an exact identity of df_add on normalised pairs)
         for (int u0 = 0; u0 < P; u0 += kThreads / 16) {
             const int u = u0 + (tid >> 4), v = tid & 15;
             float2 a = make_float2(0.0f, 0.0f);
             if (u < P && S[u / kSums].phase != 2) {
-#pragma unroll 4
-                for (unsigned b = v; b < G; b += 16)
+                constexpr int kBatch = 8;
+                float2 pv[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; j++) {
+                    const unsigned b = v + 16u * j;
+                    pv[j] = b < G ? __ldcg(slot + (size_t)b * P + u) : make_float2(0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; j++) a = df_add(a, pv[j]);
+                for (unsigned b = v + 16u * kBatch; b < G; b += 16)
                     a = df_add(a, __ldcg(slot + (size_t)b * P + u));
             }
 #pragma unroll

@@ -26,7 +26,8 @@
 // approximate rsqrt, theta = pi/2 + asin by an odd polynomial: no Newton
 // step, no square root, no fold, no select); every voxel within 78.46 deg of
 // the axis or of its opposite, the one-sided form (no fold, no select, a
-// shorter polynomial); the rest, the general form.  Rings with eta > pi/2
+// shorter polynomial: degree 4 within 63.26 deg, else degree 5); the rest,
+// the general form.  Rings with eta > pi/2
 // are mirrored (a -> -a, eta -> pi - eta).  The pipeline (TMA bulk tiles
 // through a 4-stage mbarrier ring, ring splits over CTAs with a fixed-order
 // Kahan reduction, block argmax) is the far-field sweep's, with 64-byte
@@ -268,7 +269,9 @@ struct NearSmem {
 // (2 - h <= 0.8); the fold and the select then have one outcome, and the
 // acos polynomial is the degree-5 fit on [0, 0.8] (fit_acos.py: 2.6e-7 rad
 // evaluated in FP32, as accurate as the general form's degree 7 on [0, 1]:
-// 2.3e-7).  SIDE 5: the equatorial form (below).
+// 2.3e-7).  SIDE 3 / 4: within acos(0.45) = 63.26 deg of the axis / of its
+// opposite (s <= 0.55), the degree-4 fit on [0, 0.55] (2.4e-7).  SIDE 5: the
+// equatorial form (below).
 template <int DP, bool KCUT, int SIDE>
 __device__ __forceinline__ void near_pairs(const NearRec &Rr, const float2 (&px2)[DP],
                                            const float2 (&py2)[DP], const float2 (&pz2)[DP],
@@ -501,7 +504,8 @@ k_backproject(const NearRec *__restrict__ rec, const int64_t *__restrict__ nkept
             // rad^2) - cos(A) rad.  Near side (far side) when alpha + beta
             // <= T (pi - alpha + beta <= T), T = acos(0.2) - 1e-3:
             // +-a . (C - apex) >= cos(T) sqrt(dist^2 - rad^2) + sin(T) rad,
-            // with beta <= T.  The rest take the general form.
+            // with beta <= T; the same with T2 = acos(0.45) - 1e-3 for the
+            // degree-4 polynomial.  The rest take the general form.
             unsigned em[kTile / 32], nm[kTile / 32], fm[kTile / 32], n2m[kTile / 32],
                 f2m[kTile / 32];
             int ne = 0, nn = 0, nf = 0, nn2 = 0, nf2 = 0;
