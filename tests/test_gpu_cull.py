@@ -138,9 +138,19 @@ def test_skipping_is_exact(cc, dmax_deg, kcut, nside):
     assert ((m_nest[idx] >= lo_m - b) & (m_nest[idx] <= hi_m + b)).all()
 
 
-def test_batched_sweep_with_skipping_equals_alone(cc):
+@pytest.mark.parametrize("nside,kept_order", [(32, False), (128, True), (256, True)])
+def test_batched_sweep_with_skipping_equals_alone(cc, nside, kept_order):
+    """With the angular selection, each burst of a batched sweep alone and in
+    the batch bit for bit, and close to the single-burst sweep (a different
+    ring split, so a different FP32 summation).  A NESTED grid as given, and
+    RING grids kept with their order at nside 128 and 256, where the sweeps
+    take the short polynomials."""
     from tests.test_gpu_serve import batch_localize
-    g = cc.grid_healpix_nest(32, "cuda:0")
+    if kept_order:
+        g = cc.grid_healpix_ring(nside, "cuda:0")
+        g = tuple(g) + (cc.grid_order(g),)
+    else:
+        g = cc.grid_healpix_nest(nside, "cuda:0")
     p = cc.Params(k_cut=5.0, topk=2, nms_rad=math.radians(5))
     sets = []
     for n, seed in ((3000, 1), (20000, 2), (700, 3)):
